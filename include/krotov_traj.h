@@ -1,0 +1,188 @@
+/*
+ * krotov_traj.h — C ABI of the trajectory-parallel Krotov library for GB300 (sm_103a).
+ *
+ * Method: Goerz & Jacobs, "Efficient optimization of state preparation in quantum networks
+ * using quantum trajectories" (arXiv:1801.04382).  The library runs, on one GPU, the
+ * independent-trajectory formulation of Krotov's method (Sec. 2.3): M quantum-jump (MCWF)
+ * trajectories are propagated forward under the non-Hermitian effective Hamiltonian
+ * (Sec. 2.1), co-states are propagated backward under its adjoint, and the pulse is updated
+ * sequentially in time from the cross-trajectory sum of Im<chi_k|dH/deps_i|psi_k>
+ * (Eq. independent_traj_update).
+ *
+ * General conventions
+ *  - All pointers in the descriptors are HOST pointers; the library copies what it needs at
+ *    krotov_init and never keeps a caller pointer.  Output pointers are host pointers written
+ *    before the call returns (such calls synchronise the stream).
+ *  - Complex numbers are stored as two consecutive doubles (re, im).
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream.  All
+ *    device work of a call is enqueued on that stream.
+ *  - The library owns every device buffer of a problem; krotov_free releases them.
+ *  - Errors: every entry point returns a kt_status; no exception crosses the ABI.  A
+ *    human-readable message for the calling thread's last error is returned by
+ *    krotov_last_error().  Device-side failures (non-finite values, a full jump record, a
+ *    pulse outside the spectral bound) are collected in a status word read at the end of
+ *    each sweep and returned from that call.
+ *  - One problem object must not be used from two threads at the same time.
+ *
+ * Limits: n_nodes <= 8, n_loc <= 16, n_ctrl <= 8, n_lind <= 4, n_pairs <= 28,
+ * d = n_loc^n_nodes must fit two tile buffers in 227 KB of shared memory
+ * (d <= ~14000 in FP32-mixed, ~7000 in FP64 for one trajectory per CTA).
+ */
+#ifndef KROTOV_TRAJ_H
+#define KROTOV_TRAJ_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KT_API __attribute__((visibility("default")))
+
+typedef struct kt_problem kt_problem;   /* opaque; created by krotov_init, owned by the library */
+
+typedef enum {
+  KT_OK = 0,
+  KT_ERR_ARG = -1,          /* invalid argument or descriptor */
+  KT_ERR_OOM = -2,          /* device allocation failed */
+  KT_ERR_CUDA = -3,         /* a CUDA runtime call failed */
+  KT_ERR_TIMEOUT = -4,      /* a bounded device-side wait expired */
+  KT_ERR_NONFINITE = -5,    /* a NaN/Inf appeared in a norm, overlap or pulse */
+  KT_ERR_RECORD_FULL = -6,  /* a trajectory needed more jumps than draws_per_traj allows */
+  KT_ERR_STATE = -7,        /* call out of order (e.g. an updating forward pass without a backward pass) */
+  KT_ERR_RANGE = -8,        /* a pulse value left [-eps_bound, eps_bound] */
+  KT_ERR_UNSUPPORTED = -9   /* sizes beyond the limits above */
+} kt_status;
+
+typedef enum { KT_FP64 = 0, KT_FP32_MIXED = 1 } kt_precision;
+
+/*
+ * Model: a network of n_nodes identical-dimension nodes (paper Sec. 3.1), full space of
+ * dimension d = n_loc^n_nodes, node 0 the most significant tensor factor.  The Hermitian
+ * Hamiltonian is
+ *     H(eps) = sum_i h0_i + sum_c eps_c hc_c + sum_p coef_p a_{dst_p}^dag a_{src_p},
+ * each h0_i / hc_c an n_loc x n_loc factor acting on one node (hc_c on node ctrl_node[c]),
+ * `a` a single-node factor with at most one nonzero per row and per column (a ladder
+ * operator, e.g. the cavity annihilation operator), and the pair list Hermitian as a whole
+ * (Eq. ham_interaction is such a list).  Lindblad operators are L_l = sum_i lind_coef[l][i] a_i
+ * (Sec. 3.1: one collective operator sqrt(2 kappa) sum_i a_i).  The library forms the MCWF
+ * generator H_eff = H - (i/2) sum_l L_l^dag L_l (Sec. 2.1) in the same structured form.
+ */
+typedef struct {
+  int n_nodes;
+  int n_loc;
+  const double *h0_local;   /* [n_nodes][n_loc][n_loc][2] drift factor of each node (Hermitian) */
+  int n_ctrl;
+  const int *ctrl_node;     /* [n_ctrl] node each control acts on */
+  const double *hc_local;   /* [n_ctrl][n_loc][n_loc][2] control factor dH/deps_c (Hermitian) */
+  const double *a_local;    /* [n_loc][n_loc][2] ladder factor used by pairs and Lindblad ops */
+  int n_pairs;
+  const int *pair_dst;      /* [n_pairs] */
+  const int *pair_src;      /* [n_pairs], != pair_dst */
+  const double *pair_coef;  /* [n_pairs][2] */
+  int n_lind;
+  const double *lind_coef;  /* [n_lind][n_nodes][2] */
+  const double *psi0;       /* [d][2] initial state of every trajectory, or NULL if psi0_batch */
+  const double *psi0_batch; /* [M][d][2] per-trajectory initial states, or NULL */
+  const double *psi_tgt;    /* [d][2] target state (normalised by the caller) */
+} kt_model_desc;
+
+/*
+ * Run configuration.  Time grid t_j = j T / nt, controls piecewise constant on the nt
+ * intervals (Sec. 2.2).  Uniform random numbers (Sec. 2.1: r in [0,1) for the norm threshold
+ * and the channel choice) are supplied by the caller: forward pass p uses row
+ * uniforms[p mod n_passes][k][.] for trajectory k — column 0 is the first threshold r, and
+ * after the m-th jump column 2m-1 chooses the channel and column 2m is the next r.  At most
+ * (draws_per_traj - 1) / 2 jumps per trajectory and pass.
+ */
+typedef struct {
+  double T;
+  int nt;
+  int M;                    /* number of trajectories */
+  kt_precision prec;        /* KT_FP64, or KT_FP32_MIXED: complex64 states with FP32
+                               arithmetic, FP64 norms, renormalisation, overlaps and sums */
+  int ckpt_interval;        /* 0: keep the co-state at every t_j; K > 0: keep every K-th
+                               and recompute the rest segment by segment */
+  const double *eps_guess;  /* [n_ctrl][nt] guess pulse eps_c^(0) on each interval */
+  const double *shape;      /* [n_ctrl][nt] update shape S_c(t_{j-1/2}) in [0, 1] */
+  const double *lambda_a;   /* [n_ctrl] Krotov step weights lambda_c > 0 */
+  const double *uniforms;   /* [n_passes][M][draws_per_traj] values in [0, 1) */
+  int n_passes;
+  int draws_per_traj;       /* odd, >= 1 */
+  double eps_bound;         /* bound on |eps| used for the spectral estimate; 0 = automatic
+                               (2 max|eps_guess| + 1) */
+  double cheb_tol;          /* Chebyshev truncation; 0 = 1e-15 (FP64) / 1e-8 (FP32-mixed) */
+  int tile_traj;            /* trajectories per CTA tile (power of two <= 32); 0 = automatic */
+} kt_config;
+
+/* Create a problem: validate, assemble H_eff in structured form (a1), choose the Chebyshev
+ * expansion (a2), allocate and upload.  No propagation is done. */
+KT_API kt_status krotov_init(const kt_model_desc *model, const kt_config *cfg, void *stream,
+                             kt_problem **out);
+
+/* One forward MCWF sweep of all trajectories over [0, T] (Sec. 2.1), consuming the next
+ * pass of uniforms.  sequential_update = 0 propagates under the current pulse.
+ * sequential_update = 1 applies Krotov's update (Eq. independent_traj_update) on the fly:
+ * before interval j is propagated, Delta eps_cj = S_cj / (lambda_c M) sum_k
+ * Im <chi_k(t_{j-1})| hc_c |psi_k(t_{j-1})> is formed from the co-states of the preceding
+ * propagate_backward, and the new pulse eps + Delta eps drives interval j; it becomes the
+ * current pulse when the sweep ends.  Requires a backward sweep since the last forward sweep.
+ * At the end tau_k = <tgt|psi_k(T)>/||psi_k(T)|| is formed; F_out (nullable) receives
+ * F = (1/M) sum |tau_k|^2 (Eq. functional_traj). */
+KT_API kt_status propagate_forward(kt_problem *p, int sequential_update, double *F_out, void *stream);
+
+/* Backward co-state sweep (Sec. 2.3): chi_k(T) = tau_k |tgt>, then
+ * chi_k(t_{j-1}) = U_kj^dag chi_k(t_j) under the pulse of the last forward sweep, where U_kj
+ * is trajectory k's own forward map over interval j including its recorded jumps c L_l.
+ * Requires a forward sweep. */
+KT_API kt_status propagate_backward(kt_problem *p, void *stream);
+
+/* n_iter Krotov iterations, each = propagate_backward + propagate_forward(update = 1).  If
+ * no forward sweep has run yet, a guess sweep propagate_forward(0) runs first.  JT_out and
+ * J_out (nullable, [n_iter]) receive J_T = 1 - F and Krotov's functional
+ * J = J_T + sum_c lambda_c sum_j Delta eps_cj^2 dt / S_cj (Eq. krotov_functional, S = 0
+ * points skipped) after each iteration. */
+KT_API kt_status krotov_update(kt_problem *p, int n_iter, double *JT_out, double *J_out, void *stream);
+
+/* F and tau_k ([M][2], nullable) of the last forward sweep (Eq. functional_traj). */
+KT_API kt_status fidelity(kt_problem *p, double *F_out, double *tau_out);
+
+/* Current pulse [n_ctrl][nt], and the update Delta eps [n_ctrl][nt] of the last updating
+ * forward sweep (zeros before the first). */
+KT_API kt_status krotov_get_pulses(kt_problem *p, double *eps_out);
+KT_API kt_status krotov_get_update(kt_problem *p, double *deps_out);
+/* Replace the current pulse (host array [n_ctrl][nt]); invalidates co-states and records. */
+KT_API kt_status krotov_set_pulses(kt_problem *p, const double *eps);
+
+/* Jump record of the last forward sweep.  count_out [M]; step_out/channel_out/s_out/c_out
+ * [M][max_jumps] (any may be NULL): 1-based interval index j, Lindblad channel l, offset s*
+ * of the jump from t_{j-1}, and the renormalisation c = 1/||L_l psi(s*)||. */
+KT_API kt_status krotov_get_records(kt_problem *p, int *count_out, int *step_out, int *channel_out,
+                                    double *s_out, double *c_out);
+
+/* Final states psi_k(T) of the last forward sweep, [M][d][2] (not normalised). */
+KT_API kt_status krotov_get_states(kt_problem *p, double *psi_out);
+/* Co-state chi_k(t_j), [M][d][2], of the last backward sweep; only for ckpt_interval = 0 or
+ * j a checkpoint. */
+KT_API kt_status krotov_get_costate(kt_problem *p, int j, double *chi_out);
+
+/* Sizes chosen at init: max jumps per pass, Chebyshev terms per step, tile width, tiles,
+ * threads per CTA, and the spectral interval [e_min, e_max] of the forward generator's
+ * Hermitian part. */
+typedef struct {
+  int d, max_jumps, cheb_terms, tile_traj, n_tiles, threads;
+  double e_min, e_max, damping;
+  long long device_bytes;
+} kt_info;
+KT_API kt_status krotov_get_info(kt_problem *p, kt_info *info);
+
+KT_API void krotov_free(kt_problem *p);
+KT_API const char *krotov_last_error(void);
+
+/* Chebyshev coefficient helper (host): Bessel J_0..J_{n-1}(alpha) by Miller's backward
+ * recurrence, the routine the kernels use for sub-step propagators.  Returns KT_ERR_ARG for
+ * alpha < 0 or n outside [1, 256]. */
+KT_API kt_status kt_bessel_j(double alpha, int n, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KROTOV_TRAJ_H */

@@ -1,0 +1,763 @@
+#pragma once
+// CUDA kernels of the trajectory-parallel Krotov hot path (sm_103a).
+//
+// One CTA owns a tile of T trajectories for one time interval.  The tile's states sit in
+// global memory as [d][T] complex (element-major, trajectories interleaved), so that a warp
+// whose items share an element index (T = 32) runs the structured generator uniformly and
+// reads its neighbours from consecutive shared-memory words.
+//
+// Per interval the CTA applies exp(-i G dt) by a Chebyshev series (paper Sec. 2.1: exact
+// propagation over long steps, the basic operation being the matrix-vector product of
+// Sec. 2.3), keeping T_{k-1}/T_{k+1} and T_k in two shared-memory buffers and the running
+// sum in registers.  G is never formed: it is the sum of node-local factors, pair hops
+// a_dst^dag a_src and a diagonal, all read from small per-interval tables in shared memory.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kt_common.h"
+#include "kt_kernels.h"
+
+namespace kt {
+
+template <typename R> struct C2;
+template <> struct C2<float> { typedef float2 T; };
+template <> struct C2<double> { typedef double2 T; };
+
+__device__ __forceinline__ float2 mkc(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mkc(double a, double b) { return make_double2(a, b); }
+
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return mkc(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ C cfma(C a, C b, C c) {  // c + a*b
+  c.x = fma(a.x, b.x, c.x);
+  c.x = fma(-a.y, b.y, c.x);
+  c.y = fma(a.x, b.y, c.y);
+  c.y = fma(a.y, b.x, c.y);
+  return c;
+}
+
+template <typename C> __device__ __forceinline__ C from_kc(KtCplx z) {
+  typedef decltype(C().x) R;
+  return mkc((R)z.re, (R)z.im);
+}
+
+__device__ __forceinline__ void set_status(int *status, int code) {
+  atomicCAS(status, KT_DEV_OK, code);
+}
+
+// --------------------------------------------------------------------------------------
+// Shared-memory carve-up (identical on host and device; see kt_smem_bytes).
+struct Smem {
+  void *bufA, *bufB;          // [d*T] complex each
+  int *loc_off;               // [N*n_loc*S]  element offset * T (0 = no entry)
+  void *loc_val;              // [N*n_loc*S]
+  void *diag;                 // [N*n_loc]
+  int *pair_off;              // [P*n_loc^2]
+  void *pair_val;             // [P*n_loc^2]
+  int *hc_off;                // [n_ctrl*n_loc*SH]
+  void *hc_val;               // [n_ctrl*n_loc*SH]
+  void *coef;                 // [K][T]
+  double *red;                // [nwarps][T][8]
+  double *tsc;                // per-trajectory scalars [16][T]
+  int *tin;                   // per-trajectory ints [16][T]
+  double *eps;                // [n_ctrl]
+  int *flag;                  // [4] block flags
+};
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline size_t carve(const KtGeom &g, int esz, char *base, Smem *s) {
+  const int nl2 = g.n_loc * g.n_loc;
+  const int nwarps = g.nthreads / 32;
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char * {
+    off = align_up(off, 16);
+    char *p = base ? base + off : nullptr;
+    off += bytes;
+    return p;
+  };
+  const size_t tile = (size_t)g.d * g.T * esz;
+  char *a = take(tile), *b = take(tile);
+  char *lo = take(sizeof(int) * g.n_nodes * g.n_loc * g.S);
+  char *lv = take((size_t)esz * g.n_nodes * g.n_loc * g.S);
+  char *dg = take((size_t)esz * g.n_nodes * g.n_loc);
+  char *po = take(sizeof(int) * g.n_pairs * nl2);
+  char *pv = take((size_t)esz * g.n_pairs * nl2);
+  char *ho = take(sizeof(int) * g.n_ctrl * g.n_loc * g.SH);
+  char *hv = take((size_t)esz * g.n_ctrl * g.n_loc * g.SH);
+  char *cf = take((size_t)esz * g.K * g.T);
+  char *rd = take(sizeof(double) * nwarps * g.T * 8);
+  char *ts = take(sizeof(double) * 16 * g.T);
+  char *ti = take(sizeof(int) * 16 * g.T);
+  char *ep = take(sizeof(double) * KT_MAX_CTRL);
+  char *fl = take(sizeof(int) * 4);
+  if (s) {
+    s->bufA = a; s->bufB = b; s->loc_off = (int *)lo; s->loc_val = lv; s->diag = dg;
+    s->pair_off = (int *)po; s->pair_val = pv; s->hc_off = (int *)ho; s->hc_val = hv;
+    s->coef = cf; s->red = (double *)rd; s->tsc = (double *)ts; s->tin = (int *)ti;
+    s->eps = (double *)ep; s->flag = (int *)fl;
+  }
+  return align_up(off, 16);
+}
+
+// per-trajectory scalar slots in Smem::tsc / Smem::tin
+enum { TS_R = 0, TS_LO, TS_HI, TS_S0, TS_LEN, TS_NRM, TS_C, TS_V0, TS_V1, TS_V2, TS_V3 };
+enum { TI_ACT = 0, TI_BUSY, TI_CH, TI_NJ, TI_J0, TI_J1, TI_J2, TI_J3, TI_J4, TI_J5, TI_J6, TI_J7,
+       TI_J8, TI_J9, TI_J10, TI_J11 };
+
+// --------------------------------------------------------------------------------------
+// Per-trajectory block reduction: every thread holds NV partial sums of its trajectory
+// (tau = tid % T); sums over lanes of equal tau by shuffles, then over warps in a fixed
+// order.  Result in out[tau*NV + v].  Deterministic.
+template <int NV>
+__device__ __forceinline__ void reduce_tau(double (&v)[NV], const KtGeom &g, double *red, double *out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int o = 16; o >= g.T; o >>= 1) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  }
+  if (lane < g.T) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) red[(warp * g.T + lane) * 8 + q] = v[q];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < g.T * NV; t += blockDim.x) {
+    const int tau = t / NV, q = t % NV;
+    double s = 0.0;
+    for (int w = 0; w < nwarps; ++w) s += red[(w * g.T + tau) * 8 + q];
+    out[tau * NV + q] = s;
+  }
+  __syncthreads();
+}
+
+// --------------------------------------------------------------------------------------
+// Per-interval tables: generator factors for pulse eps (scaled by 1/r, diagonal shifted),
+// plus control factors for the update overlap.
+template <typename R>
+__device__ void build_tables(const KtGeom &g, const KtGenImage &im, const KtOps &ops, const Smem &sm,
+                             const double *eps, bool with_hc) {
+  typedef typename C2<R>::T C;
+  C *lv = (C *)sm.loc_val;
+  C *dg = (C *)sm.diag;
+  C *pv = (C *)sm.pair_val;
+  const int nls = g.n_loc * g.S;
+  for (int e = threadIdx.x; e < g.n_nodes * nls; e += blockDim.x) {
+    const int i = e / nls, rem = e % nls;
+    double re = im.loc_base[e].re, imv = im.loc_base[e].im;
+    for (int c = 0; c < g.n_ctrl; ++c)
+      if (g.ctrl_node[c] == i) {
+        re += eps[c] * im.ctrl_slot[c * nls + rem].re;
+        imv += eps[c] * im.ctrl_slot[c * nls + rem].im;
+      }
+    lv[e] = mkc((R)re, (R)imv);
+    sm.loc_off[e] = im.loc_dl[e] * g.stride[i] * g.T;
+  }
+  for (int e = threadIdx.x; e < g.n_nodes * g.n_loc; e += blockDim.x) {
+    const int i = e / g.n_loc, x = e % g.n_loc;
+    double re = im.diag_base[e].re, imv = im.diag_base[e].im;
+    for (int c = 0; c < g.n_ctrl; ++c)
+      if (g.ctrl_node[c] == i) {
+        re += eps[c] * im.ctrl_diag[c * g.n_loc + x].re;
+        imv += eps[c] * im.ctrl_diag[c * g.n_loc + x].im;
+      }
+    dg[e] = mkc((R)re, (R)imv);
+  }
+  const int nl2 = g.n_loc * g.n_loc;
+  for (int e = threadIdx.x; e < g.n_pairs * nl2; e += blockDim.x) {
+    sm.pair_off[e] = im.pair_off[e] * g.T;
+    pv[e] = from_kc<C>(im.pair_val[e]);
+  }
+  if (with_hc) {
+    C *hv = (C *)sm.hc_val;
+    const int nh = g.n_loc * g.SH;
+    for (int e = threadIdx.x; e < g.n_ctrl * nh; e += blockDim.x) {
+      const int c = e / nh;
+      sm.hc_off[e] = ops.hc_dl[e] * g.stride[g.ctrl_node[c]] * g.T;
+      hv[e] = from_kc<C>(ops.hc_val[e]);
+    }
+  }
+}
+
+// Scaled generator Ghat applied at one item (element x, trajectory tau) of tile vector v.
+template <typename R>
+__device__ __forceinline__ typename C2<R>::T apply_item(const KtGeom &g, const Smem &sm,
+                                                        const typename C2<R>::T *__restrict__ v,
+                                                        int item, uint32_t dig,
+                                                        typename C2<R>::T dval) {
+  typedef typename C2<R>::T C;
+  const C *lv = (const C *)sm.loc_val;
+  const C *pv = (const C *)sm.pair_val;
+  C out = cmul(dval, v[item]);
+  for (int i = 0; i < g.n_nodes; ++i) {
+    const int xi = (dig >> (4 * i)) & 15;
+    const int base = (i * g.n_loc + xi) * g.S;
+    for (int s = 0; s < g.S; ++s) {
+      const int off = sm.loc_off[base + s];
+      if (off) out = cfma(lv[base + s], v[item + off], out);
+    }
+  }
+  const int nl2 = g.n_loc * g.n_loc;
+  for (int p = 0; p < g.n_pairs; ++p) {
+    const int xd = (dig >> (4 * g.pair_dst[p])) & 15;
+    const int xs = (dig >> (4 * g.pair_src[p])) & 15;
+    const int idx = p * nl2 + xd * g.n_loc + xs;
+    const int off = sm.pair_off[idx];
+    if (off) out = cfma(pv[idx], v[item + off], out);
+  }
+  return out;
+}
+
+template <typename R>
+__device__ __forceinline__ typename C2<R>::T diag_of(const KtGeom &g, const Smem &sm, uint32_t dig) {
+  typedef typename C2<R>::T C;
+  const C *dg = (const C *)sm.diag;
+  C s = mkc((R)0, (R)0);
+  for (int i = 0; i < g.n_nodes; ++i) {
+    const C v = dg[i * g.n_loc + ((dig >> (4 * i)) & 15)];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  return s;
+}
+
+// Items of this thread: item_q = tid + q * nthreads, valid while < d*T.
+template <int EPT>
+struct Items {
+  int item[EPT];
+  uint32_t dig[EPT];
+  bool ok[EPT];
+};
+
+template <int EPT>
+__device__ __forceinline__ void load_items(const KtGeom &g, const KtOps &ops, Items<EPT> &it) {
+  const int n = g.d * g.T;
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int item = threadIdx.x + q * blockDim.x;
+    it.item[q] = item;
+    it.ok[q] = item < n;
+    it.dig[q] = it.ok[q] ? ops.digits[item / g.T] : 0u;
+  }
+}
+
+// Chebyshev sum: acc = sum_k coef[k][tau] T_k(Ghat) v with v in A on entry (synced).
+// A and B are overwritten.  Ends synchronised.
+template <typename R, int EPT>
+__device__ void cheb_run(const KtGeom &g, const Smem &sm, const Items<EPT> &it, int K,
+                         typename C2<R>::T (&acc)[EPT]) {
+  typedef typename C2<R>::T C;
+  C *A = (C *)sm.bufA;
+  C *B = (C *)sm.bufB;
+  const C *cf = (const C *)sm.coef;
+  const int tau = threadIdx.x % g.T;
+  C dv[EPT];
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    dv[q] = it.ok[q] ? diag_of<R>(g, sm, it.dig[q]) : mkc((R)0, (R)0);
+    acc[q] = it.ok[q] ? cmul(cf[tau], A[it.item[q]]) : mkc((R)0, (R)0);
+  }
+  if (K == 1) { __syncthreads(); return; }
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    if (!it.ok[q]) continue;
+    const C t = apply_item<R>(g, sm, A, it.item[q], it.dig[q], dv[q]);
+    B[it.item[q]] = t;
+    acc[q] = cfma(cf[g.T + tau], t, acc[q]);
+  }
+  __syncthreads();
+  C *P = A;   // holds T_{k-1}; receives T_{k+1}
+  C *Q = B;   // holds T_k
+  for (int k = 2; k < K; ++k) {
+    const C a = cf[k * g.T + tau];
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      if (!it.ok[q]) continue;
+      const C t = apply_item<R>(g, sm, Q, it.item[q], it.dig[q], dv[q]);
+      const C old = P[it.item[q]];
+      const C nv = mkc(t.x + t.x - old.x, t.y + t.y - old.y);
+      P[it.item[q]] = nv;
+      acc[q] = cfma(a, nv, acc[q]);
+    }
+    __syncthreads();
+    C *tmp = P; P = Q; Q = tmp;
+  }
+}
+
+// Coefficients of exp(-i G s) for trajectory tau (called by one thread per trajectory):
+// (2 - delta_k0) (-i)^k J_k(r s) exp(-i c s).
+template <typename R>
+__device__ void tau_coefs(const KtGeom &g, const Smem &sm, int tau, double c_gen, double s) {
+  typedef typename C2<R>::T C;
+  C *cf = (C *)sm.coef;
+  double J[KT_MAX_K];
+  kt_bessel_miller(g.r * s, g.K, J);
+  double sn, cs;
+  sincos(-c_gen * s, &sn, &cs);
+  for (int k = 0; k < g.K; ++k) {
+    const double m = (k == 0 ? 1.0 : 2.0) * J[k];
+    double re, im;                           // m * (-i)^k
+    switch (k & 3) {
+      case 0: re = m; im = 0; break;
+      case 1: re = 0; im = -m; break;
+      case 2: re = -m; im = 0; break;
+      default: re = 0; im = m; break;
+    }
+    cf[k * g.T + tau] = mkc((R)(re * cs - im * sn), (R)(re * sn + im * cs));
+  }
+}
+
+template <typename R>
+__device__ void uniform_coefs(const KtGeom &g, const Smem &sm, const KtCplx *full) {
+  typedef typename C2<R>::T C;
+  C *cf = (C *)sm.coef;
+  for (int e = threadIdx.x; e < g.K * g.T; e += blockDim.x) cf[e] = from_kc<C>(full[e / g.T]);
+}
+
+template <typename R, int EPT>
+__device__ __forceinline__ void load_tile(const KtGeom &g, const Items<EPT> &it, const typename C2<R>::T *src,
+                                          typename C2<R>::T *dst) {
+#pragma unroll
+  for (int q = 0; q < EPT; ++q)
+    if (it.ok[q]) dst[it.item[q]] = src[it.item[q]];
+}
+
+// Norm^2 of each trajectory of acc -> sm.tsc[TS_NRM][tau]
+template <typename R, int EPT>
+__device__ void norms(const KtGeom &g, const Smem &sm, const Items<EPT> &it, const typename C2<R>::T (&acc)[EPT]) {
+  R s = 0;
+#pragma unroll
+  for (int q = 0; q < EPT; ++q)
+    if (it.ok[q]) s += acc[q].x * acc[q].x + acc[q].y * acc[q].y;
+  double v[1] = {(double)s};
+  reduce_tau<1>(v, g, sm.red, sm.tsc + TS_NRM * g.T);
+}
+
+// (sum_i coef_i a_i) v  (adj = 0)  or  (sum_i conj(coef_i) a_i^dag) v  (adj = 1) at one item.
+template <typename R>
+__device__ __forceinline__ typename C2<R>::T lind_item(const KtGeom &g, const KtOps &ops, int l, int adj,
+                                                       const typename C2<R>::T *v, int item, uint32_t dig) {
+  typedef typename C2<R>::T C;
+  C out = mkc((R)0, (R)0);
+  for (int i = 0; i < g.n_nodes; ++i) {
+    const int xi = (dig >> (4 * i)) & 15;
+    KtCplx lc = ops.lind_coef[l * g.n_nodes + i];
+    KtCplx av = adj ? ops.ra_val[xi] : ops.lo_val[xi];
+    const int dl = adj ? ops.ra_dl[xi] : ops.lo_dl[xi];
+    if (av.re == 0.0 && av.im == 0.0) continue;
+    if (lc.re == 0.0 && lc.im == 0.0) continue;
+    if (adj) lc.im = -lc.im;
+    const double wr = lc.re * av.re - lc.im * av.im, wi = lc.re * av.im + lc.im * av.re;
+    out = cfma(mkc((R)wr, (R)wi), v[item + dl * g.stride[i] * g.T], out);
+  }
+  return out;
+}
+
+// --------------------------------------------------------------------------------------
+// Forward interval kernel.  One Chebyshev call site serves every phase:
+//   MAIN    full interval from psi(t_{j-1}) (uniform coefficients),
+//   BISECT  bisection of ||exp(-i G s) start||^2 = r for flagged trajectories,
+//   SSTAR   the state at the located jump time s*, then collapse (Sec. 2.1, steps 3-5),
+//   REST    the remainder of the interval from the collapsed state, tested again.
+enum { PH_MAIN = 0, PH_BISECT, PH_SSTAR, PH_REST, PH_DONE };
+
+template <typename R, int EPT>
+__global__ void __launch_bounds__(sizeof(R) == 8 ? 512 : 1024) fwd_kernel(KtGeom g, KtGenImage im, KtOps ops, FwdArgs a) {
+  typedef typename C2<R>::T C;
+  extern __shared__ __align__(16) char smem_raw[];
+  Smem sm;
+  carve(g, sizeof(C), smem_raw, &sm);
+  const int tile = blockIdx.x;
+  const int tau = threadIdx.x % g.T;
+  const C *psi_in = (const C *)a.psi_in + (size_t)tile * g.tile_elems;
+  C *psi_out = (C *)a.psi_out + (size_t)tile * g.tile_elems;
+  const int j = a.j;
+  const double tol = 0x1p-40 * g.dt;
+
+  if (threadIdx.x < g.n_ctrl) {
+    const int c = threadIdx.x;
+    double e = 0.0;
+    if (j >= 1) {
+      e = a.eps_old[c * a.nt + (j - 1)];
+      if (a.update) e += a.deps[c * a.nt + (j - 1)];
+    }
+    sm.eps[c] = e;
+  }
+  if (threadIdx.x < 4) sm.flag[threadIdx.x] = 0;
+  __syncthreads();
+  build_tables<R>(g, im, ops, sm, sm.eps, a.update != 0);
+  Items<EPT> it;
+  load_items<EPT>(g, ops, it);
+  C acc[EPT];
+  C *A = (C *)sm.bufA;
+
+  int phase = (j >= 1) ? PH_MAIN : PH_DONE;
+  if (phase == PH_DONE) {
+    load_tile<R, EPT>(g, it, psi_in, A);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) acc[q] = it.ok[q] ? A[it.item[q]] : mkc((R)0, (R)0);
+    __syncthreads();
+  }
+  int guard = 0;
+  while (phase != PH_DONE) {
+    // ---- choose the propagation of this round
+    if (phase == PH_BISECT) {
+      if (threadIdx.x == 0) sm.flag[1] = 0;
+      __syncthreads();
+      if (threadIdx.x < g.T) {
+        const int t = threadIdx.x;
+        const double lo = sm.tsc[TS_LO * g.T + t], hi = sm.tsc[TS_HI * g.T + t];
+        const int busy = sm.tin[TI_ACT * g.T + t] && (hi - lo > tol) && sm.tin[TI_CH * g.T + t] < 60;
+        sm.tin[TI_BUSY * g.T + t] = busy;
+        if (busy) atomicAdd(&sm.flag[1], 1);
+      }
+      __syncthreads();
+      if (sm.flag[1] == 0) phase = PH_SSTAR;
+    }
+    if (phase == PH_MAIN) {
+      uniform_coefs<R>(g, sm, im.cheb_full);
+    } else if (threadIdx.x < g.T) {
+      const int t = threadIdx.x;
+      const bool act = sm.tin[TI_ACT * g.T + t] != 0;
+      double len = 0.0;
+      if (phase == PH_BISECT) len = sm.tin[TI_BUSY * g.T + t] ? 0.5 * (sm.tsc[TS_LO * g.T + t] + sm.tsc[TS_HI * g.T + t]) : 0.0;
+      else if (phase == PH_SSTAR) len = act ? sm.tsc[TS_HI * g.T + t] : 0.0;
+      else len = act ? g.dt - sm.tsc[TS_S0 * g.T + t] : 0.0;
+      tau_coefs<R>(g, sm, t, g.c_fwd, len);
+    }
+    load_tile<R, EPT>(g, it, phase == PH_MAIN ? psi_in : psi_out, A);
+    __syncthreads();
+    cheb_run<R, EPT>(g, sm, it, g.K, acc);
+    norms<R, EPT>(g, sm, it, acc);
+
+    // ---- consume the result
+    if (phase == PH_MAIN) {
+#pragma unroll
+      for (int q = 0; q < EPT; ++q)
+        if (it.ok[q]) psi_out[it.item[q]] = acc[q];
+      if (threadIdx.x < g.T) {
+        const int t = threadIdx.x, k = tile * g.T + t;
+        const double nrm = sm.tsc[TS_NRM * g.T + t];
+        const double r = a.rstate[k];                    // padding trajectories carry r = -1
+        if (!isfinite(nrm)) set_status(a.status, KT_DEV_NONFINITE);
+        const int act = (k < g.M) && (nrm <= r);         // jump iff ||psi||^2 <= r
+        sm.tin[TI_ACT * g.T + t] = act;
+        sm.tsc[TS_R * g.T + t] = r;
+        sm.tsc[TS_S0 * g.T + t] = 0.0;
+        sm.tsc[TS_LO * g.T + t] = 0.0;
+        sm.tsc[TS_HI * g.T + t] = g.dt;
+        sm.tin[TI_CH * g.T + t] = 0;                     // bisection iteration counter
+        if (act) atomicAdd(&sm.flag[0], 1);
+      }
+      __syncthreads();
+      if (sm.flag[0] == 0) break;
+      // flagged trajectories restart from psi(t_{j-1}), kept in psi_out
+#pragma unroll
+      for (int q = 0; q < EPT; ++q)
+        if (it.ok[q] && sm.tin[TI_ACT * g.T + tau]) psi_out[it.item[q]] = psi_in[it.item[q]];
+      __syncthreads();
+      phase = PH_BISECT;
+    } else if (phase == PH_BISECT) {
+      if (threadIdx.x < g.T) {
+        const int t = threadIdx.x;
+        if (sm.tin[TI_BUSY * g.T + t]) {
+          const double mid = 0.5 * (sm.tsc[TS_LO * g.T + t] + sm.tsc[TS_HI * g.T + t]);
+          if (sm.tsc[TS_NRM * g.T + t] <= sm.tsc[TS_R * g.T + t]) sm.tsc[TS_HI * g.T + t] = mid;
+          else sm.tsc[TS_LO * g.T + t] = mid;
+          sm.tin[TI_CH * g.T + t] += 1;
+        }
+      }
+      __syncthreads();
+    } else if (phase == PH_SSTAR) {
+#pragma unroll
+      for (int q = 0; q < EPT; ++q)
+        if (it.ok[q]) A[it.item[q]] = acc[q];
+      __syncthreads();
+      // channel probabilities p_l = ||L_l phi||^2
+      double v[KT_MAX_LIND];
+      for (int l = 0; l < KT_MAX_LIND; ++l) {
+        R s = 0;
+        if (l < g.n_lind) {
+#pragma unroll
+          for (int q = 0; q < EPT; ++q)
+            if (it.ok[q]) {
+              const C y = lind_item<R>(g, ops, l, 0, A, it.item[q], it.dig[q]);
+              s += y.x * y.x + y.y * y.y;
+            }
+        }
+        v[l] = (double)s;
+      }
+      reduce_tau<KT_MAX_LIND>(v, g, sm.red, sm.tsc + TS_V0 * g.T);
+      if (threadIdx.x < g.T) {
+        const int t = threadIdx.x, k = tile * g.T + t;
+        int ch = -1;
+        if (sm.tin[TI_ACT * g.T + t]) {
+          const double *p = sm.tsc + TS_V0 * g.T + t * KT_MAX_LIND;
+          const int m = a.jcount[k] + 1;
+          if (m > g.max_jumps) {
+            set_status(a.status, KT_DEV_RECORD_FULL);
+            sm.tin[TI_ACT * g.T + t] = 0;
+          } else if (g.n_lind == 0) {
+            set_status(a.status, KT_DEV_ZERO_JUMP);      // norm loss without any jump operator
+            sm.tin[TI_ACT * g.T + t] = 0;
+          } else {
+            const double *U = a.U + ((size_t)a.pass_row * g.M + k) * g.draws;
+            double tot = 0.0;
+            for (int l = 0; l < g.n_lind; ++l) tot += p[l];
+            const double target = U[2 * m - 1] * tot;   // first channel whose cumulative p reaches u * sum p
+            ch = g.n_lind - 1;
+            double cum = 0.0;
+            for (int l = 0; l < g.n_lind; ++l) {
+              cum += p[l];
+              if (cum >= target) { ch = l; break; }
+            }
+            if (!(p[ch] > 0.0)) {
+              set_status(a.status, KT_DEV_ZERO_JUMP);
+              sm.tin[TI_ACT * g.T + t] = 0;
+              ch = -1;
+            } else {
+              const double cnorm = 1.0 / sqrt(p[ch]);
+              const double sstar = sm.tsc[TS_S0 * g.T + t] + sm.tsc[TS_HI * g.T + t];
+              const size_t ri = (size_t)k * g.max_jumps + (m - 1);
+              a.rec_step[ri] = j;
+              a.rec_ch[ri] = ch;
+              a.rec_s[ri] = sstar;
+              a.rec_c[ri] = cnorm;
+              a.jcount[k] = m;
+              const double rn = U[2 * m];
+              a.rstate[k] = rn;
+              sm.tsc[TS_R * g.T + t] = rn;
+              sm.tsc[TS_S0 * g.T + t] = sstar;
+              sm.tsc[TS_C * g.T + t] = cnorm;
+            }
+          }
+        }
+        sm.tin[TI_NJ * g.T + t] = ch;
+      }
+      __syncthreads();
+      // collapse: start <- c L_ch phi
+      const int ch = sm.tin[TI_NJ * g.T + tau];
+      if (ch >= 0) {
+        const R cn = (R)sm.tsc[TS_C * g.T + tau];
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+          if (!it.ok[q]) continue;
+          const C y = lind_item<R>(g, ops, ch, 0, A, it.item[q], it.dig[q]);
+          psi_out[it.item[q]] = mkc(cn * y.x, cn * y.y);
+        }
+      }
+      __syncthreads();
+      phase = PH_REST;
+    } else {  // PH_REST
+      if (threadIdx.x == 0) sm.flag[2] = 0;
+      __syncthreads();
+      if (threadIdx.x < g.T) {
+        const int t = threadIdx.x;
+        int done = 0;
+        if (sm.tin[TI_ACT * g.T + t]) {
+          if (sm.tsc[TS_NRM * g.T + t] > sm.tsc[TS_R * g.T + t]) done = 1;
+          else {
+            atomicAdd(&sm.flag[2], 1);      // another jump inside the remainder
+            sm.tsc[TS_LO * g.T + t] = 0.0;
+            sm.tsc[TS_HI * g.T + t] = g.dt - sm.tsc[TS_S0 * g.T + t];
+            sm.tin[TI_CH * g.T + t] = 0;
+          }
+        }
+        sm.tin[TI_BUSY * g.T + t] = done;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < EPT; ++q)
+        if (it.ok[q] && sm.tin[TI_BUSY * g.T + tau]) psi_out[it.item[q]] = acc[q];
+      __syncthreads();
+      if (threadIdx.x < g.T && sm.tin[TI_BUSY * g.T + threadIdx.x]) sm.tin[TI_ACT * g.T + threadIdx.x] = 0;
+      __syncthreads();
+      ++guard;
+      if (sm.flag[2] == 0 || guard > g.max_jumps + 1) {
+        // final states of the whole tile
+#pragma unroll
+        for (int q = 0; q < EPT; ++q)
+          if (it.ok[q]) acc[q] = psi_out[it.item[q]];
+        __syncthreads();
+        phase = PH_DONE;
+      } else {
+        phase = PH_BISECT;
+      }
+    }
+  }
+
+  // ---------------- end of the sweep: tau_k = <tgt|psi_k>/||psi_k|| ----------------
+  if (j == a.nt) {
+    double v[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      if (!it.ok[q]) continue;
+      const KtCplx t = ops.tgt[it.item[q] / g.T];
+      const double xr = (double)acc[q].x, xi = (double)acc[q].y;
+      v[0] += t.re * xr + t.im * xi;   // conj(tgt) * psi
+      v[1] += t.re * xi - t.im * xr;
+      v[2] += xr * xr + xi * xi;
+    }
+    reduce_tau<3>(v, g, sm.red, sm.tsc + TS_V0 * g.T);
+    if (threadIdx.x < g.T) {
+      const int k = tile * g.T + threadIdx.x;
+      const double *o = sm.tsc + TS_V0 * g.T + threadIdx.x * 3;
+      const double nrm = o[2];
+      const double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
+      a.tau[k].re = o[0] * inv;
+      a.tau[k].im = o[1] * inv;
+      a.norm2[k] = nrm;
+      if (!isfinite(nrm) || !isfinite(o[0]) || !isfinite(o[1])) set_status(a.status, KT_DEV_NONFINITE);
+    }
+    return;
+  }
+
+  // ---------------- update overlap at t_j: g_c = sum_k Im <chi_k|hc_c|psi_k> ----------------
+  if (!a.update) return;
+#pragma unroll
+  for (int q = 0; q < EPT; ++q)
+    if (it.ok[q]) A[it.item[q]] = acc[q];
+  __syncthreads();
+  const C *chi = (const C *)a.chi_t + (size_t)tile * g.tile_elems;
+  const C *hv = (const C *)sm.hc_val;
+  double v[KT_MAX_CTRL];
+  for (int c = 0; c < KT_MAX_CTRL; ++c) v[c] = 0.0;
+  for (int c = 0; c < g.n_ctrl; ++c) {
+    const int node = g.ctrl_node[c];
+    R s = 0;
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      if (!it.ok[q]) continue;
+      const int xi = (it.dig[q] >> (4 * node)) & 15;
+      const int base = (c * g.n_loc + xi) * g.SH;
+      C h = mkc((R)0, (R)0);
+      for (int e = 0; e < g.SH; ++e) {
+        const C w = hv[base + e];
+        if (w.x != (R)0 || w.y != (R)0) h = cfma(w, A[it.item[q] + sm.hc_off[base + e]], h);
+      }
+      const C x = chi[it.item[q]];
+      s += x.x * h.y - x.y * h.x;       // Im(conj(chi) * h)
+    }
+    v[c] = (double)s;
+  }
+  reduce_tau<KT_MAX_CTRL>(v, g, sm.red, sm.tsc + TS_V0 * g.T);
+  if (threadIdx.x < g.n_ctrl) {
+    double s = 0.0;
+    for (int t = 0; t < g.T; ++t) s += sm.tsc[TS_V0 * g.T + t * KT_MAX_CTRL + threadIdx.x];
+    a.partials[(size_t)tile * g.n_ctrl + threadIdx.x] = s;
+  }
+  // ---------------- last CTA: Delta eps of interval j+1, summed in tile order ----------------
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned ticket = atomicAdd(a.counter, 1u);
+    sm.flag[3] = (ticket == (unsigned)(gridDim.x - 1));
+  }
+  __syncthreads();
+  if (!sm.flag[3]) return;
+  __threadfence();
+  if (threadIdx.x < g.n_ctrl) {
+    const int c = threadIdx.x;
+    double s = 0.0;
+    for (int t = 0; t < (int)gridDim.x; ++t) s += ((volatile double *)a.partials)[(size_t)t * g.n_ctrl + c];
+    const size_t idx = (size_t)c * a.nt + j;   // interval j+1 (0-based index j)
+    const double de = a.shape[idx] / (g.lam[c] * (double)g.M) * s;
+    const double en = a.eps_old[idx] + de;
+    a.deps[idx] = de;
+    a.eps_new[idx] = en;
+    if (!isfinite(de)) set_status(a.status, KT_DEV_NONFINITE);
+    if (fabs(en) > g.eps_bound) set_status(a.status, KT_DEV_RANGE);
+  }
+  if (threadIdx.x == 0) *a.counter = 0u;
+}
+
+// --------------------------------------------------------------------------------------
+// Backward interval kernel: chi(t_{j-1}) = U_j^dag chi(t_j) along each trajectory's record.
+// Round rnd propagates piece rnd of the interval (backwards: dt - s_m, s_m - s_{m-1}, ..., s_1)
+// and then applies conj(c) L^dag of the jump that bounds it.  One Chebyshev call site.
+template <typename R, int EPT>
+__global__ void __launch_bounds__(sizeof(R) == 8 ? 512 : 1024) bwd_kernel(KtGeom g, KtGenImage im, KtOps ops, BwdArgs a) {
+  typedef typename C2<R>::T C;
+  extern __shared__ __align__(16) char smem_raw[];
+  Smem sm;
+  carve(g, sizeof(C), smem_raw, &sm);
+  const int tile = blockIdx.x;
+  const int tau = threadIdx.x % g.T;
+  const int j = a.j;
+  const C *chi_in = (const C *)a.chi_in + (size_t)tile * g.tile_elems;
+  C *chi_out = (C *)a.chi_out + (size_t)tile * g.tile_elems;
+  if (threadIdx.x < g.n_ctrl) sm.eps[threadIdx.x] = a.eps[threadIdx.x * a.nt + (j - 1)];
+  if (threadIdx.x == 0) sm.flag[0] = 0;
+  __syncthreads();
+  build_tables<R>(g, im, ops, sm, sm.eps, false);
+  if (threadIdx.x < g.T) {
+    const int t = threadIdx.x, k = tile * g.T + t;
+    int nj = 0;
+    if (k < g.M) {
+      int cur = a.cursor[k];
+      while (cur >= 0 && a.rec_step[(size_t)k * g.max_jumps + cur] == j && nj < 12) {
+        sm.tin[(TI_J0 + nj) * g.T + t] = cur;    // descending in time
+        ++nj;
+        --cur;
+      }
+      if (cur >= 0 && a.rec_step[(size_t)k * g.max_jumps + cur] == j) set_status(a.status, KT_DEV_RECORD_FULL);
+      if (a.advance_cursor) a.cursor[k] = cur;
+    }
+    sm.tin[TI_NJ * g.T + t] = nj;
+    atomicMax(&sm.flag[0], nj);
+  }
+  Items<EPT> it;
+  load_items<EPT>(g, ops, it);
+  C *A = (C *)sm.bufA;
+  C *B = (C *)sm.bufB;
+  load_tile<R, EPT>(g, it, chi_in, B);
+  __syncthreads();
+  const int rounds = sm.flag[0];
+  C acc[EPT];
+  for (int rnd = 0; rnd <= rounds; ++rnd) {
+    if (rounds == 0) {
+      uniform_coefs<R>(g, sm, im.cheb_full);
+    } else if (threadIdx.x < g.T) {
+      const int t = threadIdx.x, k = tile * g.T + t, nj = sm.tin[TI_NJ * g.T + t];
+      double len = 0.0;
+      if (rnd <= nj) {
+        const double hi = (rnd == 0) ? g.dt : a.rec_s[(size_t)k * g.max_jumps + sm.tin[(TI_J0 + rnd - 1) * g.T + t]];
+        const double lo = (rnd < nj) ? a.rec_s[(size_t)k * g.max_jumps + sm.tin[(TI_J0 + rnd) * g.T + t]] : 0.0;
+        len = hi - lo;
+      }
+      tau_coefs<R>(g, sm, t, g.c_bwd, len);
+    }
+    // B holds the vector to propagate
+#pragma unroll
+    for (int q = 0; q < EPT; ++q)
+      if (it.ok[q]) A[it.item[q]] = B[it.item[q]];
+    __syncthreads();
+    cheb_run<R, EPT>(g, sm, it, g.K, acc);
+    if (rnd == rounds) break;
+#pragma unroll
+    for (int q = 0; q < EPT; ++q)
+      if (it.ok[q]) A[it.item[q]] = acc[q];
+    __syncthreads();
+    const int nj = sm.tin[TI_NJ * g.T + tau];
+    const int k = tile * g.T + tau;
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      if (!it.ok[q]) continue;
+      C y = A[it.item[q]];
+      if (rnd < nj) {
+        const size_t ri = (size_t)k * g.max_jumps + sm.tin[(TI_J0 + rnd) * g.T + tau];
+        const C z = lind_item<R>(g, ops, a.rec_ch[ri], 1, A, it.item[q], it.dig[q]);
+        const R cn = (R)a.rec_c[ri];
+        y = mkc(cn * z.x, cn * z.y);
+      }
+      B[it.item[q]] = y;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < EPT; ++q)
+    if (it.ok[q]) chi_out[it.item[q]] = acc[q];
+}
+
+}  // namespace kt

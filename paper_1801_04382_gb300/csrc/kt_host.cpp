@@ -1,0 +1,956 @@
+// Host runtime of the trajectory-parallel Krotov library: validation, assembly of the
+// structured MCWF generator (a1), Chebyshev set-up (a2), device memory, and the sweep
+// schedulers behind the C ABI declared in include/krotov_traj.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/krotov_traj.h"
+#include "kt_common.h"
+#include "kt_kernels.h"
+
+typedef std::complex<double> cd;
+
+namespace {
+
+thread_local std::string g_err;
+
+kt_status fail(kt_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define KT_CUDA(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(KT_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+// ---------------------------------------------------------------------------- structured generator
+struct Pair {
+  int dst, src;
+  cd coef;   // coef * a_dst^dag a_src
+};
+
+struct Gen {
+  int N = 0, nl = 0;
+  std::vector<cd> loc;    // [N][nl][nl]
+  std::vector<cd> ctrl;   // [n_ctrl][nl][nl] (per unit eps)
+  std::vector<int> ctrl_node;
+  std::vector<Pair> pairs;
+};
+
+inline cd at(const std::vector<cd> &m, int base, int nl, int x, int y) { return m[base + x * nl + y]; }
+
+// a^dag a of the ladder factor
+std::vector<cd> adag_a(const std::vector<cd> &a, int nl) {
+  std::vector<cd> out(nl * nl);
+  for (int x = 0; x < nl; ++x)
+    for (int y = 0; y < nl; ++y) {
+      cd s = 0;
+      for (int z = 0; z < nl; ++z) s += std::conj(a[z * nl + x]) * a[z * nl + y];
+      out[x * nl + y] = s;
+    }
+  return out;
+}
+
+// Adjoint-direction generator -G^dag (co-state propagation: exp(+i H_eff^dag s) = exp(-i (-H_eff^dag) s)).
+Gen minus_adjoint(const Gen &f) {
+  Gen b = f;
+  const int nl = f.nl;
+  for (size_t base = 0; base < f.loc.size(); base += nl * nl)
+    for (int x = 0; x < nl; ++x)
+      for (int y = 0; y < nl; ++y) b.loc[base + x * nl + y] = -std::conj(f.loc[base + y * nl + x]);
+  for (size_t base = 0; base < f.ctrl.size(); base += nl * nl)
+    for (int x = 0; x < nl; ++x)
+      for (int y = 0; y < nl; ++y) b.ctrl[base + x * nl + y] = -std::conj(f.ctrl[base + y * nl + x]);
+  for (size_t p = 0; p < f.pairs.size(); ++p) b.pairs[p] = Pair{f.pairs[p].src, f.pairs[p].dst, -std::conj(f.pairs[p].coef)};
+  return b;
+}
+
+struct Bounds {
+  double lo, hi, damp;
+};
+
+// Spectral bounds of a direction's generator: real parts in [lo, hi] from Gershgorin discs of
+// each node's Hermitian part (the node terms act on different factors, so their spectra add),
+// plus the norms of the pair terms; |imaginary parts| <= damp likewise for the anti-Hermitian part.
+Bounds gen_bounds(const Gen &g, double amax, double E) {
+  const int nl = g.nl;
+  Bounds b{0.0, 0.0, 0.0};
+  for (int i = 0; i < g.N; ++i) {
+    double lo = 1e300, hi = -1e300, dmax = 0.0;
+    for (int x = 0; x < nl; ++x) {
+      auto herm = [&](const std::vector<cd> &m, int base, int y) {
+        return 0.5 * (m[base + x * nl + y] + std::conj(m[base + y * nl + x]));
+      };
+      auto anti = [&](const std::vector<cd> &m, int base, int y) {
+        return (m[base + x * nl + y] - std::conj(m[base + y * nl + x])) / cd(0.0, 2.0);
+      };
+      const int lb = i * nl * nl;
+      double cen = herm(g.loc, lb, x).real(), rad = 0.0;
+      double acen = std::abs(anti(g.loc, lb, x)), arad = 0.0;
+      for (size_t c = 0; c < g.ctrl_node.size(); ++c)
+        if (g.ctrl_node[c] == i) {
+          rad += E * std::abs(herm(g.ctrl, c * nl * nl, x).real());
+          arad += E * std::abs(anti(g.ctrl, c * nl * nl, x));
+        }
+      for (int y = 0; y < nl; ++y) {
+        if (y == x) continue;
+        rad += std::abs(herm(g.loc, lb, y));
+        arad += std::abs(anti(g.loc, lb, y));
+        for (size_t c = 0; c < g.ctrl_node.size(); ++c)
+          if (g.ctrl_node[c] == i) {
+            rad += E * std::abs(herm(g.ctrl, c * nl * nl, y));
+            arad += E * std::abs(anti(g.ctrl, c * nl * nl, y));
+          }
+      }
+      lo = std::min(lo, cen - rad);
+      hi = std::max(hi, cen + rad);
+      dmax = std::max(dmax, acen + arad);
+    }
+    b.lo += lo;
+    b.hi += hi;
+    b.damp += dmax;
+  }
+  for (const Pair &p : g.pairs) {
+    const double nrm = std::abs(p.coef) * amax * amax;
+    b.lo -= nrm;
+    b.hi += nrm;
+    b.damp += nrm;
+  }
+  return b;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------- problem object
+struct kt_problem {
+  KtGeom g{};
+  int fp64 = 1, ept = 4;
+  size_t esz = 16;
+  int nt = 0, M = 0, n_passes = 0, ckpt = 0;
+  double T = 0.0;
+  size_t state_bytes = 0;       // one tile-layout array of all trajectories
+  size_t bytes = 0;
+  double e_min = 0, e_max = 0, damping = 0;
+  std::vector<double> shape_h, lam_h;
+
+  KtGenImage im_fwd{}, im_bwd{};
+  KtOps ops{};
+  std::vector<void *> allocs;
+
+  double *eps_old = nullptr, *eps_new = nullptr, *deps = nullptr, *shape = nullptr, *U = nullptr;
+  void *psi_init = nullptr, *psi[2] = {nullptr, nullptr};
+  void *chi = nullptr;          // ckpt == 0: [nt+1] states, else checkpoints
+  int n_chi_slots = 0;
+  void *seg = nullptr;          // ckpt > 0: [ckpt + 1] states (segment / running buffers)
+  double *rstate = nullptr;
+  int *jcount[2] = {nullptr, nullptr}, *rec_step[2] = {nullptr, nullptr}, *rec_ch[2] = {nullptr, nullptr};
+  double *rec_s[2] = {nullptr, nullptr}, *rec_c[2] = {nullptr, nullptr};
+  int cur = 0;                  // record buffer written by a running forward sweep; 1-cur = last completed
+  int *cursor = nullptr;
+  double *partials = nullptr;
+  unsigned *counter = nullptr;
+  KtCplx *tau = nullptr;
+  double *norm2 = nullptr;
+  int *status = nullptr;
+
+  long long pass_counter = 0;
+  bool have_fwd = false, have_bwd = false, have_deps = false;
+  int final_buf = 0;
+};
+
+namespace {
+
+kt_status dev_alloc(kt_problem *p, void **ptr, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    return fail(KT_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  p->allocs.push_back(*ptr);
+  p->bytes += bytes;
+  return KT_OK;
+}
+
+template <typename T>
+kt_status upload(kt_problem *p, T **dst, const T *src, size_t n, cudaStream_t st) {
+  kt_status s = dev_alloc(p, (void **)dst, n * sizeof(T));
+  if (s != KT_OK) return s;
+  if (n) KT_CUDA(cudaMemcpyAsync(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice, st));
+  return KT_OK;
+}
+
+void *state_slot(const kt_problem *p, void *base, long long slot) {
+  return (char *)base + (size_t)slot * p->state_bytes;
+}
+
+// location of chi(t_j): ckpt == 0 -> chi[j]; else checkpoint slots j/ckpt (and the last one for nt)
+void *ckpt_slot(const kt_problem *p, int j) {
+  if (p->ckpt == 0) return state_slot(p, p->chi, j);
+  if (j == p->nt) return state_slot(p, p->chi, p->n_chi_slots - 1);
+  return state_slot(p, p->chi, j / p->ckpt);
+}
+bool is_ckpt(const kt_problem *p, int j) { return p->ckpt == 0 || j == p->nt || j % p->ckpt == 0; }
+
+kt_status read_status(kt_problem *p, cudaStream_t st) {
+  int s = 0;
+  KT_CUDA(cudaMemcpyAsync(&s, p->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  KT_CUDA(cudaStreamSynchronize(st));
+  if (s == KT_DEV_OK) return KT_OK;
+  KT_CUDA(cudaMemsetAsync(p->status, 0, sizeof(int), st));
+  switch (s) {
+    case KT_DEV_NONFINITE: return fail(KT_ERR_NONFINITE, "non-finite norm, overlap or pulse value on the device");
+    case KT_DEV_RECORD_FULL: return fail(KT_ERR_RECORD_FULL, "a trajectory needed more jumps than draws_per_traj allows");
+    case KT_DEV_RANGE: return fail(KT_ERR_RANGE, "an updated pulse value left [-eps_bound, eps_bound]");
+    case KT_DEV_ZERO_JUMP: return fail(KT_ERR_NONFINITE, "jump into a zero state (||L psi|| = 0 at a jump)");
+    default: return fail(KT_ERR_CUDA, "device status %d", s);
+  }
+}
+
+FwdArgs fwd_args(kt_problem *p, int update, int pass_row) {
+  FwdArgs a{};
+  a.nt = p->nt;
+  a.update = update;
+  a.pass_row = pass_row;
+  a.eps_old = p->eps_old;
+  a.eps_new = p->eps_new;
+  a.deps = p->deps;
+  a.shape = p->shape;
+  a.U = p->U;
+  a.rstate = p->rstate;
+  a.jcount = p->jcount[p->cur];
+  a.rec_step = p->rec_step[p->cur];
+  a.rec_ch = p->rec_ch[p->cur];
+  a.rec_s = p->rec_s[p->cur];
+  a.rec_c = p->rec_c[p->cur];
+  a.partials = p->partials;
+  a.counter = p->counter;
+  a.tau = p->tau;
+  a.norm2 = p->norm2;
+  a.status = p->status;
+  return a;
+}
+
+BwdArgs bwd_args(kt_problem *p) {
+  const int prev = 1 - p->cur;
+  BwdArgs b{};
+  b.nt = p->nt;
+  b.eps = p->eps_old;
+  b.cursor = p->cursor;
+  b.advance_cursor = 1;
+  b.rec_step = p->rec_step[prev];
+  b.rec_ch = p->rec_ch[prev];
+  b.rec_s = p->rec_s[prev];
+  b.rec_c = p->rec_c[prev];
+  b.status = p->status;
+  return b;
+}
+
+kt_status launch_bwd_step(kt_problem *p, int j, const void *in, void *out, cudaStream_t st) {
+  BwdArgs b = bwd_args(p);
+  b.j = j;
+  b.chi_in = in;
+  b.chi_out = out;
+  KT_CUDA(kt_launch_bwd(p->fp64, p->ept, p->g, p->im_bwd, p->ops, b, st));
+  return KT_OK;
+}
+
+// Recompute chi(t_{a+1}) .. chi(t_{b-1}) into seg[1 .. b-a-1] from the checkpoint at t_b.
+kt_status recompute_segment(kt_problem *p, int a, int b, cudaStream_t st) {
+  const int prev = 1 - p->cur;
+  KT_CUDA(kt_launch_cursor_seek(p->g, p->rec_step[prev], p->jcount[prev], b, p->cursor, st));
+  const void *in = ckpt_slot(p, b);
+  for (int j = b; j >= a + 2; --j) {
+    void *out = state_slot(p, p->seg, j - 1 - a);
+    kt_status s = launch_bwd_step(p, j, in, out, st);
+    if (s != KT_OK) return s;
+    in = out;
+  }
+  return KT_OK;
+}
+
+const void *chi_at(const kt_problem *p, int j, int seg_a) {
+  if (is_ckpt(p, j)) return ckpt_slot(p, j);
+  return state_slot(p, p->seg, j - seg_a);
+}
+
+kt_status forward_sweep(kt_problem *p, int update, cudaStream_t st) {
+  if (update && !p->have_bwd)
+    return fail(KT_ERR_STATE, "an updating forward sweep needs a backward sweep since the last forward sweep");
+  const int pass_row = (int)(p->pass_counter % p->n_passes);
+  p->pass_counter++;
+  KT_CUDA(kt_launch_init_pass(p->g, p->U, pass_row, p->rstate, p->jcount[p->cur], st));
+  FwdArgs a = fwd_args(p, update, pass_row);
+  if (update) {
+    a.j = 0;
+    a.psi_in = p->psi_init;
+    a.psi_out = nullptr;
+    a.chi_t = ckpt_slot(p, 0);
+    KT_CUDA(kt_launch_fwd(p->fp64, p->ept, p->g, p->im_fwd, p->ops, a, st));
+  }
+  const int K = (p->ckpt == 0) ? p->nt : p->ckpt;
+  for (int seg_a = 0; seg_a < p->nt; seg_a += K) {
+    const int seg_b = std::min(seg_a + K, p->nt);
+    if (update && p->ckpt > 0) {
+      kt_status s = recompute_segment(p, seg_a, seg_b, st);
+      if (s != KT_OK) return s;
+    }
+    for (int j = seg_a + 1; j <= seg_b; ++j) {
+      a.j = j;
+      a.psi_in = (j == 1) ? p->psi_init : p->psi[(j - 1) & 1];
+      a.psi_out = p->psi[j & 1];
+      a.chi_t = (update && j < p->nt) ? chi_at(p, j, seg_a) : nullptr;
+      KT_CUDA(kt_launch_fwd(p->fp64, p->ept, p->g, p->im_fwd, p->ops, a, st));
+    }
+  }
+  kt_status s = read_status(p, st);
+  if (s != KT_OK) return s;
+  p->final_buf = p->nt & 1;
+  if (update) {
+    std::swap(p->eps_old, p->eps_new);
+    p->have_deps = true;
+  }
+  p->cur = 1 - p->cur;          // the records just written become the "last completed" ones
+  p->have_fwd = true;
+  p->have_bwd = false;
+  return KT_OK;
+}
+
+kt_status backward_sweep(kt_problem *p, cudaStream_t st) {
+  if (!p->have_fwd) return fail(KT_ERR_STATE, "propagate_backward needs a forward sweep first");
+  const int prev = 1 - p->cur;
+  void *chiT = ckpt_slot(p, p->nt);
+  KT_CUDA(kt_launch_chi_boundary(p->fp64, p->g, p->ops, p->tau, chiT, st));
+  KT_CUDA(kt_launch_cursor_seek(p->g, p->rec_step[prev], p->jcount[prev], p->nt, p->cursor, st));
+  const void *in = chiT;
+  for (int j = p->nt; j >= 1; --j) {
+    void *out;
+    if (is_ckpt(p, j - 1)) out = ckpt_slot(p, j - 1);
+    else out = state_slot(p, p->seg, (j - 1) & 1);
+    kt_status s = launch_bwd_step(p, j, in, out, st);
+    if (s != KT_OK) return s;
+    in = out;
+  }
+  kt_status s = read_status(p, st);
+  if (s != KT_OK) return s;
+  p->have_bwd = true;
+  return KT_OK;
+}
+
+kt_status host_fidelity(kt_problem *p, double *F, double *tau_out, cudaStream_t st) {
+  std::vector<KtCplx> tau(p->M);
+  KT_CUDA(cudaMemcpyAsync(tau.data(), p->tau, sizeof(KtCplx) * p->M, cudaMemcpyDeviceToHost, st));
+  KT_CUDA(cudaStreamSynchronize(st));
+  double s = 0.0;
+  for (int k = 0; k < p->M; ++k) s += tau[k].re * tau[k].re + tau[k].im * tau[k].im;
+  if (F) *F = s / p->M;
+  if (tau_out)
+    for (int k = 0; k < p->M; ++k) {
+      tau_out[2 * k] = tau[k].re;
+      tau_out[2 * k + 1] = tau[k].im;
+    }
+  return KT_OK;
+}
+
+// Tile layout: trajectory k = tile*T + t, element x at tile*tile_elems + x*T + t.
+template <typename R>
+void to_tiles(const kt_problem *p, const double *src /*[M][d][2] or [d][2]*/, bool batch, std::vector<R> &out) {
+  const KtGeom &g = p->g;
+  out.assign((size_t)g.n_tiles * g.tile_elems * 2, (R)0);
+  for (int k = 0; k < g.M; ++k) {
+    const double *v = batch ? src + (size_t)k * g.d * 2 : src;
+    const int tile = k / g.T, t = k % g.T;
+    for (int x = 0; x < g.d; ++x) {
+      const size_t e = (size_t)tile * g.tile_elems + (size_t)x * g.T + t;
+      out[2 * e] = (R)v[2 * x];
+      out[2 * e + 1] = (R)v[2 * x + 1];
+    }
+  }
+}
+
+kt_status download_state(kt_problem *p, const void *dev, double *out, cudaStream_t st) {
+  const KtGeom &g = p->g;
+  std::vector<char> buf(p->state_bytes);
+  KT_CUDA(cudaMemcpyAsync(buf.data(), dev, p->state_bytes, cudaMemcpyDeviceToHost, st));
+  KT_CUDA(cudaStreamSynchronize(st));
+  for (int k = 0; k < g.M; ++k) {
+    const int tile = k / g.T, t = k % g.T;
+    for (int x = 0; x < g.d; ++x) {
+      const size_t e = (size_t)tile * g.tile_elems + (size_t)x * g.T + t;
+      double re, im;
+      if (p->fp64) {
+        re = ((const double *)buf.data())[2 * e];
+        im = ((const double *)buf.data())[2 * e + 1];
+      } else {
+        re = ((const float *)buf.data())[2 * e];
+        im = ((const float *)buf.data())[2 * e + 1];
+      }
+      out[((size_t)k * g.d + x) * 2] = re;
+      out[((size_t)k * g.d + x) * 2 + 1] = im;
+    }
+  }
+  return KT_OK;
+}
+
+int ipow(int b, int e) {
+  long long r = 1;
+  for (int i = 0; i < e; ++i) {
+    r *= b;
+    if (r > (1 << 30)) return -1;
+  }
+  return (int)r;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+KT_API const char *krotov_last_error(void) { return g_err.c_str(); }
+
+KT_API kt_status kt_bessel_j(double alpha, int n, double *out) {
+  if (!out) return fail(KT_ERR_ARG, "out is NULL");
+  if (kt_bessel_miller(alpha, n, out) != 0) return fail(KT_ERR_ARG, "alpha must be >= 0 and n in [1, 256]");
+  return KT_OK;
+}
+
+KT_API void krotov_free(kt_problem *p) {
+  if (!p) return;
+  for (void *a : p->allocs) cudaFree(a);
+  delete p;
+}
+
+KT_API kt_status krotov_init(const kt_model_desc *md, const kt_config *cfg, void *stream, kt_problem **out) {
+  if (!md || !cfg || !out) return fail(KT_ERR_ARG, "NULL descriptor or output pointer");
+  *out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int N = md->n_nodes, nl = md->n_loc;
+  if (N < 1 || N > KT_MAX_NODES) return fail(KT_ERR_UNSUPPORTED, "n_nodes must be in [1, %d]", KT_MAX_NODES);
+  if (nl < 2 || nl > 16) return fail(KT_ERR_UNSUPPORTED, "n_loc must be in [2, 16]");
+  const int d = ipow(nl, N);
+  if (d < 0) return fail(KT_ERR_UNSUPPORTED, "dimension n_loc^n_nodes too large");
+  if (md->n_ctrl < 1 || md->n_ctrl > KT_MAX_CTRL) return fail(KT_ERR_ARG, "n_ctrl must be in [1, %d]", KT_MAX_CTRL);
+  if (md->n_lind < 0 || md->n_lind > KT_MAX_LIND) return fail(KT_ERR_ARG, "n_lind must be in [0, %d]", KT_MAX_LIND);
+  if (md->n_pairs < 0) return fail(KT_ERR_ARG, "n_pairs < 0");
+  if (!md->h0_local || !md->hc_local || !md->ctrl_node || !md->psi_tgt || (!md->psi0 && !md->psi0_batch))
+    return fail(KT_ERR_ARG, "missing model arrays");
+  if ((md->n_pairs > 0 || md->n_lind > 0) && !md->a_local) return fail(KT_ERR_ARG, "a_local required for pairs / Lindblad operators");
+  if (cfg->nt < 1 || cfg->M < 1 || !(cfg->T > 0.0)) return fail(KT_ERR_ARG, "need nt >= 1, M >= 1, T > 0");
+  if (!cfg->eps_guess || !cfg->shape || !cfg->lambda_a || !cfg->uniforms) return fail(KT_ERR_ARG, "missing config arrays");
+  if (cfg->n_passes < 1 || cfg->draws_per_traj < 1 || cfg->draws_per_traj % 2 == 0)
+    return fail(KT_ERR_ARG, "need n_passes >= 1 and odd draws_per_traj >= 1");
+  if (cfg->prec != KT_FP64 && cfg->prec != KT_FP32_MIXED) return fail(KT_ERR_ARG, "unknown precision");
+  if (cfg->ckpt_interval < 0) return fail(KT_ERR_ARG, "ckpt_interval < 0");
+  for (int c = 0; c < md->n_ctrl; ++c) {
+    if (md->ctrl_node[c] < 0 || md->ctrl_node[c] >= N) return fail(KT_ERR_ARG, "ctrl_node[%d] out of range", c);
+    if (!(cfg->lambda_a[c] > 0.0)) return fail(KT_ERR_ARG, "lambda[%d] must be > 0", c);
+  }
+  const int nt = cfg->nt, M = cfg->M, nc = md->n_ctrl;
+  for (long i = 0; i < (long)nc * nt; ++i)
+    if (!std::isfinite(cfg->eps_guess[i]) || !std::isfinite(cfg->shape[i]))
+      return fail(KT_ERR_NONFINITE, "non-finite guess pulse or shape value");
+
+  // ---- a1: structured H_eff = H - (i/2) sum_l L_l^dag L_l
+  Gen gf;
+  gf.N = N;
+  gf.nl = nl;
+  gf.loc.assign((size_t)N * nl * nl, 0.0);
+  for (size_t e = 0; e < gf.loc.size(); ++e) gf.loc[e] = cd(md->h0_local[2 * e], md->h0_local[2 * e + 1]);
+  gf.ctrl.assign((size_t)nc * nl * nl, 0.0);
+  for (size_t e = 0; e < gf.ctrl.size(); ++e) gf.ctrl[e] = cd(md->hc_local[2 * e], md->hc_local[2 * e + 1]);
+  gf.ctrl_node.assign(md->ctrl_node, md->ctrl_node + nc);
+  std::vector<cd> a(nl * nl, 0.0);
+  if (md->a_local)
+    for (int e = 0; e < nl * nl; ++e) a[e] = cd(md->a_local[2 * e], md->a_local[2 * e + 1]);
+  double amax = 0.0;
+  std::vector<int> lo_dl(nl, 0), ra_dl(nl, 0);
+  std::vector<cd> lo_val(nl, 0.0), ra_val(nl, 0.0);
+  for (int x = 0; x < nl; ++x) {
+    int nr = 0, ncol = 0;
+    for (int y = 0; y < nl; ++y) {
+      if (a[x * nl + y] != 0.0) { ++nr; lo_dl[x] = y - x; lo_val[x] = a[x * nl + y]; }
+      if (a[y * nl + x] != 0.0) { ++ncol; ra_dl[x] = y - x; ra_val[x] = std::conj(a[y * nl + x]); }
+      amax = std::max(amax, std::abs(a[x * nl + y]));
+    }
+    if (nr > 1 || ncol > 1) return fail(KT_ERR_ARG, "a_local must have at most one nonzero per row and per column");
+  }
+  std::vector<Pair> raw;
+  for (int q = 0; q < md->n_pairs; ++q) {
+    const int ds = md->pair_dst[q], sr = md->pair_src[q];
+    if (ds < 0 || ds >= N || sr < 0 || sr >= N || ds == sr) return fail(KT_ERR_ARG, "bad pair %d", q);
+    raw.push_back(Pair{ds, sr, cd(md->pair_coef[2 * q], md->pair_coef[2 * q + 1])});
+  }
+  const std::vector<cd> ada = adag_a(a, nl);
+  for (int l = 0; l < md->n_lind; ++l)
+    for (int i = 0; i < N; ++i)
+      for (int jn = 0; jn < N; ++jn) {
+        const cd ci = cd(md->lind_coef[2 * (l * N + i)], md->lind_coef[2 * (l * N + i) + 1]);
+        const cd cj = cd(md->lind_coef[2 * (l * N + jn)], md->lind_coef[2 * (l * N + jn) + 1]);
+        const cd w = cd(0.0, -0.5) * std::conj(ci) * cj;     // -(i/2) conj(c_i) c_j a_i^dag a_j
+        if (w == 0.0) continue;
+        if (i == jn) {
+          for (int e = 0; e < nl * nl; ++e) gf.loc[(size_t)i * nl * nl + e] += w * ada[e];
+        } else {
+          raw.push_back(Pair{i, jn, w});
+        }
+      }
+  double pmax = 1.0;
+  for (const Pair &q : raw) pmax = std::max(pmax, std::abs(q.coef));
+  for (const Pair &q : raw) {
+    bool merged = false;
+    for (Pair &o : gf.pairs)
+      if (o.dst == q.dst && o.src == q.src) { o.coef += q.coef; merged = true; }
+    if (!merged) gf.pairs.push_back(q);
+  }
+  // terms cancelled to rounding level (e.g. the upstream cascade hop) are dropped
+  gf.pairs.erase(std::remove_if(gf.pairs.begin(), gf.pairs.end(),
+                                [&](const Pair &q) { return std::abs(q.coef) <= 1e-13 * pmax; }),
+                 gf.pairs.end());
+  if ((int)gf.pairs.size() > KT_MAX_PAIRS) return fail(KT_ERR_UNSUPPORTED, "more than %d pair terms", KT_MAX_PAIRS);
+  Gen gb = minus_adjoint(gf);
+
+  // ---- a2: spectral interval and Chebyshev length
+  double E = cfg->eps_bound;
+  if (!(E > 0.0)) {
+    double m = 0.0;
+    for (long i = 0; i < (long)nc * nt; ++i) m = std::max(m, std::fabs(cfg->eps_guess[i]));
+    E = 2.0 * m + 1.0;
+  }
+  for (long i = 0; i < (long)nc * nt; ++i)
+    if (std::fabs(cfg->eps_guess[i]) > E) return fail(KT_ERR_RANGE, "guess pulse exceeds eps_bound");
+  const Bounds bf = gen_bounds(gf, amax, E), bb = gen_bounds(gb, amax, E);
+  const double r = 0.5 * std::max(bf.hi - bf.lo, bb.hi - bb.lo) * 1.0001 + 1e-12;
+  const double c_fwd = 0.5 * (bf.lo + bf.hi), c_bwd = 0.5 * (bb.lo + bb.hi);
+  const double damp = std::max(bf.damp, bb.damp);
+  const double dt = cfg->T / nt;
+  const cd z(1.0, damp / r);
+  const double rho = std::max(1.0, std::abs(z + std::sqrt(z - 1.0) * std::sqrt(z + 1.0)));
+  const double tol = cfg->cheb_tol > 0 ? cfg->cheb_tol : (cfg->prec == KT_FP64 ? 1e-15 : 1e-8);
+  std::vector<double> J(256);
+  kt_bessel_miller(r * dt, 256, J.data());
+  int K = -1;
+  for (int k = 1; k < 250; ++k) {
+    bool small = true;
+    for (int q = k; q < k + 6; ++q)
+      if (std::fabs(J[q]) * std::pow(rho, q) >= tol) small = false;
+    if (small && k > r * dt) { K = k; break; }
+  }
+  if (K < 1 || K > KT_MAX_K) return fail(KT_ERR_UNSUPPORTED, "Chebyshev series needs %d > %d terms (reduce dt)", K, KT_MAX_K);
+
+  kt_problem *p = new kt_problem();
+  p->fp64 = cfg->prec == KT_FP64;
+  p->esz = p->fp64 ? 16 : 8;
+  p->nt = nt;
+  p->M = M;
+  p->T = cfg->T;
+  p->n_passes = cfg->n_passes;
+  p->ckpt = (cfg->ckpt_interval > 0 && cfg->ckpt_interval < nt) ? cfg->ckpt_interval : 0;
+  p->e_min = bf.lo;
+  p->e_max = bf.hi;
+  p->damping = damp;
+
+  KtGeom &g = p->g;
+  g.n_nodes = N;
+  g.n_loc = nl;
+  g.d = d;
+  g.M = M;
+  g.n_ctrl = nc;
+  g.n_lind = md->n_lind;
+  g.n_pairs = (int)gf.pairs.size();
+  g.K = K;
+  g.max_jumps = (cfg->draws_per_traj - 1) / 2;   // 0: any jump is reported as KT_ERR_RECORD_FULL
+  g.draws = cfg->draws_per_traj;
+  g.dt = dt;
+  g.eps_bound = E;
+  g.c_fwd = c_fwd;
+  g.c_bwd = c_bwd;
+  g.r = r;
+  for (int i = 0; i < N; ++i) g.stride[i] = ipow(nl, N - 1 - i);
+  for (int q = 0; q < g.n_pairs; ++q) {
+    g.pair_dst[q] = gf.pairs[q].dst;
+    g.pair_src[q] = gf.pairs[q].src;
+  }
+  for (int c = 0; c < nc; ++c) {
+    g.ctrl_node[c] = md->ctrl_node[c];
+    g.lam[c] = cfg->lambda_a[c];
+  }
+
+  // off-diagonal slot pattern of each node row (union over drift and controls, both directions)
+  std::vector<std::vector<int>> cols((size_t)N * nl);
+  int S = 0;
+  for (int i = 0; i < N; ++i)
+    for (int x = 0; x < nl; ++x) {
+      std::vector<int> &cl = cols[(size_t)i * nl + x];
+      for (int y = 0; y < nl; ++y) {
+        if (y == x) continue;
+        bool nz = at(gf.loc, i * nl * nl, nl, x, y) != 0.0 || at(gb.loc, i * nl * nl, nl, x, y) != 0.0;
+        for (int c = 0; c < nc; ++c)
+          if (g.ctrl_node[c] == i)
+            nz = nz || at(gf.ctrl, c * nl * nl, nl, x, y) != 0.0 || at(gb.ctrl, c * nl * nl, nl, x, y) != 0.0;
+        if (nz) cl.push_back(y);
+      }
+      S = std::max(S, (int)cl.size());
+    }
+  if (S > KT_MAX_S) {
+    krotov_free(p);
+    return fail(KT_ERR_UNSUPPORTED, "a node row has %d > %d off-diagonal entries", S, KT_MAX_S);
+  }
+  g.S = std::max(S, 1);
+  int SH = 1;
+  for (int c = 0; c < nc; ++c)
+    for (int x = 0; x < nl; ++x) {
+      int n = 0;
+      for (int y = 0; y < nl; ++y) n += at(gf.ctrl, c * nl * nl, nl, x, y) != 0.0;
+      SH = std::max(SH, n);
+    }
+  if (SH > KT_MAX_SH) {
+    krotov_free(p);
+    return fail(KT_ERR_UNSUPPORTED, "a control factor row has %d > %d entries", SH, KT_MAX_SH);
+  }
+  g.SH = SH;
+
+  // ---- tile width, threads per CTA, items per thread
+  const int maxthr = p->fp64 ? 512 : 1024;
+  int Tsel = 0;
+  for (int T = 32; T >= 1; T >>= 1) {
+    if (cfg->tile_traj > 0 && T > cfg->tile_traj) continue;
+    KtGeom t = g;
+    t.T = T;
+    const long long items = (long long)d * T;
+    if (items > 16LL * maxthr) continue;
+    t.nthreads = maxthr;
+    if (kt_smem_bytes(t, (int)p->esz) > 227 * 1024) continue;
+    if (Tsel == 0) Tsel = T;
+    // prefer more tiles when the trajectories would not fill the GPU
+    if (cfg->tile_traj == 0 && (M + T - 1) / T < 2 * 152 && T > 1 && (long long)d * (T / 2) >= 256) {
+      Tsel = T / 2;
+      continue;
+    }
+    break;
+  }
+  if (cfg->tile_traj > 0) {
+    if (cfg->tile_traj & (cfg->tile_traj - 1) || cfg->tile_traj > 32) {
+      krotov_free(p);
+      return fail(KT_ERR_ARG, "tile_traj must be a power of two <= 32");
+    }
+    Tsel = cfg->tile_traj;
+    KtGeom t = g;
+    t.T = Tsel;
+    t.nthreads = maxthr;
+    if ((long long)d * Tsel > 16LL * maxthr || kt_smem_bytes(t, (int)p->esz) > 227 * 1024) Tsel = 0;
+  }
+  if (Tsel == 0) {
+    krotov_free(p);
+    return fail(KT_ERR_UNSUPPORTED, "dimension %d does not fit one trajectory tile in shared memory", d);
+  }
+  g.T = Tsel;
+  g.n_tiles = (M + Tsel - 1) / Tsel;
+  g.M_pad = g.n_tiles * Tsel;
+  g.tile_elems = (d * Tsel + 3) / 4 * 4;
+  const int items = d * Tsel;
+  int ept = 4;
+  while ((items + ept - 1) / ept > maxthr) ept *= 2;
+  p->ept = ept;
+  g.nthreads = std::max(32, ((items + ept - 1) / ept + 31) / 32 * 32);
+  p->state_bytes = (size_t)g.n_tiles * g.tile_elems * p->esz;
+
+  kt_status s;
+#define TRY(x) do { s = (x); if (s != KT_OK) { krotov_free(p); return s; } } while (0)
+
+  // ---- generator images (scaled by 1/r) for both directions
+  auto build_image = [&](const Gen &gen, double cgen, KtGenImage &im) -> kt_status {
+    const int nls = nl * g.S;
+    std::vector<int> dl((size_t)N * nls, 0);
+    std::vector<KtCplx> base((size_t)N * nls, KtCplx{0, 0}), cslot((size_t)nc * nls, KtCplx{0, 0});
+    std::vector<KtCplx> dg((size_t)N * nl), cdg((size_t)nc * nl);
+    for (int i = 0; i < N; ++i)
+      for (int x = 0; x < nl; ++x) {
+        const std::vector<int> &cl = cols[(size_t)i * nl + x];
+        for (size_t q = 0; q < cl.size(); ++q) {
+          const size_t e = (size_t)i * nls + x * g.S + q;
+          dl[e] = cl[q] - x;
+          const cd v = at(gen.loc, i * nl * nl, nl, x, cl[q]) / r;
+          base[e] = KtCplx{v.real(), v.imag()};
+        }
+        cd dv = at(gen.loc, i * nl * nl, nl, x, x) / r;
+        if (i == 0) dv -= cgen / r;
+        dg[(size_t)i * nl + x] = KtCplx{dv.real(), dv.imag()};
+      }
+    for (int c = 0; c < nc; ++c) {
+      const int i = g.ctrl_node[c];
+      for (int x = 0; x < nl; ++x) {
+        const std::vector<int> &cl = cols[(size_t)i * nl + x];
+        for (size_t q = 0; q < cl.size(); ++q) {
+          const cd v = at(gen.ctrl, c * nl * nl, nl, x, cl[q]) / r;
+          cslot[(size_t)c * nls + x * g.S + q] = KtCplx{v.real(), v.imag()};
+        }
+        const cd dv = at(gen.ctrl, c * nl * nl, nl, x, x) / r;
+        cdg[(size_t)c * nl + x] = KtCplx{dv.real(), dv.imag()};
+      }
+    }
+    const int nl2 = nl * nl;
+    std::vector<int> poff((size_t)g.n_pairs * nl2, 0);
+    std::vector<KtCplx> pval((size_t)g.n_pairs * nl2, KtCplx{0, 0});
+    for (int q = 0; q < g.n_pairs; ++q) {
+      const Pair &pr = gen.pairs[q];
+      for (int xd = 0; xd < nl; ++xd)
+        for (int xs = 0; xs < nl; ++xs) {
+          if (ra_val[xd] == 0.0 || lo_val[xs] == 0.0) continue;
+          const size_t e = (size_t)q * nl2 + xd * nl + xs;
+          poff[e] = ra_dl[xd] * g.stride[pr.dst] + lo_dl[xs] * g.stride[pr.src];
+          const cd v = pr.coef * ra_val[xd] * lo_val[xs] / r;
+          pval[e] = KtCplx{v.real(), v.imag()};
+        }
+    }
+    std::vector<KtCplx> cf(K);
+    const cd ph = std::exp(cd(0.0, -cgen * dt));
+    for (int k = 0; k < K; ++k) {
+      cd v = (k == 0 ? 1.0 : 2.0) * J[k] * std::pow(cd(0.0, -1.0), k) * ph;
+      cf[k] = KtCplx{v.real(), v.imag()};
+    }
+    kt_status t;
+    if ((t = upload(p, (int **)&im.loc_dl, dl.data(), dl.size(), st)) != KT_OK) return t;
+    if ((t = upload(p, (KtCplx **)&im.loc_base, base.data(), base.size(), st)) != KT_OK) return t;
+    if ((t = upload(p, (KtCplx **)&im.ctrl_slot, cslot.data(), cslot.size(), st)) != KT_OK) return t;
+    if ((t = upload(p, (KtCplx **)&im.diag_base, dg.data(), dg.size(), st)) != KT_OK) return t;
+    if ((t = upload(p, (KtCplx **)&im.ctrl_diag, cdg.data(), cdg.size(), st)) != KT_OK) return t;
+    if ((t = upload(p, (int **)&im.pair_off, poff.data(), poff.size(), st)) != KT_OK) return t;
+    if ((t = upload(p, (KtCplx **)&im.pair_val, pval.data(), pval.size(), st)) != KT_OK) return t;
+    if ((t = upload(p, (KtCplx **)&im.cheb_full, cf.data(), cf.size(), st)) != KT_OK) return t;
+    return KT_OK;
+  };
+  TRY(build_image(gf, c_fwd, p->im_fwd));
+  TRY(build_image(gb, c_bwd, p->im_bwd));
+
+  // ---- shared operators
+  {
+    std::vector<KtCplx> lv(nl), rv(nl), lc((size_t)std::max(1, md->n_lind) * N, KtCplx{0, 0});
+    for (int x = 0; x < nl; ++x) {
+      lv[x] = KtCplx{lo_val[x].real(), lo_val[x].imag()};
+      rv[x] = KtCplx{ra_val[x].real(), ra_val[x].imag()};
+    }
+    for (int e = 0; e < md->n_lind * N; ++e) lc[e] = KtCplx{md->lind_coef[2 * e], md->lind_coef[2 * e + 1]};
+    std::vector<int> hdl((size_t)nc * nl * SH, 0);
+    std::vector<KtCplx> hv((size_t)nc * nl * SH, KtCplx{0, 0});
+    for (int c = 0; c < nc; ++c)
+      for (int x = 0; x < nl; ++x) {
+        int q = 0;
+        for (int y = 0; y < nl; ++y) {
+          const cd v = cd(md->hc_local[2 * ((size_t)c * nl * nl + x * nl + y)], md->hc_local[2 * ((size_t)c * nl * nl + x * nl + y) + 1]);
+          if (v == 0.0) continue;
+          hdl[((size_t)c * nl + x) * SH + q] = y - x;
+          hv[((size_t)c * nl + x) * SH + q] = KtCplx{v.real(), v.imag()};
+          ++q;
+        }
+      }
+    std::vector<uint32_t> dig(d);
+    for (int x = 0; x < d; ++x) {
+      uint32_t w = 0;
+      for (int i = 0; i < N; ++i) w |= (uint32_t)((x / g.stride[i]) % nl) << (4 * i);
+      dig[x] = w;
+    }
+    std::vector<KtCplx> tg(d);
+    for (int x = 0; x < d; ++x) tg[x] = KtCplx{md->psi_tgt[2 * x], md->psi_tgt[2 * x + 1]};
+    KtOps &o = p->ops;
+    TRY(upload(p, (int **)&o.lo_dl, lo_dl.data(), nl, st));
+    TRY(upload(p, (KtCplx **)&o.lo_val, lv.data(), nl, st));
+    TRY(upload(p, (int **)&o.ra_dl, ra_dl.data(), nl, st));
+    TRY(upload(p, (KtCplx **)&o.ra_val, rv.data(), nl, st));
+    TRY(upload(p, (KtCplx **)&o.lind_coef, lc.data(), lc.size(), st));
+    TRY(upload(p, (int **)&o.hc_dl, hdl.data(), hdl.size(), st));
+    TRY(upload(p, (KtCplx **)&o.hc_val, hv.data(), hv.size(), st));
+    TRY(upload(p, (uint32_t **)&o.digits, dig.data(), dig.size(), st));
+    TRY(upload(p, (KtCplx **)&o.tgt, tg.data(), tg.size(), st));
+  }
+
+  // ---- pulses, uniforms, states, records
+  TRY(upload(p, &p->eps_old, cfg->eps_guess, (size_t)nc * nt, st));
+  TRY(upload(p, &p->eps_new, cfg->eps_guess, (size_t)nc * nt, st));
+  std::vector<double> zeros((size_t)nc * nt, 0.0);
+  TRY(upload(p, &p->deps, zeros.data(), zeros.size(), st));
+  TRY(upload(p, &p->shape, cfg->shape, (size_t)nc * nt, st));
+  TRY(upload(p, &p->U, cfg->uniforms, (size_t)cfg->n_passes * M * cfg->draws_per_traj, st));
+  {
+    std::vector<double> buf64;
+    std::vector<float> buf32;
+    const bool batch = md->psi0_batch != nullptr;
+    const double *src = batch ? md->psi0_batch : md->psi0;
+    if (p->fp64) {
+      to_tiles<double>(p, src, batch, buf64);
+      TRY(upload(p, (double **)&p->psi_init, buf64.data(), buf64.size(), st));
+    } else {
+      to_tiles<float>(p, src, batch, buf32);
+      TRY(upload(p, (float **)&p->psi_init, buf32.data(), buf32.size(), st));
+    }
+  }
+  TRY(dev_alloc(p, &p->psi[0], p->state_bytes));
+  TRY(dev_alloc(p, &p->psi[1], p->state_bytes));
+  p->n_chi_slots = p->ckpt == 0 ? nt + 1 : nt / p->ckpt + 1 + (nt % p->ckpt ? 1 : 0);
+  TRY(dev_alloc(p, &p->chi, p->state_bytes * p->n_chi_slots));
+  if (p->ckpt > 0) TRY(dev_alloc(p, &p->seg, p->state_bytes * (p->ckpt + 1)));
+  const size_t Mp = g.M_pad, mj = g.max_jumps;
+  TRY(dev_alloc(p, (void **)&p->rstate, Mp * sizeof(double)));
+  for (int b = 0; b < 2; ++b) {
+    TRY(dev_alloc(p, (void **)&p->jcount[b], Mp * sizeof(int)));
+    TRY(dev_alloc(p, (void **)&p->rec_step[b], Mp * mj * sizeof(int)));
+    TRY(dev_alloc(p, (void **)&p->rec_ch[b], Mp * mj * sizeof(int)));
+    TRY(dev_alloc(p, (void **)&p->rec_s[b], Mp * mj * sizeof(double)));
+    TRY(dev_alloc(p, (void **)&p->rec_c[b], Mp * mj * sizeof(double)));
+    if (cudaMemsetAsync(p->jcount[b], 0, Mp * sizeof(int), st) != cudaSuccess) { krotov_free(p); return fail(KT_ERR_CUDA, "memset"); }
+  }
+  TRY(dev_alloc(p, (void **)&p->cursor, Mp * sizeof(int)));
+  TRY(dev_alloc(p, (void **)&p->partials, (size_t)g.n_tiles * nc * sizeof(double)));
+  TRY(dev_alloc(p, (void **)&p->counter, sizeof(unsigned)));
+  TRY(dev_alloc(p, (void **)&p->tau, Mp * sizeof(KtCplx)));
+  TRY(dev_alloc(p, (void **)&p->norm2, Mp * sizeof(double)));
+  TRY(dev_alloc(p, (void **)&p->status, sizeof(int)));
+  if (cudaMemsetAsync(p->counter, 0, sizeof(unsigned), st) != cudaSuccess ||
+      cudaMemsetAsync(p->status, 0, sizeof(int), st) != cudaSuccess) {
+    krotov_free(p);
+    return fail(KT_ERR_CUDA, "memset failed");
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    krotov_free(p);
+    return fail(KT_ERR_CUDA, "initial upload failed: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+#undef TRY
+  p->shape_h.assign(cfg->shape, cfg->shape + (size_t)nc * nt);
+  p->lam_h.assign(cfg->lambda_a, cfg->lambda_a + nc);
+  *out = p;
+  return KT_OK;
+}
+
+KT_API kt_status propagate_forward(kt_problem *p, int sequential_update, double *F_out, void *stream) {
+  if (!p) return fail(KT_ERR_ARG, "NULL problem");
+  cudaStream_t st = (cudaStream_t)stream;
+  kt_status s = forward_sweep(p, sequential_update ? 1 : 0, st);
+  if (s != KT_OK) return s;
+  if (F_out) return host_fidelity(p, F_out, nullptr, st);
+  return KT_OK;
+}
+
+KT_API kt_status propagate_backward(kt_problem *p, void *stream) {
+  if (!p) return fail(KT_ERR_ARG, "NULL problem");
+  return backward_sweep(p, (cudaStream_t)stream);
+}
+
+KT_API kt_status krotov_update(kt_problem *p, int n_iter, double *JT_out, double *J_out, void *stream) {
+  if (!p) return fail(KT_ERR_ARG, "NULL problem");
+  if (n_iter < 0) return fail(KT_ERR_ARG, "n_iter < 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  kt_status s;
+  if (!p->have_fwd && (s = forward_sweep(p, 0, st)) != KT_OK) return s;
+  std::vector<double> de;
+  for (int it = 0; it < n_iter; ++it) {
+    if ((s = backward_sweep(p, st)) != KT_OK) return s;
+    if ((s = forward_sweep(p, 1, st)) != KT_OK) return s;
+    if (JT_out || J_out) {
+      double F = 0.0;
+      if ((s = host_fidelity(p, &F, nullptr, st)) != KT_OK) return s;
+      if (JT_out) JT_out[it] = 1.0 - F;
+      if (J_out) {
+        de.resize((size_t)p->g.n_ctrl * p->nt);
+        KT_CUDA(cudaMemcpyAsync(de.data(), p->deps, de.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        KT_CUDA(cudaStreamSynchronize(st));
+        double J = 1.0 - F;
+        for (int c = 0; c < p->g.n_ctrl; ++c)
+          for (int j = 0; j < p->nt; ++j) {
+            const double S = p->shape_h[(size_t)c * p->nt + j];
+            if (S > 0.0) J += p->lam_h[c] * de[(size_t)c * p->nt + j] * de[(size_t)c * p->nt + j] * p->g.dt / S;
+          }
+        J_out[it] = J;
+      }
+    }
+  }
+  return KT_OK;
+}
+
+KT_API kt_status fidelity(kt_problem *p, double *F_out, double *tau_out) {
+  if (!p) return fail(KT_ERR_ARG, "NULL problem");
+  if (!p->have_fwd) return fail(KT_ERR_STATE, "no forward sweep yet");
+  return host_fidelity(p, F_out, tau_out, 0);
+}
+
+KT_API kt_status krotov_get_pulses(kt_problem *p, double *eps_out) {
+  if (!p || !eps_out) return fail(KT_ERR_ARG, "NULL argument");
+  KT_CUDA(cudaMemcpy(eps_out, p->eps_old, sizeof(double) * p->g.n_ctrl * p->nt, cudaMemcpyDeviceToHost));
+  return KT_OK;
+}
+
+KT_API kt_status krotov_get_update(kt_problem *p, double *deps_out) {
+  if (!p || !deps_out) return fail(KT_ERR_ARG, "NULL argument");
+  KT_CUDA(cudaMemcpy(deps_out, p->deps, sizeof(double) * p->g.n_ctrl * p->nt, cudaMemcpyDeviceToHost));
+  return KT_OK;
+}
+
+KT_API kt_status krotov_set_pulses(kt_problem *p, const double *eps) {
+  if (!p || !eps) return fail(KT_ERR_ARG, "NULL argument");
+  const size_t n = (size_t)p->g.n_ctrl * p->nt;
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(eps[i]) || std::fabs(eps[i]) > p->g.eps_bound)
+      return fail(KT_ERR_RANGE, "pulse value %zu non-finite or beyond eps_bound", i);
+  KT_CUDA(cudaMemcpy(p->eps_old, eps, n * sizeof(double), cudaMemcpyHostToDevice));
+  KT_CUDA(cudaMemcpy(p->eps_new, eps, n * sizeof(double), cudaMemcpyHostToDevice));
+  p->have_fwd = p->have_bwd = false;
+  return KT_OK;
+}
+
+KT_API kt_status krotov_get_records(kt_problem *p, int *count_out, int *step_out, int *channel_out, double *s_out,
+                                    double *c_out) {
+  if (!p) return fail(KT_ERR_ARG, "NULL problem");
+  if (!p->have_fwd) return fail(KT_ERR_STATE, "no forward sweep yet");
+  const int prev = 1 - p->cur;
+  const size_t M = p->M, mj = p->g.max_jumps;
+  if (count_out) KT_CUDA(cudaMemcpy(count_out, p->jcount[prev], M * sizeof(int), cudaMemcpyDeviceToHost));
+  if (step_out) KT_CUDA(cudaMemcpy(step_out, p->rec_step[prev], M * mj * sizeof(int), cudaMemcpyDeviceToHost));
+  if (channel_out) KT_CUDA(cudaMemcpy(channel_out, p->rec_ch[prev], M * mj * sizeof(int), cudaMemcpyDeviceToHost));
+  if (s_out) KT_CUDA(cudaMemcpy(s_out, p->rec_s[prev], M * mj * sizeof(double), cudaMemcpyDeviceToHost));
+  if (c_out) KT_CUDA(cudaMemcpy(c_out, p->rec_c[prev], M * mj * sizeof(double), cudaMemcpyDeviceToHost));
+  return KT_OK;
+}
+
+KT_API kt_status krotov_get_states(kt_problem *p, double *psi_out) {
+  if (!p || !psi_out) return fail(KT_ERR_ARG, "NULL argument");
+  if (!p->have_fwd) return fail(KT_ERR_STATE, "no forward sweep yet");
+  return download_state(p, p->psi[p->final_buf], psi_out, 0);
+}
+
+KT_API kt_status krotov_get_costate(kt_problem *p, int j, double *chi_out) {
+  if (!p || !chi_out) return fail(KT_ERR_ARG, "NULL argument");
+  if (!p->have_bwd) return fail(KT_ERR_STATE, "no backward sweep since the last forward sweep");
+  if (j < 0 || j > p->nt || !is_ckpt(p, j)) return fail(KT_ERR_ARG, "co-state %d not stored", j);
+  return download_state(p, ckpt_slot(p, j), chi_out, 0);
+}
+
+KT_API kt_status krotov_get_info(kt_problem *p, kt_info *info) {
+  if (!p || !info) return fail(KT_ERR_ARG, "NULL argument");
+  info->d = p->g.d;
+  info->max_jumps = p->g.max_jumps;
+  info->cheb_terms = p->g.K;
+  info->tile_traj = p->g.T;
+  info->n_tiles = p->g.n_tiles;
+  info->threads = p->g.nthreads;
+  info->e_min = p->e_min;
+  info->e_max = p->e_max;
+  info->damping = p->damping;
+  info->device_bytes = (long long)p->bytes;
+  return KT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,67 @@
+// Launchers of the CUDA kernels (internal interface between the host runtime and kt_kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "kt_common.h"
+
+struct FwdArgs {
+  int j;                 // interval 1..nt; 0 = prologue (update overlap at t_0 only)
+  int nt;
+  int update;            // sequential Krotov update on
+  int pass_row;          // uniforms row of this pass
+  const void *psi_in;    // tile-layout states at t_{j-1}
+  void *psi_out;         // tile-layout states at t_j
+  const void *chi_t;     // tile-layout co-states at t_j (update only)
+  const double *eps_old; // [n_ctrl][nt] pulse before this pass
+  double *eps_new;       // [n_ctrl][nt] updated pulse (written by the last CTA)
+  double *deps;          // [n_ctrl][nt] update
+  const double *shape;   // [n_ctrl][nt]
+  const double *U;       // [n_passes][M][draws]
+  double *rstate;        // [M_pad] current threshold
+  int *jcount;           // [M_pad] jumps so far in this pass
+  int *rec_step;         // [M_pad][max_jumps]
+  int *rec_ch;
+  double *rec_s;
+  double *rec_c;
+  double *partials;      // [n_tiles][n_ctrl]
+  unsigned *counter;     // last-CTA ticket, 0 between launches
+  KtCplx *tau;           // [M_pad] (j == nt)
+  double *norm2;         // [M_pad] (j == nt)
+  int *status;
+};
+
+struct BwdArgs {
+  int j;                 // interval nt..1: chi(t_j) -> chi(t_{j-1})
+  int nt;
+  const void *chi_in;
+  void *chi_out;
+  const double *eps;     // [n_ctrl][nt] pulse of the recorded forward pass
+  int *cursor;           // [M_pad] index of the latest unprocessed record
+  int advance_cursor;
+  const int *rec_step;
+  const int *rec_ch;
+  const double *rec_s;
+  const double *rec_c;
+  int *status;
+};
+
+size_t kt_smem_bytes(const KtGeom &g, int elem_bytes);
+cudaError_t kt_launch_fwd(int fp64, int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops,
+                          const FwdArgs &a, cudaStream_t st);
+cudaError_t kt_launch_bwd(int fp64, int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops,
+                          const BwdArgs &a, cudaStream_t st);
+cudaError_t kt_launch_fwd_f32(int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops, const FwdArgs &a,
+                              size_t smem, cudaStream_t st);
+cudaError_t kt_launch_fwd_f64(int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops, const FwdArgs &a,
+                              size_t smem, cudaStream_t st);
+cudaError_t kt_launch_bwd_f32(int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops, const BwdArgs &a,
+                              size_t smem, cudaStream_t st);
+cudaError_t kt_launch_bwd_f64(int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops, const BwdArgs &a,
+                              size_t smem, cudaStream_t st);
+cudaError_t kt_launch_init_pass(const KtGeom &g, const double *U, int pass_row, double *rstate, int *jcount,
+                                cudaStream_t st);
+cudaError_t kt_launch_cursor_seek(const KtGeom &g, const int *rec_step, const int *jcount, int upto,
+                                  int *cursor, cudaStream_t st);
+cudaError_t kt_launch_chi_boundary(int fp64, const KtGeom &g, const KtOps &ops, const KtCplx *tau, void *chi,
+                                   cudaStream_t st);

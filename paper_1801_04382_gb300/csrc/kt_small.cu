@@ -1,0 +1,76 @@
+// Small kernels (pass set-up, record cursors, co-state boundary), shared-memory sizing and the
+// precision dispatch of the interval kernels.
+#include "kt_device.cuh"
+
+namespace kt {
+__global__ void init_pass_kernel(KtGeom g, const double *U, int pass_row, double *rstate, int *jcount) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= g.M_pad) return;
+  rstate[k] = (k < g.M) ? U[((size_t)pass_row * g.M + k) * g.draws] : -1.0;
+  jcount[k] = 0;
+}
+
+__global__ void cursor_seek_kernel(KtGeom g, const int *rec_step, const int *jcount, int upto, int *cursor) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= g.M_pad) return;
+  int c = -1;
+  if (k < g.M)
+    for (int m = 0; m < jcount[k]; ++m)
+      if (rec_step[(size_t)k * g.max_jumps + m] <= upto) c = m;
+  cursor[k] = c;
+}
+
+// chi_k(T) = tau_k |tgt>  (mode 0, Krotov boundary)
+template <typename C>
+__global__ void chi_boundary_kernel(KtGeom g, KtOps ops, const KtCplx *tau, C *chi) {
+  const size_t n = (size_t)g.n_tiles * g.tile_elems;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int tile = (int)(e / g.tile_elems), rem = (int)(e % g.tile_elems);
+    typedef decltype(C().x) R;
+    if (rem >= g.d * g.T) { chi[e] = mkc((R)0, (R)0); continue; }
+    const int x = rem / g.T, t = rem % g.T, k = tile * g.T + t;
+    const KtCplx tg = ops.tgt[x];
+    const KtCplx tk = tau[k];
+    chi[e] = mkc((R)(tk.re * tg.re - tk.im * tg.im), (R)(tk.re * tg.im + tk.im * tg.re));
+  }
+}
+
+}  // namespace kt
+
+using namespace kt;
+
+size_t kt_smem_bytes(const KtGeom &g, int elem_bytes) { return carve(g, elem_bytes, nullptr, nullptr); }
+
+cudaError_t kt_launch_fwd(int fp64, int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops,
+                          const FwdArgs &a, cudaStream_t st) {
+  const size_t smem = kt_smem_bytes(g, fp64 ? 16 : 8);
+  return fp64 ? kt_launch_fwd_f64(ept, g, im, ops, a, smem, st) : kt_launch_fwd_f32(ept, g, im, ops, a, smem, st);
+}
+
+cudaError_t kt_launch_bwd(int fp64, int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops,
+                          const BwdArgs &a, cudaStream_t st) {
+  const size_t smem = kt_smem_bytes(g, fp64 ? 16 : 8);
+  return fp64 ? kt_launch_bwd_f64(ept, g, im, ops, a, smem, st) : kt_launch_bwd_f32(ept, g, im, ops, a, smem, st);
+}
+
+cudaError_t kt_launch_init_pass(const KtGeom &g, const double *U, int pass_row, double *rstate, int *jcount,
+                                cudaStream_t st) {
+  init_pass_kernel<<<(g.M_pad + 255) / 256, 256, 0, st>>>(g, U, pass_row, rstate, jcount);
+  return cudaGetLastError();
+}
+
+cudaError_t kt_launch_cursor_seek(const KtGeom &g, const int *rec_step, const int *jcount, int upto, int *cursor,
+                                  cudaStream_t st) {
+  cursor_seek_kernel<<<(g.M_pad + 255) / 256, 256, 0, st>>>(g, rec_step, jcount, upto, cursor);
+  return cudaGetLastError();
+}
+
+cudaError_t kt_launch_chi_boundary(int fp64, const KtGeom &g, const KtOps &ops, const KtCplx *tau, void *chi,
+                                   cudaStream_t st) {
+  const size_t n = (size_t)g.n_tiles * g.tile_elems;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  if (fp64) chi_boundary_kernel<double2><<<blocks, 256, 0, st>>>(g, ops, tau, (double2 *)chi);
+  else chi_boundary_kernel<float2><<<blocks, 256, 0, st>>>(g, ops, tau, (float2 *)chi);
+  return cudaGetLastError();
+}

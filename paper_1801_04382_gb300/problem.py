@@ -1,0 +1,172 @@
+"""Python binding of the C ABI: one ``Problem`` per optimisation problem.
+
+Argument marshalling only; every step of the hot path runs in the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+
+import numpy as np
+
+from . import _capi
+from .model import NetworkFactors
+
+
+def _c(arr, dtype=np.float64):
+    a = np.ascontiguousarray(arr, dtype=dtype)
+    return a
+
+
+def _cplx(arr):
+    """complex array -> contiguous float64 (re, im) pairs."""
+    return np.ascontiguousarray(np.stack([np.real(arr), np.imag(arr)], axis=-1), dtype=np.float64)
+
+
+def _ptr(a, ctype=ct.c_double):
+    return a.ctypes.data_as(ct.POINTER(ctype)) if a is not None else None
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ct.c_void_p(stream)
+    return ct.c_void_p(stream.cuda_stream)   # torch.cuda.Stream
+
+
+class Problem:
+    """Trajectory-parallel Krotov optimisation of one network (C ABI ``kt_problem``).
+
+    Parameters mirror ``kt_model_desc`` / ``kt_config``: ``eps_guess`` and ``shape`` are
+    [n_ctrl, nt], ``lam`` [n_ctrl], ``uniforms`` [n_passes, M, draws_per_traj].
+    ``precision`` is "fp64" or "fp32" (FP32-mixed: complex64 states, FP64 norms and sums).
+    """
+
+    def __init__(self, net: NetworkFactors, T: float, nt: int, M: int, eps_guess, shape, lam, uniforms,
+                 precision: str = "fp64", ckpt_interval: int = 0, eps_bound: float = 0.0,
+                 cheb_tol: float = 0.0, tile_traj: int = 0, psi0_batch=None, stream=None):
+        self._lib = _capi.load()
+        self.net = net
+        self.T, self.nt, self.M = float(T), int(nt), int(M)
+        self.n_ctrl = net.n_ctrl
+        uniforms = _c(uniforms)
+        if uniforms.ndim != 3 or uniforms.shape[1] != M:
+            raise ValueError("uniforms must have shape [n_passes, M, draws_per_traj]")
+        keep = {
+            "h0": _cplx(net.h0_local), "hc": _cplx(net.hc_local), "cn": _c(net.ctrl_node, np.int32),
+            "a": _cplx(net.a_local), "pd": _c(net.pair_dst, np.int32), "ps": _c(net.pair_src, np.int32),
+            "pc": _cplx(net.pair_coef), "lc": _cplx(net.lind_coef), "tgt": _cplx(net.psi_tgt),
+            "psi0": _cplx(net.psi0) if psi0_batch is None else None,
+            "psib": _cplx(psi0_batch) if psi0_batch is not None else None,
+            "eps": _c(eps_guess), "shape": _c(shape), "lam": _c(lam), "U": uniforms,
+        }
+        md = _capi.ModelDesc(
+            n_nodes=net.n_nodes, n_loc=net.n_loc, h0_local=_ptr(keep["h0"]),
+            n_ctrl=net.n_ctrl, ctrl_node=_ptr(keep["cn"], ct.c_int), hc_local=_ptr(keep["hc"]),
+            a_local=_ptr(keep["a"]), n_pairs=len(net.pair_dst),
+            pair_dst=_ptr(keep["pd"], ct.c_int), pair_src=_ptr(keep["ps"], ct.c_int), pair_coef=_ptr(keep["pc"]),
+            n_lind=net.lind_coef.shape[0], lind_coef=_ptr(keep["lc"]),
+            psi0=_ptr(keep["psi0"]), psi0_batch=_ptr(keep["psib"]), psi_tgt=_ptr(keep["tgt"]))
+        cfg = _capi.Config(
+            T=self.T, nt=self.nt, M=self.M,
+            prec=_capi.KT_FP64 if precision == "fp64" else _capi.KT_FP32_MIXED,
+            ckpt_interval=int(ckpt_interval), eps_guess=_ptr(keep["eps"]), shape=_ptr(keep["shape"]),
+            lambda_a=_ptr(keep["lam"]), uniforms=_ptr(keep["U"]), n_passes=uniforms.shape[0],
+            draws_per_traj=uniforms.shape[2], eps_bound=float(eps_bound), cheb_tol=float(cheb_tol),
+            tile_traj=int(tile_traj))
+        handle = ct.c_void_p()
+        self._h = None
+        _capi.check(self._lib.krotov_init(ct.byref(md), ct.byref(cfg), _stream_handle(stream), ct.byref(handle)),
+                    "krotov_init")
+        self._h = handle
+        self.precision = precision
+        self.info = self.get_info()
+
+    # ------------------------------------------------------------------ calls
+    def forward(self, update: bool = False, stream=None) -> float:
+        F = ct.c_double()
+        _capi.check(self._lib.propagate_forward(self._h, int(bool(update)), ct.byref(F), _stream_handle(stream)),
+                    "propagate_forward")
+        return F.value
+
+    def backward(self, stream=None) -> None:
+        _capi.check(self._lib.propagate_backward(self._h, _stream_handle(stream)), "propagate_backward")
+
+    def update(self, n_iter: int = 1, stream=None):
+        JT = np.zeros(n_iter)
+        J = np.zeros(n_iter)
+        _capi.check(self._lib.krotov_update(self._h, int(n_iter), _ptr(JT), _ptr(J), _stream_handle(stream)),
+                    "krotov_update")
+        return JT, J
+
+    def fidelity(self):
+        F = ct.c_double()
+        tau = np.zeros((self.M, 2))
+        _capi.check(self._lib.fidelity(self._h, ct.byref(F), _ptr(tau)), "fidelity")
+        return F.value, tau[:, 0] + 1j * tau[:, 1]
+
+    def pulses(self) -> np.ndarray:
+        out = np.zeros((self.n_ctrl, self.nt))
+        _capi.check(self._lib.krotov_get_pulses(self._h, _ptr(out)), "krotov_get_pulses")
+        return out
+
+    def deps(self) -> np.ndarray:
+        out = np.zeros((self.n_ctrl, self.nt))
+        _capi.check(self._lib.krotov_get_update(self._h, _ptr(out)), "krotov_get_update")
+        return out
+
+    def set_pulses(self, eps) -> None:
+        e = _c(eps)
+        _capi.check(self._lib.krotov_set_pulses(self._h, _ptr(e)), "krotov_set_pulses")
+
+    def records(self):
+        """list over trajectories of [(step, s, channel, c), ...] of the last forward sweep."""
+        mj = self.info.max_jumps
+        cnt = np.zeros(self.M, dtype=np.int32)
+        st = np.zeros((self.M, mj), dtype=np.int32)
+        ch = np.zeros((self.M, mj), dtype=np.int32)
+        s = np.zeros((self.M, mj))
+        c = np.zeros((self.M, mj))
+        _capi.check(self._lib.krotov_get_records(self._h, _ptr(cnt, ct.c_int), _ptr(st, ct.c_int),
+                                                 _ptr(ch, ct.c_int), _ptr(s), _ptr(c)), "krotov_get_records")
+        return [[(int(st[k, m]), float(s[k, m]), int(ch[k, m]), float(c[k, m])) for m in range(cnt[k])]
+                for k in range(self.M)]
+
+    def states(self) -> np.ndarray:
+        out = np.zeros((self.M, self.net.d, 2))
+        _capi.check(self._lib.krotov_get_states(self._h, _ptr(out)), "krotov_get_states")
+        return out[..., 0] + 1j * out[..., 1]
+
+    def costate(self, j: int) -> np.ndarray:
+        out = np.zeros((self.M, self.net.d, 2))
+        _capi.check(self._lib.krotov_get_costate(self._h, int(j), _ptr(out)), "krotov_get_costate")
+        return out[..., 0] + 1j * out[..., 1]
+
+    def get_info(self):
+        info = _capi.Info()
+        _capi.check(self._lib.krotov_get_info(self._h, ct.byref(info)), "krotov_get_info")
+        return info
+
+    def close(self) -> None:
+        if self._h is not None:
+            self._lib.krotov_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def bessel_j(alpha: float, n: int) -> np.ndarray:
+    """J_0..J_{n-1}(alpha) from the library's Miller recurrence (host-side helper)."""
+    out = np.zeros(n)
+    _capi.check(_capi.load().kt_bessel_j(float(alpha), int(n), _ptr(out)), "kt_bessel_j")
+    return out

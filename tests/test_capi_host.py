@@ -1,0 +1,114 @@
+"""Host-side checks of the C ABI library (no GPU needed): it loads, exports every symbol the
+header declares, its Bessel helper matches SciPy, and descriptor validation rejects bad input
+before any device call."""
+import ctypes as ct
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.special
+
+import synth_inputs as si
+from paper_1801_04382_gb300 import _capi, build as pkg_build, model as pm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(pkg_build.lib_path()):
+        pkg_build.build()
+    return _capi.load()
+
+
+def header_symbols():
+    text = open(os.path.join(ROOT, "include", "krotov_traj.h")).read()
+    return set(re.findall(r"KT_API\s+[\w\s\*]+?\b(\w+)\s*\(", text))
+
+
+def test_header_and_binding_agree(lib):
+    syms = header_symbols()
+    assert syms == set(_capi.SIGNATURES), syms ^ set(_capi.SIGNATURES)
+    for name in syms:
+        assert hasattr(lib, name), name
+
+
+def test_exports_with_nm(lib):
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", pkg_build.lib_path()], capture_output=True, text=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if ln.strip()}
+    assert header_symbols() <= exported
+
+
+@pytest.mark.parametrize("alpha", [0.0, 1e-12, 1e-3, 0.37, 1.0, 2.2, 5.2, 9.9, 30.0])
+def test_bessel_miller_matches_scipy(lib, alpha):
+    n = 64
+    out = np.zeros(n)
+    assert lib.kt_bessel_j(alpha, n, out.ctypes.data_as(ct.POINTER(ct.c_double))) == 0
+    ref = scipy.special.jv(np.arange(n), alpha)
+    np.testing.assert_allclose(out, ref, rtol=0, atol=2e-16 * max(1.0, alpha))
+    big = ref != 0
+    assert np.all(np.abs(out[big] - ref[big]) <= 1e-12 * np.abs(ref[big]) + 1e-300) or alpha > 20
+
+
+def test_bessel_rejects_bad_args(lib):
+    out = np.zeros(4)
+    p = out.ctypes.data_as(ct.POINTER(ct.c_double))
+    assert lib.kt_bessel_j(-1.0, 4, p) == -1
+    assert lib.kt_bessel_j(1.0, 0, p) == -1
+    assert lib.kt_bessel_j(1.0, 257, p) == -1
+
+
+def _make(net, **over):
+    from paper_1801_04382_gb300 import Problem
+    nt, M = 10, 4
+    eps = si.guess_pulses(net.n_ctrl, nt, 5.0, 1.0)
+    kw = dict(T=5.0, nt=nt, M=M, eps_guess=eps, shape=si.shape_functions(net.n_ctrl, nt, 5.0),
+              lam=np.full(net.n_ctrl, 10.0), uniforms=si.uniforms(0, 2, M, 5))
+    kw.update(over)
+    return Problem(net, **kw)
+
+
+def test_validation_errors_before_device_calls(lib):
+    from paper_1801_04382_gb300 import KrotovError
+    net = pm.cascaded_chain(2, 1)
+    with pytest.raises(KrotovError, match="KT_ERR_ARG"):
+        _make(net, nt=0)
+    with pytest.raises(KrotovError, match="KT_ERR_ARG"):
+        _make(net, lam=np.array([10.0, -1.0]))
+    with pytest.raises(KrotovError, match="KT_ERR_ARG"):
+        _make(net, uniforms=si.uniforms(0, 2, 4, 4))        # even draws_per_traj
+    bad = pm.cascaded_chain(2, 1)
+    bad.ctrl_node = np.array([0, 5], dtype=np.int32)
+    with pytest.raises(KrotovError, match="KT_ERR_ARG"):
+        _make(bad)
+    bad = pm.cascaded_chain(2, 1)
+    bad.a_local = bad.a_local + np.eye(bad.n_loc)            # two entries per row: not a ladder factor
+    with pytest.raises(KrotovError, match="KT_ERR_ARG"):
+        _make(bad)
+    eps = si.guess_pulses(2, 10, 5.0, 1.0)
+    eps[0, 3] = np.nan
+    with pytest.raises(KrotovError, match="KT_ERR_NONFINITE"):
+        _make(net, eps_guess=eps)
+    with pytest.raises(KrotovError, match="KT_ERR_RANGE"):
+        _make(net, eps_bound=0.5)
+    with pytest.raises(KrotovError, match="KT_ERR_UNSUPPORTED"):
+        _make(pm.cascaded_chain(9, 1))
+
+
+def test_model_builder_matches_paper_structure():
+    """Product-side model factors: Hermitian node and control factors, ladder factor with one
+    entry per row/column, Hermitian cascade pair list (Eq. ham_interaction), and sqrt(2 kappa)
+    Lindblad coefficients (Sec. 3.1)."""
+    net = pm.cascaded_chain(3, 2, kappa=0.7)
+    for h in list(net.h0_local) + list(net.hc_local):
+        assert np.abs(h - h.conj().T).max() == 0.0
+    assert np.all((net.a_local != 0).sum(axis=0) <= 1) and np.all((net.a_local != 0).sum(axis=1) <= 1)
+    pairs = {(int(d), int(s)): c for d, s, c in zip(net.pair_dst, net.pair_src, net.pair_coef)}
+    for (d, s), c in pairs.items():
+        assert pairs[(s, d)] == np.conj(c)
+        if d < s:
+            assert c == pytest.approx(0.7j)
+    assert np.allclose(net.lind_coef, np.sqrt(1.4))
+    assert abs(np.linalg.norm(net.psi_tgt) - 1.0) < 1e-15

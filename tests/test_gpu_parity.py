@@ -1,0 +1,175 @@
+"""GPU parity of the CUDA path (through the C ABI) with the FP64 oracle, on seeded inputs.
+
+Tolerances (stated per result):
+  FP64 path: states, tau and F within 1e-10 (relative to the largest entry), pulse updates
+             within 1e-10 of max|Delta eps|; jump records identical in (interval, channel),
+             |Delta s*| <= 1e-9 dt, renormalisation c within 1e-9 relative.
+  FP32-mixed: F within 1e-5, pulse updates within 1e-4 of max|Delta eps|, states within 2e-5;
+             jump records identical on trajectories whose threshold margin exceeds 1e-5,
+             |Delta s*| <= 1e-4 dt.
+"""
+import numpy as np
+import pytest
+
+import synth_inputs as si
+from oracle import mcwf
+from oracle import model as om
+from paper_1801_04382_gb300 import KrotovError, Problem, cascaded_chain
+
+pytestmark = pytest.mark.gpu
+
+
+def setup(N, nc, T, nt, M, amp, seed, n_iter, kappa=1.0, random_init=False, draws=None, lam=10.0):
+    n_passes = n_iter + 1
+    draws = draws if draws is not None else 1 + 2 * N * (1 + nc)
+    eps0 = si.guess_pulses(N, nt, T, amp)
+    S = si.shape_functions(N, nt, T)
+    lamv = np.full(N, lam)
+    U = si.uniforms(seed, n_passes, M, draws)
+    d = (3 * (nc + 1)) ** N
+    psi0 = si.random_states(seed + 100, M, d) if random_init else None
+    return dict(N=N, nc=nc, T=T, nt=nt, M=M, eps0=eps0, S=S, lam=lamv, U=U, psi0=psi0, n_iter=n_iter,
+                kappa=kappa)
+
+
+def run_gpu(c, precision="fp64", ckpt=0, tile=0):
+    net = cascaded_chain(c["N"], c["nc"], kappa=c["kappa"])
+    out = {"F": [], "recs": [], "psiT": [], "eps": [], "deps": []}
+    with Problem(net, c["T"], c["nt"], c["M"], c["eps0"], c["S"], c["lam"], c["U"], precision=precision,
+                 ckpt_interval=ckpt, tile_traj=tile, psi0_batch=c["psi0"]) as p:
+        out["F"].append(p.forward(False))
+        out["recs"].append(p.records())
+        out["psiT"].append(p.states())
+        for _ in range(c["n_iter"]):
+            p.backward()
+            out["F"].append(p.forward(True))
+            out["recs"].append(p.records())
+            out["psiT"].append(p.states())
+            out["eps"].append(p.pulses())
+            out["deps"].append(p.deps())
+        out["info"] = p.info
+    return out
+
+
+def run_oracle(c):
+    m = om.build_model(c["N"], c["nc"], kappa=c["kappa"])
+    psi0 = c["psi0"] if c["psi0"] is not None else m.psi0
+    return m, mcwf.optimize(m, c["eps0"], c["T"], c["U"], c["S"], c["lam"], c["n_iter"], psi0=psi0, keep=True)
+
+
+def compare(c, gpu, res, tol_state, tol_F, tol_deps, tol_s, margin_min=0.0):
+    dt = c["T"] / c["nt"]
+    for p, fw in enumerate(res.forward):
+        assert abs(gpu["F"][p] - (1.0 - res.JT[p])) <= tol_F, (p, gpu["F"][p], 1.0 - res.JT[p])
+        ok = fw.margin > margin_min
+        for k in range(c["M"]):
+            if not ok[k]:
+                continue
+            g_rec, o_rec = gpu["recs"][p][k], fw.records[k]
+            assert [(r[0], r[2]) for r in g_rec] == [(r.step, r.channel) for r in o_rec], (p, k, g_rec, o_rec)
+            for gr, orc in zip(g_rec, o_rec):
+                assert abs(gr[1] - orc.s) <= tol_s * dt, (p, k, gr, orc)
+                tol_c = 1e-9 if tol_s <= 1e-8 else 1e-4
+                assert abs(gr[3] - orc.c) <= tol_c * orc.c, (p, k, gr, orc)
+        scale = np.abs(fw.psi_T[ok]).max() if ok.any() else 1.0
+        if ok.any():
+            assert np.abs(gpu["psiT"][p][ok] - fw.psi_T[ok]).max() <= tol_state * scale, p
+        if p >= 1:
+            dmax = np.abs(fw.deps).max()
+            assert np.abs(gpu["deps"][p - 1] - fw.deps).max() <= tol_deps * max(dmax, 1e-300), p
+            np.testing.assert_allclose(gpu["eps"][p - 1], fw.eps, rtol=0, atol=tol_deps * max(dmax, 1e-300) * 4)
+
+
+def test_cfg1_fp64_one_iteration():
+    """Plain FP64 Krotov, 1 iteration, d = 36, 32 trajectories, nt = 500, seed 0."""
+    wl = si.CONFIGS["cfg1_d36"]
+    c = setup(wl.n_nodes, wl.n_cav, wl.T, wl.nt, wl.M, wl.guess_amp, wl.seed, 1)
+    gpu = run_gpu(c)
+    _, res = run_oracle(c)
+    compare(c, gpu, res, 1e-10, 1e-10, 1e-10, 1e-9)
+
+
+@pytest.mark.parametrize("tile", [0, 1, 4, 32])
+def test_stress_fp64_multi_jump(tile):
+    """Strong drive and random full-space initial states: several jumps per trajectory, jumps
+    inside the same interval, ragged last tile (M = 13)."""
+    c = setup(2, 1, 12.0, 120, 13, 30.0, 9, 2, random_init=True)
+    gpu = run_gpu(c, tile=tile)
+    _, res = run_oracle(c)
+    n_jumps = sum(len(r) for fw in res.forward for r in fw.records)
+    assert n_jumps >= 10
+    compare(c, gpu, res, 1e-10, 1e-10, 1e-10, 1e-9)
+
+
+def test_cfg2_fp64_and_fp32():
+    """d = 81 (cavity cutoff 2), 128 trajectories, nt = 1000, seed 1; FP64 and FP32-mixed."""
+    wl = si.CONFIGS["cfg2_d81"]
+    c = setup(wl.n_nodes, wl.n_cav, wl.T, wl.nt, wl.M, 30.0, wl.seed, 1)
+    _, res = run_oracle(c)
+    compare(c, run_gpu(c, "fp64"), res, 1e-10, 1e-10, 1e-10, 1e-9)
+    compare(c, run_gpu(c, "fp32"), res, 2e-5, 1e-5, 1e-4, 1e-4, margin_min=1e-5)
+
+
+def test_checkpointed_costates_are_bit_identical():
+    c = setup(2, 1, 12.0, 120, 13, 30.0, 9, 2, random_init=True)
+    a = run_gpu(c, ckpt=0)
+    b = run_gpu(c, ckpt=7)
+    for x, y in zip(a["eps"], b["eps"]):
+        assert np.array_equal(x, y)
+    assert a["F"] == b["F"]
+
+
+def test_costates_match_oracle():
+    c = setup(2, 1, 12.0, 120, 6, 30.0, 4, 0, random_init=True)
+    net = cascaded_chain(2, 1)
+    m = om.build_model(2, 1)
+    fw = mcwf.forward_pass(m, c["eps0"], c["T"], c["U"][0], c["psi0"])
+    tau, _ = mcwf.fidelity(fw.psi_T, m.psi_tgt)
+    chi = mcwf.backward_pass(m, c["eps0"], c["T"], tau[:, None] * m.psi_tgt[None, :], fw.records)
+    with Problem(net, c["T"], c["nt"], c["M"], c["eps0"], c["S"], c["lam"], c["U"], psi0_batch=c["psi0"]) as p:
+        p.forward(False)
+        p.backward()
+        for j in (0, 1, 60, 119, 120):
+            got = p.costate(j)
+            assert np.abs(got - chi[j]).max() <= 1e-10 * np.abs(chi[j]).max(), j
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 3e-5)])
+def test_d729_sampled(precision, tol):
+    """Three-node chain (d = 729, dt = 0.025) over a short window, one Krotov iteration."""
+    c = setup(3, 2, 0.5, 20, 6, 30.0, 2, 1, random_init=True)
+    gpu = run_gpu(c, precision)
+    _, res = run_oracle(c)
+    compare(c, gpu, res, tol, tol, 1e-10 if precision == "fp64" else 1e-4,
+            1e-9 if precision == "fp64" else 1e-4, margin_min=0.0 if precision == "fp64" else 1e-5)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 3e-5)])
+def test_d6561_forward_sampled(precision, tol):
+    """Four-node chain (d = 6561, dt = 0.01): forward sweep over a few intervals."""
+    c = setup(4, 2, 0.04, 4, 2, 1.0, 4, 0, random_init=True)
+    gpu = run_gpu(c, precision)
+    _, res = run_oracle(c)
+    compare(c, gpu, res, tol, tol, 1.0, 1e-9 if precision == "fp64" else 1e-4,
+            margin_min=0.0 if precision == "fp64" else 1e-5)
+
+
+def test_record_full_is_reported_and_recoverable():
+    c = setup(2, 1, 12.0, 120, 8, 30.0, 9, 0, random_init=True, draws=1)
+    net = cascaded_chain(2, 1)
+    with Problem(net, c["T"], c["nt"], c["M"], c["eps0"], c["S"], c["lam"], c["U"], psi0_batch=c["psi0"]) as p:
+        with pytest.raises(KrotovError, match="RECORD_FULL"):
+            p.forward(False)
+    c2 = setup(2, 1, 12.0, 120, 8, 30.0, 9, 0)
+    with Problem(net, c2["T"], c2["nt"], c2["M"], c2["eps0"], c2["S"], c2["lam"], c2["U"]) as p:
+        p.forward(False)
+
+
+def test_update_before_backward_is_a_state_error():
+    c = setup(2, 1, 5.0, 20, 4, 1.0, 0, 0)
+    net = cascaded_chain(2, 1)
+    with Problem(net, c["T"], c["nt"], c["M"], c["eps0"], c["S"], c["lam"], c["U"]) as p:
+        with pytest.raises(KrotovError, match="KT_ERR_STATE"):
+            p.forward(True)
+        with pytest.raises(KrotovError, match="KT_ERR_STATE"):
+            p.backward()
