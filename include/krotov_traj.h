@@ -182,6 +182,14 @@ KT_API const char *krotov_last_error(void);
  * alpha < 0 or n outside [1, 256]. */
 KT_API kt_status kt_bessel_j(double alpha, int n, double *out);
 
+/* Host-only check helper: the structured generator tables built by krotov_init for the given
+ * model and configuration, expanded into a dense matrix out [d][d][2] with the same indexing the
+ * kernels use (every neighbour index bounds-checked; KT_ERR_RANGE if one leaves the space).
+ * direction 0: H_eff(eps) = H(eps) - (i/2) sum_l L_l^dag L_l (Sec. 2.1); direction 1: -H_eff(eps)^dag,
+ * the generator of the backward co-state propagation.  eps: [n_ctrl] pulse values.  No device call. */
+KT_API kt_status kt_generator_dense(const kt_model_desc *model, const kt_config *cfg, int direction,
+                                    const double *eps, double *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,6 +66,7 @@ SIGNATURES = {
     "krotov_free": (None, [ct.c_void_p]),
     "krotov_last_error": (ct.c_char_p, []),
     "kt_bessel_j": (ct.c_int, [ct.c_double, ct.c_int, dp]),
+    "kt_generator_dense": (ct.c_int, [ct.POINTER(ModelDesc), ct.POINTER(Config), ct.c_int, dp, dp]),
 }
 
 _LIB = None

@@ -75,7 +75,6 @@ struct KtGeom {
   int K;                             // Chebyshev terms of a full step
   int max_jumps, draws;              // jump cap and uniforms per trajectory and pass
   int stride[KT_MAX_NODES];          // element stride of node i (n_loc^(N-1-i))
-  int pair_dst[KT_MAX_PAIRS], pair_src[KT_MAX_PAIRS];
   int ctrl_node[KT_MAX_CTRL];
   double lam[KT_MAX_CTRL];
   double dt, eps_bound;
@@ -92,6 +91,8 @@ struct KtGenImage {
   const int *pair_off;        // [P][n_loc*n_loc] element offset (in elements, before *T); 0 = none
   const KtCplx *pair_val;     // [P][n_loc*n_loc] scaled
   const KtCplx *cheb_full;    // [K] full-step coefficients, phase exp(-i c dt) folded in
+  int pair_dst[KT_MAX_PAIRS]; // node raised by pair term p of this direction
+  int pair_src[KT_MAX_PAIRS]; // node lowered by pair term p of this direction
 };
 
 // Pulse-independent operators shared by both directions.

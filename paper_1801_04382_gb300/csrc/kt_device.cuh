@@ -181,7 +181,7 @@ __device__ void build_tables(const KtGeom &g, const KtGenImage &im, const KtOps 
 
 // Scaled generator Ghat applied at one item (element x, trajectory tau) of tile vector v.
 template <typename R>
-__device__ __forceinline__ typename C2<R>::T apply_item(const KtGeom &g, const Smem &sm,
+__device__ __forceinline__ typename C2<R>::T apply_item(const KtGeom &g, const KtGenImage &im, const Smem &sm,
                                                         const typename C2<R>::T *__restrict__ v,
                                                         int item, uint32_t dig,
                                                         typename C2<R>::T dval) {
@@ -199,8 +199,8 @@ __device__ __forceinline__ typename C2<R>::T apply_item(const KtGeom &g, const S
   }
   const int nl2 = g.n_loc * g.n_loc;
   for (int p = 0; p < g.n_pairs; ++p) {
-    const int xd = (dig >> (4 * g.pair_dst[p])) & 15;
-    const int xs = (dig >> (4 * g.pair_src[p])) & 15;
+    const int xd = (dig >> (4 * im.pair_dst[p])) & 15;
+    const int xs = (dig >> (4 * im.pair_src[p])) & 15;
     const int idx = p * nl2 + xd * g.n_loc + xs;
     const int off = sm.pair_off[idx];
     if (off) out = cfma(pv[idx], v[item + off], out);
@@ -244,7 +244,7 @@ __device__ __forceinline__ void load_items(const KtGeom &g, const KtOps &ops, It
 // Chebyshev sum: acc = sum_k coef[k][tau] T_k(Ghat) v with v in A on entry (synced).
 // A and B are overwritten.  Ends synchronised.
 template <typename R, int EPT>
-__device__ void cheb_run(const KtGeom &g, const Smem &sm, const Items<EPT> &it, int K,
+__device__ void cheb_run(const KtGeom &g, const KtGenImage &im, const Smem &sm, const Items<EPT> &it, int K,
                          typename C2<R>::T (&acc)[EPT]) {
   typedef typename C2<R>::T C;
   C *A = (C *)sm.bufA;
@@ -261,7 +261,7 @@ __device__ void cheb_run(const KtGeom &g, const Smem &sm, const Items<EPT> &it, 
 #pragma unroll
   for (int q = 0; q < EPT; ++q) {
     if (!it.ok[q]) continue;
-    const C t = apply_item<R>(g, sm, A, it.item[q], it.dig[q], dv[q]);
+    const C t = apply_item<R>(g, im, sm, A, it.item[q], it.dig[q], dv[q]);
     B[it.item[q]] = t;
     acc[q] = cfma(cf[g.T + tau], t, acc[q]);
   }
@@ -273,7 +273,7 @@ __device__ void cheb_run(const KtGeom &g, const Smem &sm, const Items<EPT> &it, 
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
       if (!it.ok[q]) continue;
-      const C t = apply_item<R>(g, sm, Q, it.item[q], it.dig[q], dv[q]);
+      const C t = apply_item<R>(g, im, sm, Q, it.item[q], it.dig[q], dv[q]);
       const C old = P[it.item[q]];
       const C nv = mkc(t.x + t.x - old.x, t.y + t.y - old.y);
       P[it.item[q]] = nv;
@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 512 : 1024) fwd_kernel(KtGeom
     }
     load_tile<R, EPT>(g, it, phase == PH_MAIN ? psi_in : psi_out, A);
     __syncthreads();
-    cheb_run<R, EPT>(g, sm, it, g.K, acc);
+    cheb_run<R, EPT>(g, im, sm, it, g.K, acc);
     norms<R, EPT>(g, sm, it, acc);
 
     // ---- consume the result
@@ -733,7 +733,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 512 : 1024) bwd_kernel(KtGeom
     for (int q = 0; q < EPT; ++q)
       if (it.ok[q]) A[it.item[q]] = B[it.item[q]];
     __syncthreads();
-    cheb_run<R, EPT>(g, sm, it, g.K, acc);
+    cheb_run<R, EPT>(g, im, sm, it, g.K, acc);
     if (rnd == rounds) break;
 #pragma unroll
     for (int q = 0; q < EPT; ++q)

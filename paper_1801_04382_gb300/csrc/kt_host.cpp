@@ -436,10 +436,31 @@ KT_API void krotov_free(kt_problem *p) {
   delete p;
 }
 
-KT_API kt_status krotov_init(const kt_model_desc *md, const kt_config *cfg, void *stream, kt_problem **out) {
-  if (!md || !cfg || !out) return fail(KT_ERR_ARG, "NULL descriptor or output pointer");
-  *out = nullptr;
-  cudaStream_t st = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace {
+
+// Everything krotov_init computes on the host, before any device call.
+struct HostImage {
+  std::vector<int> dl, poff;
+  std::vector<KtCplx> base, cslot, dg, cdg, pval, cf;
+  int pdst[KT_MAX_PAIRS], psrc[KT_MAX_PAIRS];
+};
+
+struct HostPlan {
+  KtGeom g{};
+  int fp64 = 1, ept = 4, ckpt = 0;
+  double e_min = 0, e_max = 0, damping = 0;
+  HostImage fwd, bwd;
+  std::vector<int> lo_dl, ra_dl, hc_dl;
+  std::vector<KtCplx> lo_val, ra_val, lind, hc_val, tgt;
+  std::vector<uint32_t> digits;
+};
+
+// Validation, a1 (structured H_eff = H - (i/2) sum_l L_l^dag L_l), a2 (spectral interval and
+// Chebyshev length), tile geometry and the scaled generator tables of both directions.
+kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
+  if (!md || !cfg) return fail(KT_ERR_ARG, "NULL descriptor");
   const int N = md->n_nodes, nl = md->n_loc;
   if (N < 1 || N > KT_MAX_NODES) return fail(KT_ERR_UNSUPPORTED, "n_nodes must be in [1, %d]", KT_MAX_NODES);
   if (nl < 2 || nl > 16) return fail(KT_ERR_UNSUPPORTED, "n_loc must be in [2, 16]");
@@ -451,6 +472,8 @@ KT_API kt_status krotov_init(const kt_model_desc *md, const kt_config *cfg, void
   if (!md->h0_local || !md->hc_local || !md->ctrl_node || !md->psi_tgt || (!md->psi0 && !md->psi0_batch))
     return fail(KT_ERR_ARG, "missing model arrays");
   if ((md->n_pairs > 0 || md->n_lind > 0) && !md->a_local) return fail(KT_ERR_ARG, "a_local required for pairs / Lindblad operators");
+  if (md->n_pairs > 0 && (!md->pair_dst || !md->pair_src || !md->pair_coef)) return fail(KT_ERR_ARG, "missing pair arrays");
+  if (md->n_lind > 0 && !md->lind_coef) return fail(KT_ERR_ARG, "missing lind_coef");
   if (cfg->nt < 1 || cfg->M < 1 || !(cfg->T > 0.0)) return fail(KT_ERR_ARG, "need nt >= 1, M >= 1, T > 0");
   if (!cfg->eps_guess || !cfg->shape || !cfg->lambda_a || !cfg->uniforms) return fail(KT_ERR_ARG, "missing config arrays");
   if (cfg->n_passes < 1 || cfg->draws_per_traj < 1 || cfg->draws_per_traj % 2 == 0)
@@ -466,7 +489,7 @@ KT_API kt_status krotov_init(const kt_model_desc *md, const kt_config *cfg, void
     if (!std::isfinite(cfg->eps_guess[i]) || !std::isfinite(cfg->shape[i]))
       return fail(KT_ERR_NONFINITE, "non-finite guess pulse or shape value");
 
-  // ---- a1: structured H_eff = H - (i/2) sum_l L_l^dag L_l
+  // ---- a1
   Gen gf;
   gf.N = N;
   gf.nl = nl;
@@ -523,9 +546,9 @@ KT_API kt_status krotov_init(const kt_model_desc *md, const kt_config *cfg, void
                                 [&](const Pair &q) { return std::abs(q.coef) <= 1e-13 * pmax; }),
                  gf.pairs.end());
   if ((int)gf.pairs.size() > KT_MAX_PAIRS) return fail(KT_ERR_UNSUPPORTED, "more than %d pair terms", KT_MAX_PAIRS);
-  Gen gb = minus_adjoint(gf);
+  const Gen gb = minus_adjoint(gf);
 
-  // ---- a2: spectral interval and Chebyshev length
+  // ---- a2
   double E = cfg->eps_bound;
   if (!(E > 0.0)) {
     double m = 0.0;
@@ -553,19 +576,13 @@ KT_API kt_status krotov_init(const kt_model_desc *md, const kt_config *cfg, void
   }
   if (K < 1 || K > KT_MAX_K) return fail(KT_ERR_UNSUPPORTED, "Chebyshev series needs %d > %d terms (reduce dt)", K, KT_MAX_K);
 
-  kt_problem *p = new kt_problem();
-  p->fp64 = cfg->prec == KT_FP64;
-  p->esz = p->fp64 ? 16 : 8;
-  p->nt = nt;
-  p->M = M;
-  p->T = cfg->T;
-  p->n_passes = cfg->n_passes;
-  p->ckpt = (cfg->ckpt_interval > 0 && cfg->ckpt_interval < nt) ? cfg->ckpt_interval : 0;
-  p->e_min = bf.lo;
-  p->e_max = bf.hi;
-  p->damping = damp;
-
-  KtGeom &g = p->g;
+  P.fp64 = cfg->prec == KT_FP64;
+  P.ckpt = (cfg->ckpt_interval > 0 && cfg->ckpt_interval < nt) ? cfg->ckpt_interval : 0;
+  P.e_min = bf.lo;
+  P.e_max = bf.hi;
+  P.damping = damp;
+  KtGeom &g = P.g;
+  g = KtGeom{};
   g.n_nodes = N;
   g.n_loc = nl;
   g.d = d;
@@ -582,10 +599,6 @@ KT_API kt_status krotov_init(const kt_model_desc *md, const kt_config *cfg, void
   g.c_bwd = c_bwd;
   g.r = r;
   for (int i = 0; i < N; ++i) g.stride[i] = ipow(nl, N - 1 - i);
-  for (int q = 0; q < g.n_pairs; ++q) {
-    g.pair_dst[q] = gf.pairs[q].dst;
-    g.pair_src[q] = gf.pairs[q].src;
-  }
   for (int c = 0; c < nc; ++c) {
     g.ctrl_node[c] = md->ctrl_node[c];
     g.lam[c] = cfg->lambda_a[c];
@@ -607,10 +620,7 @@ KT_API kt_status krotov_init(const kt_model_desc *md, const kt_config *cfg, void
       }
       S = std::max(S, (int)cl.size());
     }
-  if (S > KT_MAX_S) {
-    krotov_free(p);
-    return fail(KT_ERR_UNSUPPORTED, "a node row has %d > %d off-diagonal entries", S, KT_MAX_S);
-  }
+  if (S > KT_MAX_S) return fail(KT_ERR_UNSUPPORTED, "a node row has %d > %d off-diagonal entries", S, KT_MAX_S);
   g.S = std::max(S, 1);
   int SH = 1;
   for (int c = 0; c < nc; ++c)
@@ -619,46 +629,28 @@ KT_API kt_status krotov_init(const kt_model_desc *md, const kt_config *cfg, void
       for (int y = 0; y < nl; ++y) n += at(gf.ctrl, c * nl * nl, nl, x, y) != 0.0;
       SH = std::max(SH, n);
     }
-  if (SH > KT_MAX_SH) {
-    krotov_free(p);
-    return fail(KT_ERR_UNSUPPORTED, "a control factor row has %d > %d entries", SH, KT_MAX_SH);
-  }
+  if (SH > KT_MAX_SH) return fail(KT_ERR_UNSUPPORTED, "a control factor row has %d > %d entries", SH, KT_MAX_SH);
   g.SH = SH;
 
   // ---- tile width, threads per CTA, items per thread
-  const int maxthr = p->fp64 ? 512 : 1024;
+  const int esz = P.fp64 ? 16 : 8;
+  const int maxthr = P.fp64 ? 512 : 1024;
+  if (cfg->tile_traj > 0 && ((cfg->tile_traj & (cfg->tile_traj - 1)) || cfg->tile_traj > 32))
+    return fail(KT_ERR_ARG, "tile_traj must be a power of two <= 32");
   int Tsel = 0;
   for (int T = 32; T >= 1; T >>= 1) {
-    if (cfg->tile_traj > 0 && T > cfg->tile_traj) continue;
+    if (cfg->tile_traj > 0 && T != cfg->tile_traj) continue;
     KtGeom t = g;
     t.T = T;
-    const long long items = (long long)d * T;
-    if (items > 16LL * maxthr) continue;
+    if ((long long)d * T > 16LL * maxthr) continue;
     t.nthreads = maxthr;
-    if (kt_smem_bytes(t, (int)p->esz) > 227 * 1024) continue;
-    if (Tsel == 0) Tsel = T;
+    if (kt_smem_bytes(t, esz) > 227 * 1024) continue;
+    Tsel = T;
     // prefer more tiles when the trajectories would not fill the GPU
-    if (cfg->tile_traj == 0 && (M + T - 1) / T < 2 * 152 && T > 1 && (long long)d * (T / 2) >= 256) {
-      Tsel = T / 2;
-      continue;
-    }
+    if (cfg->tile_traj == 0 && (M + T - 1) / T < 2 * 152 && T > 1 && (long long)d * (T / 2) >= 256) continue;
     break;
   }
-  if (cfg->tile_traj > 0) {
-    if (cfg->tile_traj & (cfg->tile_traj - 1) || cfg->tile_traj > 32) {
-      krotov_free(p);
-      return fail(KT_ERR_ARG, "tile_traj must be a power of two <= 32");
-    }
-    Tsel = cfg->tile_traj;
-    KtGeom t = g;
-    t.T = Tsel;
-    t.nthreads = maxthr;
-    if ((long long)d * Tsel > 16LL * maxthr || kt_smem_bytes(t, (int)p->esz) > 227 * 1024) Tsel = 0;
-  }
-  if (Tsel == 0) {
-    krotov_free(p);
-    return fail(KT_ERR_UNSUPPORTED, "dimension %d does not fit one trajectory tile in shared memory", d);
-  }
+  if (Tsel == 0) return fail(KT_ERR_UNSUPPORTED, "dimension %d does not fit one trajectory tile in shared memory", d);
   g.T = Tsel;
   g.n_tiles = (M + Tsel - 1) / Tsel;
   g.M_pad = g.n_tiles * Tsel;
@@ -666,31 +658,29 @@ KT_API kt_status krotov_init(const kt_model_desc *md, const kt_config *cfg, void
   const int items = d * Tsel;
   int ept = 4;
   while ((items + ept - 1) / ept > maxthr) ept *= 2;
-  p->ept = ept;
+  P.ept = ept;
   g.nthreads = std::max(32, ((items + ept - 1) / ept + 31) / 32 * 32);
-  p->state_bytes = (size_t)g.n_tiles * g.tile_elems * p->esz;
 
-  kt_status s;
-#define TRY(x) do { s = (x); if (s != KT_OK) { krotov_free(p); return s; } } while (0)
-
-  // ---- generator images (scaled by 1/r) for both directions
-  auto build_image = [&](const Gen &gen, double cgen, KtGenImage &im) -> kt_status {
+  // ---- generator tables (scaled by 1/r) for both directions
+  auto build_image = [&](const Gen &gen, double cgen, HostImage &im) {
     const int nls = nl * g.S;
-    std::vector<int> dl((size_t)N * nls, 0);
-    std::vector<KtCplx> base((size_t)N * nls, KtCplx{0, 0}), cslot((size_t)nc * nls, KtCplx{0, 0});
-    std::vector<KtCplx> dg((size_t)N * nl), cdg((size_t)nc * nl);
+    im.dl.assign((size_t)N * nls, 0);
+    im.base.assign((size_t)N * nls, KtCplx{0, 0});
+    im.cslot.assign((size_t)nc * nls, KtCplx{0, 0});
+    im.dg.assign((size_t)N * nl, KtCplx{0, 0});
+    im.cdg.assign((size_t)nc * nl, KtCplx{0, 0});
     for (int i = 0; i < N; ++i)
       for (int x = 0; x < nl; ++x) {
         const std::vector<int> &cl = cols[(size_t)i * nl + x];
         for (size_t q = 0; q < cl.size(); ++q) {
           const size_t e = (size_t)i * nls + x * g.S + q;
-          dl[e] = cl[q] - x;
+          im.dl[e] = cl[q] - x;
           const cd v = at(gen.loc, i * nl * nl, nl, x, cl[q]) / r;
-          base[e] = KtCplx{v.real(), v.imag()};
+          im.base[e] = KtCplx{v.real(), v.imag()};
         }
         cd dv = at(gen.loc, i * nl * nl, nl, x, x) / r;
         if (i == 0) dv -= cgen / r;
-        dg[(size_t)i * nl + x] = KtCplx{dv.real(), dv.imag()};
+        im.dg[(size_t)i * nl + x] = KtCplx{dv.real(), dv.imag()};
       }
     for (int c = 0; c < nc; ++c) {
       const int i = g.ctrl_node[c];
@@ -698,86 +688,133 @@ KT_API kt_status krotov_init(const kt_model_desc *md, const kt_config *cfg, void
         const std::vector<int> &cl = cols[(size_t)i * nl + x];
         for (size_t q = 0; q < cl.size(); ++q) {
           const cd v = at(gen.ctrl, c * nl * nl, nl, x, cl[q]) / r;
-          cslot[(size_t)c * nls + x * g.S + q] = KtCplx{v.real(), v.imag()};
+          im.cslot[(size_t)c * nls + x * g.S + q] = KtCplx{v.real(), v.imag()};
         }
         const cd dv = at(gen.ctrl, c * nl * nl, nl, x, x) / r;
-        cdg[(size_t)c * nl + x] = KtCplx{dv.real(), dv.imag()};
+        im.cdg[(size_t)c * nl + x] = KtCplx{dv.real(), dv.imag()};
       }
     }
     const int nl2 = nl * nl;
-    std::vector<int> poff((size_t)g.n_pairs * nl2, 0);
-    std::vector<KtCplx> pval((size_t)g.n_pairs * nl2, KtCplx{0, 0});
+    im.poff.assign((size_t)g.n_pairs * nl2, 0);
+    im.pval.assign((size_t)g.n_pairs * nl2, KtCplx{0, 0});
     for (int q = 0; q < g.n_pairs; ++q) {
       const Pair &pr = gen.pairs[q];
+      im.pdst[q] = pr.dst;
+      im.psrc[q] = pr.src;
       for (int xd = 0; xd < nl; ++xd)
         for (int xs = 0; xs < nl; ++xs) {
           if (ra_val[xd] == 0.0 || lo_val[xs] == 0.0) continue;
           const size_t e = (size_t)q * nl2 + xd * nl + xs;
-          poff[e] = ra_dl[xd] * g.stride[pr.dst] + lo_dl[xs] * g.stride[pr.src];
+          im.poff[e] = ra_dl[xd] * g.stride[pr.dst] + lo_dl[xs] * g.stride[pr.src];
           const cd v = pr.coef * ra_val[xd] * lo_val[xs] / r;
-          pval[e] = KtCplx{v.real(), v.imag()};
+          im.pval[e] = KtCplx{v.real(), v.imag()};
         }
     }
-    std::vector<KtCplx> cf(K);
+    im.cf.resize(K);
     const cd ph = std::exp(cd(0.0, -cgen * dt));
     for (int k = 0; k < K; ++k) {
-      cd v = (k == 0 ? 1.0 : 2.0) * J[k] * std::pow(cd(0.0, -1.0), k) * ph;
-      cf[k] = KtCplx{v.real(), v.imag()};
+      const cd v = (k == 0 ? 1.0 : 2.0) * J[k] * std::pow(cd(0.0, -1.0), k) * ph;
+      im.cf[k] = KtCplx{v.real(), v.imag()};
     }
-    kt_status t;
-    if ((t = upload(p, (int **)&im.loc_dl, dl.data(), dl.size(), st)) != KT_OK) return t;
-    if ((t = upload(p, (KtCplx **)&im.loc_base, base.data(), base.size(), st)) != KT_OK) return t;
-    if ((t = upload(p, (KtCplx **)&im.ctrl_slot, cslot.data(), cslot.size(), st)) != KT_OK) return t;
-    if ((t = upload(p, (KtCplx **)&im.diag_base, dg.data(), dg.size(), st)) != KT_OK) return t;
-    if ((t = upload(p, (KtCplx **)&im.ctrl_diag, cdg.data(), cdg.size(), st)) != KT_OK) return t;
-    if ((t = upload(p, (int **)&im.pair_off, poff.data(), poff.size(), st)) != KT_OK) return t;
-    if ((t = upload(p, (KtCplx **)&im.pair_val, pval.data(), pval.size(), st)) != KT_OK) return t;
-    if ((t = upload(p, (KtCplx **)&im.cheb_full, cf.data(), cf.size(), st)) != KT_OK) return t;
-    return KT_OK;
   };
-  TRY(build_image(gf, c_fwd, p->im_fwd));
-  TRY(build_image(gb, c_bwd, p->im_bwd));
+  build_image(gf, c_fwd, P.fwd);
+  build_image(gb, c_bwd, P.bwd);
 
   // ---- shared operators
-  {
-    std::vector<KtCplx> lv(nl), rv(nl), lc((size_t)std::max(1, md->n_lind) * N, KtCplx{0, 0});
-    for (int x = 0; x < nl; ++x) {
-      lv[x] = KtCplx{lo_val[x].real(), lo_val[x].imag()};
-      rv[x] = KtCplx{ra_val[x].real(), ra_val[x].imag()};
-    }
-    for (int e = 0; e < md->n_lind * N; ++e) lc[e] = KtCplx{md->lind_coef[2 * e], md->lind_coef[2 * e + 1]};
-    std::vector<int> hdl((size_t)nc * nl * SH, 0);
-    std::vector<KtCplx> hv((size_t)nc * nl * SH, KtCplx{0, 0});
-    for (int c = 0; c < nc; ++c)
-      for (int x = 0; x < nl; ++x) {
-        int q = 0;
-        for (int y = 0; y < nl; ++y) {
-          const cd v = cd(md->hc_local[2 * ((size_t)c * nl * nl + x * nl + y)], md->hc_local[2 * ((size_t)c * nl * nl + x * nl + y) + 1]);
-          if (v == 0.0) continue;
-          hdl[((size_t)c * nl + x) * SH + q] = y - x;
-          hv[((size_t)c * nl + x) * SH + q] = KtCplx{v.real(), v.imag()};
-          ++q;
-        }
-      }
-    std::vector<uint32_t> dig(d);
-    for (int x = 0; x < d; ++x) {
-      uint32_t w = 0;
-      for (int i = 0; i < N; ++i) w |= (uint32_t)((x / g.stride[i]) % nl) << (4 * i);
-      dig[x] = w;
-    }
-    std::vector<KtCplx> tg(d);
-    for (int x = 0; x < d; ++x) tg[x] = KtCplx{md->psi_tgt[2 * x], md->psi_tgt[2 * x + 1]};
-    KtOps &o = p->ops;
-    TRY(upload(p, (int **)&o.lo_dl, lo_dl.data(), nl, st));
-    TRY(upload(p, (KtCplx **)&o.lo_val, lv.data(), nl, st));
-    TRY(upload(p, (int **)&o.ra_dl, ra_dl.data(), nl, st));
-    TRY(upload(p, (KtCplx **)&o.ra_val, rv.data(), nl, st));
-    TRY(upload(p, (KtCplx **)&o.lind_coef, lc.data(), lc.size(), st));
-    TRY(upload(p, (int **)&o.hc_dl, hdl.data(), hdl.size(), st));
-    TRY(upload(p, (KtCplx **)&o.hc_val, hv.data(), hv.size(), st));
-    TRY(upload(p, (uint32_t **)&o.digits, dig.data(), dig.size(), st));
-    TRY(upload(p, (KtCplx **)&o.tgt, tg.data(), tg.size(), st));
+  P.lo_dl = lo_dl;
+  P.ra_dl = ra_dl;
+  P.lo_val.resize(nl);
+  P.ra_val.resize(nl);
+  for (int x = 0; x < nl; ++x) {
+    P.lo_val[x] = KtCplx{lo_val[x].real(), lo_val[x].imag()};
+    P.ra_val[x] = KtCplx{ra_val[x].real(), ra_val[x].imag()};
   }
+  P.lind.assign((size_t)std::max(1, md->n_lind) * N, KtCplx{0, 0});
+  for (int e = 0; e < md->n_lind * N; ++e) P.lind[e] = KtCplx{md->lind_coef[2 * e], md->lind_coef[2 * e + 1]};
+  P.hc_dl.assign((size_t)nc * nl * SH, 0);
+  P.hc_val.assign((size_t)nc * nl * SH, KtCplx{0, 0});
+  for (int c = 0; c < nc; ++c)
+    for (int x = 0; x < nl; ++x) {
+      int q = 0;
+      for (int y = 0; y < nl; ++y) {
+        const size_t e = (size_t)c * nl * nl + x * nl + y;
+        const cd v = cd(md->hc_local[2 * e], md->hc_local[2 * e + 1]);
+        if (v == 0.0) continue;
+        P.hc_dl[((size_t)c * nl + x) * SH + q] = y - x;
+        P.hc_val[((size_t)c * nl + x) * SH + q] = KtCplx{v.real(), v.imag()};
+        ++q;
+      }
+    }
+  P.digits.resize(d);
+  for (int x = 0; x < d; ++x) {
+    uint32_t w = 0;
+    for (int i = 0; i < N; ++i) w |= (uint32_t)((x / g.stride[i]) % nl) << (4 * i);
+    P.digits[x] = w;
+  }
+  P.tgt.resize(d);
+  for (int x = 0; x < d; ++x) P.tgt[x] = KtCplx{md->psi_tgt[2 * x], md->psi_tgt[2 * x + 1]};
+  return KT_OK;
+}
+
+kt_status upload_image(kt_problem *p, const HostImage &h, KtGenImage &im, cudaStream_t st) {
+  kt_status t;
+  if ((t = upload(p, (int **)&im.loc_dl, h.dl.data(), h.dl.size(), st)) != KT_OK) return t;
+  if ((t = upload(p, (KtCplx **)&im.loc_base, h.base.data(), h.base.size(), st)) != KT_OK) return t;
+  if ((t = upload(p, (KtCplx **)&im.ctrl_slot, h.cslot.data(), h.cslot.size(), st)) != KT_OK) return t;
+  if ((t = upload(p, (KtCplx **)&im.diag_base, h.dg.data(), h.dg.size(), st)) != KT_OK) return t;
+  if ((t = upload(p, (KtCplx **)&im.ctrl_diag, h.cdg.data(), h.cdg.size(), st)) != KT_OK) return t;
+  if ((t = upload(p, (int **)&im.pair_off, h.poff.data(), h.poff.size(), st)) != KT_OK) return t;
+  if ((t = upload(p, (KtCplx **)&im.pair_val, h.pval.data(), h.pval.size(), st)) != KT_OK) return t;
+  if ((t = upload(p, (KtCplx **)&im.cheb_full, h.cf.data(), h.cf.size(), st)) != KT_OK) return t;
+  for (int q = 0; q < KT_MAX_PAIRS; ++q) {
+    im.pair_dst[q] = h.pdst[q];
+    im.pair_src[q] = h.psrc[q];
+  }
+  return KT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+KT_API kt_status krotov_init(const kt_model_desc *md, const kt_config *cfg, void *stream, kt_problem **out) {
+  if (!md || !cfg || !out) return fail(KT_ERR_ARG, "NULL descriptor or output pointer");
+  *out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  HostPlan P;
+  kt_status s = plan(md, cfg, P);
+  if (s != KT_OK) return s;
+  const int nt = cfg->nt, M = cfg->M, nc = md->n_ctrl;
+
+  kt_problem *p = new kt_problem();
+  p->g = P.g;
+  p->fp64 = P.fp64;
+  p->ept = P.ept;
+  p->esz = P.fp64 ? 16 : 8;
+  p->nt = nt;
+  p->M = M;
+  p->T = cfg->T;
+  p->n_passes = cfg->n_passes;
+  p->ckpt = P.ckpt;
+  p->e_min = P.e_min;
+  p->e_max = P.e_max;
+  p->damping = P.damping;
+  const KtGeom &g = p->g;
+  p->state_bytes = (size_t)g.n_tiles * g.tile_elems * p->esz;
+
+#define TRY(x) do { s = (x); if (s != KT_OK) { krotov_free(p); return s; } } while (0)
+  TRY(upload_image(p, P.fwd, p->im_fwd, st));
+  TRY(upload_image(p, P.bwd, p->im_bwd, st));
+  KtOps &o = p->ops;
+  TRY(upload(p, (int **)&o.lo_dl, P.lo_dl.data(), P.lo_dl.size(), st));
+  TRY(upload(p, (KtCplx **)&o.lo_val, P.lo_val.data(), P.lo_val.size(), st));
+  TRY(upload(p, (int **)&o.ra_dl, P.ra_dl.data(), P.ra_dl.size(), st));
+  TRY(upload(p, (KtCplx **)&o.ra_val, P.ra_val.data(), P.ra_val.size(), st));
+  TRY(upload(p, (KtCplx **)&o.lind_coef, P.lind.data(), P.lind.size(), st));
+  TRY(upload(p, (int **)&o.hc_dl, P.hc_dl.data(), P.hc_dl.size(), st));
+  TRY(upload(p, (KtCplx **)&o.hc_val, P.hc_val.data(), P.hc_val.size(), st));
+  TRY(upload(p, (uint32_t **)&o.digits, P.digits.data(), P.digits.size(), st));
+  TRY(upload(p, (KtCplx **)&o.tgt, P.tgt.data(), P.tgt.size(), st));
 
   // ---- pulses, uniforms, states, records
   TRY(upload(p, &p->eps_old, cfg->eps_guess, (size_t)nc * nt, st));
@@ -833,6 +870,55 @@ KT_API kt_status krotov_init(const kt_model_desc *md, const kt_config *cfg, void
   p->shape_h.assign(cfg->shape, cfg->shape + (size_t)nc * nt);
   p->lam_h.assign(cfg->lambda_a, cfg->lambda_a + nc);
   *out = p;
+  return KT_OK;
+}
+
+// Host-only expansion of the generator tables into a dense matrix, indexed exactly the way the
+// kernels index them (digits, slot offsets, pair tables, diagonal), with a bounds check on every
+// neighbour.  direction 0: G = H_eff(eps); direction 1: G = -H_eff(eps)^dag.  out [d][d][2].
+KT_API kt_status kt_generator_dense(const kt_model_desc *md, const kt_config *cfg, int direction, const double *eps,
+                                    double *out) {
+  if (!out || !eps) return fail(KT_ERR_ARG, "NULL argument");
+  HostPlan P;
+  kt_status s = plan(md, cfg, P);
+  if (s != KT_OK) return s;
+  const KtGeom &g = P.g;
+  const HostImage &im = direction ? P.bwd : P.fwd;
+  const double cgen = direction ? g.c_bwd : g.c_fwd;
+  const int d = g.d, nl = g.n_loc, nls = nl * g.S, nl2 = nl * nl;
+  std::fill(out, out + (size_t)d * d * 2, 0.0);
+  auto add = [&](int x, int y, cd v) -> bool {
+    if (y < 0 || y >= d) return false;
+    out[((size_t)x * d + y) * 2] += v.real();
+    out[((size_t)x * d + y) * 2 + 1] += v.imag();
+    return true;
+  };
+  for (int x = 0; x < d; ++x) {
+    const uint32_t dig = P.digits[x];
+    cd dv = 0.0;
+    for (int i = 0; i < g.n_nodes; ++i) {
+      const int xi = (dig >> (4 * i)) & 15;
+      dv += cd(im.dg[(size_t)i * nl + xi].re, im.dg[(size_t)i * nl + xi].im);
+      for (int c = 0; c < g.n_ctrl; ++c)
+        if (g.ctrl_node[c] == i) dv += eps[c] * cd(im.cdg[(size_t)c * nl + xi].re, im.cdg[(size_t)c * nl + xi].im);
+      for (int q = 0; q < g.S; ++q) {
+        const size_t e = (size_t)i * nls + xi * g.S + q;
+        if (!im.dl[e]) continue;
+        cd v(im.base[e].re, im.base[e].im);
+        for (int c = 0; c < g.n_ctrl; ++c)
+          if (g.ctrl_node[c] == i) v += eps[c] * cd(im.cslot[(size_t)c * nls + xi * g.S + q].re, im.cslot[(size_t)c * nls + xi * g.S + q].im);
+        if (!add(x, x + im.dl[e] * g.stride[i], v * g.r)) return fail(KT_ERR_RANGE, "node entry leaves the space at row %d", x);
+      }
+    }
+    for (int q = 0; q < g.n_pairs; ++q) {
+      const int xd = (dig >> (4 * im.pdst[q])) & 15, xs = (dig >> (4 * im.psrc[q])) & 15;
+      const size_t e = (size_t)q * nl2 + xd * nl + xs;
+      if (!im.poff[e]) continue;
+      if (!add(x, x + im.poff[e], cd(im.pval[e].re, im.pval[e].im) * g.r))
+        return fail(KT_ERR_RANGE, "pair entry leaves the space at row %d", x);
+    }
+    add(x, x, dv * g.r + cgen);
+  }
   return KT_OK;
 }
 

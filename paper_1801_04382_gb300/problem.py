@@ -52,28 +52,8 @@ class Problem:
         uniforms = _c(uniforms)
         if uniforms.ndim != 3 or uniforms.shape[1] != M:
             raise ValueError("uniforms must have shape [n_passes, M, draws_per_traj]")
-        keep = {
-            "h0": _cplx(net.h0_local), "hc": _cplx(net.hc_local), "cn": _c(net.ctrl_node, np.int32),
-            "a": _cplx(net.a_local), "pd": _c(net.pair_dst, np.int32), "ps": _c(net.pair_src, np.int32),
-            "pc": _cplx(net.pair_coef), "lc": _cplx(net.lind_coef), "tgt": _cplx(net.psi_tgt),
-            "psi0": _cplx(net.psi0) if psi0_batch is None else None,
-            "psib": _cplx(psi0_batch) if psi0_batch is not None else None,
-            "eps": _c(eps_guess), "shape": _c(shape), "lam": _c(lam), "U": uniforms,
-        }
-        md = _capi.ModelDesc(
-            n_nodes=net.n_nodes, n_loc=net.n_loc, h0_local=_ptr(keep["h0"]),
-            n_ctrl=net.n_ctrl, ctrl_node=_ptr(keep["cn"], ct.c_int), hc_local=_ptr(keep["hc"]),
-            a_local=_ptr(keep["a"]), n_pairs=len(net.pair_dst),
-            pair_dst=_ptr(keep["pd"], ct.c_int), pair_src=_ptr(keep["ps"], ct.c_int), pair_coef=_ptr(keep["pc"]),
-            n_lind=net.lind_coef.shape[0], lind_coef=_ptr(keep["lc"]),
-            psi0=_ptr(keep["psi0"]), psi0_batch=_ptr(keep["psib"]), psi_tgt=_ptr(keep["tgt"]))
-        cfg = _capi.Config(
-            T=self.T, nt=self.nt, M=self.M,
-            prec=_capi.KT_FP64 if precision == "fp64" else _capi.KT_FP32_MIXED,
-            ckpt_interval=int(ckpt_interval), eps_guess=_ptr(keep["eps"]), shape=_ptr(keep["shape"]),
-            lambda_a=_ptr(keep["lam"]), uniforms=_ptr(keep["U"]), n_passes=uniforms.shape[0],
-            draws_per_traj=uniforms.shape[2], eps_bound=float(eps_bound), cheb_tol=float(cheb_tol),
-            tile_traj=int(tile_traj))
+        keep, md, cfg = _descriptors(net, self.T, self.nt, self.M, eps_guess, shape, lam, uniforms, precision,
+                                     ckpt_interval, eps_bound, cheb_tol, tile_traj, psi0_batch)
         handle = ct.c_void_p()
         self._h = None
         _capi.check(self._lib.krotov_init(ct.byref(md), ct.byref(cfg), _stream_handle(stream), ct.byref(handle)),
@@ -170,3 +150,44 @@ def bessel_j(alpha: float, n: int) -> np.ndarray:
     out = np.zeros(n)
     _capi.check(_capi.load().kt_bessel_j(float(alpha), int(n), _ptr(out)), "kt_bessel_j")
     return out
+
+
+def _descriptors(net, T, nt, M, eps_guess, shape, lam, uniforms, precision="fp64", ckpt_interval=0,
+                 eps_bound=0.0, cheb_tol=0.0, tile_traj=0, psi0_batch=None):
+    """kt_model_desc / kt_config for ``net`` (the returned ``keep`` dict owns the host arrays)."""
+    uniforms = _c(uniforms)
+    keep = {
+        "h0": _cplx(net.h0_local), "hc": _cplx(net.hc_local), "cn": _c(net.ctrl_node, np.int32),
+        "a": _cplx(net.a_local), "pd": _c(net.pair_dst, np.int32), "ps": _c(net.pair_src, np.int32),
+        "pc": _cplx(net.pair_coef), "lc": _cplx(net.lind_coef), "tgt": _cplx(net.psi_tgt),
+        "psi0": _cplx(net.psi0) if psi0_batch is None else None,
+        "psib": _cplx(psi0_batch) if psi0_batch is not None else None,
+        "eps": _c(eps_guess), "shape": _c(shape), "lam": _c(lam), "U": uniforms,
+    }
+    md = _capi.ModelDesc(
+        n_nodes=net.n_nodes, n_loc=net.n_loc, h0_local=_ptr(keep["h0"]),
+        n_ctrl=net.n_ctrl, ctrl_node=_ptr(keep["cn"], ct.c_int), hc_local=_ptr(keep["hc"]),
+        a_local=_ptr(keep["a"]), n_pairs=len(net.pair_dst),
+        pair_dst=_ptr(keep["pd"], ct.c_int), pair_src=_ptr(keep["ps"], ct.c_int), pair_coef=_ptr(keep["pc"]),
+        n_lind=net.lind_coef.shape[0], lind_coef=_ptr(keep["lc"]),
+        psi0=_ptr(keep["psi0"]), psi0_batch=_ptr(keep["psib"]), psi_tgt=_ptr(keep["tgt"]))
+    cfg = _capi.Config(
+        T=float(T), nt=int(nt), M=int(M),
+        prec=_capi.KT_FP64 if precision == "fp64" else _capi.KT_FP32_MIXED,
+        ckpt_interval=int(ckpt_interval), eps_guess=_ptr(keep["eps"]), shape=_ptr(keep["shape"]),
+        lambda_a=_ptr(keep["lam"]), uniforms=_ptr(keep["U"]), n_passes=uniforms.shape[0],
+        draws_per_traj=uniforms.shape[2], eps_bound=float(eps_bound), cheb_tol=float(cheb_tol),
+        tile_traj=int(tile_traj))
+    return keep, md, cfg
+
+
+def generator_dense(net, T, nt, M, eps_guess, shape, lam, uniforms, eps, direction=0, precision="fp64"):
+    """Dense d x d generator expanded from the library's structured tables (host only):
+    direction 0 gives H_eff(eps), direction 1 gives -H_eff(eps)^dag."""
+    keep, md, cfg = _descriptors(net, T, nt, M, eps_guess, shape, lam, uniforms, precision)
+    d = net.d
+    out = np.zeros((d, d, 2))
+    e = _c(eps)
+    _capi.check(_capi.load().kt_generator_dense(ct.byref(md), ct.byref(cfg), int(direction), _ptr(e), _ptr(out)),
+                "kt_generator_dense")
+    return out[..., 0] + 1j * out[..., 1]

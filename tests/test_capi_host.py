@@ -112,3 +112,26 @@ def test_model_builder_matches_paper_structure():
             assert c == pytest.approx(0.7j)
     assert np.allclose(net.lind_coef, np.sqrt(1.4))
     assert abs(np.linalg.norm(net.psi_tgt) - 1.0) < 1e-15
+
+
+@pytest.mark.parametrize("N,nc,kappa", [(2, 1, 1.0), (2, 2, 0.7), (3, 1, 1.3), (1, 2, 1.0)])
+def test_structured_generator_tables_match_dense_heff(lib, N, nc, kappa):
+    """The library's structured generator tables, expanded with the kernels' own indexing
+    (digits, slot offsets, per-direction pair tables), equal the oracle's dense
+    H_eff = H - (i/2) L^dag L (direction 0) and -H_eff^dag (direction 1, co-state propagation)."""
+    from oracle import model as om
+    from paper_1801_04382_gb300.problem import generator_dense
+    net = pm.cascaded_chain(N, nc, kappa=kappa)
+    m = om.build_model(N, nc, kappa=kappa)
+    nt, T, M = 8, 1.0, 3
+    rng = np.random.default_rng(N * 10 + nc)
+    eps_guess = si.guess_pulses(N, nt, T, 2.0)
+    args = (net, T, nt, M, eps_guess, si.shape_functions(N, nt, T), np.full(N, 10.0), si.uniforms(0, 1, M, 5))
+    for trial in range(3):
+        eps = rng.uniform(-2.0, 2.0, size=N)
+        Heff = m.Heff(eps)
+        scale = np.abs(Heff).max()
+        G0 = generator_dense(*args, eps=eps, direction=0)
+        G1 = generator_dense(*args, eps=eps, direction=1)
+        assert np.abs(G0 - Heff).max() <= 1e-12 * scale
+        assert np.abs(G1 + Heff.conj().T).max() <= 1e-12 * scale
