@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Benchmark: Krotov iterations per second of the trajectory-parallel Krotov hot path on GB300.
+
+Workload (one "step" = one Krotov iteration = backward co-state sweep + updating forward sweep,
+including the checkpoint recompute): four-node cascaded atom-cavity chain, three-level atoms,
+cavity cutoff 2 (d = 6561), 1024 trajectories, nt = 5000 intervals of dt = 0.01, four controls,
+FP32-mixed precision (complex64 states, FP64 norms and sums), co-state checkpoints every 100
+intervals, synthetic seeded inputs (guess pulse sin^2 of amplitude 1, uniforms from seed 4).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (under torchrun): every rank optimises an independent problem (its own seed); there is
+no data-path collective ("weak" scaling).  --impl reference times the FP64 CPU oracle on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth_inputs as si  # noqa: E402
+
+METRIC = "Krotov iters/s and traj·steps/s, FP32-mixed vs FP64 path, % of HBM roofline"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+SM_COUNT, FP32_LANES = 152, 128
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def workload(rank: int = 0, precision: str = "fp32"):
+    wl = si.CONFIGS["cfg5_d6561"]
+    return wl.with_(seed=wl.seed + 1000 * rank, precision=precision)
+
+
+def avg_row_nonzeros(net) -> float:
+    """Average nonzeros per row of the structured H_eff (diagonal counted once): node-local
+    off-diagonals + pair hops, averaged over uniformly distributed digits."""
+    nl, N = net.n_loc, net.n_nodes
+    tot = 1.0
+    for i in range(N):
+        pattern = np.abs(net.h0_local[i]) > 0
+        for c, node in enumerate(net.ctrl_node):
+            if node == i:
+                pattern |= np.abs(net.hc_local[c]) > 0
+        off = pattern.sum(axis=1) - np.diag(pattern)
+        tot += off.mean()
+    has_lower = (np.abs(net.a_local) > 0).any(axis=1)          # row x of a nonzero
+    has_raise = (np.abs(net.a_local) > 0).any(axis=0)          # column x of a nonzero -> row x of a^dag
+    # pair terms of H_eff: user pairs plus L^dag L cross terms, merged; the cascade leaves
+    # exactly one direction per node pair (upstream hops cancel)
+    n_pairs = N * (N - 1) // 2
+    tot += n_pairs * has_raise.mean() * has_lower.mean()
+    return float(tot)
+
+
+# ------------------------------------------------------------------------------------------
+def clocks_start(path):
+    cmd = ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+           "--format=csv,noheader,nounits", "-lms", "200"]
+    try:
+        f = open(path, "w")
+        return subprocess.Popen(cmd, stdout=f, stderr=subprocess.DEVNULL), f
+    except (OSError, FileNotFoundError):
+        return None, None
+
+
+def clocks_stop(proc, fh, path, gpu_index):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        proc.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+    fh.close()
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 9 or parts[0] != str(gpu_index):
+            continue
+        try:
+            sm.append(float(parts[1]))
+            mx.append(float(parts[2]))
+        except ValueError:
+            continue
+        for name, val in zip(names, parts[5:9]):
+            if val.lower() == "active":
+                reasons.add(name)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+def cpu_baseline(wl, budget_s: float = 20.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload: one trajectory over a
+    window of the nt intervals (guess sweep, backward sweep, updating sweep), extrapolated to the
+    full workload as Krotov iterations/s (oracle traj.steps: 2 sweeps x M x nt per iteration)."""
+    from oracle import mcwf
+    from oracle import model as om
+    m = om.build_model(wl.n_nodes, wl.n_cav, wl.delta, wl.g, wl.kappa)
+    M_s = 1
+    nt_s = 10
+    T_s = wl.dt * nt_s
+    U = si.uniforms(wl.seed, 2, M_s, wl.draws_per_traj)
+    eps = si.guess_pulses(wl.n_nodes, nt_s, T_s, wl.guess_amp)
+    S = si.shape_functions(wl.n_nodes, nt_s, T_s)
+    lam = np.full(wl.n_nodes, wl.lam)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        mcwf.optimize(m, eps, T_s, U, S, lam, 1, psi0=m.psi0)
+        reps += 1
+        if time.perf_counter() - t0 > budget_s / 2 or reps >= 50:
+            break
+    el = time.perf_counter() - t0
+    # per rep: guess forward + backward + updating forward = 3 sweeps of M_s * nt_s traj.steps;
+    # the iteration itself is 2 of them
+    traj_steps = reps * 3 * M_s * nt_s
+    tsps = traj_steps / el
+    iters = tsps / (2.0 * wl.M * wl.nt)
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count() or 1
+    return {"value": iters, "unit": "Krotov iters/s", "cores": cores, "kind": "oracle",
+            "traj_steps_per_s": tsps,
+            "sample": f"{reps} x (guess+backward+updating sweep) of {M_s} trajectory x {nt_s} intervals "
+                      f"(d={wl.d}, dt={wl.dt}), extrapolated to M={wl.M}, nt={wl.nt}"}
+
+
+# ------------------------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    wl = workload(0)
+    steps = []
+    base = None
+    for _ in range(args.warmup):
+        cpu_baseline(wl, budget_s=4.0)
+    for _ in range(args.steps):
+        base = cpu_baseline(wl, budget_s=8.0)
+        steps.append(base["value"])
+    value = statistics.median(steps)
+    ms = 1000.0 / value
+    line = {"metric": METRIC, "value": value, "unit": "Krotov iters/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "d": wl.d, "M": wl.M, "nt": wl.nt},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "Krotov iters/s", "cores": base["cores"], "kind": "oracle",
+                             "sample": base["sample"]},
+            "e2e": {"value": value, "unit": "Krotov iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, rank, world):
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU (GB300); the CUDA path has no CPU fallback")
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1801_04382_gb300 import Problem, cascaded_chain
+
+    wl = workload(rank, args.precision)
+    net = cascaded_chain(wl.n_nodes, wl.n_cav, wl.delta, wl.g, wl.kappa)
+    n_passes = 1 + args.warmup + args.steps
+    eps0 = si.guess_pulses(net.n_ctrl, wl.nt, wl.T, wl.guess_amp)
+    S = si.shape_functions(net.n_ctrl, wl.nt, wl.T)
+    lam = np.full(net.n_ctrl, wl.lam)
+    U = si.uniforms(wl.seed, n_passes, wl.M, wl.draws_per_traj)
+    stream = torch.cuda.current_stream()
+    prob = Problem(net, wl.T, wl.nt, wl.M, eps0, S, lam, U, precision=wl.precision,
+                   ckpt_interval=wl.ckpt_interval, stream=stream)
+    info = prob.info
+    prob.forward(False, stream=stream)                  # guess sweep (pass 0)
+    for _ in range(args.warmup):
+        prob.update(1, stream=stream)
+
+    # ---------------- timed region: K Krotov iterations, inputs resident in HBM
+    clk_path = os.path.join(tempfile.gettempdir(), f"kt_clocks_{os.getpid()}.csv")
+    proc, fh = clocks_start(clk_path)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    prob.set_profiling(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    JT = None
+    for _ in range(args.steps):
+        JT, _ = prob.update(1, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    prof = prob.profile()
+    prob.set_profiling(False)
+    clocks = clocks_stop(proc, fh, clk_path, local)
+    if dist:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    iters_per_s = world * 1000.0 / ms_step
+    traj_steps_per_s = iters_per_s * 2 * wl.M * wl.nt
+
+    # ---------------- end to end through the public API, host buffers each step
+    e2e_steps = max(1, min(args.steps, 3))
+    pin = torch.empty((1, wl.M, wl.draws_per_traj), dtype=torch.float64, pin_memory=True)
+    host_U = si.uniforms(wl.seed + 7, e2e_steps, wl.M, wl.draws_per_traj)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s_ in range(e2e_steps):
+        pin.numpy()[0] = host_U[s_]
+        prob.set_uniforms(pin.numpy(), stream=stream)   # H2D: this step's random numbers
+        JT_e2e, _ = prob.update(1, stream=stream)        # D2H: J_T (tau_k of all trajectories)
+        eps_host = prob.pulses()                         # D2H: the updated pulse
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1000.0 / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = wl.M * wl.draws_per_traj * 8
+    d2h = wl.M * 16 + net.n_ctrl * wl.nt * 8
+
+    # ---------------- roofline of the dominant kernel
+    peaks, peak_src = measured_peaks()
+    fam = max(prof, key=lambda k: prof[k][0])
+    f_ms, f_n = prof[fam]
+    avg_s = f_ms / max(f_n, 1) / 1000.0
+    nnz = avg_row_nonzeros(net)
+    K = info.cheb_terms
+    flops_per_elem_term = 8.0 * nnz + 12.0          # complex MACs, recurrence, accumulation
+    flops_per_launch = flops_per_elem_term * K * wl.d * wl.M
+    clk_max = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = SM_COUNT * FP32_LANES * 2 * clk_max * 1e6 / 1e12
+    achieved = flops_per_launch / avg_s / 1e12
+    s_bytes = 8 if wl.precision == "fp32" else 16
+    bytes_per_iter = 5.0 * s_bytes * wl.d * wl.M * wl.nt
+    hbm_achieved = bytes_per_iter * (iters_per_s / world) / 1e9
+    kernel_bytes = (3 if fam == "fwd" else 2) * s_bytes * wl.d * wl.M
+    roof = {"bound": "alu", "kernel": f"{fam}_kernel", "achieved": achieved, "peak": fp32_peak,
+            "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+            "avg_launch_ms": avg_s * 1e3, "launches": f_n,
+            "flops_per_launch": flops_per_launch, "algorithmic_bytes_per_launch": kernel_bytes,
+            "hbm_gbs_of_kernel": kernel_bytes / avg_s / 1e9,
+            "peak_source": f"FP32 FFMA: {SM_COUNT} SMs x {FP32_LANES} lanes x 2 x {clk_max:.0f} MHz"}
+    line = {
+        "metric": METRIC, "value": iters_per_s, "unit": "Krotov iters/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64+f64" if wl.precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "d": wl.d, "M": wl.M, "nt": wl.nt, "dt": wl.dt,
+                   "precision": "FP32-mixed" if wl.precision == "fp32" else "FP64",
+                   "ckpt_interval": wl.ckpt_interval, "cheb_terms": K, "tile_traj": info.tile_traj,
+                   "threads": info.threads, "l2": "inputs larger than L2 (co-state checkpoints and segment "
+                   f"buffers {info.device_bytes / 1e9:.1f} GB per GPU)", "parallelism": f"replicas{world}"},
+        "traj_steps_per_s": traj_steps_per_s,
+        "hbm_roofline": {"achieved_gbs": hbm_achieved, "peak_gbs": peaks["hbm_gbs"],
+                         "frac": hbm_achieved / peaks["hbm_gbs"], "peak_source": peak_src,
+                         "bytes_per_iter": bytes_per_iter},
+        "final_JT": float(JT[-1]) if JT is not None else None,
+        "roofline": roof,
+        "e2e": {"value": world * 1000.0 / e2e_ms, "unit": "Krotov iters/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(prof["fwd"][1] + prof["bwd"][1] + 4 * args.steps),
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    prob.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

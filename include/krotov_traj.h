@@ -164,6 +164,25 @@ KT_API kt_status krotov_get_states(kt_problem *p, double *psi_out);
  * j a checkpoint. */
 KT_API kt_status krotov_get_costate(kt_problem *p, int j, double *chi_out);
 
+/* Replace the uniform random numbers (host array [n_passes][M][draws_per_traj], 1 <= n_passes
+ * <= the value given at init, draws as at init); later passes cycle through these n_passes rows,
+ * starting again at row 0.  Asynchronous on `stream`; the host
+ * array must stay valid until the stream reaches the copy (pinned memory recommended). */
+KT_API kt_status krotov_set_uniforms(kt_problem *p, const double *uniforms, int n_passes, void *stream);
+
+/* Per-launch timing of the interval kernels with CUDA events recorded on the calling stream
+ * around every launch (on = 1), e.g. to derive each kernel's average duration during a
+ * benchmark.  Turning it on or off clears the totals.  krotov_get_profile returns, per family
+ * (KT_PROF_FWD: forward interval kernel incl. the pulse update; KT_PROF_BWD: backward interval
+ * kernel incl. checkpoint recompute; KT_PROF_OTHER: reserved), the summed milliseconds and
+ * the launch count since profiling was turned on; arrays of KT_PROF_FAMILIES entries. */
+#define KT_PROF_FWD 0
+#define KT_PROF_BWD 1
+#define KT_PROF_OTHER 2
+#define KT_PROF_FAMILIES 3
+KT_API kt_status krotov_set_profiling(kt_problem *p, int on);
+KT_API kt_status krotov_get_profile(kt_problem *p, double *ms_out, long long *launches_out);
+
 /* Sizes chosen at init: max jumps per pass, Chebyshev terms per step, tile width, tiles,
  * threads per CTA, and the spectral interval [e_min, e_max] of the forward generator's
  * Hermitian part. */

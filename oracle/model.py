@@ -26,8 +26,10 @@ from dataclasses import dataclass
 from functools import reduce
 
 import numpy as np
+import scipy.sparse as sp
 
 G, E, R = 0, 1, 2  # atom levels
+SPARSE_ABOVE = 729  # full-space dimension above which operators are held as scipy.sparse CSR
 
 
 def atom_op(row: int, col: int) -> np.ndarray:
@@ -60,8 +62,12 @@ def local_operators(n_cav: int) -> dict:
     }
 
 
-def embed(op: np.ndarray, node: int, n_nodes: int) -> np.ndarray:
+def embed(op, node: int, n_nodes: int, sparse: bool = False):
     """op acting on node ``node`` of ``n_nodes`` identical nodes (node 0 most significant)."""
+    if sparse:
+        ident = sp.identity(op.shape[0], dtype=np.complex128, format="csr")
+        factors = [sp.csr_matrix(op) if i == node else ident for i in range(n_nodes)]
+        return reduce(lambda x, y: sp.kron(x, y, format="csr"), factors)
     ident = np.eye(op.shape[0], dtype=np.complex128)
     factors = [op if i == node else ident for i in range(n_nodes)]
     return reduce(np.kron, factors)
@@ -89,8 +95,8 @@ class DenseModel:
             out = out + e * hc
         return out
 
-    def LdagL(self) -> np.ndarray:
-        out = np.zeros_like(self.H0)
+    def LdagL(self):
+        out = 0 * self.H0
         for l_op in self.L:
             out = out + l_op.conj().T @ l_op
         return out
@@ -114,19 +120,20 @@ def build_model(n_nodes: int, n_cav: int, delta: float = 100.0, g: float = 1.0,
     """Cascaded chain of ``n_nodes`` atom-cavity nodes (paper Sec. 3.1)."""
     loc = local_operators(n_cav)
     d = (3 * (n_cav + 1)) ** n_nodes
-    H0 = np.zeros((d, d), dtype=np.complex128)
-    a_full = [embed(loc["a"], i, n_nodes) for i in range(n_nodes)]
+    sparse = d > SPARSE_ABOVE      # same operators, stored sparse so that d = 6561 fits in memory
+    H0 = sp.csr_matrix((d, d), dtype=np.complex128) if sparse else np.zeros((d, d), dtype=np.complex128)
+    a_full = [embed(loc["a"], i, n_nodes, sparse) for i in range(n_nodes)]
     h0_node = (-delta * loc["Pi_r"] - (g * g / delta) * loc["n"]
                + g * (loc["sigma_rg"] @ loc["a"] + (loc["sigma_rg"] @ loc["a"]).conj().T))
     for i in range(n_nodes):
-        H0 += embed(h0_node, i, n_nodes)
+        H0 = H0 + embed(h0_node, i, n_nodes, sparse)
     for i in range(n_nodes):
         for j in range(i + 1, n_nodes):
-            H0 += 1j * kappa * a_full[i].conj().T @ a_full[j]
-            H0 += -1j * kappa * a_full[j].conj().T @ a_full[i]
+            H0 = H0 + 1j * kappa * (a_full[i].conj().T @ a_full[j])
+            H0 = H0 + (-1j * kappa) * (a_full[j].conj().T @ a_full[i])
     hc_node = 0.5j * (loc["sigma_re"] - loc["sigma_re"].conj().T)
-    Hc = [embed(hc_node, i, n_nodes) for i in range(n_nodes)]
-    L = [np.sqrt(2.0 * kappa) * sum(a_full)]
+    Hc = [embed(hc_node, i, n_nodes, sparse) for i in range(n_nodes)]
+    L = [np.sqrt(2.0 * kappa) * reduce(lambda x, y: x + y, a_full)]
     psi0 = np.zeros(d, dtype=np.complex128)
     psi0[basis_index(n_cav, [E] + [G] * (n_nodes - 1), [0] * n_nodes)] = 1.0
     tgt = np.zeros(d, dtype=np.complex128)

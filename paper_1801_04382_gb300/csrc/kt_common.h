@@ -19,6 +19,14 @@
 #define KT_MAX_T 32       // trajectories per tile
 #define KT_MAX_ROUNDS 16  // jump-separated pieces of one interval in one kernel
 
+// Kernel families timed by krotov_set_profiling (mirror KT_PROF_* in the public header).
+#ifndef KT_PROF_FAMILIES
+#define KT_PROF_FAMILIES 3
+#define KT_PROF_FWD 0
+#define KT_PROF_BWD 1
+#define KT_PROF_OTHER 2
+#endif
+
 // Device status word values (first error wins); mirror kt_status.
 #define KT_DEV_OK 0
 #define KT_DEV_NONFINITE 5

@@ -142,7 +142,7 @@ struct kt_problem {
   KtGeom g{};
   int fp64 = 1, ept = 4;
   size_t esz = 16;
-  int nt = 0, M = 0, n_passes = 0, ckpt = 0;
+  int nt = 0, M = 0, n_passes = 0, n_passes_alloc = 0, ckpt = 0;
   double T = 0.0;
   size_t state_bytes = 0;       // one tile-layout array of all trajectories
   size_t bytes = 0;
@@ -172,9 +172,49 @@ struct kt_problem {
   long long pass_counter = 0;
   bool have_fwd = false, have_bwd = false, have_deps = false;
   int final_buf = 0;
+
+  // optional per-launch timing of the interval kernels (krotov_set_profiling)
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;            // pairs: [2i] before, [2i+1] after launch i
+  std::vector<int> ev_family;                  // kernel family of pending pair i
+  int ev_used = 0;
+  double prof_ms[KT_PROF_FAMILIES] = {0, 0, 0};
+  long long prof_launches[KT_PROF_FAMILIES] = {0, 0, 0};
 };
 
 namespace {
+
+// Event pair around one launch of the given family (only while profiling).
+kt_status prof_begin(kt_problem *p, int family, cudaStream_t st) {
+  if (!p->profiling) return KT_OK;
+  const size_t need = 2 * (size_t)(p->ev_used + 1);
+  while (p->ev_pool.size() < need) {
+    cudaEvent_t e;
+    KT_CUDA(cudaEventCreate(&e));
+    p->ev_pool.push_back(e);
+  }
+  if (p->ev_family.size() < (size_t)p->ev_used + 1) p->ev_family.resize(p->ev_used + 1);
+  p->ev_family[p->ev_used] = family;
+  KT_CUDA(cudaEventRecord(p->ev_pool[2 * p->ev_used], st));
+  return KT_OK;
+}
+kt_status prof_end(kt_problem *p, cudaStream_t st) {
+  if (!p->profiling) return KT_OK;
+  KT_CUDA(cudaEventRecord(p->ev_pool[2 * p->ev_used + 1], st));
+  p->ev_used++;
+  return KT_OK;
+}
+// After the stream has been synchronised: fold the pending pairs into the totals.
+kt_status prof_collect(kt_problem *p) {
+  for (int i = 0; i < p->ev_used; ++i) {
+    float ms = 0.f;
+    KT_CUDA(cudaEventElapsedTime(&ms, p->ev_pool[2 * i], p->ev_pool[2 * i + 1]));
+    p->prof_ms[p->ev_family[i]] += ms;
+    p->prof_launches[p->ev_family[i]] += 1;
+  }
+  p->ev_used = 0;
+  return KT_OK;
+}
 
 kt_status dev_alloc(kt_problem *p, void **ptr, size_t bytes) {
   if (bytes == 0) bytes = 16;
@@ -212,6 +252,10 @@ kt_status read_status(kt_problem *p, cudaStream_t st) {
   int s = 0;
   KT_CUDA(cudaMemcpyAsync(&s, p->status, sizeof(int), cudaMemcpyDeviceToHost, st));
   KT_CUDA(cudaStreamSynchronize(st));
+  if (p->profiling) {
+    kt_status ps = prof_collect(p);
+    if (ps != KT_OK) return ps;
+  }
   if (s == KT_DEV_OK) return KT_OK;
   KT_CUDA(cudaMemsetAsync(p->status, 0, sizeof(int), st));
   switch (s) {
@@ -267,8 +311,10 @@ kt_status launch_bwd_step(kt_problem *p, int j, const void *in, void *out, cudaS
   b.j = j;
   b.chi_in = in;
   b.chi_out = out;
+  kt_status s = prof_begin(p, KT_PROF_BWD, st);
+  if (s != KT_OK) return s;
   KT_CUDA(kt_launch_bwd(p->fp64, p->ept, p->g, p->im_bwd, p->ops, b, st));
-  return KT_OK;
+  return prof_end(p, st);
 }
 
 // Recompute chi(t_{a+1}) .. chi(t_{b-1}) into seg[1 .. b-a-1] from the checkpoint at t_b.
@@ -302,7 +348,10 @@ kt_status forward_sweep(kt_problem *p, int update, cudaStream_t st) {
     a.psi_in = p->psi_init;
     a.psi_out = nullptr;
     a.chi_t = ckpt_slot(p, 0);
+    kt_status s = prof_begin(p, KT_PROF_FWD, st);
+    if (s != KT_OK) return s;
     KT_CUDA(kt_launch_fwd(p->fp64, p->ept, p->g, p->im_fwd, p->ops, a, st));
+    if ((s = prof_end(p, st)) != KT_OK) return s;
   }
   const int K = (p->ckpt == 0) ? p->nt : p->ckpt;
   for (int seg_a = 0; seg_a < p->nt; seg_a += K) {
@@ -316,7 +365,10 @@ kt_status forward_sweep(kt_problem *p, int update, cudaStream_t st) {
       a.psi_in = (j == 1) ? p->psi_init : p->psi[(j - 1) & 1];
       a.psi_out = p->psi[j & 1];
       a.chi_t = (update && j < p->nt) ? chi_at(p, j, seg_a) : nullptr;
+      kt_status s = prof_begin(p, KT_PROF_FWD, st);
+      if (s != KT_OK) return s;
       KT_CUDA(kt_launch_fwd(p->fp64, p->ept, p->g, p->im_fwd, p->ops, a, st));
+      if ((s = prof_end(p, st)) != KT_OK) return s;
     }
   }
   kt_status s = read_status(p, st);
@@ -432,6 +484,7 @@ KT_API kt_status kt_bessel_j(double alpha, int n, double *out) {
 
 KT_API void krotov_free(kt_problem *p) {
   if (!p) return;
+  for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
   for (void *a : p->allocs) cudaFree(a);
   delete p;
 }
@@ -795,6 +848,7 @@ KT_API kt_status krotov_init(const kt_model_desc *md, const kt_config *cfg, void
   p->M = M;
   p->T = cfg->T;
   p->n_passes = cfg->n_passes;
+  p->n_passes_alloc = cfg->n_passes;
   p->ckpt = P.ckpt;
   p->e_min = P.e_min;
   p->e_max = P.e_max;
@@ -1022,6 +1076,38 @@ KT_API kt_status krotov_get_costate(kt_problem *p, int j, double *chi_out) {
   if (!p->have_bwd) return fail(KT_ERR_STATE, "no backward sweep since the last forward sweep");
   if (j < 0 || j > p->nt || !is_ckpt(p, j)) return fail(KT_ERR_ARG, "co-state %d not stored", j);
   return download_state(p, ckpt_slot(p, j), chi_out, 0);
+}
+
+KT_API kt_status krotov_set_uniforms(kt_problem *p, const double *uniforms, int n_passes, void *stream) {
+  if (!p || !uniforms) return fail(KT_ERR_ARG, "NULL argument");
+  if (n_passes < 1 || n_passes > p->n_passes_alloc)
+    return fail(KT_ERR_ARG, "n_passes must be in [1, %d] (the value given at init)", p->n_passes_alloc);
+  const size_t n = (size_t)n_passes * p->M * p->g.draws;
+  cudaStream_t st = (cudaStream_t)stream;
+  KT_CUDA(cudaMemcpyAsync(p->U, uniforms, n * sizeof(double), cudaMemcpyHostToDevice, st));
+  p->n_passes = n_passes;
+  p->pass_counter = 0;
+  return KT_OK;
+}
+
+KT_API kt_status krotov_set_profiling(kt_problem *p, int on) {
+  if (!p) return fail(KT_ERR_ARG, "NULL problem");
+  p->profiling = on != 0;
+  p->ev_used = 0;
+  for (int f = 0; f < KT_PROF_FAMILIES; ++f) {
+    p->prof_ms[f] = 0.0;
+    p->prof_launches[f] = 0;
+  }
+  return KT_OK;
+}
+
+KT_API kt_status krotov_get_profile(kt_problem *p, double *ms_out, long long *launches_out) {
+  if (!p) return fail(KT_ERR_ARG, "NULL problem");
+  for (int f = 0; f < KT_PROF_FAMILIES; ++f) {
+    if (ms_out) ms_out[f] = p->prof_ms[f];
+    if (launches_out) launches_out[f] = p->prof_launches[f];
+  }
+  return KT_OK;
 }
 
 KT_API kt_status krotov_get_info(kt_problem *p, kt_info *info) {

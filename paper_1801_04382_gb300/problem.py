@@ -122,6 +122,24 @@ class Problem:
         _capi.check(self._lib.krotov_get_costate(self._h, int(j), _ptr(out)), "krotov_get_costate")
         return out[..., 0] + 1j * out[..., 1]
 
+    def set_uniforms(self, uniforms, stream=None) -> None:
+        """Upload a fresh [n_passes, M, draws] block of uniforms (pass counter restarts)."""
+        u = _c(uniforms)
+        self._u_keep = u          # host buffer must outlive the asynchronous copy
+        _capi.check(self._lib.krotov_set_uniforms(self._h, _ptr(u), int(u.shape[0]), _stream_handle(stream)),
+                    "krotov_set_uniforms")
+
+    def set_profiling(self, on: bool = True) -> None:
+        _capi.check(self._lib.krotov_set_profiling(self._h, int(bool(on))), "krotov_set_profiling")
+
+    def profile(self):
+        """{family: (total_ms, launches)} for 'fwd' and 'bwd' interval kernels since profiling was enabled."""
+        ms = np.zeros(3)
+        n = np.zeros(3, dtype=np.int64)
+        _capi.check(self._lib.krotov_get_profile(self._h, _ptr(ms), n.ctypes.data_as(ct.POINTER(ct.c_longlong))),
+                    "krotov_get_profile")
+        return {"fwd": (float(ms[0]), int(n[0])), "bwd": (float(ms[1]), int(n[1]))}
+
     def get_info(self):
         info = _capi.Info()
         _capi.check(self._lib.krotov_get_info(self._h, ct.byref(info)), "krotov_get_info")
