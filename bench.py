@@ -72,6 +72,16 @@ def avg_row_nonzeros(net) -> float:
     return float(tot)
 
 
+def reduce_max(value: float, dist, device) -> float:
+    """Max of a per-rank float over all ranks (identity without a process group)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ------------------------------------------------------------------------------------------
 def clocks_start(path):
     cmd = ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -226,10 +236,7 @@ def run_ours(args, rank, world):
     prof = prob.profile()
     prob.set_profiling(False)
     clocks = clocks_stop(proc, fh, clk_path, local)
-    if dist:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = reduce_max(ms_total, dist, "cuda")
     ms_step = ms_total / args.steps
     iters_per_s = world * 1000.0 / ms_step
     traj_steps_per_s = iters_per_s * 2 * wl.M * wl.nt
@@ -249,10 +256,7 @@ def run_ours(args, rank, world):
         eps_host = prob.pulses()                         # D2H: the updated pulse
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1000.0 / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = reduce_max(e2e_ms, dist, "cuda")
     h2d = wl.M * wl.draws_per_traj * 8
     d2h = wl.M * 16 + net.n_ctrl * wl.nt * 8
 
