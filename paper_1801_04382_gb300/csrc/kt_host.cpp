@@ -691,11 +691,13 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
   if (cfg->tile_traj > 0 && ((cfg->tile_traj & (cfg->tile_traj - 1)) || cfg->tile_traj > 32))
     return fail(KT_ERR_ARG, "tile_traj must be a power of two <= 32");
   int Tsel = 0;
+  // items per thread above 8 spill registers: use them only when nothing else fits
+  const long long max_items = ((long long)d > 8LL * maxthr) ? 16LL * maxthr : 8LL * maxthr;
   for (int T = 32; T >= 1; T >>= 1) {
     if (cfg->tile_traj > 0 && T != cfg->tile_traj) continue;
     KtGeom t = g;
     t.T = T;
-    if ((long long)d * T > 16LL * maxthr) continue;
+    if ((long long)d * T > (cfg->tile_traj > 0 ? 16LL * maxthr : max_items)) continue;
     t.nthreads = maxthr;
     if (kt_smem_bytes(t, esz) > 227 * 1024) continue;
     Tsel = T;
