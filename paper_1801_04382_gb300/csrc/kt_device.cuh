@@ -229,15 +229,153 @@ struct Items {
   bool ok[EPT];
 };
 
-template <int EPT>
+template <int EPT, int NL>
 __device__ __forceinline__ void load_items(const KtGeom &g, const KtOps &ops, Items<EPT> &it) {
   const int n = g.d * g.T;
+  if (NL > 0) {
+    // fiber mapping: thread -> (fiber f, trajectory tau); its NL items run along the last
+    // node's digit (stride T in the interleaved tile), so node-local and pair coefficients of
+    // the other nodes are fixed per thread and the last node's are uniform per item slot
+    const int f = threadIdx.x / g.T, tau = threadIdx.x % g.T;
+    const bool ok = f < g.d / NL;
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      const int item = (f * NL + q) * g.T + tau;
+      it.item[q] = item;
+      it.ok[q] = ok;
+      it.dig[q] = ok ? ops.digits[f * NL + q] : 0u;
+    }
+    return;
+  }
 #pragma unroll
   for (int q = 0; q < EPT; ++q) {
     const int item = threadIdx.x + q * blockDim.x;
     it.item[q] = item;
     it.ok[q] = item < n;
     it.dig[q] = it.ok[q] ? ops.digits[item / g.T] : 0u;
+  }
+}
+
+// Ghat applied to the whole fiber of this thread: out[q] = (Ghat v)[item_q], q < NL.
+// Coefficients of nodes other than the last are looked up once per fiber; those of the last
+// node depend only on q and are the same for every lane.
+template <typename R, int NL>
+__device__ __forceinline__ void apply_fiber(const KtGeom &g, const KtGenImage &im, const Smem &sm,
+                                            const typename C2<R>::T *__restrict__ v, int base, uint32_t fdig,
+                                            typename C2<R>::T Df, typename C2<R>::T (&out)[NL]) {
+  typedef typename C2<R>::T C;
+  const C *lv = (const C *)sm.loc_val;
+  const C *pv = (const C *)sm.pair_val;
+  const C *dg = (const C *)sm.diag;
+  const int last = g.n_nodes - 1;
+  const int T = g.T;
+#pragma unroll
+  for (int q = 0; q < NL; ++q) {
+    const C dq = dg[last * NL + q];
+    out[q] = cmul(mkc(Df.x + dq.x, Df.y + dq.y), v[base + q * T]);
+  }
+  // last node: row q of its factor
+#pragma unroll
+  for (int q = 0; q < NL; ++q) {
+    const int e0 = (last * NL + q) * g.S;
+    for (int s = 0; s < g.S; ++s) {
+      const int off = sm.loc_off[e0 + s];
+      if (off) out[q] = cfma(lv[e0 + s], v[base + q * T + off], out[q]);
+    }
+  }
+  // other nodes: one row per fiber
+  for (int i = 0; i < last; ++i) {
+    const int e0 = (i * NL + ((fdig >> (4 * i)) & 15)) * g.S;
+    for (int s = 0; s < g.S; ++s) {
+      const int off = sm.loc_off[e0 + s];
+      if (off) {
+        const C w = lv[e0 + s];
+#pragma unroll
+        for (int q = 0; q < NL; ++q) out[q] = cfma(w, v[base + q * T + off], out[q]);
+      }
+    }
+  }
+  // pair hops a_dst^dag a_src
+  for (int p = 0; p < g.n_pairs; ++p) {
+    const int pd = im.pair_dst[p], ps = im.pair_src[p];
+    const int pb = p * NL * NL;
+    if (pd != last && ps != last) {
+      const int e = pb + ((fdig >> (4 * pd)) & 15) * NL + ((fdig >> (4 * ps)) & 15);
+      const int off = sm.pair_off[e];
+      if (off) {
+        const C w = pv[e];
+#pragma unroll
+        for (int q = 0; q < NL; ++q) out[q] = cfma(w, v[base + q * T + off], out[q]);
+      }
+    } else if (pd == last) {
+      const int e0 = pb + ((fdig >> (4 * ps)) & 15);
+#pragma unroll
+      for (int q = 0; q < NL; ++q) {
+        const int off = sm.pair_off[e0 + q * NL];
+        if (off) out[q] = cfma(pv[e0 + q * NL], v[base + q * T + off], out[q]);
+      }
+    } else {
+      const int e0 = pb + ((fdig >> (4 * pd)) & 15) * NL;
+#pragma unroll
+      for (int q = 0; q < NL; ++q) {
+        const int off = sm.pair_off[e0 + q];
+        if (off) out[q] = cfma(pv[e0 + q], v[base + q * T + off], out[q]);
+      }
+    }
+  }
+}
+
+// Chebyshev sum in fiber mapping (see cheb_run).
+template <typename R, int NL>
+__device__ void cheb_run_fiber(const KtGeom &g, const KtGenImage &im, const Smem &sm, const Items<NL> &it, int K,
+                               typename C2<R>::T (&acc)[NL]) {
+  typedef typename C2<R>::T C;
+  C *A = (C *)sm.bufA;
+  C *B = (C *)sm.bufB;
+  const C *cf = (const C *)sm.coef;
+  const C *dg = (const C *)sm.diag;
+  const int tau = threadIdx.x % g.T;
+  const bool ok = it.ok[0];
+  const int base = it.item[0];
+  const uint32_t fdig = it.dig[0];
+  const int last = g.n_nodes - 1;
+  C Df = mkc((R)0, (R)0);
+  for (int i = 0; i < last; ++i) {
+    const C v = dg[i * NL + ((fdig >> (4 * i)) & 15)];
+    Df.x += v.x;
+    Df.y += v.y;
+  }
+  const C c0 = cf[tau];
+#pragma unroll
+  for (int q = 0; q < NL; ++q) acc[q] = ok ? cmul(c0, A[base + q * g.T]) : mkc((R)0, (R)0);
+  if (K == 1) { __syncthreads(); return; }
+  C t[NL];
+  if (ok) {
+    apply_fiber<R, NL>(g, im, sm, A, base, fdig, Df, t);
+    const C c1 = cf[g.T + tau];
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      B[base + q * g.T] = t[q];
+      acc[q] = cfma(c1, t[q], acc[q]);
+    }
+  }
+  __syncthreads();
+  C *P = A;   // holds T_{k-1}; receives T_{k+1}
+  C *Q = B;   // holds T_k
+  for (int k = 2; k < K; ++k) {
+    if (ok) {
+      const C a = cf[k * g.T + tau];
+      apply_fiber<R, NL>(g, im, sm, Q, base, fdig, Df, t);
+#pragma unroll
+      for (int q = 0; q < NL; ++q) {
+        const C old = P[base + q * g.T];
+        const C nv = mkc(t[q].x + t[q].x - old.x, t[q].y + t[q].y - old.y);
+        P[base + q * g.T] = nv;
+        acc[q] = cfma(a, nv, acc[q]);
+      }
+    }
+    __syncthreads();
+    C *tmp = P; P = Q; Q = tmp;
   }
 }
 
@@ -353,6 +491,13 @@ __device__ __forceinline__ typename C2<R>::T lind_item(const KtGeom &g, const Kt
   return out;
 }
 
+template <typename R, int EPT, int NL>
+__device__ __forceinline__ void cheb_dispatch(const KtGeom &g, const KtGenImage &im, const Smem &sm,
+                                              const Items<EPT> &it, int K, typename C2<R>::T (&acc)[EPT]) {
+  if constexpr (NL > 0) cheb_run_fiber<R, NL>(g, im, sm, it, K, acc);
+  else cheb_run<R, EPT>(g, im, sm, it, K, acc);
+}
+
 // --------------------------------------------------------------------------------------
 // Forward interval kernel.  One Chebyshev call site serves every phase:
 //   MAIN    full interval from psi(t_{j-1}) (uniform coefficients),
@@ -361,8 +506,8 @@ __device__ __forceinline__ typename C2<R>::T lind_item(const KtGeom &g, const Kt
 //   REST    the remainder of the interval from the collapsed state, tested again.
 enum { PH_MAIN = 0, PH_BISECT, PH_SSTAR, PH_REST, PH_DONE };
 
-template <typename R, int EPT>
-__global__ void __launch_bounds__(sizeof(R) == 8 ? 512 : 1024) fwd_kernel(KtGeom g, KtGenImage im, KtOps ops, FwdArgs a) {
+template <typename R, int EPT, int NL>
+__global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) fwd_kernel(KtGeom g, KtGenImage im, KtOps ops, FwdArgs a) {
   typedef typename C2<R>::T C;
   extern __shared__ __align__(16) char smem_raw[];
   Smem sm;
@@ -387,7 +532,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 512 : 1024) fwd_kernel(KtGeom
   __syncthreads();
   build_tables<R>(g, im, ops, sm, sm.eps, a.update != 0);
   Items<EPT> it;
-  load_items<EPT>(g, ops, it);
+  load_items<EPT, NL>(g, ops, it);
   C acc[EPT];
   C *A = (C *)sm.bufA;
 
@@ -428,7 +573,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 512 : 1024) fwd_kernel(KtGeom
     }
     load_tile<R, EPT>(g, it, phase == PH_MAIN ? psi_in : psi_out, A);
     __syncthreads();
-    cheb_run<R, EPT>(g, im, sm, it, g.K, acc);
+    cheb_dispatch<R, EPT, NL>(g, im, sm, it, g.K, acc);
     norms<R, EPT>(g, sm, it, acc);
 
     // ---- consume the result
@@ -676,8 +821,8 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 512 : 1024) fwd_kernel(KtGeom
 // Backward interval kernel: chi(t_{j-1}) = U_j^dag chi(t_j) along each trajectory's record.
 // Round rnd propagates piece rnd of the interval (backwards: dt - s_m, s_m - s_{m-1}, ..., s_1)
 // and then applies conj(c) L^dag of the jump that bounds it.  One Chebyshev call site.
-template <typename R, int EPT>
-__global__ void __launch_bounds__(sizeof(R) == 8 ? 512 : 1024) bwd_kernel(KtGeom g, KtGenImage im, KtOps ops, BwdArgs a) {
+template <typename R, int EPT, int NL>
+__global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) bwd_kernel(KtGeom g, KtGenImage im, KtOps ops, BwdArgs a) {
   typedef typename C2<R>::T C;
   extern __shared__ __align__(16) char smem_raw[];
   Smem sm;
@@ -708,7 +853,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 512 : 1024) bwd_kernel(KtGeom
     atomicMax(&sm.flag[0], nj);
   }
   Items<EPT> it;
-  load_items<EPT>(g, ops, it);
+  load_items<EPT, NL>(g, ops, it);
   C *A = (C *)sm.bufA;
   C *B = (C *)sm.bufB;
   load_tile<R, EPT>(g, it, chi_in, B);
@@ -733,7 +878,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 512 : 1024) bwd_kernel(KtGeom
     for (int q = 0; q < EPT; ++q)
       if (it.ok[q]) A[it.item[q]] = B[it.item[q]];
     __syncthreads();
-    cheb_run<R, EPT>(g, im, sm, it, g.K, acc);
+    cheb_dispatch<R, EPT, NL>(g, im, sm, it, g.K, acc);
     if (rnd == rounds) break;
 #pragma unroll
     for (int q = 0; q < EPT; ++q)

@@ -690,15 +690,24 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
   const int maxthr = P.fp64 ? 512 : 1024;
   if (cfg->tile_traj > 0 && ((cfg->tile_traj & (cfg->tile_traj - 1)) || cfg->tile_traj > 32))
     return fail(KT_ERR_ARG, "tile_traj must be a power of two <= 32");
+  // fiber mapping (one thread per run of n_loc elements along the last node) for the compiled
+  // local dimensions; otherwise the strided mapping with 4, 8 or 16 items per thread
+  const bool fiber = (nl == 6 || nl == 9);
+  const int fiber_max_threads = 768;
   int Tsel = 0;
-  // items per thread above 8 spill registers: use them only when nothing else fits
+  // strided mapping: items per thread above 8 spill registers, so only when nothing else fits
   const long long max_items = ((long long)d > 8LL * maxthr) ? 16LL * maxthr : 8LL * maxthr;
   for (int T = 32; T >= 1; T >>= 1) {
     if (cfg->tile_traj > 0 && T != cfg->tile_traj) continue;
     KtGeom t = g;
     t.T = T;
-    if ((long long)d * T > (cfg->tile_traj > 0 ? 16LL * maxthr : max_items)) continue;
-    t.nthreads = maxthr;
+    if (fiber) {
+      if ((long long)(d / nl) * T > fiber_max_threads) continue;
+      t.nthreads = ((d / nl) * T + 31) / 32 * 32;
+    } else {
+      if ((long long)d * T > (cfg->tile_traj > 0 ? 16LL * maxthr : max_items)) continue;
+      t.nthreads = maxthr;
+    }
     if (kt_smem_bytes(t, esz) > 227 * 1024) continue;
     Tsel = T;
     // prefer more tiles when the trajectories would not fill the GPU
@@ -710,11 +719,16 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
   g.n_tiles = (M + Tsel - 1) / Tsel;
   g.M_pad = g.n_tiles * Tsel;
   g.tile_elems = (d * Tsel + 3) / 4 * 4;
-  const int items = d * Tsel;
-  int ept = 4;
-  while ((items + ept - 1) / ept > maxthr) ept *= 2;
-  P.ept = ept;
-  g.nthreads = std::max(32, ((items + ept - 1) / ept + 31) / 32 * 32);
+  if (fiber) {
+    P.ept = -nl;                                  // launcher code of the fiber kernels
+    g.nthreads = std::max(32, ((d / nl) * Tsel + 31) / 32 * 32);
+  } else {
+    const int items = d * Tsel;
+    int ept = 4;
+    while ((items + ept - 1) / ept > maxthr) ept *= 2;
+    P.ept = ept;
+    g.nthreads = std::max(32, ((items + ept - 1) / ept + 31) / 32 * 32);
+  }
 
   // ---- generator tables (scaled by 1/r) for both directions
   auto build_image = [&](const Gen &gen, double cgen, HostImage &im) {
