@@ -99,6 +99,7 @@ struct KtGenImage {
   const int *pair_off;        // [P][n_loc*n_loc] element offset (in elements, before *T); 0 = none
   const KtCplx *pair_val;     // [P][n_loc*n_loc] scaled
   const KtCplx *cheb_full;    // [K] full-step coefficients, phase exp(-i c dt) folded in
+  const KtCplx *pair_coef;    // [P] scaled coefficient of pair term p (value = coef * a^dag a entries)
   int pair_dst[KT_MAX_PAIRS]; // node raised by pair term p of this direction
   int pair_src[KT_MAX_PAIRS]; // node lowered by pair term p of this direction
 };

@@ -63,6 +63,9 @@ struct Smem {
   int *tin;                   // per-trajectory ints [16][T]
   double *eps;                // [n_ctrl]
   int *flag;                  // [4] block flags
+  void *ldense;               // [n_loc][n_loc] last node's factor, dense (cavity-structure path)
+  void *lora;                 // [2][n_loc] ladder values a (row x) and a^dag (row x)
+  void *pcoef;                // [P] scaled pair coefficients
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -92,11 +95,15 @@ __host__ __device__ inline size_t carve(const KtGeom &g, int esz, char *base, Sm
   char *ti = take(sizeof(int) * 16 * g.T);
   char *ep = take(sizeof(double) * KT_MAX_CTRL);
   char *fl = take(sizeof(int) * 4);
+  char *ld = take((size_t)esz * g.n_loc * g.n_loc);
+  char *lr = take((size_t)esz * 2 * g.n_loc);
+  char *pc = take((size_t)esz * (g.n_pairs > 0 ? g.n_pairs : 1));
   if (s) {
     s->bufA = a; s->bufB = b; s->loc_off = (int *)lo; s->loc_val = lv; s->diag = dg;
     s->pair_off = (int *)po; s->pair_val = pv; s->hc_off = (int *)ho; s->hc_val = hv;
     s->coef = cf; s->red = (double *)rd; s->tsc = (double *)ts; s->tin = (int *)ti;
     s->eps = (double *)ep; s->flag = (int *)fl;
+    s->ldense = ld; s->lora = lr; s->pcoef = pc;
   }
   return align_up(off, 16);
 }
@@ -167,6 +174,24 @@ __device__ void build_tables(const KtGeom &g, const KtGenImage &im, const KtOps 
   for (int e = threadIdx.x; e < g.n_pairs * nl2; e += blockDim.x) {
     sm.pair_off[e] = im.pair_off[e] * g.T;
     pv[e] = from_kc<C>(im.pair_val[e]);
+  }
+  {
+    // last node's factor as a dense n_loc x n_loc table, ladder values, pair coefficients
+    C *ld = (C *)sm.ldense;
+    C *lr = (C *)sm.lora;
+    C *pc = (C *)sm.pcoef;
+    const int last = g.n_nodes - 1;
+    for (int e = threadIdx.x; e < g.n_loc * g.n_loc; e += blockDim.x) ld[e] = mkc((R)0, (R)0);
+    for (int e = threadIdx.x; e < g.n_loc; e += blockDim.x) {
+      lr[e] = from_kc<C>(ops.lo_val[e]);
+      lr[g.n_loc + e] = from_kc<C>(ops.ra_val[e]);
+    }
+    for (int e = threadIdx.x; e < g.n_pairs; e += blockDim.x) pc[e] = from_kc<C>(im.pair_coef[e]);
+    __syncthreads();
+    for (int e = threadIdx.x; e < g.n_loc * g.S; e += blockDim.x) {
+      const int idx = last * nls + e, x = e / g.S, dl = im.loc_dl[idx];
+      if (dl) ld[x * g.n_loc + x + dl] = lv[idx];
+    }
   }
   if (with_hc) {
     C *hv = (C *)sm.hc_val;
@@ -491,10 +516,164 @@ __device__ __forceinline__ typename C2<R>::T lind_item(const KtGeom &g, const Kt
   return out;
 }
 
-template <typename R, int EPT, int NL>
+// --------------------------------------------------------------------------------------
+// Cavity-structure fast path.  Valid when every node is a three-level atom {g, e, r} times a
+// cavity with photon numbers 0..NC (local index atom * (NC+1) + n), the ladder factor is the
+// cavity annihilation operator, and the last node's factor couples only (r, n-1) <-> (g, n)
+// (cavity) and (r, n) <-> (e, n) (drive) besides its diagonal -- the node of Sec. 3.1.  Then
+// every coupling inside a thread's fiber (which runs over the last node) has a position known
+// at compile time: the fiber's own T_k stays in registers and the last node's factor and the
+// pair hops that raise or lower its photon number become register-indexed FMAs.
+template <typename R, int NC>
+__device__ __forceinline__ void apply_acs(const KtGeom &g, const KtGenImage &im, const Smem &sm,
+                                          const typename C2<R>::T *__restrict__ v, int base, uint32_t fdig,
+                                          typename C2<R>::T Df, const typename C2<R>::T (&vk)[3 * (NC + 1)],
+                                          typename C2<R>::T (&out)[3 * (NC + 1)]) {
+  typedef typename C2<R>::T C;
+  constexpr int NP = NC + 1, NL = 3 * NP;
+  const C *lv = (const C *)sm.loc_val;
+  const C *pv = (const C *)sm.pair_val;
+  const C *dg = (const C *)sm.diag;
+  const C *ld = (const C *)sm.ldense;
+  const C *lo = (const C *)sm.lora;
+  const C *ra = lo + NL;
+  const C *pc = (const C *)sm.pcoef;
+  const int last = g.n_nodes - 1;
+  const int T = g.T;
+#pragma unroll
+  for (int q = 0; q < NL; ++q) {
+    const C dq = dg[last * NL + q];
+    out[q] = cmul(mkc(Df.x + dq.x, Df.y + dq.y), vk[q]);
+  }
+  // last node: cavity (r, n-1) <-> (g, n) and drive (r, n) <-> (e, n)
+#pragma unroll
+  for (int n = 1; n <= NC; ++n) {
+    const int qr = 2 * NP + n - 1, qg = n;
+    out[qr] = cfma(ld[qr * NL + qg], vk[qg], out[qr]);
+    out[qg] = cfma(ld[qg * NL + qr], vk[qr], out[qg]);
+  }
+#pragma unroll
+  for (int n = 0; n <= NC; ++n) {
+    const int qr = 2 * NP + n, qe = NP + n;
+    out[qr] = cfma(ld[qr * NL + qe], vk[qe], out[qr]);
+    out[qe] = cfma(ld[qe * NL + qr], vk[qr], out[qe]);
+  }
+  // other nodes: one row per fiber, each entry one neighbouring fiber
+  for (int i = 0; i < last; ++i) {
+    const int e0 = (i * NL + ((fdig >> (4 * i)) & 15)) * g.S;
+    for (int s = 0; s < g.S; ++s) {
+      const int off = sm.loc_off[e0 + s];
+      if (off) {
+        const C w = lv[e0 + s];
+#pragma unroll
+        for (int q = 0; q < NL; ++q) out[q] = cfma(w, v[base + off + q * T], out[q]);
+      }
+    }
+  }
+  // pair hops coef a_dst^dag a_src
+  for (int p = 0; p < g.n_pairs; ++p) {
+    const int pd = im.pair_dst[p], ps = im.pair_src[p];
+    if (pd != last && ps != last) {
+      const int e = p * NL * NL + ((fdig >> (4 * pd)) & 15) * NL + ((fdig >> (4 * ps)) & 15);
+      const int off = sm.pair_off[e];
+      if (off) {
+        const C w = pv[e];
+#pragma unroll
+        for (int q = 0; q < NL; ++q) out[q] = cfma(w, v[base + off + q * T], out[q]);
+      }
+    } else if (pd == last) {
+      // raise the last node (q <- q-1, n_q >= 1), lower node ps (x_s -> x_s + 1, n_s < NC)
+      const int xs = (fdig >> (4 * ps)) & 15;
+      if (xs % NP < NC) {
+        const int off = g.stride[ps] * T;
+        const C cf = cmul(pc[p], lo[xs]);
+#pragma unroll
+        for (int q = 0; q < NL; ++q) {
+          if (q % NP == 0) continue;
+          out[q] = cfma(cmul(cf, ra[q]), v[base + off + (q - 1) * T], out[q]);
+        }
+      }
+    } else {
+      // lower the last node (q <- q+1, n_q < NC), raise node pd (x_d -> x_d - 1, n_d >= 1)
+      const int xd = (fdig >> (4 * pd)) & 15;
+      if (xd % NP >= 1) {
+        const int off = -g.stride[pd] * T;
+        const C cf = cmul(pc[p], ra[xd]);
+#pragma unroll
+        for (int q = 0; q < NL; ++q) {
+          if (q % NP == NC) continue;
+          out[q] = cfma(cmul(cf, lo[q]), v[base + off + (q + 1) * T], out[q]);
+        }
+      }
+    }
+  }
+}
+
+template <typename R, int NC>
+__device__ void cheb_run_acs(const KtGeom &g, const KtGenImage &im, const Smem &sm, const Items<3 * (NC + 1)> &it,
+                             int K, typename C2<R>::T (&acc)[3 * (NC + 1)]) {
+  typedef typename C2<R>::T C;
+  constexpr int NL = 3 * (NC + 1);
+  C *A = (C *)sm.bufA;
+  C *B = (C *)sm.bufB;
+  const C *cf = (const C *)sm.coef;
+  const C *dg = (const C *)sm.diag;
+  const int tau = threadIdx.x % g.T;
+  const bool ok = it.ok[0];
+  const int base = it.item[0];
+  const uint32_t fdig = it.dig[0];
+  const int last = g.n_nodes - 1;
+  C Df = mkc((R)0, (R)0);
+  for (int i = 0; i < last; ++i) {
+    const C v = dg[i * NL + ((fdig >> (4 * i)) & 15)];
+    Df.x += v.x;
+    Df.y += v.y;
+  }
+  C vk[NL];
+  const C c0 = cf[tau];
+#pragma unroll
+  for (int q = 0; q < NL; ++q) {
+    vk[q] = ok ? A[base + q * g.T] : mkc((R)0, (R)0);
+    acc[q] = cmul(c0, vk[q]);
+  }
+  if (K == 1) { __syncthreads(); return; }
+  C t[NL];
+  if (ok) {
+    apply_acs<R, NC>(g, im, sm, A, base, fdig, Df, vk, t);
+    const C c1 = cf[g.T + tau];
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      B[base + q * g.T] = t[q];
+      acc[q] = cfma(c1, t[q], acc[q]);
+      vk[q] = t[q];
+    }
+  }
+  __syncthreads();
+  C *P = A;   // holds T_{k-1}; receives T_{k+1}
+  C *Q = B;   // holds T_k (this thread's fiber also in vk)
+  for (int k = 2; k < K; ++k) {
+    if (ok) {
+      const C a = cf[k * g.T + tau];
+      apply_acs<R, NC>(g, im, sm, Q, base, fdig, Df, vk, t);
+#pragma unroll
+      for (int q = 0; q < NL; ++q) {
+        const C old = P[base + q * g.T];
+        const C nv = mkc(t[q].x + t[q].x - old.x, t[q].y + t[q].y - old.y);
+        P[base + q * g.T] = nv;
+        acc[q] = cfma(a, nv, acc[q]);
+        vk[q] = nv;
+      }
+    }
+    __syncthreads();
+    C *tmp = P; P = Q; Q = tmp;
+  }
+}
+
+template <typename R, int EPT, int NL, int ACS>
 __device__ __forceinline__ void cheb_dispatch(const KtGeom &g, const KtGenImage &im, const Smem &sm,
                                               const Items<EPT> &it, int K, typename C2<R>::T (&acc)[EPT]) {
-  if constexpr (NL > 0) cheb_run_fiber<R, NL>(g, im, sm, it, K, acc);
+  if constexpr (ACS) cheb_run_acs<R, NL / 3 - 1>(g, im, sm, it, K, acc);
+  else if constexpr (NL > 0) cheb_run_fiber<R, NL>(g, im, sm, it, K, acc);
   else cheb_run<R, EPT>(g, im, sm, it, K, acc);
 }
 
@@ -506,7 +685,7 @@ __device__ __forceinline__ void cheb_dispatch(const KtGeom &g, const KtGenImage 
 //   REST    the remainder of the interval from the collapsed state, tested again.
 enum { PH_MAIN = 0, PH_BISECT, PH_SSTAR, PH_REST, PH_DONE };
 
-template <typename R, int EPT, int NL>
+template <typename R, int EPT, int NL, int ACS>
 __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) fwd_kernel(KtGeom g, KtGenImage im, KtOps ops, FwdArgs a) {
   typedef typename C2<R>::T C;
   extern __shared__ __align__(16) char smem_raw[];
@@ -573,7 +752,7 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
     }
     load_tile<R, EPT>(g, it, phase == PH_MAIN ? psi_in : psi_out, A);
     __syncthreads();
-    cheb_dispatch<R, EPT, NL>(g, im, sm, it, g.K, acc);
+    cheb_dispatch<R, EPT, NL, ACS>(g, im, sm, it, g.K, acc);
     norms<R, EPT>(g, sm, it, acc);
 
     // ---- consume the result
@@ -821,7 +1000,7 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
 // Backward interval kernel: chi(t_{j-1}) = U_j^dag chi(t_j) along each trajectory's record.
 // Round rnd propagates piece rnd of the interval (backwards: dt - s_m, s_m - s_{m-1}, ..., s_1)
 // and then applies conj(c) L^dag of the jump that bounds it.  One Chebyshev call site.
-template <typename R, int EPT, int NL>
+template <typename R, int EPT, int NL, int ACS>
 __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) bwd_kernel(KtGeom g, KtGenImage im, KtOps ops, BwdArgs a) {
   typedef typename C2<R>::T C;
   extern __shared__ __align__(16) char smem_raw[];
@@ -878,7 +1057,7 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
     for (int q = 0; q < EPT; ++q)
       if (it.ok[q]) A[it.item[q]] = B[it.item[q]];
     __syncthreads();
-    cheb_dispatch<R, EPT, NL>(g, im, sm, it, g.K, acc);
+    cheb_dispatch<R, EPT, NL, ACS>(g, im, sm, it, g.K, acc);
     if (rnd == rounds) break;
 #pragma unroll
     for (int q = 0; q < EPT; ++q)

@@ -3,16 +3,16 @@
 #include "kt_device.cuh"
 
 namespace kt {
-template <typename R, int EPT, int NL>
+template <typename R, int EPT, int NL, int ACS>
 static cudaError_t launch_fwd_t(const KtGeom &g, const KtGenImage &im, const KtOps &ops, const FwdArgs &a, size_t smem,
                                 cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(fwd_kernel<R, EPT, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(fwd_kernel<R, EPT, NL, ACS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  fwd_kernel<R, EPT, NL><<<g.n_tiles, g.nthreads, smem, st>>>(g, im, ops, a);
+  fwd_kernel<R, EPT, NL, ACS><<<g.n_tiles, g.nthreads, smem, st>>>(g, im, ops, a);
   return cudaGetLastError();
 }
 }  // namespace kt
@@ -20,11 +20,13 @@ static cudaError_t launch_fwd_t(const KtGeom &g, const KtGenImage &im, const KtO
 cudaError_t kt_launch_fwd_f32(int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops, const FwdArgs &a,
                              size_t smem, cudaStream_t st) {
   switch (ept) {
-    case 4: return kt::launch_fwd_t<float, 4, 0>(g, im, ops, a, smem, st);
-    case 8: return kt::launch_fwd_t<float, 8, 0>(g, im, ops, a, smem, st);
-    case 16: return kt::launch_fwd_t<float, 16, 0>(g, im, ops, a, smem, st);
-    case -6: return kt::launch_fwd_t<float, 6, 6>(g, im, ops, a, smem, st);   // fiber mapping, n_loc = 6
-    case -9: return kt::launch_fwd_t<float, 9, 9>(g, im, ops, a, smem, st);   // fiber mapping, n_loc = 9
+    case 4: return kt::launch_fwd_t<float, 4, 0, 0>(g, im, ops, a, smem, st);
+    case 8: return kt::launch_fwd_t<float, 8, 0, 0>(g, im, ops, a, smem, st);
+    case 16: return kt::launch_fwd_t<float, 16, 0, 0>(g, im, ops, a, smem, st);
+    case -6: return kt::launch_fwd_t<float, 6, 6, 0>(g, im, ops, a, smem, st);   // fiber mapping, n_loc = 6
+    case -9: return kt::launch_fwd_t<float, 9, 9, 0>(g, im, ops, a, smem, st);   // fiber mapping, n_loc = 9
+    case -106: return kt::launch_fwd_t<float, 6, 6, 1>(g, im, ops, a, smem, st);  // cavity structure, cutoff 1
+    case -109: return kt::launch_fwd_t<float, 9, 9, 1>(g, im, ops, a, smem, st);  // cavity structure, cutoff 2
   }
   return cudaErrorInvalidValue;
 }

@@ -496,7 +496,7 @@ namespace {
 // Everything krotov_init computes on the host, before any device call.
 struct HostImage {
   std::vector<int> dl, poff;
-  std::vector<KtCplx> base, cslot, dg, cdg, pval, cf;
+  std::vector<KtCplx> base, cslot, dg, cdg, pval, cf, pc;
   int pdst[KT_MAX_PAIRS], psrc[KT_MAX_PAIRS];
 };
 
@@ -509,6 +509,41 @@ struct HostPlan {
   std::vector<KtCplx> lo_val, ra_val, lind, hc_val, tgt;
   std::vector<uint32_t> digits;
 };
+
+// True when the model has the node structure of the cascaded atom-cavity network (Sec. 3.1):
+// local index atom * (nc+1) + n with atom in {g, e, r}, the ladder factor the cavity
+// annihilation operator, and the last node's factor (both directions, drift and controls)
+// coupling only (r, n-1) <-> (g, n) and (r, n) <-> (e, n) off the diagonal.  The kernels then
+// take the cavity-structure fast path.
+bool cavity_structure(const Gen &gf, const Gen &gb, const std::vector<int> &lo_dl, const std::vector<cd> &lo_val,
+                      const std::vector<int> &ra_dl, const std::vector<cd> &ra_val) {
+  const int nl = gf.nl;
+  if (nl != 6 && nl != 9) return false;
+  const int NP = nl / 3, NC = NP - 1;
+  for (int x = 0; x < nl; ++x) {
+    const int n = x % NP;
+    if ((lo_val[x] != 0.0) != (n < NC) || (n < NC && lo_dl[x] != 1)) return false;
+    if ((ra_val[x] != 0.0) != (n >= 1) || (n >= 1 && ra_dl[x] != -1)) return false;
+  }
+  auto allowed = [&](int x, int y) {
+    const int ax = x / NP, nx = x % NP, ay = y / NP, ny = y % NP;
+    if (((ax == 1 && ay == 2) || (ax == 2 && ay == 1)) && nx == ny) return true;   // drive e <-> r
+    if (ax == 2 && ay == 0 && ny == nx + 1) return true;                           // cavity (r,n-1) <- (g,n)
+    if (ax == 0 && ay == 2 && nx == ny + 1) return true;                           // cavity (g,n) <- (r,n-1)
+    return false;
+  };
+  const int last = gf.N - 1;
+  auto check = [&](const std::vector<cd> &m, size_t base) {
+    for (int x = 0; x < nl; ++x)
+      for (int y = 0; y < nl; ++y)
+        if (x != y && m[base + x * nl + y] != 0.0 && !allowed(x, y)) return false;
+    return true;
+  };
+  if (!check(gf.loc, (size_t)last * nl * nl) || !check(gb.loc, (size_t)last * nl * nl)) return false;
+  for (size_t c = 0; c < gf.ctrl_node.size(); ++c)
+    if (gf.ctrl_node[c] == last && (!check(gf.ctrl, c * nl * nl) || !check(gb.ctrl, c * nl * nl))) return false;
+  return true;
+}
 
 // Validation, a1 (structured H_eff = H - (i/2) sum_l L_l^dag L_l), a2 (spectral interval and
 // Chebyshev length), tile geometry and the scaled generator tables of both directions.
@@ -720,7 +755,7 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
   g.M_pad = g.n_tiles * Tsel;
   g.tile_elems = (d * Tsel + 3) / 4 * 4;
   if (fiber) {
-    P.ept = -nl;                                  // launcher code of the fiber kernels
+    P.ept = cavity_structure(gf, gb, lo_dl, lo_val, ra_dl, ra_val) ? -(100 + nl) : -nl;   // launcher codes
     g.nthreads = std::max(32, ((d / nl) * Tsel + 31) / 32 * 32);
   } else {
     const int items = d * Tsel;
@@ -764,12 +799,14 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
       }
     }
     const int nl2 = nl * nl;
+    im.pc.assign((size_t)std::max(1, g.n_pairs), KtCplx{0, 0});
     im.poff.assign((size_t)g.n_pairs * nl2, 0);
     im.pval.assign((size_t)g.n_pairs * nl2, KtCplx{0, 0});
     for (int q = 0; q < g.n_pairs; ++q) {
       const Pair &pr = gen.pairs[q];
       im.pdst[q] = pr.dst;
       im.psrc[q] = pr.src;
+      im.pc[q] = KtCplx{(pr.coef / r).real(), (pr.coef / r).imag()};
       for (int xd = 0; xd < nl; ++xd)
         for (int xs = 0; xs < nl; ++xs) {
           if (ra_val[xd] == 0.0 || lo_val[xs] == 0.0) continue;
@@ -835,6 +872,7 @@ kt_status upload_image(kt_problem *p, const HostImage &h, KtGenImage &im, cudaSt
   if ((t = upload(p, (int **)&im.pair_off, h.poff.data(), h.poff.size(), st)) != KT_OK) return t;
   if ((t = upload(p, (KtCplx **)&im.pair_val, h.pval.data(), h.pval.size(), st)) != KT_OK) return t;
   if ((t = upload(p, (KtCplx **)&im.cheb_full, h.cf.data(), h.cf.size(), st)) != KT_OK) return t;
+  if ((t = upload(p, (KtCplx **)&im.pair_coef, h.pc.data(), h.pc.size(), st)) != KT_OK) return t;
   for (int q = 0; q < KT_MAX_PAIRS; ++q) {
     im.pair_dst[q] = h.pdst[q];
     im.pair_src[q] = h.psrc[q];
