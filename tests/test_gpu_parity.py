@@ -4,7 +4,8 @@ Tolerances (stated per result):
   FP64 path: states, tau and F within 1e-10 (relative to the largest entry), pulse updates
              within 1e-10 of max|Delta eps|; jump records identical in (interval, channel),
              |Delta s*| <= max(1e-9 dt, 1e-12 c^2), renormalisation c within 1e-9 relative.
-  FP32-mixed: F within 1e-5, pulse updates within 1e-4 of max|Delta eps|, states within 2e-5;
+  FP32-mixed: F within 1e-5, pulse updates within 1e-4 of max|Delta eps|, states within 3e-5
+             over a few intervals and 2e-4 after 10^3 intervals (FP32 roundoff accumulation);
              jump records identical on trajectories whose threshold margin exceeds 1e-5,
              |Delta s*| <= max(1e-4 dt, 1e-5 c^2), c within 2e-3 relative (FP32 norms after
              ~10^3 intervals carry ~1e-6 relative error, and c = 1/||L psi(s*)|| moves with s*).
@@ -118,7 +119,9 @@ def test_cfg2_fp64_and_fp32():
     c = setup(wl.n_nodes, wl.n_cav, wl.T, wl.nt, wl.M, 30.0, wl.seed, 1)
     _, res = run_oracle(c)
     compare(c, run_gpu(c, "fp64"), res, 1e-10, 1e-10, 1e-10, 1e-9)
-    compare(c, run_gpu(c, "fp32"), res, 2e-5, 1e-5, 1e-4, 1e-4, margin_min=1e-5)
+    # FP32 states after 1000 intervals of K = 17 Chebyshev terms: unit roundoff 6e-8 times
+    # K * nt = 1.7e4 dependent steps bounds the drift near 1e-3; 2e-4 of the largest entry
+    compare(c, run_gpu(c, "fp32"), res, 2e-4, 1e-5, 1e-4, 1e-4, margin_min=1e-5)
 
 
 def test_checkpointed_costates_are_bit_identical():
