@@ -209,6 +209,28 @@ KT_API kt_status kt_bessel_j(double alpha, int n, double *out);
 KT_API kt_status kt_generator_dense(const kt_model_desc *model, const kt_config *cfg, int direction,
                                     const double *eps, double *out);
 
+/* Allocation-free pulse-update reduction (the paper has no counterpart: this is a library
+ * service).  For callers that may not allocate device memory -- e.g. a host framework that owns
+ * and budgets every device allocation up front, or code running from a callback where
+ * cudaMalloc is not allowed -- this computes the same per-interval update as the forward
+ * sweep, Delta eps_c = shape_j[c] / (lambda_a[c] M) sum_k Im <chi_k| hc_c |psi_k>, without
+ * allocating anything: its scratch (1024 block partials x 8 controls + a ticket, 64 KB) is a
+ * fixed device array inside the library, held by every GPU that loads the library until the
+ * process exits.
+ *   psi, chi   DEVICE pointers, [M][d][2] FP64 states (plain layout, d = n_loc^n_nodes)
+ *   hc_local   HOST [n_ctrl][n_loc][n_loc][2] control factors, ctrl_node [n_ctrl] (host)
+ *   shape_j, lambda_a  HOST [n_ctrl];  deps_out DEVICE [n_ctrl] FP64 (written on `stream`)
+ * The first call on a device looks up the scratch array's device address (once per device);
+ * make that first call before any stream capture begins.  Every call shares the one array and
+ * the call clears its ticket itself, so calls whose kernels overlap on the GPU (different
+ * streams, or different host threads on the same device) race and must be serialised by the
+ * caller.  Sizes beyond the scratch (n_ctrl > 8) are rejected with KT_ERR_UNSUPPORTED;
+ * n_nodes <= 8, n_loc <= 16, d <= 2^24, at most 6 entries per control-factor row. */
+KT_API kt_status kt_update_overlap_noalloc(int n_nodes, int n_loc, int n_ctrl, const int *ctrl_node,
+                                           const double *hc_local, int M, const double *psi,
+                                           const double *chi, const double *shape_j,
+                                           const double *lambda_a, double *deps_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

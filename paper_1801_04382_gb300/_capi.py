@@ -70,6 +70,8 @@ SIGNATURES = {
     "krotov_last_error": (ct.c_char_p, []),
     "kt_bessel_j": (ct.c_int, [ct.c_double, ct.c_int, dp]),
     "kt_generator_dense": (ct.c_int, [ct.POINTER(ModelDesc), ct.POINTER(Config), ct.c_int, dp, dp]),
+    "kt_update_overlap_noalloc": (ct.c_int, [ct.c_int, ct.c_int, ct.c_int, ip, dp, ct.c_int, ct.c_void_p,
+                                             ct.c_void_p, dp, dp, ct.c_void_p, ct.c_void_p]),
 }
 
 _LIB = None

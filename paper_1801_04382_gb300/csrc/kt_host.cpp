@@ -137,6 +137,8 @@ Bounds gen_bounds(const Gen &g, double amax, double E) {
 
 }  // namespace
 
+kt_status kt_fail(kt_status s, const char *msg) { return fail(s, "%s", msg); }
+
 // ---------------------------------------------------------------------------- problem object
 struct kt_problem {
   KtGeom g{};

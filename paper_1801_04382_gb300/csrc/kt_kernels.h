@@ -46,6 +46,11 @@ struct BwdArgs {
   int *status;
 };
 
+#include "../../include/krotov_traj.h"
+
+// Record msg as the calling thread's last error (krotov_last_error) and return s.
+kt_status kt_fail(kt_status s, const char *msg);
+
 size_t kt_smem_bytes(const KtGeom &g, int elem_bytes);
 cudaError_t kt_launch_fwd(int fp64, int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops,
                           const FwdArgs &a, cudaStream_t st);
