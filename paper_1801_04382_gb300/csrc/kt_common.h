@@ -33,6 +33,7 @@
 #define KT_DEV_RECORD_FULL 6
 #define KT_DEV_RANGE 8
 #define KT_DEV_ZERO_JUMP 9
+#define KT_DEV_TIMEOUT 4
 
 // Chebyshev expansion of exp(-i G s) with G = c + r * Ghat (Ghat's spectrum in an ellipse
 // around [-1, 1]):  exp(-i G s) = exp(-i c s) sum_k (2 - delta_k0) (-i)^k J_k(r s) T_k(Ghat).
@@ -82,6 +83,7 @@ struct KtGeom {
   int S, SH, n_pairs, n_ctrl, n_lind;
   int K;                             // Chebyshev terms of a full step
   int max_jumps, draws;              // jump cap and uniforms per trajectory and pass
+  int prefetch_chi;                  // forward kernel keeps a third tile buffer for chi(t_j)
   int stride[KT_MAX_NODES];          // element stride of node i (n_loc^(N-1-i))
   int ctrl_node[KT_MAX_CTRL];
   double lam[KT_MAX_CTRL];

@@ -46,10 +46,73 @@ __device__ __forceinline__ void set_status(int *status, int code) {
   atomicCAS(status, KT_DEV_OK, code);
 }
 
+// ---- bulk (TMA) copies between global and shared memory, completing on an mbarrier -------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// one thread: arm the barrier for `bytes` and start the copy global -> shared
+// (addresses 16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_load(void *dst_smem, const void *src_gmem, uint32_t bytes,
+                                          unsigned long long *bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst_smem)), "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// wait (one thread) for phase `phase` of the barrier, giving up after ~2 s of clock
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, uint32_t phase) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, phase))
+    if (clock64() - t0 > 4000000000LL) return false;
+  return true;
+}
+
+// one thread: copy shared -> global (16-byte aligned, size a multiple of 16) as one bulk group
+__device__ __forceinline__ void bulk_store(void *dst_gmem, const void *src_smem, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst_gmem), "r"(smem_u32(src_smem)),
+               "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_store_wait() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Whole-tile load by the bulk engine: thread 0 waits (bounded) and the block learns the outcome.
+// On a timeout the status word gets KT_DEV_TIMEOUT and false is returned to every thread.
+__device__ __forceinline__ bool tile_wait(unsigned long long *bar, uint32_t phase, int *flag_slot, int *status) {
+  if (threadIdx.x == 0) {
+    bool ok = mbar_wait_bounded(bar, phase);
+    if (!ok) {
+      set_status(status, KT_DEV_TIMEOUT);
+      mbar_wait_bounded(bar, phase);   // give the copy in flight a second bounded chance to land
+    }
+    *flag_slot = ok ? 1 : 0;
+  }
+  __syncthreads();
+  return *flag_slot != 0;
+}
+
 // --------------------------------------------------------------------------------------
 // Shared-memory carve-up (identical on host and device; see kt_smem_bytes).
 struct Smem {
-  void *bufA, *bufB;          // [d*T] complex each
+  void *bufA, *bufB;          // [tile_elems] complex each
+  void *bufC;                 // [tile_elems] prefetched chi(t_j) (forward kernel, when it fits)
+  unsigned long long *mbar;   // [2] transaction barriers of the bulk copies
   int *loc_off;               // [N*n_loc*S]  element offset * T (0 = no entry)
   void *loc_val;              // [N*n_loc*S]
   void *diag;                 // [N*n_loc]
@@ -62,7 +125,7 @@ struct Smem {
   double *tsc;                // per-trajectory scalars [16][T]
   int *tin;                   // per-trajectory ints [16][T]
   double *eps;                // [n_ctrl]
-  int *flag;                  // [4] block flags
+  int *flag;                  // [8] block flags
   void *ldense;               // [n_loc][n_loc] last node's factor, dense (cavity-structure path)
   void *lora;                 // [2][n_loc] ladder values a (row x) and a^dag (row x)
   void *pcoef;                // [P] scaled pair coefficients
@@ -70,7 +133,7 @@ struct Smem {
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline size_t carve(const KtGeom &g, int esz, char *base, Smem *s) {
+__host__ __device__ inline size_t carve(const KtGeom &g, int esz, char *base, Smem *s, bool with_c) {
   const int nl2 = g.n_loc * g.n_loc;
   const int nwarps = g.nthreads / 32;
   size_t off = 0;
@@ -80,8 +143,10 @@ __host__ __device__ inline size_t carve(const KtGeom &g, int esz, char *base, Sm
     off += bytes;
     return p;
   };
-  const size_t tile = (size_t)g.d * g.T * esz;
+  const size_t tile = (size_t)g.tile_elems * esz;
   char *a = take(tile), *b = take(tile);
+  char *cbuf = with_c ? take(tile) : nullptr;
+  char *mb = take(2 * sizeof(unsigned long long));
   char *lo = take(sizeof(int) * g.n_nodes * g.n_loc * g.S);
   char *lv = take((size_t)esz * g.n_nodes * g.n_loc * g.S);
   char *dg = take((size_t)esz * g.n_nodes * g.n_loc);
@@ -94,12 +159,12 @@ __host__ __device__ inline size_t carve(const KtGeom &g, int esz, char *base, Sm
   char *ts = take(sizeof(double) * 16 * g.T);
   char *ti = take(sizeof(int) * 16 * g.T);
   char *ep = take(sizeof(double) * KT_MAX_CTRL);
-  char *fl = take(sizeof(int) * 4);
+  char *fl = take(sizeof(int) * 8);
   char *ld = take((size_t)esz * g.n_loc * g.n_loc);
   char *lr = take((size_t)esz * 2 * g.n_loc);
   char *pc = take((size_t)esz * (g.n_pairs > 0 ? g.n_pairs : 1));
   if (s) {
-    s->bufA = a; s->bufB = b; s->loc_off = (int *)lo; s->loc_val = lv; s->diag = dg;
+    s->bufA = a; s->bufB = b; s->bufC = cbuf; s->mbar = (unsigned long long *)mb; s->loc_off = (int *)lo; s->loc_val = lv; s->diag = dg;
     s->pair_off = (int *)po; s->pair_val = pv; s->hc_off = (int *)ho; s->hc_val = hv;
     s->coef = cf; s->red = (double *)rd; s->tsc = (double *)ts; s->tin = (int *)ti;
     s->eps = (double *)ep; s->flag = (int *)fl;
@@ -690,7 +755,7 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
   typedef typename C2<R>::T C;
   extern __shared__ __align__(16) char smem_raw[];
   Smem sm;
-  carve(g, sizeof(C), smem_raw, &sm);
+  carve(g, sizeof(C), smem_raw, &sm, g.prefetch_chi != 0);
   const int tile = blockIdx.x;
   const int tau = threadIdx.x % g.T;
   const C *psi_in = (const C *)a.psi_in + (size_t)tile * g.tile_elems;
@@ -707,21 +772,37 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
     }
     sm.eps[c] = e;
   }
-  if (threadIdx.x < 4) sm.flag[threadIdx.x] = 0;
+  if (threadIdx.x < 8) sm.flag[threadIdx.x] = 0;
+  if (threadIdx.x == 0) {
+    mbar_init(&sm.mbar[0], 1);
+    mbar_init(&sm.mbar[1], 1);
+    fence_mbar_init();
+  }
   __syncthreads();
+  C *A = (C *)sm.bufA;
+  C *B = (C *)sm.bufB;
+  const uint32_t tile_bytes = (uint32_t)(g.tile_elems * sizeof(C));
+  const bool need_chi = a.update && j < a.nt;
+  const C *chi_g = need_chi ? (const C *)a.chi_t + (size_t)tile * g.tile_elems : nullptr;
+  // the bulk engine brings psi(t_{j-1}) (and chi(t_j) when there is room) while the tables are built
+  if (threadIdx.x == 0) {
+    bulk_load(A, psi_in, tile_bytes, &sm.mbar[0]);
+    if (need_chi && g.prefetch_chi) bulk_load(sm.bufC, chi_g, tile_bytes, &sm.mbar[1]);
+  }
   build_tables<R>(g, im, ops, sm, sm.eps, a.update != 0);
   Items<EPT> it;
   load_items<EPT, NL>(g, ops, it);
   C acc[EPT];
-  C *A = (C *)sm.bufA;
+  if (!tile_wait(&sm.mbar[0], 0, &sm.flag[4], a.status)) {
+    if (threadIdx.x == 0 && need_chi && g.prefetch_chi) mbar_wait_bounded(&sm.mbar[1], 0);
+    return;
+  }
+  bool jumped = false, stored = false;
 
   int phase = (j >= 1) ? PH_MAIN : PH_DONE;
   if (phase == PH_DONE) {
-    load_tile<R, EPT>(g, it, psi_in, A);
-    __syncthreads();
 #pragma unroll
     for (int q = 0; q < EPT; ++q) acc[q] = it.ok[q] ? A[it.item[q]] : mkc((R)0, (R)0);
-    __syncthreads();
   }
   int guard = 0;
   while (phase != PH_DONE) {
@@ -750,7 +831,7 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
       else len = act ? g.dt - sm.tsc[TS_S0 * g.T + t] : 0.0;
       tau_coefs<R>(g, sm, t, g.c_fwd, len);
     }
-    load_tile<R, EPT>(g, it, phase == PH_MAIN ? psi_in : psi_out, A);
+    if (phase != PH_MAIN) load_tile<R, EPT>(g, it, psi_out, A);   // the main round's tile came by bulk copy
     __syncthreads();
     cheb_dispatch<R, EPT, NL, ACS>(g, im, sm, it, g.K, acc);
     norms<R, EPT>(g, sm, it, acc);
@@ -759,7 +840,7 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
     if (phase == PH_MAIN) {
 #pragma unroll
       for (int q = 0; q < EPT; ++q)
-        if (it.ok[q]) psi_out[it.item[q]] = acc[q];
+        if (it.ok[q]) A[it.item[q]] = acc[q];
       if (threadIdx.x < g.T) {
         const int t = threadIdx.x, k = tile * g.T + t;
         const double nrm = sm.tsc[TS_NRM * g.T + t];
@@ -776,7 +857,11 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
       }
       __syncthreads();
       if (sm.flag[0] == 0) break;
-      // flagged trajectories restart from psi(t_{j-1}), kept in psi_out
+      // a jump: the tile's results go to psi_out now (coalesced), and flagged trajectories
+      // restart from psi(t_{j-1}), kept in psi_out
+      jumped = true;
+      for (int e = threadIdx.x; e < g.d * g.T; e += blockDim.x) psi_out[e] = A[e];
+      __syncthreads();
 #pragma unroll
       for (int q = 0; q < EPT; ++q)
         if (it.ok[q] && sm.tin[TI_ACT * g.T + tau]) psi_out[it.item[q]] = psi_in[it.item[q]];
@@ -911,6 +996,14 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
     }
   }
 
+  if (j >= 1 && !jumped) {
+    // psi(t_j) of the whole tile is in A: one bulk store to psi_out
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) bulk_store(psi_out, A, tile_bytes);
+    stored = true;
+  }
+
   // ---------------- end of the sweep: tau_k = <tgt|psi_k>/||psi_k|| ----------------
   if (j == a.nt) {
     double v[3] = {0.0, 0.0, 0.0};
@@ -934,16 +1027,35 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
       a.norm2[k] = nrm;
       if (!isfinite(nrm) || !isfinite(o[0]) || !isfinite(o[1])) set_status(a.status, KT_DEV_NONFINITE);
     }
+    if (threadIdx.x == 0 && stored) bulk_store_wait();
     return;
   }
 
   // ---------------- update overlap at t_j: g_c = sum_k Im <chi_k|hc_c|psi_k> ----------------
-  if (!a.update) return;
+  if (!a.update) {
+    if (threadIdx.x == 0 && stored) bulk_store_wait();
+    return;
+  }
+  if (jumped) {
+    // final states came back through psi_out: put them into A for the neighbour reads
 #pragma unroll
-  for (int q = 0; q < EPT; ++q)
-    if (it.ok[q]) A[it.item[q]] = acc[q];
-  __syncthreads();
-  const C *chi = (const C *)a.chi_t + (size_t)tile * g.tile_elems;
+    for (int q = 0; q < EPT; ++q)
+      if (it.ok[q]) A[it.item[q]] = acc[q];
+  }
+  const C *chi;
+  if (g.prefetch_chi) {
+    chi = (const C *)sm.bufC;
+  } else {
+    // B was written by ordinary stores during the Chebyshev rounds: order them before the copy
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) bulk_load(B, chi_g, tile_bytes, &sm.mbar[1]);
+    chi = B;
+  }
+  if (!tile_wait(&sm.mbar[1], 0, &sm.flag[5], a.status)) {
+    if (threadIdx.x == 0 && stored) bulk_store_wait();
+    return;
+  }
   const C *hv = (const C *)sm.hc_val;
   double v[KT_MAX_CTRL];
   for (int c = 0; c < KT_MAX_CTRL; ++c) v[c] = 0.0;
@@ -979,6 +1091,7 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
     sm.flag[3] = (ticket == (unsigned)(gridDim.x - 1));
   }
   __syncthreads();
+  if (threadIdx.x == 0 && stored) bulk_store_wait();
   if (!sm.flag[3]) return;
   __threadfence();
   if (threadIdx.x < g.n_ctrl) {
@@ -1005,15 +1118,21 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
   typedef typename C2<R>::T C;
   extern __shared__ __align__(16) char smem_raw[];
   Smem sm;
-  carve(g, sizeof(C), smem_raw, &sm);
+  carve(g, sizeof(C), smem_raw, &sm, false);
   const int tile = blockIdx.x;
   const int tau = threadIdx.x % g.T;
   const int j = a.j;
   const C *chi_in = (const C *)a.chi_in + (size_t)tile * g.tile_elems;
   C *chi_out = (C *)a.chi_out + (size_t)tile * g.tile_elems;
   if (threadIdx.x < g.n_ctrl) sm.eps[threadIdx.x] = a.eps[threadIdx.x * a.nt + (j - 1)];
-  if (threadIdx.x == 0) sm.flag[0] = 0;
+  if (threadIdx.x < 8) sm.flag[threadIdx.x] = 0;
+  if (threadIdx.x == 0) {
+    mbar_init(&sm.mbar[0], 1);
+    fence_mbar_init();
+  }
   __syncthreads();
+  const uint32_t tile_bytes = (uint32_t)(g.tile_elems * sizeof(C));
+  if (threadIdx.x == 0) bulk_load(sm.bufB, chi_in, tile_bytes, &sm.mbar[0]);
   build_tables<R>(g, im, ops, sm, sm.eps, false);
   if (threadIdx.x < g.T) {
     const int t = threadIdx.x, k = tile * g.T + t;
@@ -1035,8 +1154,7 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
   load_items<EPT, NL>(g, ops, it);
   C *A = (C *)sm.bufA;
   C *B = (C *)sm.bufB;
-  load_tile<R, EPT>(g, it, chi_in, B);
-  __syncthreads();
+  if (!tile_wait(&sm.mbar[0], 0, &sm.flag[4], a.status)) return;
   const int rounds = sm.flag[0];
   C acc[EPT];
   for (int rnd = 0; rnd <= rounds; ++rnd) {
@@ -1079,9 +1197,16 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
     }
     __syncthreads();
   }
+  // chi(t_{j-1}) of the whole tile: into A, then one bulk store
 #pragma unroll
   for (int q = 0; q < EPT; ++q)
-    if (it.ok[q]) chi_out[it.item[q]] = acc[q];
+    if (it.ok[q]) A[it.item[q]] = acc[q];
+  fence_proxy_async_smem();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bulk_store(chi_out, A, tile_bytes);
+    bulk_store_wait();
+  }
 }
 
 }  // namespace kt

@@ -745,7 +745,7 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
       if ((long long)d * T > (cfg->tile_traj > 0 ? 16LL * maxthr : max_items)) continue;
       t.nthreads = maxthr;
     }
-    if (kt_smem_bytes(t, esz) > 227 * 1024) continue;
+    if (kt_smem_bytes(t, esz, false) > 227 * 1024) continue;
     Tsel = T;
     // prefer more tiles when the trajectories would not fill the GPU
     if (cfg->tile_traj == 0 && (M + T - 1) / T < 2 * 152 && T > 1 && (long long)d * (T / 2) >= 256) continue;
@@ -756,6 +756,11 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
   g.n_tiles = (M + Tsel - 1) / Tsel;
   g.M_pad = g.n_tiles * Tsel;
   g.tile_elems = (d * Tsel + 3) / 4 * 4;
+  {
+    KtGeom t = g;
+    t.nthreads = fiber ? std::max(32, ((d / nl) * Tsel + 31) / 32 * 32) : maxthr;
+    g.prefetch_chi = kt_smem_bytes(t, esz, true) <= 227 * 1024 ? 1 : 0;
+  }
   if (fiber) {
     P.ept = cavity_structure(gf, gb, lo_dl, lo_val, ra_dl, ra_val) ? -(100 + nl) : -nl;   // launcher codes
     g.nthreads = std::max(32, ((d / nl) * Tsel + 31) / 32 * 32);

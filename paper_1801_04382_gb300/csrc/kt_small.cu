@@ -39,17 +39,19 @@ __global__ void chi_boundary_kernel(KtGeom g, KtOps ops, const KtCplx *tau, C *c
 
 using namespace kt;
 
-size_t kt_smem_bytes(const KtGeom &g, int elem_bytes) { return carve(g, elem_bytes, nullptr, nullptr); }
+size_t kt_smem_bytes(const KtGeom &g, int elem_bytes, bool with_chi_buffer) {
+  return carve(g, elem_bytes, nullptr, nullptr, with_chi_buffer);
+}
 
 cudaError_t kt_launch_fwd(int fp64, int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops,
                           const FwdArgs &a, cudaStream_t st) {
-  const size_t smem = kt_smem_bytes(g, fp64 ? 16 : 8);
+  const size_t smem = kt_smem_bytes(g, fp64 ? 16 : 8, g.prefetch_chi != 0);
   return fp64 ? kt_launch_fwd_f64(ept, g, im, ops, a, smem, st) : kt_launch_fwd_f32(ept, g, im, ops, a, smem, st);
 }
 
 cudaError_t kt_launch_bwd(int fp64, int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops,
                           const BwdArgs &a, cudaStream_t st) {
-  const size_t smem = kt_smem_bytes(g, fp64 ? 16 : 8);
+  const size_t smem = kt_smem_bytes(g, fp64 ? 16 : 8, false);
   return fp64 ? kt_launch_bwd_f64(ept, g, im, ops, a, smem, st) : kt_launch_bwd_f32(ept, g, im, ops, a, smem, st);
 }
 
