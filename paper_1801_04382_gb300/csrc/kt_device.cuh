@@ -1094,10 +1094,21 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
   if (threadIdx.x == 0 && stored) bulk_store_wait();
   if (!sm.flag[3]) return;
   __threadfence();
+  // every thread adds a fixed, contiguous chunk of the tiles; a fixed shuffle/warp tree adds the
+  // chunks -- the same order on every run for a given grid
+  const int chunk = ((int)gridDim.x + blockDim.x - 1) / blockDim.x;
+  const int t0 = threadIdx.x * chunk, t1 = min((int)gridDim.x, t0 + chunk);
+  for (int c = 0; c < g.n_ctrl; ++c) {
+    double v = 0.0;
+    for (int t = t0; t < t1; ++t) v += __ldcg(a.partials + (size_t)t * g.n_ctrl + c);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sm.red[(threadIdx.x >> 5) * 8 + c] = v;
+  }
+  __syncthreads();
   if (threadIdx.x < g.n_ctrl) {
     const int c = threadIdx.x;
     double s = 0.0;
-    for (int t = 0; t < (int)gridDim.x; ++t) s += ((volatile double *)a.partials)[(size_t)t * g.n_ctrl + c];
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sm.red[w * 8 + c];
     const size_t idx = (size_t)c * a.nt + j;   // interval j+1 (0-based index j)
     const double de = a.shape[idx] / (g.lam[c] * (double)g.M) * s;
     const double en = a.eps_old[idx] + de;
