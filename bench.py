@@ -299,6 +299,8 @@ def run_ours(args, rank, world):
         "roofline": roof,
         "e2e": {"value": world * 1000.0 / e2e_ms, "unit": "Krotov iters/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
+        "kernels": {f"{k}_kernel": {"launches": n, "total_ms": ms, "avg_ms": ms / max(n, 1)}
+                    for k, (ms, n) in prof.items()},
         "gpu_launches": int(prof["fwd"][1] + prof["bwd"][1] + 4 * args.steps),
         "clocks": clocks,
     }
