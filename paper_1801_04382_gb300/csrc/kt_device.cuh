@@ -312,37 +312,51 @@ __device__ __forceinline__ typename C2<R>::T diag_of(const KtGeom &g, const Smem
 }
 
 // Items of this thread: item_q = tid + q * nthreads, valid while < d*T.
-template <int EPT>
-struct Items {
-  int item[EPT];
-  uint32_t dig[EPT];
-  bool ok[EPT];
+template <int EPT, bool FIBER>
+struct ItemsT {
+  // strided mapping: item_q = tid + q * nthreads
+  int item_[EPT];
+  uint32_t dig_[EPT];
+  bool ok_[EPT];
+  __device__ __forceinline__ int item(int q) const { return item_[q]; }
+  __device__ __forceinline__ uint32_t dig(int q) const { return dig_[q]; }
+  __device__ __forceinline__ bool ok(int q) const { return ok_[q]; }
 };
+template <int EPT>
+struct ItemsT<EPT, true> {
+  // fiber mapping: the thread's items run along the last node's digit, so everything follows
+  // from the first item, the fiber's digits (last digit 0) and the tile width
+  int base, T, shift;
+  uint32_t fdig;
+  bool okf;
+  __device__ __forceinline__ int item(int q) const { return base + q * T; }
+  __device__ __forceinline__ uint32_t dig(int q) const { return fdig + ((uint32_t)q << shift); }
+  __device__ __forceinline__ bool ok(int) const { return okf; }
+};
+template <int EPT, int NL>
+using Items = ItemsT<EPT, (NL > 0)>;
 
 template <int EPT, int NL>
-__device__ __forceinline__ void load_items(const KtGeom &g, const KtOps &ops, Items<EPT> &it) {
-  const int n = g.d * g.T;
-  if (NL > 0) {
+__device__ __forceinline__ void load_items(const KtGeom &g, const KtOps &ops, Items<EPT, NL> &it) {
+  if constexpr (NL > 0) {
     // fiber mapping: thread -> (fiber f, trajectory tau); its NL items run along the last
     // node's digit (stride T in the interleaved tile), so node-local and pair coefficients of
     // the other nodes are fixed per thread and the last node's are uniform per item slot
     const int f = threadIdx.x / g.T, tau = threadIdx.x % g.T;
-    const bool ok = f < g.d / NL;
+    it.okf = f < g.d / NL;
+    it.base = f * NL * g.T + tau;
+    it.T = g.T;
+    it.shift = 4 * (g.n_nodes - 1);
+    it.fdig = it.okf ? ops.digits[f * NL] : 0u;
+  } else {
+    const int n = g.d * g.T;
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
-      const int item = (f * NL + q) * g.T + tau;
-      it.item[q] = item;
-      it.ok[q] = ok;
-      it.dig[q] = ok ? ops.digits[f * NL + q] : 0u;
+      const int item = threadIdx.x + q * blockDim.x;
+      it.item_[q] = item;
+      it.ok_[q] = item < n;
+      it.dig_[q] = it.ok_[q] ? ops.digits[item / g.T] : 0u;
     }
-    return;
-  }
-#pragma unroll
-  for (int q = 0; q < EPT; ++q) {
-    const int item = threadIdx.x + q * blockDim.x;
-    it.item[q] = item;
-    it.ok[q] = item < n;
-    it.dig[q] = it.ok[q] ? ops.digits[item / g.T] : 0u;
   }
 }
 
@@ -416,8 +430,8 @@ __device__ __forceinline__ void apply_fiber(const KtGeom &g, const KtGenImage &i
 }
 
 // Chebyshev sum in fiber mapping (see cheb_run).
-template <typename R, int NL>
-__device__ void cheb_run_fiber(const KtGeom &g, const KtGenImage &im, const Smem &sm, const Items<NL> &it, int K,
+template <typename R, int NL, class IT>
+__device__ void cheb_run_fiber(const KtGeom &g, const KtGenImage &im, const Smem &sm, const IT &it, int K,
                                typename C2<R>::T (&acc)[NL]) {
   typedef typename C2<R>::T C;
   C *A = (C *)sm.bufA;
@@ -425,9 +439,9 @@ __device__ void cheb_run_fiber(const KtGeom &g, const KtGenImage &im, const Smem
   const C *cf = (const C *)sm.coef;
   const C *dg = (const C *)sm.diag;
   const int tau = threadIdx.x % g.T;
-  const bool ok = it.ok[0];
-  const int base = it.item[0];
-  const uint32_t fdig = it.dig[0];
+  const bool ok = it.ok(0);
+  const int base = it.item(0);
+  const uint32_t fdig = it.dig(0);
   const int last = g.n_nodes - 1;
   C Df = mkc((R)0, (R)0);
   for (int i = 0; i < last; ++i) {
@@ -471,8 +485,8 @@ __device__ void cheb_run_fiber(const KtGeom &g, const KtGenImage &im, const Smem
 
 // Chebyshev sum: acc = sum_k coef[k][tau] T_k(Ghat) v with v in A on entry (synced).
 // A and B are overwritten.  Ends synchronised.
-template <typename R, int EPT>
-__device__ void cheb_run(const KtGeom &g, const KtGenImage &im, const Smem &sm, const Items<EPT> &it, int K,
+template <typename R, int EPT, class IT>
+__device__ void cheb_run(const KtGeom &g, const KtGenImage &im, const Smem &sm, const IT &it, int K,
                          typename C2<R>::T (&acc)[EPT]) {
   typedef typename C2<R>::T C;
   C *A = (C *)sm.bufA;
@@ -482,15 +496,15 @@ __device__ void cheb_run(const KtGeom &g, const KtGenImage &im, const Smem &sm, 
   C dv[EPT];
 #pragma unroll
   for (int q = 0; q < EPT; ++q) {
-    dv[q] = it.ok[q] ? diag_of<R>(g, sm, it.dig[q]) : mkc((R)0, (R)0);
-    acc[q] = it.ok[q] ? cmul(cf[tau], A[it.item[q]]) : mkc((R)0, (R)0);
+    dv[q] = it.ok(q) ? diag_of<R>(g, sm, it.dig(q)) : mkc((R)0, (R)0);
+    acc[q] = it.ok(q) ? cmul(cf[tau], A[it.item(q)]) : mkc((R)0, (R)0);
   }
   if (K == 1) { __syncthreads(); return; }
 #pragma unroll
   for (int q = 0; q < EPT; ++q) {
-    if (!it.ok[q]) continue;
-    const C t = apply_item<R>(g, im, sm, A, it.item[q], it.dig[q], dv[q]);
-    B[it.item[q]] = t;
+    if (!it.ok(q)) continue;
+    const C t = apply_item<R>(g, im, sm, A, it.item(q), it.dig(q), dv[q]);
+    B[it.item(q)] = t;
     acc[q] = cfma(cf[g.T + tau], t, acc[q]);
   }
   __syncthreads();
@@ -500,11 +514,11 @@ __device__ void cheb_run(const KtGeom &g, const KtGenImage &im, const Smem &sm, 
     const C a = cf[k * g.T + tau];
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
-      if (!it.ok[q]) continue;
-      const C t = apply_item<R>(g, im, sm, Q, it.item[q], it.dig[q], dv[q]);
-      const C old = P[it.item[q]];
+      if (!it.ok(q)) continue;
+      const C t = apply_item<R>(g, im, sm, Q, it.item(q), it.dig(q), dv[q]);
+      const C old = P[it.item(q)];
       const C nv = mkc(t.x + t.x - old.x, t.y + t.y - old.y);
-      P[it.item[q]] = nv;
+      P[it.item(q)] = nv;
       acc[q] = cfma(a, nv, acc[q]);
     }
     __syncthreads();
@@ -542,21 +556,21 @@ __device__ void uniform_coefs(const KtGeom &g, const Smem &sm, const KtCplx *ful
   for (int e = threadIdx.x; e < g.K * g.T; e += blockDim.x) cf[e] = from_kc<C>(full[e / g.T]);
 }
 
-template <typename R, int EPT>
-__device__ __forceinline__ void load_tile(const KtGeom &g, const Items<EPT> &it, const typename C2<R>::T *src,
+template <typename R, int EPT, class IT>
+__device__ __forceinline__ void load_tile(const KtGeom &g, const IT &it, const typename C2<R>::T *src,
                                           typename C2<R>::T *dst) {
 #pragma unroll
   for (int q = 0; q < EPT; ++q)
-    if (it.ok[q]) dst[it.item[q]] = src[it.item[q]];
+    if (it.ok(q)) dst[it.item(q)] = src[it.item(q)];
 }
 
 // Norm^2 of each trajectory of acc -> sm.tsc[TS_NRM][tau]
-template <typename R, int EPT>
-__device__ void norms(const KtGeom &g, const Smem &sm, const Items<EPT> &it, const typename C2<R>::T (&acc)[EPT]) {
+template <typename R, int EPT, class IT>
+__device__ void norms(const KtGeom &g, const Smem &sm, const IT &it, const typename C2<R>::T (&acc)[EPT]) {
   R s = 0;
 #pragma unroll
   for (int q = 0; q < EPT; ++q)
-    if (it.ok[q]) s += acc[q].x * acc[q].x + acc[q].y * acc[q].y;
+    if (it.ok(q)) s += acc[q].x * acc[q].x + acc[q].y * acc[q].y;
   double v[1] = {(double)s};
   reduce_tau<1>(v, g, sm.red, sm.tsc + TS_NRM * g.T);
 }
@@ -674,8 +688,8 @@ __device__ __forceinline__ void apply_acs(const KtGeom &g, const KtGenImage &im,
   }
 }
 
-template <typename R, int NC>
-__device__ void cheb_run_acs(const KtGeom &g, const KtGenImage &im, const Smem &sm, const Items<3 * (NC + 1)> &it,
+template <typename R, int NC, class IT>
+__device__ void cheb_run_acs(const KtGeom &g, const KtGenImage &im, const Smem &sm, const IT &it,
                              int K, typename C2<R>::T (&acc)[3 * (NC + 1)]) {
   typedef typename C2<R>::T C;
   constexpr int NL = 3 * (NC + 1);
@@ -684,9 +698,9 @@ __device__ void cheb_run_acs(const KtGeom &g, const KtGenImage &im, const Smem &
   const C *cf = (const C *)sm.coef;
   const C *dg = (const C *)sm.diag;
   const int tau = threadIdx.x % g.T;
-  const bool ok = it.ok[0];
-  const int base = it.item[0];
-  const uint32_t fdig = it.dig[0];
+  const bool ok = it.ok(0);
+  const int base = it.item(0);
+  const uint32_t fdig = it.dig(0);
   const int last = g.n_nodes - 1;
   C Df = mkc((R)0, (R)0);
   for (int i = 0; i < last; ++i) {
@@ -734,9 +748,9 @@ __device__ void cheb_run_acs(const KtGeom &g, const KtGenImage &im, const Smem &
   }
 }
 
-template <typename R, int EPT, int NL, int ACS>
+template <typename R, int EPT, int NL, int ACS, class IT>
 __device__ __forceinline__ void cheb_dispatch(const KtGeom &g, const KtGenImage &im, const Smem &sm,
-                                              const Items<EPT> &it, int K, typename C2<R>::T (&acc)[EPT]) {
+                                              const IT &it, int K, typename C2<R>::T (&acc)[EPT]) {
   if constexpr (ACS) cheb_run_acs<R, NL / 3 - 1>(g, im, sm, it, K, acc);
   else if constexpr (NL > 0) cheb_run_fiber<R, NL>(g, im, sm, it, K, acc);
   else cheb_run<R, EPT>(g, im, sm, it, K, acc);
@@ -790,7 +804,7 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
     if (need_chi && g.prefetch_chi) bulk_load(sm.bufC, chi_g, tile_bytes, &sm.mbar[1]);
   }
   build_tables<R>(g, im, ops, sm, sm.eps, a.update != 0);
-  Items<EPT> it;
+  Items<EPT, NL> it;
   load_items<EPT, NL>(g, ops, it);
   C acc[EPT];
   if (!tile_wait(&sm.mbar[0], 0, &sm.flag[4], a.status)) {
@@ -802,7 +816,7 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
   int phase = (j >= 1) ? PH_MAIN : PH_DONE;
   if (phase == PH_DONE) {
 #pragma unroll
-    for (int q = 0; q < EPT; ++q) acc[q] = it.ok[q] ? A[it.item[q]] : mkc((R)0, (R)0);
+    for (int q = 0; q < EPT; ++q) acc[q] = it.ok(q) ? A[it.item(q)] : mkc((R)0, (R)0);
   }
   int guard = 0;
   while (phase != PH_DONE) {
@@ -840,7 +854,7 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
     if (phase == PH_MAIN) {
 #pragma unroll
       for (int q = 0; q < EPT; ++q)
-        if (it.ok[q]) A[it.item[q]] = acc[q];
+        if (it.ok(q)) A[it.item(q)] = acc[q];
       if (threadIdx.x < g.T) {
         const int t = threadIdx.x, k = tile * g.T + t;
         const double nrm = sm.tsc[TS_NRM * g.T + t];
@@ -864,7 +878,7 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
       __syncthreads();
 #pragma unroll
       for (int q = 0; q < EPT; ++q)
-        if (it.ok[q] && sm.tin[TI_ACT * g.T + tau]) psi_out[it.item[q]] = psi_in[it.item[q]];
+        if (it.ok(q) && sm.tin[TI_ACT * g.T + tau]) psi_out[it.item(q)] = psi_in[it.item(q)];
       __syncthreads();
       phase = PH_BISECT;
     } else if (phase == PH_BISECT) {
@@ -881,7 +895,7 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
     } else if (phase == PH_SSTAR) {
 #pragma unroll
       for (int q = 0; q < EPT; ++q)
-        if (it.ok[q]) A[it.item[q]] = acc[q];
+        if (it.ok(q)) A[it.item(q)] = acc[q];
       __syncthreads();
       // channel probabilities p_l = ||L_l phi||^2
       double v[KT_MAX_LIND];
@@ -890,8 +904,8 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
         if (l < g.n_lind) {
 #pragma unroll
           for (int q = 0; q < EPT; ++q)
-            if (it.ok[q]) {
-              const C y = lind_item<R>(g, ops, l, 0, A, it.item[q], it.dig[q]);
+            if (it.ok(q)) {
+              const C y = lind_item<R>(g, ops, l, 0, A, it.item(q), it.dig(q));
               s += y.x * y.x + y.y * y.y;
             }
         }
@@ -951,9 +965,9 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
         const R cn = (R)sm.tsc[TS_C * g.T + tau];
 #pragma unroll
         for (int q = 0; q < EPT; ++q) {
-          if (!it.ok[q]) continue;
-          const C y = lind_item<R>(g, ops, ch, 0, A, it.item[q], it.dig[q]);
-          psi_out[it.item[q]] = mkc(cn * y.x, cn * y.y);
+          if (!it.ok(q)) continue;
+          const C y = lind_item<R>(g, ops, ch, 0, A, it.item(q), it.dig(q));
+          psi_out[it.item(q)] = mkc(cn * y.x, cn * y.y);
         }
       }
       __syncthreads();
@@ -978,7 +992,7 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
       __syncthreads();
 #pragma unroll
       for (int q = 0; q < EPT; ++q)
-        if (it.ok[q] && sm.tin[TI_BUSY * g.T + tau]) psi_out[it.item[q]] = acc[q];
+        if (it.ok(q) && sm.tin[TI_BUSY * g.T + tau]) psi_out[it.item(q)] = acc[q];
       __syncthreads();
       if (threadIdx.x < g.T && sm.tin[TI_BUSY * g.T + threadIdx.x]) sm.tin[TI_ACT * g.T + threadIdx.x] = 0;
       __syncthreads();
@@ -987,7 +1001,7 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
         // final states of the whole tile
 #pragma unroll
         for (int q = 0; q < EPT; ++q)
-          if (it.ok[q]) acc[q] = psi_out[it.item[q]];
+          if (it.ok(q)) acc[q] = psi_out[it.item(q)];
         __syncthreads();
         phase = PH_DONE;
       } else {
@@ -1009,8 +1023,8 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
     double v[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
-      if (!it.ok[q]) continue;
-      const KtCplx t = ops.tgt[it.item[q] / g.T];
+      if (!it.ok(q)) continue;
+      const KtCplx t = ops.tgt[it.item(q) / g.T];
       const double xr = (double)acc[q].x, xi = (double)acc[q].y;
       v[0] += t.re * xr + t.im * xi;   // conj(tgt) * psi
       v[1] += t.re * xi - t.im * xr;
@@ -1040,7 +1054,7 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
     // final states came back through psi_out: put them into A for the neighbour reads
 #pragma unroll
     for (int q = 0; q < EPT; ++q)
-      if (it.ok[q]) A[it.item[q]] = acc[q];
+      if (it.ok(q)) A[it.item(q)] = acc[q];
   }
   const C *chi;
   if (g.prefetch_chi) {
@@ -1064,15 +1078,15 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
     R s = 0;
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
-      if (!it.ok[q]) continue;
-      const int xi = (it.dig[q] >> (4 * node)) & 15;
+      if (!it.ok(q)) continue;
+      const int xi = (it.dig(q) >> (4 * node)) & 15;
       const int base = (c * g.n_loc + xi) * g.SH;
       C h = mkc((R)0, (R)0);
       for (int e = 0; e < g.SH; ++e) {
         const C w = hv[base + e];
-        if (w.x != (R)0 || w.y != (R)0) h = cfma(w, A[it.item[q] + sm.hc_off[base + e]], h);
+        if (w.x != (R)0 || w.y != (R)0) h = cfma(w, A[it.item(q) + sm.hc_off[base + e]], h);
       }
-      const C x = chi[it.item[q]];
+      const C x = chi[it.item(q)];
       s += x.x * h.y - x.y * h.x;       // Im(conj(chi) * h)
     }
     v[c] = (double)s;
@@ -1161,7 +1175,7 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
     sm.tin[TI_NJ * g.T + t] = nj;
     atomicMax(&sm.flag[0], nj);
   }
-  Items<EPT> it;
+  Items<EPT, NL> it;
   load_items<EPT, NL>(g, ops, it);
   C *A = (C *)sm.bufA;
   C *B = (C *)sm.bufB;
@@ -1184,34 +1198,34 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
     // B holds the vector to propagate
 #pragma unroll
     for (int q = 0; q < EPT; ++q)
-      if (it.ok[q]) A[it.item[q]] = B[it.item[q]];
+      if (it.ok(q)) A[it.item(q)] = B[it.item(q)];
     __syncthreads();
     cheb_dispatch<R, EPT, NL, ACS>(g, im, sm, it, g.K, acc);
     if (rnd == rounds) break;
 #pragma unroll
     for (int q = 0; q < EPT; ++q)
-      if (it.ok[q]) A[it.item[q]] = acc[q];
+      if (it.ok(q)) A[it.item(q)] = acc[q];
     __syncthreads();
     const int nj = sm.tin[TI_NJ * g.T + tau];
     const int k = tile * g.T + tau;
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
-      if (!it.ok[q]) continue;
-      C y = A[it.item[q]];
+      if (!it.ok(q)) continue;
+      C y = A[it.item(q)];
       if (rnd < nj) {
         const size_t ri = (size_t)k * g.max_jumps + sm.tin[(TI_J0 + rnd) * g.T + tau];
-        const C z = lind_item<R>(g, ops, a.rec_ch[ri], 1, A, it.item[q], it.dig[q]);
+        const C z = lind_item<R>(g, ops, a.rec_ch[ri], 1, A, it.item(q), it.dig(q));
         const R cn = (R)a.rec_c[ri];
         y = mkc(cn * z.x, cn * z.y);
       }
-      B[it.item[q]] = y;
+      B[it.item(q)] = y;
     }
     __syncthreads();
   }
   // chi(t_{j-1}) of the whole tile: into A, then one bulk store
 #pragma unroll
   for (int q = 0; q < EPT; ++q)
-    if (it.ok[q]) A[it.item[q]] = acc[q];
+    if (it.ok(q)) A[it.item(q)] = acc[q];
   fence_proxy_async_smem();
   __syncthreads();
   if (threadIdx.x == 0) {
