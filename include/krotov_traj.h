@@ -128,6 +128,19 @@ KT_API kt_status krotov_init(const kt_model_desc *model, const kt_config *cfg, v
  * At the end tau_k = <tgt|psi_k(T)>/||psi_k(T)|| is formed; F_out (nullable) receives
  * F = (1/M) sum |tau_k|^2 (Eq. functional_traj). */
 KT_API kt_status propagate_forward(kt_problem *p, int sequential_update, double *F_out, void *stream);
+/* sequential_update = 2: a sweep without update that also keeps the forward states (every
+ * ckpt_interval intervals, or all of them when ckpt_interval = 0) for krotov_gradient.  Any
+ * later forward sweep or krotov_set_pulses discards them. */
+
+/* Exact gradient dJ_T/deps [n_ctrl][nt] (host output) of the trajectory functional
+ * J_T = 1 - (1/M) sum_k |<tgt|psi_k(T)>|^2 / ||psi_k(T)||^2 (Eq. functional_traj) at the current
+ * pulse, for the jump record of the last propagate_forward(p, 2, ...) held fixed:
+ *   dJ_T/deps_ij = -(2/M) sum_k Re <chi~_k(t_j)| dU_kj/deps_i |psi_k(t_{j-1})>,
+ * chi~_k(T) = (tau_k |tgt> - |tau_k|^2 psihat_k) / ||psi_k(T)||, chi~ propagated backwards along
+ * each trajectory's own record, dU/deps exact (the discrete derivative of the propagator,
+ * Sec. 2.2, Eq. gradient).  Forward states are replayed segment by segment from the kept ones.
+ * Needs four state buffers of d in shared memory (KT_ERR_UNSUPPORTED otherwise). */
+KT_API kt_status krotov_gradient(kt_problem *p, double *dJ_out, void *stream);
 
 /* Backward co-state sweep (Sec. 2.3): chi_k(T) = tau_k |tgt>, then
  * chi_k(t_{j-1}) = U_kj^dag chi_k(t_j) under the pulse of the last forward sweep, where U_kj

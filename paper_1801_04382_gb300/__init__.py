@@ -9,3 +9,11 @@ from .model import NetworkFactors, cascaded_chain  # noqa: F401
 from .problem import Problem, bessel_j  # noqa: F401
 from . import build  # noqa: F401  (module: build.build() compiles the CUDA library)
 from ._capi import KrotovError  # noqa: F401
+
+
+def __getattr__(name):
+    # torch is only needed for the autograd binding
+    if name in ("KrotovTrajFunction", "trajectory_functional"):
+        from . import autograd
+        return getattr(autograd, name)
+    raise AttributeError(name)

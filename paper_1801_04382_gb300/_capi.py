@@ -54,6 +54,7 @@ SIGNATURES = {
     "krotov_init": (ct.c_int, [ct.POINTER(ModelDesc), ct.POINTER(Config), ct.c_void_p, ct.POINTER(ct.c_void_p)]),
     "propagate_forward": (ct.c_int, [ct.c_void_p, ct.c_int, dp, ct.c_void_p]),
     "propagate_backward": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
+    "krotov_gradient": (ct.c_int, [ct.c_void_p, dp, ct.c_void_p]),
     "krotov_update": (ct.c_int, [ct.c_void_p, ct.c_int, dp, dp, ct.c_void_p]),
     "fidelity": (ct.c_int, [ct.c_void_p, dp, dp]),
     "krotov_get_pulses": (ct.c_int, [ct.c_void_p, dp]),

@@ -1138,6 +1138,9 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
 // Backward interval kernel: chi(t_{j-1}) = U_j^dag chi(t_j) along each trajectory's record.
 // Round rnd propagates piece rnd of the interval (backwards: dt - s_m, s_m - s_{m-1}, ..., s_1)
 // and then applies conj(c) L^dag of the jump that bounds it.  One Chebyshev call site.
+// With a.forward_replay the same kernel replays a recorded forward pass instead: the image is
+// the forward generator's, pieces run forwards (s_1, s_2 - s_1, ..., dt - s_m) and each is
+// followed by c L of its jump -- the frozen-record map U_j of the gradient (no bisection).
 template <typename R, int EPT, int NL, int ACS>
 __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) bwd_kernel(KtGeom g, KtGenImage im, KtOps ops, BwdArgs a) {
   typedef typename C2<R>::T C;
@@ -1159,17 +1162,28 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
   const uint32_t tile_bytes = (uint32_t)(g.tile_elems * sizeof(C));
   if (threadIdx.x == 0) bulk_load(sm.bufB, chi_in, tile_bytes, &sm.mbar[0]);
   build_tables<R>(g, im, ops, sm, sm.eps, false);
+  const bool fw = a.forward_replay != 0;
   if (threadIdx.x < g.T) {
     const int t = threadIdx.x, k = tile * g.T + t;
     int nj = 0;
     if (k < g.M) {
       int cur = a.cursor[k];
-      while (cur >= 0 && a.rec_step[(size_t)k * g.max_jumps + cur] == j && nj < 12) {
-        sm.tin[(TI_J0 + nj) * g.T + t] = cur;    // descending in time
-        ++nj;
-        --cur;
+      if (fw) {
+        const int cnt = a.jcount[k];
+        while (cur < cnt && a.rec_step[(size_t)k * g.max_jumps + cur] == j && nj < 12) {
+          sm.tin[(TI_J0 + nj) * g.T + t] = cur;  // ascending in time
+          ++nj;
+          ++cur;
+        }
+        if (cur < cnt && a.rec_step[(size_t)k * g.max_jumps + cur] == j) set_status(a.status, KT_DEV_RECORD_FULL);
+      } else {
+        while (cur >= 0 && a.rec_step[(size_t)k * g.max_jumps + cur] == j && nj < 12) {
+          sm.tin[(TI_J0 + nj) * g.T + t] = cur;  // descending in time
+          ++nj;
+          --cur;
+        }
+        if (cur >= 0 && a.rec_step[(size_t)k * g.max_jumps + cur] == j) set_status(a.status, KT_DEV_RECORD_FULL);
       }
-      if (cur >= 0 && a.rec_step[(size_t)k * g.max_jumps + cur] == j) set_status(a.status, KT_DEV_RECORD_FULL);
       if (a.advance_cursor) a.cursor[k] = cur;
     }
     sm.tin[TI_NJ * g.T + t] = nj;
@@ -1189,11 +1203,18 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
       const int t = threadIdx.x, k = tile * g.T + t, nj = sm.tin[TI_NJ * g.T + t];
       double len = 0.0;
       if (rnd <= nj) {
-        const double hi = (rnd == 0) ? g.dt : a.rec_s[(size_t)k * g.max_jumps + sm.tin[(TI_J0 + rnd - 1) * g.T + t]];
-        const double lo = (rnd < nj) ? a.rec_s[(size_t)k * g.max_jumps + sm.tin[(TI_J0 + rnd) * g.T + t]] : 0.0;
-        len = hi - lo;
+        const double *rs = a.rec_s + (size_t)k * g.max_jumps;
+        if (fw) {   // pieces forwards: s_1 - 0, s_2 - s_1, ..., dt - s_m
+          const double lo = (rnd == 0) ? 0.0 : rs[sm.tin[(TI_J0 + rnd - 1) * g.T + t]];
+          const double hi = (rnd < nj) ? rs[sm.tin[(TI_J0 + rnd) * g.T + t]] : g.dt;
+          len = hi - lo;
+        } else {    // pieces backwards: dt - s_m, s_m - s_{m-1}, ..., s_1 - 0
+          const double hi = (rnd == 0) ? g.dt : rs[sm.tin[(TI_J0 + rnd - 1) * g.T + t]];
+          const double lo = (rnd < nj) ? rs[sm.tin[(TI_J0 + rnd) * g.T + t]] : 0.0;
+          len = hi - lo;
+        }
       }
-      tau_coefs<R>(g, sm, t, g.c_bwd, len);
+      tau_coefs<R>(g, sm, t, fw ? g.c_fwd : g.c_bwd, len);
     }
     // B holds the vector to propagate
 #pragma unroll
@@ -1214,7 +1235,7 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
       C y = A[it.item(q)];
       if (rnd < nj) {
         const size_t ri = (size_t)k * g.max_jumps + sm.tin[(TI_J0 + rnd) * g.T + tau];
-        const C z = lind_item<R>(g, ops, a.rec_ch[ri], 1, A, it.item(q), it.dig(q));
+        const C z = lind_item<R>(g, ops, a.rec_ch[ri], fw ? 0 : 1, A, it.item(q), it.dig(q));
         const R cn = (R)a.rec_c[ri];
         y = mkc(cn * z.x, cn * z.y);
       }

@@ -175,6 +175,16 @@ struct kt_problem {
   bool have_fwd = false, have_bwd = false, have_deps = false;
   int final_buf = 0;
 
+  // gradient (krotov_gradient): forward states kept every Kg intervals, replayed per segment
+  int Kg = 0, grad_ept = 4;
+  KtGeom g1{};                  // the geometry re-cut to one trajectory per CTA
+  void *psi_ck = nullptr;       // [nt/Kg + 1] states: psi(t_{s Kg}), s >= 1 (s = 0 is psi_init)
+  void *psi_seg = nullptr;      // [Kg] replayed states of one segment
+  void *chi_run[2] = {nullptr, nullptr};
+  double *gpart = nullptr, *dgrad = nullptr;
+  int *fcursor = nullptr;
+  bool grad_ready = false;
+
   // optional per-launch timing of the interval kernels (krotov_set_profiling)
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;            // pairs: [2i] before, [2i+1] after launch i
@@ -300,6 +310,8 @@ BwdArgs bwd_args(kt_problem *p) {
   b.eps = p->eps_old;
   b.cursor = p->cursor;
   b.advance_cursor = 1;
+  b.forward_replay = 0;
+  b.jcount = p->jcount[prev];
   b.rec_step = p->rec_step[prev];
   b.rec_ch = p->rec_ch[prev];
   b.rec_s = p->rec_s[prev];
@@ -338,7 +350,7 @@ const void *chi_at(const kt_problem *p, int j, int seg_a) {
   return state_slot(p, p->seg, j - seg_a);
 }
 
-kt_status forward_sweep(kt_problem *p, int update, cudaStream_t st) {
+kt_status forward_sweep(kt_problem *p, int update, cudaStream_t st, bool save_psi = false) {
   if (update && !p->have_bwd)
     return fail(KT_ERR_STATE, "an updating forward sweep needs a backward sweep since the last forward sweep");
   const int pass_row = (int)(p->pass_counter % p->n_passes);
@@ -371,6 +383,9 @@ kt_status forward_sweep(kt_problem *p, int update, cudaStream_t st) {
       if (s != KT_OK) return s;
       KT_CUDA(kt_launch_fwd(p->fp64, p->ept, p->g, p->im_fwd, p->ops, a, st));
       if ((s = prof_end(p, st)) != KT_OK) return s;
+      if (save_psi && j < p->nt && j % p->Kg == 0)
+        KT_CUDA(cudaMemcpyAsync(state_slot(p, p->psi_ck, j / p->Kg), p->psi[j & 1], p->state_bytes,
+                                cudaMemcpyDeviceToDevice, st));
     }
   }
   kt_status s = read_status(p, st);
@@ -383,7 +398,92 @@ kt_status forward_sweep(kt_problem *p, int update, cudaStream_t st) {
   p->cur = 1 - p->cur;          // the records just written become the "last completed" ones
   p->have_fwd = true;
   p->have_bwd = false;
+  p->grad_ready = save_psi;
   return KT_OK;
+}
+
+// Buffers and geometry of the gradient sweep (first use only).
+kt_status grad_setup(kt_problem *p, cudaStream_t st) {
+  if (p->psi_ck) return KT_OK;
+  KtGeom g1 = p->g;
+  g1.T = 1;
+  g1.n_tiles = p->M;
+  g1.M_pad = p->M;
+  g1.tile_elems = (g1.d + 3) / 4 * 4;
+  g1.prefetch_chi = 0;
+  // 4 items per thread up to 256 threads, else 8 up to 1024 (the compiled gradient kernels)
+  int ept = (g1.d + 3) / 4 <= 256 ? 4 : 8;
+  if ((g1.d + ept - 1) / ept > 1024) return fail(KT_ERR_UNSUPPORTED, "dimension too large for the gradient kernel");
+  g1.nthreads = std::max(32, ((g1.d + ept - 1) / ept + 31) / 32 * 32);
+  if (kt_grad_smem_bytes(g1, (int)p->esz) > 227 * 1024)
+    return fail(KT_ERR_UNSUPPORTED, "the gradient needs four state buffers of d = %d in shared memory (%s)", g1.d,
+                p->fp64 ? "use FP32-mixed" : "too large");
+  p->g1 = g1;
+  p->grad_ept = ept;
+  p->Kg = p->ckpt > 0 ? p->ckpt : p->nt;
+  kt_status s;
+  if ((s = dev_alloc(p, &p->psi_ck, p->state_bytes * (p->nt / p->Kg + 1))) != KT_OK) return s;
+  if ((s = dev_alloc(p, &p->psi_seg, p->state_bytes * p->Kg)) != KT_OK) return s;
+  if ((s = dev_alloc(p, &p->chi_run[0], p->state_bytes)) != KT_OK) return s;
+  if ((s = dev_alloc(p, &p->chi_run[1], p->state_bytes)) != KT_OK) return s;
+  if ((s = dev_alloc(p, (void **)&p->gpart, (size_t)p->M * p->g.n_ctrl * sizeof(double))) != KT_OK) return s;
+  if ((s = dev_alloc(p, (void **)&p->dgrad, (size_t)p->g.n_ctrl * p->nt * sizeof(double))) != KT_OK) return s;
+  if ((s = dev_alloc(p, (void **)&p->fcursor, (size_t)p->g.M_pad * sizeof(int))) != KT_OK) return s;
+  KT_CUDA(cudaMemsetAsync(p->dgrad, 0, (size_t)p->g.n_ctrl * p->nt * sizeof(double), st));
+  return KT_OK;
+}
+
+// state psi(t_j) of the recorded forward pass inside segment [a, b): checkpoint or replayed
+const void *psi_at(const kt_problem *p, int j, int seg_a) {
+  if (j == seg_a) return seg_a == 0 ? p->psi_init : state_slot(p, p->psi_ck, seg_a / p->Kg);
+  return state_slot(p, p->psi_seg, j - seg_a - 1);
+}
+
+// dJ_T/deps of the last (mode 2) forward sweep with its jump record frozen.
+kt_status gradient_sweep(kt_problem *p, cudaStream_t st) {
+  if (!p->grad_ready) return fail(KT_ERR_STATE, "krotov_gradient needs propagate_forward(p, 2, ...) first");
+  const int prev = 1 - p->cur;
+  KT_CUDA(kt_launch_chi_grad_boundary(p->fp64, p->g, p->ops, p->tau, p->norm2, p->psi[p->final_buf],
+                                      p->chi_run[p->nt & 1], st));
+  KT_CUDA(kt_launch_cursor_seek(p->g, p->rec_step[prev], p->jcount[prev], p->nt, p->cursor, st));
+  GradArgs ga{};
+  ga.nt = p->nt;
+  ga.eps = p->eps_old;
+  ga.cursor = p->cursor;
+  ga.rec_step = p->rec_step[prev];
+  ga.rec_ch = p->rec_ch[prev];
+  ga.rec_s = p->rec_s[prev];
+  ga.rec_c = p->rec_c[prev];
+  ga.partials = p->gpart;
+  ga.counter = p->counter;
+  ga.grad = p->dgrad;
+  ga.status = p->status;
+  for (int seg_b = p->nt; seg_b > 0;) {
+    const int seg_a = ((seg_b - 1) / p->Kg) * p->Kg;
+    if (seg_b - 1 > seg_a) {
+      KT_CUDA(kt_launch_cursor_seek_fwd(p->g, p->rec_step[prev], p->jcount[prev], seg_a + 1, p->fcursor, st));
+      for (int j = seg_a + 1; j <= seg_b - 1; ++j) {
+        BwdArgs b = bwd_args(p);
+        b.j = j;
+        b.chi_in = psi_at(p, j - 1, seg_a);
+        b.chi_out = (void *)psi_at(p, j, seg_a);
+        b.cursor = p->fcursor;
+        b.forward_replay = 1;
+        b.jcount = p->jcount[prev];
+        KT_CUDA(kt_launch_bwd(p->fp64, p->ept, p->g, p->im_fwd, p->ops, b, st));
+      }
+    }
+    for (int j = seg_b; j >= seg_a + 1; --j) {
+      ga.j = j;
+      ga.psi_prev = psi_at(p, j - 1, seg_a);
+      ga.chi_t = p->chi_run[j & 1];
+      KT_CUDA(kt_launch_grad(p->fp64, p->grad_ept, p->g1, p->g.T, p->g.tile_elems, p->im_fwd, p->im_bwd, p->ops, ga, st));
+      kt_status s = launch_bwd_step(p, j, p->chi_run[j & 1], p->chi_run[(j - 1) & 1], st);
+      if (s != KT_OK) return s;
+    }
+    seg_b = seg_a;
+  }
+  return read_status(p, st);
 }
 
 kt_status backward_sweep(kt_problem *p, cudaStream_t st) {
@@ -1040,7 +1140,10 @@ KT_API kt_status kt_generator_dense(const kt_model_desc *md, const kt_config *cf
 KT_API kt_status propagate_forward(kt_problem *p, int sequential_update, double *F_out, void *stream) {
   if (!p) return fail(KT_ERR_ARG, "NULL problem");
   cudaStream_t st = (cudaStream_t)stream;
-  kt_status s = forward_sweep(p, sequential_update ? 1 : 0, st);
+  if (sequential_update < 0 || sequential_update > 2) return fail(KT_ERR_ARG, "sequential_update must be 0, 1 or 2");
+  kt_status s;
+  if (sequential_update == 2 && (s = grad_setup(p, st)) != KT_OK) return s;
+  s = forward_sweep(p, sequential_update == 1 ? 1 : 0, st, sequential_update == 2);
   if (s != KT_OK) return s;
   if (F_out) return host_fidelity(p, F_out, nullptr, st);
   return KT_OK;
@@ -1109,6 +1212,7 @@ KT_API kt_status krotov_set_pulses(kt_problem *p, const double *eps) {
   KT_CUDA(cudaMemcpy(p->eps_old, eps, n * sizeof(double), cudaMemcpyHostToDevice));
   KT_CUDA(cudaMemcpy(p->eps_new, eps, n * sizeof(double), cudaMemcpyHostToDevice));
   p->have_fwd = p->have_bwd = false;
+  p->grad_ready = false;
   return KT_OK;
 }
 
@@ -1137,6 +1241,16 @@ KT_API kt_status krotov_get_costate(kt_problem *p, int j, double *chi_out) {
   if (!p->have_bwd) return fail(KT_ERR_STATE, "no backward sweep since the last forward sweep");
   if (j < 0 || j > p->nt || !is_ckpt(p, j)) return fail(KT_ERR_ARG, "co-state %d not stored", j);
   return download_state(p, ckpt_slot(p, j), chi_out, 0);
+}
+
+KT_API kt_status krotov_gradient(kt_problem *p, double *dJ_out, void *stream) {
+  if (!p || !dJ_out) return fail(KT_ERR_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  kt_status s = gradient_sweep(p, st);
+  if (s != KT_OK) return s;
+  KT_CUDA(cudaMemcpyAsync(dJ_out, p->dgrad, sizeof(double) * p->g.n_ctrl * p->nt, cudaMemcpyDeviceToHost, st));
+  KT_CUDA(cudaStreamSynchronize(st));
+  return KT_OK;
 }
 
 KT_API kt_status krotov_set_uniforms(kt_problem *p, const double *uniforms, int n_passes, void *stream) {

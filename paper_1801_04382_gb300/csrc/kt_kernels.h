@@ -37,8 +37,10 @@ struct BwdArgs {
   const void *chi_in;
   void *chi_out;
   const double *eps;     // [n_ctrl][nt] pulse of the recorded forward pass
-  int *cursor;           // [M_pad] index of the latest unprocessed record
+  int *cursor;           // [M_pad] backward: latest unprocessed record; forward replay: next one
   int advance_cursor;
+  int forward_replay;    // 1: psi(t_{j-1}) -> psi(t_j) under H_eff with the recorded jumps c L
+  const int *jcount;     // [M_pad] records per trajectory (forward replay walks upwards)
   const int *rec_step;
   const int *rec_ch;
   const double *rec_s;
@@ -68,5 +70,33 @@ cudaError_t kt_launch_init_pass(const KtGeom &g, const double *U, int pass_row, 
                                 cudaStream_t st);
 cudaError_t kt_launch_cursor_seek(const KtGeom &g, const int *rec_step, const int *jcount, int upto,
                                   int *cursor, cudaStream_t st);
+// cursor[k] = first record of trajectory k with interval >= from (jcount[k] if none)
+cudaError_t kt_launch_cursor_seek_fwd(const KtGeom &g, const int *rec_step, const int *jcount, int from,
+                                      int *cursor, cudaStream_t st);
+cudaError_t kt_launch_chi_grad_boundary(int fp64, const KtGeom &g, const KtOps &ops, const KtCplx *tau,
+                                        const double *norm2, const void *psi, void *chi, cudaStream_t st);
+
+// Gradient of the frozen-record trajectory functional on interval j (one CTA per trajectory).
+struct GradArgs {
+  int j, nt;
+  const void *psi_prev;  // tile-layout psi(t_{j-1}) of the recorded forward pass
+  const void *chi_t;     // tile-layout chi~(t_j)
+  const double *eps;     // [n_ctrl][nt]
+  const int *cursor;     // [M_pad] latest record with interval <= j (backward cursor, not advanced)
+  const int *rec_step;
+  const int *rec_ch;
+  const double *rec_s;
+  const double *rec_c;
+  double *partials;      // [M][n_ctrl]
+  unsigned *counter;
+  double *grad;          // [n_ctrl][nt]: dJ_T/deps of interval j written by the last CTA
+  int *status;
+};
+// g1: the problem geometry re-cut to one trajectory per CTA (T = 1)
+size_t kt_grad_smem_bytes(const KtGeom &g1, int elem_bytes);
+cudaError_t kt_launch_grad(int fp64, int ept, const KtGeom &g1, int T_layout, int tile_elems_layout,
+                           const KtGenImage &im_fwd, const KtGenImage &im_bwd, const KtOps &ops, const GradArgs &a,
+                           cudaStream_t st);
+
 cudaError_t kt_launch_chi_boundary(int fp64, const KtGeom &g, const KtOps &ops, const KtCplx *tau, void *chi,
                                    cudaStream_t st);

@@ -20,6 +20,18 @@ __global__ void cursor_seek_kernel(KtGeom g, const int *rec_step, const int *jco
   cursor[k] = c;
 }
 
+__global__ void cursor_seek_fwd_kernel(KtGeom g, const int *rec_step, const int *jcount, int from, int *cursor) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= g.M_pad) return;
+  int c = 0;
+  if (k < g.M) {
+    c = jcount[k];
+    for (int m = jcount[k] - 1; m >= 0; --m)
+      if (rec_step[(size_t)k * g.max_jumps + m] >= from) c = m;
+  }
+  cursor[k] = c;
+}
+
 // chi_k(T) = tau_k |tgt>  (mode 0, Krotov boundary)
 template <typename C>
 __global__ void chi_boundary_kernel(KtGeom g, KtOps ops, const KtCplx *tau, C *chi) {
@@ -64,6 +76,43 @@ cudaError_t kt_launch_init_pass(const KtGeom &g, const double *U, int pass_row, 
 cudaError_t kt_launch_cursor_seek(const KtGeom &g, const int *rec_step, const int *jcount, int upto, int *cursor,
                                   cudaStream_t st) {
   cursor_seek_kernel<<<(g.M_pad + 255) / 256, 256, 0, st>>>(g, rec_step, jcount, upto, cursor);
+  return cudaGetLastError();
+}
+
+// exact co-state boundary of the gradient: chi~_k(T) = (tau_k |tgt> - |tau_k|^2 psihat_k) / ||psi_k(T)||
+template <typename C>
+__global__ void chi_grad_boundary_kernel(KtGeom g, KtOps ops, const KtCplx *tau, const double *norm2, const C *psi,
+                                         C *chi) {
+  typedef decltype(C().x) R;
+  const size_t n = (size_t)g.n_tiles * g.tile_elems;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int tile = (int)(e / g.tile_elems), rem = (int)(e % g.tile_elems);
+    if (rem >= g.d * g.T) { chi[e] = mkc((R)0, (R)0); continue; }
+    const int x = rem / g.T, t = rem % g.T, k = tile * g.T + t;
+    if (k >= g.M || !(norm2[k] > 0.0)) { chi[e] = mkc((R)0, (R)0); continue; }
+    const double nrm = sqrt(norm2[k]);
+    const KtCplx tg = ops.tgt[x], tk = tau[k];
+    const double t2 = tk.re * tk.re + tk.im * tk.im;
+    const double pr = (double)psi[e].x / nrm, pi = (double)psi[e].y / nrm;
+    const double re = (tk.re * tg.re - tk.im * tg.im - t2 * pr) / nrm;
+    const double im = (tk.re * tg.im + tk.im * tg.re - t2 * pi) / nrm;
+    chi[e] = mkc((R)re, (R)im);
+  }
+}
+
+cudaError_t kt_launch_chi_grad_boundary(int fp64, const KtGeom &g, const KtOps &ops, const KtCplx *tau,
+                                        const double *norm2, const void *psi, void *chi, cudaStream_t st) {
+  const size_t n = (size_t)g.n_tiles * g.tile_elems;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  if (fp64) chi_grad_boundary_kernel<double2><<<blocks, 256, 0, st>>>(g, ops, tau, norm2, (const double2 *)psi, (double2 *)chi);
+  else chi_grad_boundary_kernel<float2><<<blocks, 256, 0, st>>>(g, ops, tau, norm2, (const float2 *)psi, (float2 *)chi);
+  return cudaGetLastError();
+}
+
+cudaError_t kt_launch_cursor_seek_fwd(const KtGeom &g, const int *rec_step, const int *jcount, int from, int *cursor,
+                                      cudaStream_t st) {
+  cursor_seek_fwd_kernel<<<(g.M_pad + 255) / 256, 256, 0, st>>>(g, rec_step, jcount, from, cursor);
   return cudaGetLastError();
 }
 

@@ -63,11 +63,23 @@ class Problem:
         self.info = self.get_info()
 
     # ------------------------------------------------------------------ calls
-    def forward(self, update: bool = False, stream=None) -> float:
+    def forward(self, update: bool = False, stream=None, keep_for_gradient: bool = False) -> float:
+        """One forward sweep; returns F.  update: sequential Krotov update on the fly;
+        keep_for_gradient: plain sweep that keeps the forward states for gradient()."""
+        if update and keep_for_gradient:
+            raise ValueError("a sweep either updates the pulse or keeps states for the gradient")
+        mode = 1 if update else (2 if keep_for_gradient else 0)
         F = ct.c_double()
-        _capi.check(self._lib.propagate_forward(self._h, int(bool(update)), ct.byref(F), _stream_handle(stream)),
+        _capi.check(self._lib.propagate_forward(self._h, mode, ct.byref(F), _stream_handle(stream)),
                     "propagate_forward")
         return F.value
+
+    def gradient(self, stream=None) -> np.ndarray:
+        """dJ_T/deps [n_ctrl, nt] at the current pulse, jump record of the last
+        forward(keep_for_gradient=True) held fixed."""
+        out = np.zeros((self.n_ctrl, self.nt))
+        _capi.check(self._lib.krotov_gradient(self._h, _ptr(out), _stream_handle(stream)), "krotov_gradient")
+        return out
 
     def backward(self, stream=None) -> None:
         _capi.check(self._lib.propagate_backward(self._h, _stream_handle(stream)), "propagate_backward")

@@ -1,0 +1,80 @@
+"""GPU gradient (krotov_gradient / KrotovTrajFunction) against the oracle's exact frozen-record
+gradient and central finite differences.
+
+FP64: dJ_T/deps within 1e-10 of max |dJ_T/deps| of the oracle (the FP64 parity tolerance);
+FP32-mixed: within 2e-4 of it (complex64 propagation of states and co-states).
+"""
+import numpy as np
+import pytest
+
+import synth_inputs as si
+from oracle import gradient as og
+from oracle import mcwf
+from oracle import model as om
+from paper_1801_04382_gb300 import Problem, cascaded_chain
+
+pytestmark = pytest.mark.gpu
+
+
+def _records_to_oracle(recs):
+    return [[mcwf.Jump(step, s, ch, c) for (step, s, ch, c) in rk] for rk in recs]
+
+
+def _case(N, nc, T, nt, M, amp, seed, random_init=True, kappa=1.0):
+    eps = si.guess_pulses(N, nt, T, amp)
+    S = si.shape_functions(N, nt, T)
+    lam = np.full(N, 10.0)
+    U = si.uniforms(seed, 2, M, 1 + 2 * N * (1 + nc))
+    d = (3 * (nc + 1)) ** N
+    psi0 = si.random_states(seed + 50, M, d) if random_init else None
+    return eps, S, lam, U, psi0
+
+
+@pytest.mark.parametrize("ckpt", [0, 7])
+def test_gradient_fp64_matches_oracle_with_jumps(ckpt):
+    N, nc, T, nt, M = 2, 1, 6.0, 60, 6
+    eps, S, lam, U, psi0 = _case(N, nc, T, nt, M, 30.0, 5)
+    with Problem(cascaded_chain(N, nc), T, nt, M, eps, S, lam, U, psi0_batch=psi0, ckpt_interval=ckpt) as p:
+        F = p.forward(keep_for_gradient=True)
+        recs = p.records()
+        grad = p.gradient()
+    assert sum(len(r) for r in recs) >= 2
+    m = om.build_model(N, nc)
+    ref, jt = og.gradient(m, eps, T, psi0, _records_to_oracle(recs))
+    assert abs((1.0 - F) - jt) <= 1e-10
+    assert np.abs(grad - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+def test_gradient_fp32_d729_matches_oracle():
+    N, nc, T, nt, M = 3, 2, 0.25, 10, 4
+    eps, S, lam, U, psi0 = _case(N, nc, T, nt, M, 30.0, 2)
+    with Problem(cascaded_chain(N, nc), T, nt, M, eps, S, lam, U, psi0_batch=psi0, precision="fp32") as p:
+        p.forward(keep_for_gradient=True)
+        recs = p.records()
+        grad = p.gradient()
+    m = om.build_model(N, nc)
+    ref, _ = og.gradient(m, eps, T, psi0, _records_to_oracle(recs))
+    assert np.abs(grad - ref).max() <= 2e-4 * np.abs(ref).max()
+
+
+def test_autograd_function_matches_central_differences_at_kappa_zero():
+    torch = pytest.importorskip("torch")
+    from paper_1801_04382_gb300 import trajectory_functional
+    N, nc, T, nt, M = 2, 1, 5.0, 50, 3
+    eps, S, lam, U, psi0 = _case(N, nc, T, nt, M, 30.0, 8, kappa=0.0)
+    net = cascaded_chain(N, nc, kappa=0.0)
+    with Problem(net, T, nt, M, eps, S, lam, U, psi0_batch=psi0) as p:
+        e = torch.tensor(eps, dtype=torch.float64, requires_grad=True)
+        J = trajectory_functional(e, p)
+        J.backward()
+        g = e.grad.numpy()
+        rng = np.random.default_rng(0)
+        h = 1e-4
+        for _ in range(20):
+            i, j = int(rng.integers(N)), int(rng.integers(nt))
+            ep = eps.copy(); ep[i, j] += h
+            em = eps.copy(); em[i, j] -= h
+            Jp = float(trajectory_functional(torch.tensor(ep), p))
+            Jm = float(trajectory_functional(torch.tensor(em), p))
+            fd = (Jp - Jm) / (2 * h)
+            assert fd == pytest.approx(g[i, j], rel=1e-6, abs=1e-11)
