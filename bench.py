@@ -164,6 +164,36 @@ def cpu_baseline(wl, budget_s: float = 20.0):
 
 
 # ------------------------------------------------------------------------------------------
+def precision_comparison(stream, n_iter: int = 50):
+    """FP32-mixed vs plain FP64 on the d = 81 workload (two nodes, cavity cutoff 2, 128
+    trajectories, nt = 1000, seed 1): Krotov iterations/s of each path over n_iter iterations
+    (CUDA events) and the final fidelities, which must agree within 1e-4."""
+    import torch
+    from paper_1801_04382_gb300 import Problem, cascaded_chain
+    wl = si.CONFIGS["cfg2_d81"]
+    net = cascaded_chain(wl.n_nodes, wl.n_cav, wl.delta, wl.g, wl.kappa)
+    eps0 = si.guess_pulses(net.n_ctrl, wl.nt, wl.T, wl.guess_amp)
+    S = si.shape_functions(net.n_ctrl, wl.nt, wl.T)
+    lam = np.full(net.n_ctrl, wl.lam)
+    U = si.uniforms(wl.seed, n_iter + 1, wl.M, wl.draws_per_traj)
+    out = {"workload": f"{wl.name} (d={wl.d}, M={wl.M}, nt={wl.nt}), {n_iter} iterations"}
+    for prec in ("fp32", "fp64"):
+        with Problem(net, wl.T, wl.nt, wl.M, eps0, S, lam, U, precision=prec, stream=stream) as p:
+            p.forward(False, stream=stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            JT, _ = p.update(n_iter, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            out[f"{prec}_iters_per_s"] = n_iter * 1000.0 / ms
+            out[f"{prec}_final_F"] = 1.0 - float(JT[-1])
+    out["final_F_abs_diff"] = abs(out["fp32_final_F"] - out["fp64_final_F"])
+    out["fp32_over_fp64"] = out["fp32_iters_per_s"] / out["fp64_iters_per_s"]
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -304,6 +334,8 @@ def run_ours(args, rank, world):
         "gpu_launches": int(prof["fwd"][1] + prof["bwd"][1] + 4 * args.steps),
         "clocks": clocks,
     }
+    if rank == 0 and not args.no_precision_comparison:
+        line["fp32_vs_fp64"] = precision_comparison(stream)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     prob.close()
@@ -323,6 +355,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision-comparison", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
