@@ -38,6 +38,7 @@ extern "C" {
 #define KT_API __attribute__((visibility("default")))
 
 typedef struct kt_problem kt_problem;   /* opaque; created by krotov_init, owned by the library */
+typedef struct kt_batch kt_batch;       /* opaque; independent problems iterated together */
 
 typedef enum {
   KT_OK = 0,
@@ -110,7 +111,10 @@ typedef struct {
   double eps_bound;         /* bound on |eps| used for the spectral estimate; 0 = automatic
                                (2 max|eps_guess| + 1) */
   double cheb_tol;          /* Chebyshev truncation; 0 = 1e-15 (FP64) / 1e-8 (FP32-mixed) */
-  int tile_traj;            /* trajectories per CTA tile (power of two <= 32); 0 = automatic */
+  int tile_traj;            /* trajectories per CTA tile (power of two <= 32); 0 = automatic
+                               (heuristic); -1 = autotuned: krotov_init times the forward
+                               interval kernel for every width that fits (12 launches each on
+                               `stream`, guess pulse) and keeps the fastest */
 } kt_config;
 
 /* Create a problem: validate, assemble H_eff in structured form (a1), choose the Chebyshev
@@ -152,7 +156,11 @@ KT_API kt_status propagate_backward(kt_problem *p, void *stream);
  * no forward sweep has run yet, a guess sweep propagate_forward(0) runs first.  JT_out and
  * J_out (nullable, [n_iter]) receive J_T = 1 - F and Krotov's functional
  * J = J_T + sum_c lambda_c sum_j Delta eps_cj^2 dt / S_cj (Eq. krotov_functional, S = 0
- * points skipped) after each iteration. */
+ * points skipped) after each iteration.  With profiling off, each iteration is one CUDA graph
+ * launch: the launches of an iteration are captured on first use for each state of the
+ * double-buffered pulse and record arrays (two alternate), and device failures are reported at
+ * the end of the iteration instead of after each sweep.  The results are identical to calling
+ * propagate_backward and propagate_forward(p, 1, ...) in turn. */
 KT_API kt_status krotov_update(kt_problem *p, int n_iter, double *JT_out, double *J_out, void *stream);
 
 /* F and tau_k ([M][2], nullable) of the last forward sweep (Eq. functional_traj). */
@@ -208,6 +216,26 @@ KT_API kt_status krotov_get_info(kt_problem *p, kt_info *info);
 
 KT_API void krotov_free(kt_problem *p);
 KT_API const char *krotov_last_error(void);
+
+/* Batches of independent optimisation problems (the trajectories of one problem are
+ * independent of every other problem, Sec. 2.3), e.g. networks of different sizes.
+ * krotov_init_batch creates n problems as krotov_init would (models[i] with cfgs[i]; on failure
+ * nothing is kept and the message names the problem index).  krotov_batch_update runs n_iter
+ * Krotov iterations of every problem; each iteration is ONE CUDA graph launch on `stream` whose
+ * branches are the problems' captured iterations, with no dependency between problems, so that
+ * the device runs the problems' interval kernels concurrently.  Problems without a forward
+ * sweep first run their guess sweeps, concurrently on internal streams.  JT_out (nullable,
+ * [n_iter][n]) receives 1 - F of each problem after each iteration.  Results are identical to
+ * krotov_update on each problem alone.  krotov_batch_problem lends problem i (owned by the
+ * batch: use it with the single-problem calls, never free it); krotov_batch_info reports the
+ * problem count, the kernel nodes of the last built batch graph and the device bytes held. */
+KT_API kt_status krotov_init_batch(const kt_model_desc *const *models, const kt_config *const *cfgs, int n,
+                                   void *stream, kt_batch **out);
+KT_API kt_status krotov_batch_update(kt_batch *b, int n_iter, double *JT_out, void *stream);
+KT_API kt_status krotov_batch_problem(kt_batch *b, int i, kt_problem **out);
+KT_API kt_status krotov_batch_info(kt_batch *b, int *n_problems, long long *graph_nodes,
+                                   long long *device_bytes);
+KT_API void krotov_batch_free(kt_batch *b);
 
 /* Chebyshev coefficient helper (host): Bessel J_0..J_{n-1}(alpha) by Miller's backward
  * recurrence, the routine the kernels use for sub-step propagators.  Returns KT_ERR_ARG for

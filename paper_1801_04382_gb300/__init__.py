@@ -6,7 +6,7 @@ behind the C ABI of ``include/krotov_traj.h``; this package holds the build scri
 ctypes binding (``Problem``) and the structured model builder.
 """
 from .model import NetworkFactors, cascaded_chain  # noqa: F401
-from .problem import Problem, bessel_j  # noqa: F401
+from .problem import Batch, Problem, bessel_j  # noqa: F401
 from . import build  # noqa: F401  (module: build.build() compiles the CUDA library)
 from ._capi import KrotovError  # noqa: F401
 

@@ -69,6 +69,12 @@ SIGNATURES = {
     "krotov_get_profile": (ct.c_int, [ct.c_void_p, dp, ct.POINTER(ct.c_longlong)]),
     "krotov_free": (None, [ct.c_void_p]),
     "krotov_last_error": (ct.c_char_p, []),
+    "krotov_init_batch": (ct.c_int, [ct.POINTER(ct.POINTER(ModelDesc)), ct.POINTER(ct.POINTER(Config)), ct.c_int,
+                                     ct.c_void_p, ct.POINTER(ct.c_void_p)]),
+    "krotov_batch_update": (ct.c_int, [ct.c_void_p, ct.c_int, dp, ct.c_void_p]),
+    "krotov_batch_problem": (ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_void_p)]),
+    "krotov_batch_info": (ct.c_int, [ct.c_void_p, ip, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_longlong)]),
+    "krotov_batch_free": (None, [ct.c_void_p]),
     "kt_bessel_j": (ct.c_int, [ct.c_double, ct.c_int, dp]),
     "kt_generator_dense": (ct.c_int, [ct.POINTER(ModelDesc), ct.POINTER(Config), ct.c_int, dp, dp]),
     "kt_update_overlap_noalloc": (ct.c_int, [ct.c_int, ct.c_int, ct.c_int, ip, dp, ct.c_int, ct.c_void_p,

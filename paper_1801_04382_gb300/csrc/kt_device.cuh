@@ -925,7 +925,7 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
             set_status(a.status, KT_DEV_ZERO_JUMP);      // norm loss without any jump operator
             sm.tin[TI_ACT * g.T + t] = 0;
           } else {
-            const double *U = a.U + ((size_t)a.pass_row * g.M + k) * g.draws;
+            const double *U = a.U + ((size_t)*a.pass_row * g.M + k) * g.draws;
             double tot = 0.0;
             for (int l = 0; l < g.n_lind; ++l) tot += p[l];
             const double target = U[2 * m - 1] * tot;   // first channel whose cumulative p reaches u * sum p

@@ -171,7 +171,8 @@ struct kt_problem {
   double *norm2 = nullptr;
   int *status = nullptr;
 
-  long long pass_counter = 0;
+  int *pass = nullptr;          // device [3]: next uniforms row, rows held, row of the running pass
+  double *eps_base = nullptr;   // the pulse buffer eps_old pointed to at init (keys the graphs)
   bool have_fwd = false, have_bwd = false, have_deps = false;
   int final_buf = 0;
 
@@ -192,6 +193,13 @@ struct kt_problem {
   int ev_used = 0;
   double prof_ms[KT_PROF_FAMILIES] = {0, 0, 0};
   long long prof_launches[KT_PROF_FAMILIES] = {0, 0, 0};
+
+  // Krotov iterations (backward sweep + updating forward sweep) captured as CUDA graphs, one per
+  // buffer state: the record buffer being written (cur) and which pulse buffer holds the old pulse.
+  // Both flip every iteration, so a run alternates between two of the four.
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t iter_graph[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaGraphExec_t iter_exec[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -279,11 +287,11 @@ kt_status read_status(kt_problem *p, cudaStream_t st) {
   }
 }
 
-FwdArgs fwd_args(kt_problem *p, int update, int pass_row) {
+FwdArgs fwd_args(kt_problem *p, int update) {
   FwdArgs a{};
   a.nt = p->nt;
   a.update = update;
-  a.pass_row = pass_row;
+  a.pass_row = p->pass + 2;
   a.eps_old = p->eps_old;
   a.eps_new = p->eps_new;
   a.deps = p->deps;
@@ -350,13 +358,11 @@ const void *chi_at(const kt_problem *p, int j, int seg_a) {
   return state_slot(p, p->seg, j - seg_a);
 }
 
-kt_status forward_sweep(kt_problem *p, int update, cudaStream_t st, bool save_psi = false) {
-  if (update && !p->have_bwd)
-    return fail(KT_ERR_STATE, "an updating forward sweep needs a backward sweep since the last forward sweep");
-  const int pass_row = (int)(p->pass_counter % p->n_passes);
-  p->pass_counter++;
-  KT_CUDA(kt_launch_init_pass(p->g, p->U, pass_row, p->rstate, p->jcount[p->cur], st));
-  FwdArgs a = fwd_args(p, update, pass_row);
+// Launches of one forward sweep: no synchronisation and no change of host state, so that the
+// sequence can be captured into a graph.
+kt_status enqueue_forward(kt_problem *p, int update, cudaStream_t st, bool save_psi) {
+  KT_CUDA(kt_launch_init_pass(p->g, p->U, p->pass, p->rstate, p->jcount[p->cur], st));
+  FwdArgs a = fwd_args(p, update);
   if (update) {
     a.j = 0;
     a.psi_in = p->psi_init;
@@ -388,8 +394,11 @@ kt_status forward_sweep(kt_problem *p, int update, cudaStream_t st, bool save_ps
                                 cudaMemcpyDeviceToDevice, st));
     }
   }
-  kt_status s = read_status(p, st);
-  if (s != KT_OK) return s;
+  return KT_OK;
+}
+
+// Host bookkeeping of a completed forward sweep.
+void commit_forward(kt_problem *p, int update, bool save_psi) {
   p->final_buf = p->nt & 1;
   if (update) {
     std::swap(p->eps_old, p->eps_new);
@@ -399,6 +408,15 @@ kt_status forward_sweep(kt_problem *p, int update, cudaStream_t st, bool save_ps
   p->have_fwd = true;
   p->have_bwd = false;
   p->grad_ready = save_psi;
+}
+
+kt_status forward_sweep(kt_problem *p, int update, cudaStream_t st, bool save_psi = false) {
+  if (update && !p->have_bwd)
+    return fail(KT_ERR_STATE, "an updating forward sweep needs a backward sweep since the last forward sweep");
+  kt_status s = enqueue_forward(p, update, st, save_psi);
+  if (s != KT_OK) return s;
+  if ((s = read_status(p, st)) != KT_OK) return s;
+  commit_forward(p, update, save_psi);
   return KT_OK;
 }
 
@@ -486,8 +504,8 @@ kt_status gradient_sweep(kt_problem *p, cudaStream_t st) {
   return read_status(p, st);
 }
 
-kt_status backward_sweep(kt_problem *p, cudaStream_t st) {
-  if (!p->have_fwd) return fail(KT_ERR_STATE, "propagate_backward needs a forward sweep first");
+// Launches of one backward sweep (capturable, like enqueue_forward).
+kt_status enqueue_backward(kt_problem *p, cudaStream_t st) {
   const int prev = 1 - p->cur;
   void *chiT = ckpt_slot(p, p->nt);
   KT_CUDA(kt_launch_chi_boundary(p->fp64, p->g, p->ops, p->tau, chiT, st));
@@ -501,9 +519,67 @@ kt_status backward_sweep(kt_problem *p, cudaStream_t st) {
     if (s != KT_OK) return s;
     in = out;
   }
-  kt_status s = read_status(p, st);
+  return KT_OK;
+}
+
+kt_status backward_sweep(kt_problem *p, cudaStream_t st) {
+  if (!p->have_fwd) return fail(KT_ERR_STATE, "propagate_backward needs a forward sweep first");
+  kt_status s = enqueue_backward(p, st);
   if (s != KT_OK) return s;
+  if ((s = read_status(p, st)) != KT_OK) return s;
   p->have_bwd = true;
+  return KT_OK;
+}
+
+int iter_key(const kt_problem *p) { return p->cur | (p->eps_old == p->eps_base ? 2 : 0); }
+
+// Capture one Krotov iteration (backward sweep with the last records and the old pulse, then the
+// updating forward sweep) for the current buffer state.  Capture runs on the problem's own
+// stream, because the legacy default stream cannot be captured.
+kt_status capture_iteration(kt_problem *p, cudaGraph_t *out) {
+  const int key = iter_key(p);
+  if (p->iter_graph[key]) {
+    *out = p->iter_graph[key];
+    return KT_OK;
+  }
+  if (!p->cap_stream) KT_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+  KT_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeRelaxed));
+  kt_status s = enqueue_backward(p, p->cap_stream);
+  if (s == KT_OK) s = enqueue_forward(p, 1, p->cap_stream, false);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(p->cap_stream, &graph);
+  if (s != KT_OK || e != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return s != KT_OK ? s : fail(KT_ERR_CUDA, "graph capture of a Krotov iteration failed: %s", cudaGetErrorString(e));
+  }
+  p->iter_graph[key] = graph;
+  *out = graph;
+  return KT_OK;
+}
+
+// Host bookkeeping of a completed graph iteration.
+void commit_iteration(kt_problem *p) {
+  p->have_bwd = true;
+  commit_forward(p, 1, false);
+}
+
+// One Krotov iteration as a single graph launch on st.
+kt_status graph_iteration(kt_problem *p, cudaStream_t st) {
+  const int key = iter_key(p);
+  if (!p->iter_exec[key]) {
+    cudaGraph_t graph;
+    kt_status s = capture_iteration(p, &graph);
+    if (s != KT_OK) return s;
+    KT_CUDA(cudaGraphInstantiate(&p->iter_exec[key], graph, 0));
+  }
+  KT_CUDA(cudaGraphLaunch(p->iter_exec[key], st));
+  kt_status s = read_status(p, st);
+  if (s != KT_OK) {
+    p->have_fwd = p->have_bwd = false;    // the iteration's sweeps are incomplete: restart from a forward sweep
+    return s;
+  }
+  commit_iteration(p);
   return KT_OK;
 }
 
@@ -587,6 +663,11 @@ KT_API kt_status kt_bessel_j(double alpha, int n, double *out) {
 KT_API void krotov_free(kt_problem *p) {
   if (!p) return;
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  for (int k = 0; k < 4; ++k) {
+    if (p->iter_exec[k]) cudaGraphExecDestroy(p->iter_exec[k]);
+    if (p->iter_graph[k]) cudaGraphDestroy(p->iter_graph[k]);
+  }
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   for (void *a : p->allocs) cudaFree(a);
   delete p;
 }
@@ -670,6 +751,7 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
     return fail(KT_ERR_ARG, "need n_passes >= 1 and odd draws_per_traj >= 1");
   if (cfg->prec != KT_FP64 && cfg->prec != KT_FP32_MIXED) return fail(KT_ERR_ARG, "unknown precision");
   if (cfg->ckpt_interval < 0) return fail(KT_ERR_ARG, "ckpt_interval < 0");
+  if (cfg->tile_traj < -1) return fail(KT_ERR_ARG, "tile_traj must be -1 (autotuned), 0 (automatic) or a power of two <= 32");
   for (int c = 0; c < md->n_ctrl; ++c) {
     if (md->ctrl_node[c] < 0 || md->ctrl_node[c] >= N) return fail(KT_ERR_ARG, "ctrl_node[%d] out of range", c);
     if (!(cfg->lambda_a[c] > 0.0)) return fail(KT_ERR_ARG, "lambda[%d] must be > 0", c);
@@ -848,7 +930,7 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
     if (kt_smem_bytes(t, esz, false) > 227 * 1024) continue;
     Tsel = T;
     // prefer more tiles when the trajectories would not fill the GPU
-    if (cfg->tile_traj == 0 && (M + T - 1) / T < 2 * 152 && T > 1 && (long long)d * (T / 2) >= 256) continue;
+    if (cfg->tile_traj <= 0 && (M + T - 1) / T < 2 * 152 && T > 1 && (long long)d * (T / 2) >= 256) continue;
     break;
   }
   if (Tsel == 0) return fail(KT_ERR_UNSUPPORTED, "dimension %d does not fit one trajectory tile in shared memory", d);
@@ -991,13 +1073,14 @@ kt_status upload_image(kt_problem *p, const HostImage &h, KtGenImage &im, cudaSt
 
 extern "C" {
 
-KT_API kt_status krotov_init(const kt_model_desc *md, const kt_config *cfg, void *stream, kt_problem **out) {
-  if (!md || !cfg || !out) return fail(KT_ERR_ARG, "NULL descriptor or output pointer");
-  *out = nullptr;
-  cudaStream_t st = (cudaStream_t)stream;
-  HostPlan P;
-  kt_status s = plan(md, cfg, P);
-  if (s != KT_OK) return s;
+}  // extern "C"
+
+namespace {
+
+// Allocate and upload a problem for the plan P.  A probe (autotuning) keeps no co-state storage.
+kt_status create_problem(const kt_model_desc *md, const kt_config *cfg, const HostPlan &P, cudaStream_t st,
+                         bool probe, kt_problem **out) {
+  kt_status s;
   const int nt = cfg->nt, M = cfg->M, nc = md->n_ctrl;
 
   kt_problem *p = new kt_problem();
@@ -1053,9 +1136,11 @@ KT_API kt_status krotov_init(const kt_model_desc *md, const kt_config *cfg, void
   }
   TRY(dev_alloc(p, &p->psi[0], p->state_bytes));
   TRY(dev_alloc(p, &p->psi[1], p->state_bytes));
-  p->n_chi_slots = p->ckpt == 0 ? nt + 1 : nt / p->ckpt + 1 + (nt % p->ckpt ? 1 : 0);
-  TRY(dev_alloc(p, &p->chi, p->state_bytes * p->n_chi_slots));
-  if (p->ckpt > 0) TRY(dev_alloc(p, &p->seg, p->state_bytes * (p->ckpt + 1)));
+  if (!probe) {
+    p->n_chi_slots = p->ckpt == 0 ? nt + 1 : nt / p->ckpt + 1 + (nt % p->ckpt ? 1 : 0);
+    TRY(dev_alloc(p, &p->chi, p->state_bytes * p->n_chi_slots));
+    if (p->ckpt > 0) TRY(dev_alloc(p, &p->seg, p->state_bytes * (p->ckpt + 1)));
+  }
   const size_t Mp = g.M_pad, mj = g.max_jumps;
   TRY(dev_alloc(p, (void **)&p->rstate, Mp * sizeof(double)));
   for (int b = 0; b < 2; ++b) {
@@ -1072,7 +1157,10 @@ KT_API kt_status krotov_init(const kt_model_desc *md, const kt_config *cfg, void
   TRY(dev_alloc(p, (void **)&p->tau, Mp * sizeof(KtCplx)));
   TRY(dev_alloc(p, (void **)&p->norm2, Mp * sizeof(double)));
   TRY(dev_alloc(p, (void **)&p->status, sizeof(int)));
-  if (cudaMemsetAsync(p->counter, 0, sizeof(unsigned), st) != cudaSuccess ||
+  TRY(dev_alloc(p, (void **)&p->pass, 3 * sizeof(int)));
+  p->eps_base = p->eps_old;
+  if (kt_launch_pass_reset(p->pass, p->n_passes, st) != cudaSuccess ||
+      cudaMemsetAsync(p->counter, 0, sizeof(unsigned), st) != cudaSuccess ||
       cudaMemsetAsync(p->status, 0, sizeof(int), st) != cudaSuccess) {
     krotov_free(p);
     return fail(KT_ERR_CUDA, "memset failed");
@@ -1086,6 +1174,84 @@ KT_API kt_status krotov_init(const kt_model_desc *md, const kt_config *cfg, void
   p->lam_h.assign(cfg->lambda_a, cfg->lambda_a + nc);
   *out = p;
   return KT_OK;
+}
+
+// Average duration of the forward interval kernel of probe q (no update, guess pulse), timed with
+// events on st over a few intervals after two warm-up launches.
+kt_status probe_forward_ms(kt_problem *q, cudaStream_t st, double *ms_out) {
+  const int warm = 2, timed = 12;
+  KT_CUDA(kt_launch_init_pass(q->g, q->U, q->pass, q->rstate, q->jcount[0], st));
+  FwdArgs a = fwd_args(q, 0);
+  a.chi_t = nullptr;
+  cudaEvent_t e[2];
+  KT_CUDA(cudaEventCreate(&e[0]));
+  if (cudaEventCreate(&e[1]) != cudaSuccess) {
+    cudaEventDestroy(e[0]);
+    return fail(KT_ERR_CUDA, "cudaEventCreate failed");
+  }
+  cudaError_t err = cudaSuccess;
+  for (int i = 0; i < warm + timed && err == cudaSuccess; ++i) {
+    if (i == warm) err = cudaEventRecord(e[0], st);
+    a.j = 1 + i % q->nt;
+    a.psi_in = i == 0 ? q->psi_init : q->psi[(i - 1) & 1];
+    a.psi_out = q->psi[i & 1];
+    if (err == cudaSuccess) err = kt_launch_fwd(q->fp64, q->ept, q->g, q->im_fwd, q->ops, a, st);
+  }
+  if (err == cudaSuccess) err = cudaEventRecord(e[1], st);
+  if (err == cudaSuccess) err = cudaEventSynchronize(e[1]);
+  float ms = 0.f;
+  if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e[0], e[1]);
+  cudaEventDestroy(e[0]);
+  cudaEventDestroy(e[1]);
+  if (err != cudaSuccess) return fail(KT_ERR_CUDA, "autotuning launch failed: %s", cudaGetErrorString(err));
+  *ms_out = ms / timed;
+  return KT_OK;
+}
+
+// Tile-width autotuner: plan every power-of-two tile width that fits, time the forward interval
+// kernel of each (thread count and items per thread follow from the width), keep the fastest.
+kt_status autotune(const kt_model_desc *md, const kt_config *cfg, cudaStream_t st, HostPlan &best) {
+  double best_ms = 0.0;
+  int best_T = 0;
+  kt_status last = KT_ERR_UNSUPPORTED;
+  for (int T = 1; T <= 32; T <<= 1) {
+    kt_config c = *cfg;
+    c.tile_traj = T;
+    HostPlan P;
+    kt_status s = plan(md, &c, P);
+    if (s != KT_OK) {
+      if (s != KT_ERR_UNSUPPORTED) return s;       // a descriptor error, the same for every width
+      last = s;
+      continue;
+    }
+    kt_problem *q = nullptr;
+    if ((s = create_problem(md, &c, P, st, true, &q)) != KT_OK) return s;
+    double ms = 0.0;
+    s = probe_forward_ms(q, st, &ms);
+    krotov_free(q);
+    if (s != KT_OK) return s;
+    if (best_T == 0 || ms < best_ms) {
+      best_ms = ms;
+      best_T = T;
+      best = P;
+    }
+  }
+  if (best_T == 0) return last == KT_OK ? fail(KT_ERR_UNSUPPORTED, "no tile width fits") : last;
+  return KT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+KT_API kt_status krotov_init(const kt_model_desc *md, const kt_config *cfg, void *stream, kt_problem **out) {
+  if (!md || !cfg || !out) return fail(KT_ERR_ARG, "NULL descriptor or output pointer");
+  *out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  HostPlan P;
+  kt_status s = cfg->tile_traj == -1 ? autotune(md, cfg, st, P) : plan(md, cfg, P);
+  if (s != KT_OK) return s;
+  return create_problem(md, cfg, P, st, false, out);
 }
 
 // Host-only expansion of the generator tables into a dense matrix, indexed exactly the way the
@@ -1162,8 +1328,13 @@ KT_API kt_status krotov_update(kt_problem *p, int n_iter, double *JT_out, double
   if (!p->have_fwd && (s = forward_sweep(p, 0, st)) != KT_OK) return s;
   std::vector<double> de;
   for (int it = 0; it < n_iter; ++it) {
-    if ((s = backward_sweep(p, st)) != KT_OK) return s;
-    if ((s = forward_sweep(p, 1, st)) != KT_OK) return s;
+    if (p->profiling) {
+      // per-launch event pairs need the launches issued one by one
+      if ((s = backward_sweep(p, st)) != KT_OK) return s;
+      if ((s = forward_sweep(p, 1, st)) != KT_OK) return s;
+    } else if ((s = graph_iteration(p, st)) != KT_OK) {
+      return s;
+    }
     if (JT_out || J_out) {
       double F = 0.0;
       if ((s = host_fidelity(p, &F, nullptr, st)) != KT_OK) return s;
@@ -1260,8 +1431,8 @@ KT_API kt_status krotov_set_uniforms(kt_problem *p, const double *uniforms, int 
   const size_t n = (size_t)n_passes * p->M * p->g.draws;
   cudaStream_t st = (cudaStream_t)stream;
   KT_CUDA(cudaMemcpyAsync(p->U, uniforms, n * sizeof(double), cudaMemcpyHostToDevice, st));
+  KT_CUDA(kt_launch_pass_reset(p->pass, n_passes, st));
   p->n_passes = n_passes;
-  p->pass_counter = 0;
   return KT_OK;
 }
 
@@ -1298,6 +1469,190 @@ KT_API kt_status krotov_get_info(kt_problem *p, kt_info *info) {
   info->damping = p->damping;
   info->device_bytes = (long long)p->bytes;
   return KT_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================ batches of problems
+// Independent problems (their own model, size, precision and buffers) whose Krotov iterations
+// run as one CUDA graph launch: each problem's captured iteration is a child graph of the batch
+// graph, with no edges between problems, so the device schedules their interval kernels
+// concurrently.
+struct kt_batch {
+  std::vector<kt_problem *> probs;
+  struct Entry {
+    std::vector<int> keys;      // iter_key of every problem the graph was built for
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long nodes = 0;
+  };
+  Entry cache[2];               // the two buffer states an iteration alternates between
+  int next_slot = 0;
+};
+
+namespace {
+
+void drop_entry(kt_batch::Entry &e) {
+  if (e.exec) cudaGraphExecDestroy(e.exec);
+  if (e.graph) cudaGraphDestroy(e.graph);
+  e = kt_batch::Entry{};
+}
+
+kt_status batch_graph(kt_batch *b, kt_batch::Entry **out) {
+  std::vector<int> keys(b->probs.size());
+  for (size_t i = 0; i < b->probs.size(); ++i) keys[i] = iter_key(b->probs[i]);
+  for (kt_batch::Entry &e : b->cache)
+    if (e.exec && e.keys == keys) {
+      *out = &e;
+      return KT_OK;
+    }
+  kt_batch::Entry &e = b->cache[b->next_slot];
+  b->next_slot ^= 1;
+  drop_entry(e);
+  KT_CUDA(cudaGraphCreate(&e.graph, 0));
+  for (size_t i = 0; i < b->probs.size(); ++i) {
+    cudaGraph_t child;
+    kt_status s = capture_iteration(b->probs[i], &child);
+    if (s != KT_OK) {
+      drop_entry(e);
+      return s;
+    }
+    size_t n = 0;
+    cudaGraphNode_t node;
+    if (cudaGraphGetNodes(child, nullptr, &n) != cudaSuccess ||
+        cudaGraphAddChildGraphNode(&node, e.graph, nullptr, 0, child) != cudaSuccess) {
+      drop_entry(e);
+      return fail(KT_ERR_CUDA, "building the batch graph failed at problem %zu", i);
+    }
+    e.nodes += (long long)n;
+  }
+  const cudaError_t err = cudaGraphInstantiate(&e.exec, e.graph, 0);
+  if (err != cudaSuccess) {
+    drop_entry(e);
+    return fail(KT_ERR_CUDA, "batch graph instantiation failed: %s", cudaGetErrorString(err));
+  }
+  e.keys = keys;
+  *out = &e;
+  return KT_OK;
+}
+
+// Prefix the calling thread's last error with the problem index.
+kt_status batch_fail(kt_status s, size_t i) {
+  const std::string msg = g_err;
+  return fail(s, "problem %zu: %s", i, msg.c_str());
+}
+
+}  // namespace
+
+extern "C" {
+
+KT_API kt_status krotov_init_batch(const kt_model_desc *const *models, const kt_config *const *cfgs, int n,
+                                   void *stream, kt_batch **out) {
+  if (!models || !cfgs || !out) return fail(KT_ERR_ARG, "NULL descriptor array or output pointer");
+  *out = nullptr;
+  if (n < 1) return fail(KT_ERR_ARG, "a batch needs n >= 1 problems");
+  kt_batch *b = new kt_batch();
+  for (int i = 0; i < n; ++i) {
+    kt_problem *p = nullptr;
+    const kt_status s = krotov_init(models[i], cfgs[i], stream, &p);
+    if (s != KT_OK) {
+      krotov_batch_free(b);
+      return batch_fail(s, (size_t)i);
+    }
+    b->probs.push_back(p);
+  }
+  *out = b;
+  return KT_OK;
+}
+
+KT_API kt_status krotov_batch_update(kt_batch *b, int n_iter, double *JT_out, void *stream) {
+  if (!b) return fail(KT_ERR_ARG, "NULL batch");
+  if (n_iter < 0) return fail(KT_ERR_ARG, "n_iter < 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t n = b->probs.size();
+  kt_status s;
+  // guess sweeps, on the problems' own streams so that they overlap
+  {
+    cudaEvent_t ready;
+    KT_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ready, st);
+    std::vector<size_t> started;
+    for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
+      kt_problem *p = b->probs[i];
+      if (p->have_fwd) continue;
+      if (!p->cap_stream) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(p->cap_stream, ready, 0);
+      if (e != cudaSuccess) break;
+      if ((s = enqueue_forward(p, 0, p->cap_stream, false)) != KT_OK) {
+        cudaEventDestroy(ready);
+        return batch_fail(s, i);
+      }
+      started.push_back(i);
+    }
+    cudaEventDestroy(ready);
+    if (e != cudaSuccess) return fail(KT_ERR_CUDA, "guess sweeps: %s", cudaGetErrorString(e));
+    for (size_t i : started) {
+      if ((s = read_status(b->probs[i], b->probs[i]->cap_stream)) != KT_OK) return batch_fail(s, i);
+      commit_forward(b->probs[i], 0, false);
+    }
+  }
+  for (int it = 0; it < n_iter; ++it) {
+    kt_batch::Entry *e = nullptr;
+    if ((s = batch_graph(b, &e)) != KT_OK) return s;
+    KT_CUDA(cudaGraphLaunch(e->exec, st));
+    kt_status first = KT_OK;
+    size_t first_i = 0;
+    for (size_t i = 0; i < n; ++i) {
+      kt_problem *p = b->probs[i];
+      s = read_status(p, st);
+      if (s != KT_OK) {
+        if (first == KT_OK) {
+          first = s;
+          first_i = i;
+        }
+        p->have_fwd = p->have_bwd = false;
+        continue;
+      }
+      commit_iteration(p);
+    }
+    if (first != KT_OK) return batch_fail(first, first_i);
+    if (JT_out)
+      for (size_t i = 0; i < n; ++i) {
+        double F = 0.0;
+        if ((s = host_fidelity(b->probs[i], &F, nullptr, st)) != KT_OK) return batch_fail(s, i);
+        JT_out[(size_t)it * n + i] = 1.0 - F;
+      }
+  }
+  return KT_OK;
+}
+
+KT_API kt_status krotov_batch_problem(kt_batch *b, int i, kt_problem **out) {
+  if (!b || !out) return fail(KT_ERR_ARG, "NULL argument");
+  if (i < 0 || i >= (int)b->probs.size()) return fail(KT_ERR_ARG, "problem index %d out of range", i);
+  *out = b->probs[i];
+  return KT_OK;
+}
+
+KT_API kt_status krotov_batch_info(kt_batch *b, int *n_problems, long long *graph_nodes, long long *device_bytes) {
+  if (!b) return fail(KT_ERR_ARG, "NULL batch");
+  if (n_problems) *n_problems = (int)b->probs.size();
+  if (graph_nodes) {
+    *graph_nodes = 0;
+    for (const kt_batch::Entry &e : b->cache) *graph_nodes = std::max(*graph_nodes, e.nodes);
+  }
+  if (device_bytes) {
+    long long t = 0;
+    for (const kt_problem *p : b->probs) t += (long long)p->bytes;
+    *device_bytes = t;
+  }
+  return KT_OK;
+}
+
+KT_API void krotov_batch_free(kt_batch *b) {
+  if (!b) return;
+  for (kt_batch::Entry &e : b->cache) drop_entry(e);
+  for (kt_problem *p : b->probs) krotov_free(p);
+  delete b;
 }
 
 }  // extern "C"

@@ -9,7 +9,7 @@ struct FwdArgs {
   int j;                 // interval 1..nt; 0 = prologue (update overlap at t_0 only)
   int nt;
   int update;            // sequential Krotov update on
-  int pass_row;          // uniforms row of this pass
+  const int *pass_row;   // device: uniforms row of the running pass (written by init_pass)
   const void *psi_in;    // tile-layout states at t_{j-1}
   void *psi_out;         // tile-layout states at t_j
   const void *chi_t;     // tile-layout co-states at t_j (update only)
@@ -66,8 +66,12 @@ cudaError_t kt_launch_bwd_f32(int ept, const KtGeom &g, const KtGenImage &im, co
                               size_t smem, cudaStream_t st);
 cudaError_t kt_launch_bwd_f64(int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops, const BwdArgs &a,
                               size_t smem, cudaStream_t st);
-cudaError_t kt_launch_init_pass(const KtGeom &g, const double *U, int pass_row, double *rstate, int *jcount,
+// pass[0] = uniforms row of the next pass, pass[1] = rows held, pass[2] = row of the running pass.
+// init_pass takes pass[0] for the new pass, advances it cyclically and resets thresholds and counts.
+cudaError_t kt_launch_init_pass(const KtGeom &g, const double *U, int *pass, double *rstate, int *jcount,
                                 cudaStream_t st);
+// pass[0] = 0, pass[1] = n_passes
+cudaError_t kt_launch_pass_reset(int *pass, int n_passes, cudaStream_t st);
 cudaError_t kt_launch_cursor_seek(const KtGeom &g, const int *rec_step, const int *jcount, int upto,
                                   int *cursor, cudaStream_t st);
 // cursor[k] = first record of trajectory k with interval >= from (jcount[k] if none)

@@ -3,11 +3,24 @@
 #include "kt_device.cuh"
 
 namespace kt {
-__global__ void init_pass_kernel(KtGeom g, const double *U, int pass_row, double *rstate, int *jcount) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= g.M_pad) return;
-  rstate[k] = (k < g.M) ? U[((size_t)pass_row * g.M + k) * g.draws] : -1.0;
-  jcount[k] = 0;
+// One block: every thread reads the row before thread 0 advances the cyclic pass counter.
+__global__ void init_pass_kernel(KtGeom g, const double *U, int *pass, double *rstate, int *jcount) {
+  const int row = pass[0];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    pass[2] = row;
+    pass[0] = (row + 1) % pass[1];
+  }
+  for (int k = threadIdx.x; k < g.M_pad; k += blockDim.x) {
+    rstate[k] = (k < g.M) ? U[((size_t)row * g.M + k) * g.draws] : -1.0;
+    jcount[k] = 0;
+  }
+}
+
+__global__ void pass_reset_kernel(int *pass, int n_passes) {
+  pass[0] = 0;
+  pass[1] = n_passes;
+  pass[2] = 0;
 }
 
 __global__ void cursor_seek_kernel(KtGeom g, const int *rec_step, const int *jcount, int upto, int *cursor) {
@@ -67,9 +80,14 @@ cudaError_t kt_launch_bwd(int fp64, int ept, const KtGeom &g, const KtGenImage &
   return fp64 ? kt_launch_bwd_f64(ept, g, im, ops, a, smem, st) : kt_launch_bwd_f32(ept, g, im, ops, a, smem, st);
 }
 
-cudaError_t kt_launch_init_pass(const KtGeom &g, const double *U, int pass_row, double *rstate, int *jcount,
+cudaError_t kt_launch_init_pass(const KtGeom &g, const double *U, int *pass, double *rstate, int *jcount,
                                 cudaStream_t st) {
-  init_pass_kernel<<<(g.M_pad + 255) / 256, 256, 0, st>>>(g, U, pass_row, rstate, jcount);
+  init_pass_kernel<<<1, 256, 0, st>>>(g, U, pass, rstate, jcount);
+  return cudaGetLastError();
+}
+
+cudaError_t kt_launch_pass_reset(int *pass, int n_passes, cudaStream_t st) {
+  pass_reset_kernel<<<1, 1, 0, st>>>(pass, n_passes);
   return cudaGetLastError();
 }
 

@@ -40,6 +40,7 @@ class Problem:
     Parameters mirror ``kt_model_desc`` / ``kt_config``: ``eps_guess`` and ``shape`` are
     [n_ctrl, nt], ``lam`` [n_ctrl], ``uniforms`` [n_passes, M, draws_per_traj].
     ``precision`` is "fp64" or "fp32" (FP32-mixed: complex64 states, FP64 norms and sums).
+    ``tile_traj``: 0 automatic, -1 autotuned at init, else trajectories per CTA tile.
     """
 
     def __init__(self, net: NetworkFactors, T: float, nt: int, M: int, eps_guess, shape, lam, uniforms,
@@ -59,8 +60,23 @@ class Problem:
         _capi.check(self._lib.krotov_init(ct.byref(md), ct.byref(cfg), _stream_handle(stream), ct.byref(handle)),
                     "krotov_init")
         self._h = handle
+        self._owned = True
         self.precision = precision
         self.info = self.get_info()
+
+    @classmethod
+    def _borrow(cls, handle, net, T, nt, M, precision):
+        """View of a problem owned by a Batch (never freed through this object)."""
+        self = cls.__new__(cls)
+        self._lib = _capi.load()
+        self.net = net
+        self.T, self.nt, self.M = float(T), int(nt), int(M)
+        self.n_ctrl = net.n_ctrl
+        self._h = handle
+        self._owned = False
+        self.precision = precision
+        self.info = self.get_info()
+        return self
 
     # ------------------------------------------------------------------ calls
     def forward(self, update: bool = False, stream=None, keep_for_gradient: bool = False) -> float:
@@ -159,7 +175,81 @@ class Problem:
 
     def close(self) -> None:
         if self._h is not None:
-            self._lib.krotov_free(self._h)
+            if self._owned:
+                self._lib.krotov_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Independent problems whose Krotov iterations run as one CUDA graph launch each
+    (C ABI ``kt_batch``).  ``specs`` is a list of dicts of ``Problem`` constructor arguments
+    (net, T, nt, M, eps_guess, shape, lam, uniforms and the optional keywords)."""
+
+    _KEYS = ("precision", "ckpt_interval", "eps_bound", "cheb_tol", "tile_traj", "psi0_batch")
+
+    def __init__(self, specs, stream=None):
+        self._lib = _capi.load()
+        self._h = None
+        n = len(specs)
+        keeps, mds, cfgs = [], [], []      # keeps: host arrays the descriptors point into
+        for sp in specs:
+            u = _c(sp["uniforms"])
+            if u.ndim != 3 or u.shape[1] != int(sp["M"]):
+                raise ValueError("uniforms must have shape [n_passes, M, draws_per_traj]")
+            kw = {k: sp[k] for k in self._KEYS if k in sp}
+            keep, md, cfg = _descriptors(sp["net"], float(sp["T"]), int(sp["nt"]), int(sp["M"]), sp["eps_guess"],
+                                         sp["shape"], sp["lam"], u, **kw)
+            keeps.append(keep)
+            mds.append(md)
+            cfgs.append(cfg)
+        md_arr = (ct.POINTER(_capi.ModelDesc) * n)(*[ct.pointer(m) for m in mds])
+        cfg_arr = (ct.POINTER(_capi.Config) * n)(*[ct.pointer(c) for c in cfgs])
+        handle = ct.c_void_p()
+        _capi.check(self._lib.krotov_init_batch(md_arr, cfg_arr, n, _stream_handle(stream), ct.byref(handle)),
+                    "krotov_init_batch")
+        self._h = handle
+        self.problems = []
+        for i, sp in enumerate(specs):
+            ph = ct.c_void_p()
+            _capi.check(self._lib.krotov_batch_problem(self._h, i, ct.byref(ph)), "krotov_batch_problem")
+            self.problems.append(Problem._borrow(ph, sp["net"], sp["T"], sp["nt"], sp["M"],
+                                                 sp.get("precision", "fp64")))
+
+    def __len__(self):
+        return len(self.problems)
+
+    def update(self, n_iter: int = 1, stream=None) -> np.ndarray:
+        """n_iter Krotov iterations of every problem; returns J_T = 1 - F as [n_iter, n_problems]."""
+        JT = np.zeros((int(n_iter), len(self.problems)))
+        _capi.check(self._lib.krotov_batch_update(self._h, int(n_iter), _ptr(JT), _stream_handle(stream)),
+                    "krotov_batch_update")
+        return JT
+
+    def info(self) -> dict:
+        n = ct.c_int()
+        nodes = ct.c_longlong()
+        nbytes = ct.c_longlong()
+        _capi.check(self._lib.krotov_batch_info(self._h, ct.byref(n), ct.byref(nodes), ct.byref(nbytes)),
+                    "krotov_batch_info")
+        return {"n_problems": n.value, "graph_nodes": nodes.value, "device_bytes": nbytes.value}
+
+    def close(self) -> None:
+        if self._h is not None:
+            for p in self.problems:
+                p._h = None
+            self._lib.krotov_batch_free(self._h)
             self._h = None
 
     def __del__(self):

@@ -125,3 +125,42 @@ def random_states(seed: int, M: int, d: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     z = rng.normal(size=(M, d)) + 1j * rng.normal(size=(M, d))
     return z / np.linalg.norm(z, axis=1, keepdims=True)
+
+
+def batch_mix(seed: int = 3, n: int = 64, hbm_budget: float = 150e9, n_iter: int = 1) -> list:
+    """A batch of n independent problems of mixed size: N in {2, 3, 4} nodes with cavity cutoff 2
+    (d = 81, 729, 6561), M = 2**U{7..11} trajectories, nt in {1000, 2000} (T = 50), kappa ~ U[0.5, 2],
+    FP32-mixed.  Co-states are kept at every step where the batch fits ``hbm_budget`` bytes;
+    otherwise the problems holding the most co-state memory are switched, largest first, to
+    checkpoints every round(sqrt(nt)) steps, which minimises checkpoints + segment buffer."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        N = int(rng.integers(2, 5))
+        M = 2 ** int(rng.integers(7, 12))
+        nt = int(rng.choice([1000, 2000]))
+        kappa = float(rng.uniform(0.5, 2.0))
+        out.append(Workload(f"mix{i:02d}_N{N}_M{M}_nt{nt}", n_nodes=N, n_cav=2, T=50.0, nt=nt, M=M,
+                            seed=seed * 1000 + i, n_iter=n_iter, kappa=kappa, precision="fp32"))
+
+    def held(w):
+        return costate_bytes(w) + 4 * w.M * w.d * 8     # co-states + initial/running states
+
+    total = sum(held(w) for w in out)
+    for i in sorted(range(n), key=lambda i: -held(out[i])):
+        if total <= hbm_budget:
+            break
+        before = held(out[i])
+        out[i] = out[i].with_(ckpt_interval=int(round(math.sqrt(out[i].nt))))
+        total += held(out[i]) - before
+    return out
+
+
+def costate_bytes(w: Workload) -> int:
+    """Device bytes of the co-state storage of workload w in its precision: every step, or
+    checkpoints every ckpt_interval steps plus the segment buffer."""
+    state = w.M * w.d * (8 if w.precision == "fp32" else 16)
+    if w.ckpt_interval == 0:
+        return (w.nt + 1) * state
+    K = w.ckpt_interval
+    return (w.nt // K + 1 + (1 if w.nt % K else 0) + K + 1) * state

@@ -95,6 +95,20 @@ def test_validation_errors_before_device_calls(lib):
         _make(net, eps_bound=0.5)
     with pytest.raises(KrotovError, match="KT_ERR_UNSUPPORTED"):
         _make(pm.cascaded_chain(9, 1))
+    with pytest.raises(KrotovError, match="KT_ERR_ARG"):
+        _make(net, tile_traj=-2)
+
+
+def test_batch_validation_before_device_calls(lib):
+    from paper_1801_04382_gb300 import Batch, KrotovError
+    with pytest.raises(KrotovError, match="KT_ERR_ARG"):
+        Batch([])
+    net = pm.cascaded_chain(2, 1)
+    nt, M = 10, 4
+    spec = dict(net=net, T=5.0, nt=nt, M=M, eps_guess=si.guess_pulses(2, nt, 5.0, 1.0),
+                shape=si.shape_functions(2, nt, 5.0), lam=np.full(2, 10.0), uniforms=si.uniforms(0, 2, M, 5))
+    with pytest.raises(KrotovError, match="problem 0: .*lambda"):
+        Batch([dict(spec, lam=np.array([10.0, 0.0])), spec])
 
 
 def test_model_builder_matches_paper_structure():
