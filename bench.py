@@ -8,6 +8,12 @@ FP32-mixed precision (complex64 states, FP64 norms and sums), co-state checkpoin
 intervals, synthetic seeded inputs (guess pulse sin^2 of amplitude 1, uniforms from seed 4).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --workload mix64 [--steps K] [--warmup W]
+
+--workload mix64 times the batch of 64 independent problems of mixed size (2, 3 and 4 nodes,
+d = 81 / 729 / 6561, 128..2048 trajectories, nt 1000 or 2000, kappa in [0.5, 2], FP32-mixed,
+seed 3); one step is one Krotov iteration of every problem, issued as one graph launch; the
+same problems iterated one after another (one graph launch each) are timed beside it.
 
 N > 1 (under torchrun): every rank optimises an independent problem (its own seed); there is
 no data-path collective ("weak" scaling).  --impl reference times the FP64 CPU oracle on a
@@ -194,6 +200,110 @@ def precision_comparison(stream, n_iter: int = 50):
     return out
 
 
+def run_mix(args, rank, world):
+    """Batch of independent mixed-size problems, one graph launch per Krotov iteration."""
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU (GB300); the CUDA path has no CPU fallback")
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1801_04382_gb300 import Batch, cascaded_chain
+
+    mix = si.batch_mix(seed=3 + 1000 * rank)
+    n_passes = 2 + args.warmup + args.steps
+    specs, flops_it, bytes_it, tsteps_it = [], 0.0, 0.0, 0.0
+    for w in mix:
+        net = cascaded_chain(w.n_nodes, w.n_cav, w.delta, w.g, w.kappa)
+        specs.append(dict(net=net, T=w.T, nt=w.nt, M=w.M, eps_guess=si.guess_pulses(net.n_ctrl, w.nt, w.T, w.guess_amp),
+                          shape=si.shape_functions(net.n_ctrl, w.nt, w.T), lam=np.full(net.n_ctrl, w.lam),
+                          uniforms=si.uniforms(w.seed, n_passes, w.M, w.draws_per_traj), precision=w.precision,
+                          ckpt_interval=w.ckpt_interval, tile_traj=-1))
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    bt = Batch(specs, stream=stream)
+    init_s = time.perf_counter() - t0
+    for w, sp, p in zip(mix, specs, bt.problems):
+        K = p.info.cheb_terms
+        nnz = avg_row_nonzeros(sp["net"])
+        flops_it += 2 * (8.0 * nnz + 12.0) * K * w.d * w.M * w.nt      # forward + backward sweep
+        bytes_it += 5.0 * 8 * w.d * w.M * w.nt
+        tsteps_it += 2.0 * w.M * w.nt
+    t0 = time.perf_counter()
+    bt.update(1, stream=stream)            # guess sweeps, graph capture and one iteration
+    first_s = time.perf_counter() - t0
+    for _ in range(max(0, args.warmup - 1)):
+        bt.update(1, stream=stream)
+
+    clk_path = os.path.join(tempfile.gettempdir(), f"kt_clocks_{os.getpid()}.csv")
+    proc, fh = clocks_start(clk_path)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    JT = bt.update(args.steps, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_step = reduce_max(ev0.elapsed_time(ev1) / args.steps, dist, "cuda")
+    clocks = clocks_stop(proc, fh, clk_path, local)
+    info = bt.info()
+
+    # the same problems, one after another (each one graph launch per iteration)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for p in bt.problems:                  # capture each problem's own graph outside the timing
+        p.update(1, stream=stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for p in bt.problems:
+        p.update(1, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+
+    peaks, peak_src = measured_peaks()
+    clk_max = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = SM_COUNT * FP32_LANES * 2 * clk_max * 1e6 / 1e12
+    iters_per_s = world * 1000.0 / ms_step
+    achieved = flops_it / (ms_step / 1000.0) / 1e12
+    counts = {}
+    for w in mix:
+        counts[w.d] = counts.get(w.d, 0) + 1
+    line = {
+        "metric": METRIC, "value": iters_per_s, "unit": "batch Krotov iters/s (64 problems each)",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic",
+        "config": {"workload": "mix64: 64 independent problems, seed 3", "problems_by_d": counts,
+                   "trajectories": sum(w.M for w in mix), "checkpointed": sum(1 for w in mix if w.ckpt_interval),
+                   "tiles": "autotuned per problem", "device_bytes": info["device_bytes"],
+                   "graph_kernel_nodes": info["graph_nodes"],
+                   "l2": "inputs larger than L2 (co-states of all problems)", "parallelism": f"replicas{world}"},
+        "traj_steps_per_s": tsteps_it * iters_per_s,
+        "roofline": {"bound": "alu", "kernel": "all interval kernels of the batch", "achieved": achieved,
+                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                     "peak_source": f"FP32 FFMA: {SM_COUNT} SMs x {FP32_LANES} lanes x 2 x {clk_max:.0f} MHz"},
+        "hbm_roofline": {"achieved_gbs": bytes_it * iters_per_s / world / 1e9, "peak_gbs": peaks["hbm_gbs"],
+                         "frac": bytes_it * iters_per_s / world / 1e9 / peaks["hbm_gbs"], "peak_source": peak_src},
+        "sequential_same_problems": {"ms_per_step": seq_ms, "batch_speedup": seq_ms / ms_step},
+        "init_s": init_s, "first_iteration_s": first_s,
+        "mean_final_JT": float(np.mean(JT[-1])),
+        "gpu_launches": int(info["graph_nodes"]) * args.steps,
+        "clocks": clocks,
+    }
+    bt.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -356,11 +466,14 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-comparison", action="store_true")
+    ap.add_argument("--workload", choices=["cfg5", "mix64"], default="cfg5")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "mix64":
+        return run_mix(args, rank, world)
     return run_ours(args, rank, world)
 
 

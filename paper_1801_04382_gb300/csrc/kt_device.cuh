@@ -603,7 +603,7 @@ __device__ __forceinline__ typename C2<R>::T lind_item(const KtGeom &g, const Kt
 // every coupling inside a thread's fiber (which runs over the last node) has a position known
 // at compile time: the fiber's own T_k stays in registers and the last node's factor and the
 // pair hops that raise or lower its photon number become register-indexed FMAs.
-template <typename R, int NC>
+template <typename R, int NC, int TT>
 __device__ __forceinline__ void apply_acs(const KtGeom &g, const KtGenImage &im, const Smem &sm,
                                           const typename C2<R>::T *__restrict__ v, int base, uint32_t fdig,
                                           typename C2<R>::T Df, const typename C2<R>::T (&vk)[3 * (NC + 1)],
@@ -618,7 +618,7 @@ __device__ __forceinline__ void apply_acs(const KtGeom &g, const KtGenImage &im,
   const C *ra = lo + NL;
   const C *pc = (const C *)sm.pcoef;
   const int last = g.n_nodes - 1;
-  const int T = g.T;
+  const int T = TT > 0 ? TT : g.T;   // TT > 0: tile width fixed at compile time
 #pragma unroll
   for (int q = 0; q < NL; ++q) {
     const C dq = dg[last * NL + q];
@@ -688,7 +688,7 @@ __device__ __forceinline__ void apply_acs(const KtGeom &g, const KtGenImage &im,
   }
 }
 
-template <typename R, int NC, class IT>
+template <typename R, int NC, int TT, class IT>
 __device__ void cheb_run_acs(const KtGeom &g, const KtGenImage &im, const Smem &sm, const IT &it,
                              int K, typename C2<R>::T (&acc)[3 * (NC + 1)]) {
   typedef typename C2<R>::T C;
@@ -697,7 +697,8 @@ __device__ void cheb_run_acs(const KtGeom &g, const KtGenImage &im, const Smem &
   C *B = (C *)sm.bufB;
   const C *cf = (const C *)sm.coef;
   const C *dg = (const C *)sm.diag;
-  const int tau = threadIdx.x % g.T;
+  const int T = TT > 0 ? TT : g.T;
+  const int tau = TT == 1 ? 0 : (int)(threadIdx.x % T);
   const bool ok = it.ok(0);
   const int base = it.item(0);
   const uint32_t fdig = it.dig(0);
@@ -712,17 +713,17 @@ __device__ void cheb_run_acs(const KtGeom &g, const KtGenImage &im, const Smem &
   const C c0 = cf[tau];
 #pragma unroll
   for (int q = 0; q < NL; ++q) {
-    vk[q] = ok ? A[base + q * g.T] : mkc((R)0, (R)0);
+    vk[q] = ok ? A[base + q * T] : mkc((R)0, (R)0);
     acc[q] = cmul(c0, vk[q]);
   }
   if (K == 1) { __syncthreads(); return; }
   C t[NL];
   if (ok) {
-    apply_acs<R, NC>(g, im, sm, A, base, fdig, Df, vk, t);
-    const C c1 = cf[g.T + tau];
+    apply_acs<R, NC, TT>(g, im, sm, A, base, fdig, Df, vk, t);
+    const C c1 = cf[T + tau];
 #pragma unroll
     for (int q = 0; q < NL; ++q) {
-      B[base + q * g.T] = t[q];
+      B[base + q * T] = t[q];
       acc[q] = cfma(c1, t[q], acc[q]);
       vk[q] = t[q];
     }
@@ -732,13 +733,13 @@ __device__ void cheb_run_acs(const KtGeom &g, const KtGenImage &im, const Smem &
   C *Q = B;   // holds T_k (this thread's fiber also in vk)
   for (int k = 2; k < K; ++k) {
     if (ok) {
-      const C a = cf[k * g.T + tau];
-      apply_acs<R, NC>(g, im, sm, Q, base, fdig, Df, vk, t);
+      const C a = cf[k * T + tau];
+      apply_acs<R, NC, TT>(g, im, sm, Q, base, fdig, Df, vk, t);
 #pragma unroll
       for (int q = 0; q < NL; ++q) {
-        const C old = P[base + q * g.T];
+        const C old = P[base + q * T];
         const C nv = mkc(t[q].x + t[q].x - old.x, t[q].y + t[q].y - old.y);
-        P[base + q * g.T] = nv;
+        P[base + q * T] = nv;
         acc[q] = cfma(a, nv, acc[q]);
         vk[q] = nv;
       }
@@ -751,7 +752,7 @@ __device__ void cheb_run_acs(const KtGeom &g, const KtGenImage &im, const Smem &
 template <typename R, int EPT, int NL, int ACS, class IT>
 __device__ __forceinline__ void cheb_dispatch(const KtGeom &g, const KtGenImage &im, const Smem &sm,
                                               const IT &it, int K, typename C2<R>::T (&acc)[EPT]) {
-  if constexpr (ACS) cheb_run_acs<R, NL / 3 - 1>(g, im, sm, it, K, acc);
+  if constexpr (ACS) cheb_run_acs<R, NL / 3 - 1, ACS == 2 ? 1 : 0>(g, im, sm, it, K, acc);   // ACS 2: T = 1
   else if constexpr (NL > 0) cheb_run_fiber<R, NL>(g, im, sm, it, K, acc);
   else cheb_run<R, EPT>(g, im, sm, it, K, acc);
 }

@@ -27,6 +27,8 @@ cudaError_t kt_launch_fwd_f32(int ept, const KtGeom &g, const KtGenImage &im, co
     case -9: return kt::launch_fwd_t<float, 9, 9, 0>(g, im, ops, a, smem, st);   // fiber mapping, n_loc = 9
     case -106: return kt::launch_fwd_t<float, 6, 6, 1>(g, im, ops, a, smem, st);  // cavity structure, cutoff 1
     case -109: return kt::launch_fwd_t<float, 9, 9, 1>(g, im, ops, a, smem, st);  // cavity structure, cutoff 2
+    case -206: return kt::launch_fwd_t<float, 6, 6, 2>(g, im, ops, a, smem, st);  // cavity structure, cutoff 1, T = 1
+    case -209: return kt::launch_fwd_t<float, 9, 9, 2>(g, im, ops, a, smem, st);  // cavity structure, cutoff 2, T = 1
   }
   return cudaErrorInvalidValue;
 }

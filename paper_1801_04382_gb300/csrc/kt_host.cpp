@@ -283,6 +283,7 @@ kt_status read_status(kt_problem *p, cudaStream_t st) {
     case KT_DEV_RECORD_FULL: return fail(KT_ERR_RECORD_FULL, "a trajectory needed more jumps than draws_per_traj allows");
     case KT_DEV_RANGE: return fail(KT_ERR_RANGE, "an updated pulse value left [-eps_bound, eps_bound]");
     case KT_DEV_ZERO_JUMP: return fail(KT_ERR_NONFINITE, "jump into a zero state (||L psi|| = 0 at a jump)");
+    case KT_DEV_TIMEOUT: return fail(KT_ERR_TIMEOUT, "a bounded device-side wait for a bulk copy expired");
     default: return fail(KT_ERR_CUDA, "device status %d", s);
   }
 }
@@ -944,7 +945,8 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
     g.prefetch_chi = kt_smem_bytes(t, esz, true) <= 227 * 1024 ? 1 : 0;
   }
   if (fiber) {
-    P.ept = cavity_structure(gf, gb, lo_dl, lo_val, ra_dl, ra_val) ? -(100 + nl) : -nl;   // launcher codes
+    // launcher codes: -nl fiber, -(100 + nl) cavity structure, -(200 + nl) the same with T = 1 compiled in
+    P.ept = cavity_structure(gf, gb, lo_dl, lo_val, ra_dl, ra_val) ? -((Tsel == 1 ? 200 : 100) + nl) : -nl;
     g.nthreads = std::max(32, ((d / nl) * Tsel + 31) / 32 * 32);
   } else {
     const int items = d * Tsel;
