@@ -27,8 +27,10 @@ cudaError_t kt_launch_bwd_f32(int ept, const KtGeom &g, const KtGenImage &im, co
     case -9: return kt::launch_bwd_t<float, 9, 9, 0>(g, im, ops, a, smem, st);   // fiber mapping, n_loc = 9
     case -106: return kt::launch_bwd_t<float, 6, 6, 1>(g, im, ops, a, smem, st);  // cavity structure, cutoff 1
     case -109: return kt::launch_bwd_t<float, 9, 9, 1>(g, im, ops, a, smem, st);  // cavity structure, cutoff 2
-    case -206: return kt::launch_bwd_t<float, 6, 6, 2>(g, im, ops, a, smem, st);  // cavity structure, cutoff 1, T = 1
     case -209: return kt::launch_bwd_t<float, 9, 9, 2>(g, im, ops, a, smem, st);  // cavity structure, cutoff 2, T = 1
+    case -306: return kt::launch_bwd_t<float, 6, 6, 3>(g, im, ops, a, smem, st);  // real / imaginary couplings, cutoff 1
+    case -309: return kt::launch_bwd_t<float, 9, 9, 3>(g, im, ops, a, smem, st);  // real / imaginary couplings, cutoff 2
+    case -409: return kt::launch_bwd_t<float, 9, 9, 4>(g, im, ops, a, smem, st);  // the same with T = 1
   }
   return cudaErrorInvalidValue;
 }

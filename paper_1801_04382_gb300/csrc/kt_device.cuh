@@ -37,6 +37,19 @@ template <typename C> __device__ __forceinline__ C cfma(C a, C b, C c) {  // c +
   return c;
 }
 
+// c + a*b for a purely real (rfma, a) or purely imaginary (ifma, i b) coefficient: the two
+// FMAs of cfma whose coefficient part is nonzero, in cfma's order, so the result is bit-identical.
+template <typename C, typename R> __device__ __forceinline__ C rfma(R a, C b, C c) {
+  c.x = fma(a, b.x, c.x);
+  c.y = fma(a, b.y, c.y);
+  return c;
+}
+template <typename C, typename R> __device__ __forceinline__ C ifma(R bi, C b, C c) {
+  c.x = fma(-bi, b.y, c.x);
+  c.y = fma(bi, b.x, c.y);
+  return c;
+}
+
 template <typename C> __device__ __forceinline__ C from_kc(KtCplx z) {
   typedef decltype(C().x) R;
   return mkc((R)z.re, (R)z.im);
@@ -603,7 +616,10 @@ __device__ __forceinline__ typename C2<R>::T lind_item(const KtGeom &g, const Kt
 // every coupling inside a thread's fiber (which runs over the last node) has a position known
 // at compile time: the fiber's own T_k stays in registers and the last node's factor and the
 // pair hops that raise or lower its photon number become register-indexed FMAs.
-template <typename R, int NC, int TT>
+// RI: the couplings are purely real or imaginary by class (host check: node rows hold
+// [real, imaginary] slots, last-node cavity real and drive imaginary, pair coefficients imaginary,
+// ladder values real), applied with two FMAs each.
+template <typename R, int NC, int TT, bool RI>
 __device__ __forceinline__ void apply_acs(const KtGeom &g, const KtGenImage &im, const Smem &sm,
                                           const typename C2<R>::T *__restrict__ v, int base, uint32_t fdig,
                                           typename C2<R>::T Df, const typename C2<R>::T (&vk)[3 * (NC + 1)],
@@ -628,24 +644,51 @@ __device__ __forceinline__ void apply_acs(const KtGeom &g, const KtGenImage &im,
 #pragma unroll
   for (int n = 1; n <= NC; ++n) {
     const int qr = 2 * NP + n - 1, qg = n;
-    out[qr] = cfma(ld[qr * NL + qg], vk[qg], out[qr]);
-    out[qg] = cfma(ld[qg * NL + qr], vk[qr], out[qg]);
+    if constexpr (RI) {
+      out[qr] = rfma(ld[qr * NL + qg].x, vk[qg], out[qr]);
+      out[qg] = rfma(ld[qg * NL + qr].x, vk[qr], out[qg]);
+    } else {
+      out[qr] = cfma(ld[qr * NL + qg], vk[qg], out[qr]);
+      out[qg] = cfma(ld[qg * NL + qr], vk[qr], out[qg]);
+    }
   }
 #pragma unroll
   for (int n = 0; n <= NC; ++n) {
     const int qr = 2 * NP + n, qe = NP + n;
-    out[qr] = cfma(ld[qr * NL + qe], vk[qe], out[qr]);
-    out[qe] = cfma(ld[qe * NL + qr], vk[qr], out[qe]);
+    if constexpr (RI) {
+      out[qr] = ifma(ld[qr * NL + qe].y, vk[qe], out[qr]);
+      out[qe] = ifma(ld[qe * NL + qr].y, vk[qr], out[qe]);
+    } else {
+      out[qr] = cfma(ld[qr * NL + qe], vk[qe], out[qr]);
+      out[qe] = cfma(ld[qe * NL + qr], vk[qr], out[qe]);
+    }
   }
   // other nodes: one row per fiber, each entry one neighbouring fiber
-  for (int i = 0; i < last; ++i) {
-    const int e0 = (i * NL + ((fdig >> (4 * i)) & 15)) * g.S;
-    for (int s = 0; s < g.S; ++s) {
-      const int off = sm.loc_off[e0 + s];
-      if (off) {
-        const C w = lv[e0 + s];
+  if constexpr (RI) {
+    for (int i = 0; i < last; ++i) {
+      const int e0 = (i * NL + ((fdig >> (4 * i)) & 15)) * 2;
+      const int off0 = sm.loc_off[e0], off1 = sm.loc_off[e0 + 1];
+      if (off0) {
+        const R a = lv[e0].x;
 #pragma unroll
-        for (int q = 0; q < NL; ++q) out[q] = cfma(w, v[base + off + q * T], out[q]);
+        for (int q = 0; q < NL; ++q) out[q] = rfma(a, v[base + off0 + q * T], out[q]);
+      }
+      if (off1) {
+        const R b = lv[e0 + 1].y;
+#pragma unroll
+        for (int q = 0; q < NL; ++q) out[q] = ifma(b, v[base + off1 + q * T], out[q]);
+      }
+    }
+  } else {
+    for (int i = 0; i < last; ++i) {
+      const int e0 = (i * NL + ((fdig >> (4 * i)) & 15)) * g.S;
+      for (int s = 0; s < g.S; ++s) {
+        const int off = sm.loc_off[e0 + s];
+        if (off) {
+          const C w = lv[e0 + s];
+#pragma unroll
+          for (int q = 0; q < NL; ++q) out[q] = cfma(w, v[base + off + q * T], out[q]);
+        }
       }
     }
   }
@@ -656,20 +699,35 @@ __device__ __forceinline__ void apply_acs(const KtGeom &g, const KtGenImage &im,
       const int e = p * NL * NL + ((fdig >> (4 * pd)) & 15) * NL + ((fdig >> (4 * ps)) & 15);
       const int off = sm.pair_off[e];
       if (off) {
-        const C w = pv[e];
+        if constexpr (RI) {
+          const R b = pv[e].y;
 #pragma unroll
-        for (int q = 0; q < NL; ++q) out[q] = cfma(w, v[base + off + q * T], out[q]);
+          for (int q = 0; q < NL; ++q) out[q] = ifma(b, v[base + off + q * T], out[q]);
+        } else {
+          const C w = pv[e];
+#pragma unroll
+          for (int q = 0; q < NL; ++q) out[q] = cfma(w, v[base + off + q * T], out[q]);
+        }
       }
     } else if (pd == last) {
       // raise the last node (q <- q-1, n_q >= 1), lower node ps (x_s -> x_s + 1, n_s < NC)
       const int xs = (fdig >> (4 * ps)) & 15;
       if (xs % NP < NC) {
         const int off = g.stride[ps] * T;
-        const C cf = cmul(pc[p], lo[xs]);
+        if constexpr (RI) {
+          const R cb = pc[p].y * lo[xs].x;
 #pragma unroll
-        for (int q = 0; q < NL; ++q) {
-          if (q % NP == 0) continue;
-          out[q] = cfma(cmul(cf, ra[q]), v[base + off + (q - 1) * T], out[q]);
+          for (int q = 0; q < NL; ++q) {
+            if (q % NP == 0) continue;
+            out[q] = ifma(cb * ra[q].x, v[base + off + (q - 1) * T], out[q]);
+          }
+        } else {
+          const C cf = cmul(pc[p], lo[xs]);
+#pragma unroll
+          for (int q = 0; q < NL; ++q) {
+            if (q % NP == 0) continue;
+            out[q] = cfma(cmul(cf, ra[q]), v[base + off + (q - 1) * T], out[q]);
+          }
         }
       }
     } else {
@@ -677,18 +735,27 @@ __device__ __forceinline__ void apply_acs(const KtGeom &g, const KtGenImage &im,
       const int xd = (fdig >> (4 * pd)) & 15;
       if (xd % NP >= 1) {
         const int off = -g.stride[pd] * T;
-        const C cf = cmul(pc[p], ra[xd]);
+        if constexpr (RI) {
+          const R cb = pc[p].y * ra[xd].x;
 #pragma unroll
-        for (int q = 0; q < NL; ++q) {
-          if (q % NP == NC) continue;
-          out[q] = cfma(cmul(cf, lo[q]), v[base + off + (q + 1) * T], out[q]);
+          for (int q = 0; q < NL; ++q) {
+            if (q % NP == NC) continue;
+            out[q] = ifma(cb * lo[q].x, v[base + off + (q + 1) * T], out[q]);
+          }
+        } else {
+          const C cf = cmul(pc[p], ra[xd]);
+#pragma unroll
+          for (int q = 0; q < NL; ++q) {
+            if (q % NP == NC) continue;
+            out[q] = cfma(cmul(cf, lo[q]), v[base + off + (q + 1) * T], out[q]);
+          }
         }
       }
     }
   }
 }
 
-template <typename R, int NC, int TT, class IT>
+template <typename R, int NC, int TT, bool RI, class IT>
 __device__ void cheb_run_acs(const KtGeom &g, const KtGenImage &im, const Smem &sm, const IT &it,
                              int K, typename C2<R>::T (&acc)[3 * (NC + 1)]) {
   typedef typename C2<R>::T C;
@@ -719,7 +786,7 @@ __device__ void cheb_run_acs(const KtGeom &g, const KtGenImage &im, const Smem &
   if (K == 1) { __syncthreads(); return; }
   C t[NL];
   if (ok) {
-    apply_acs<R, NC, TT>(g, im, sm, A, base, fdig, Df, vk, t);
+    apply_acs<R, NC, TT, RI>(g, im, sm, A, base, fdig, Df, vk, t);
     const C c1 = cf[T + tau];
 #pragma unroll
     for (int q = 0; q < NL; ++q) {
@@ -734,7 +801,7 @@ __device__ void cheb_run_acs(const KtGeom &g, const KtGenImage &im, const Smem &
   for (int k = 2; k < K; ++k) {
     if (ok) {
       const C a = cf[k * T + tau];
-      apply_acs<R, NC, TT>(g, im, sm, Q, base, fdig, Df, vk, t);
+      apply_acs<R, NC, TT, RI>(g, im, sm, Q, base, fdig, Df, vk, t);
 #pragma unroll
       for (int q = 0; q < NL; ++q) {
         const C old = P[base + q * T];
@@ -752,7 +819,8 @@ __device__ void cheb_run_acs(const KtGeom &g, const KtGenImage &im, const Smem &
 template <typename R, int EPT, int NL, int ACS, class IT>
 __device__ __forceinline__ void cheb_dispatch(const KtGeom &g, const KtGenImage &im, const Smem &sm,
                                               const IT &it, int K, typename C2<R>::T (&acc)[EPT]) {
-  if constexpr (ACS) cheb_run_acs<R, NL / 3 - 1, ACS == 2 ? 1 : 0>(g, im, sm, it, K, acc);   // ACS 2: T = 1
+  // ACS: 1 cavity structure, 2 the same with T = 1, 3 with real / imaginary couplings, 4 both
+  if constexpr (ACS) cheb_run_acs<R, NL / 3 - 1, (ACS == 2 || ACS == 4) ? 1 : 0, (ACS >= 3)>(g, im, sm, it, K, acc);
   else if constexpr (NL > 0) cheb_run_fiber<R, NL>(g, im, sm, it, K, acc);
   else cheb_run<R, EPT>(g, im, sm, it, K, acc);
 }

@@ -729,6 +729,61 @@ bool cavity_structure(const Gen &gf, const Gen &gb, const std::vector<int> &lo_d
   return true;
 }
 
+// Real / imaginary coupling classes, checked on top of the cavity structure: every off-diagonal
+// entry of every node factor (drift and controls, both directions) is purely real or purely
+// imaginary, a row has at most one entry of each class, the last node's cavity couplings are real
+// and its drive couplings imaginary, every pair coefficient is imaginary and the ladder factor is
+// real (true of the node of Sec. 3.1: g real, drive (i/2)(sigma_re - sigma_er), cascade -2i kappa).
+// Then each row's slots are re-ordered [real entry, imaginary entry] (x itself marks an empty
+// slot), and the kernels apply each coupling with two real FMAs instead of a complex one; the
+// result is bit-identical, the products with the zero part being exact zeros.
+bool ri_classes(const Gen &gf, const Gen &gb, const std::vector<cd> &lo_val, const std::vector<cd> &ra_val,
+                std::vector<std::vector<int>> &cols) {
+  const int N = gf.N, nl = gf.nl, NP = nl / 3;
+  for (int x = 0; x < nl; ++x)
+    if (lo_val[x].imag() != 0.0 || ra_val[x].imag() != 0.0) return false;
+  for (const Gen *gen : {&gf, &gb})
+    for (const Pair &q : gen->pairs)
+      if (q.coef.real() != 0.0) return false;
+  // 0: zero, 1: real, 2: imaginary, 3: neither
+  auto cls = [&](int i, int x, int y) {
+    bool re = false, im = false;
+    auto take = [&](cd v) {
+      if (v.real() != 0.0) re = true;
+      if (v.imag() != 0.0) im = true;
+    };
+    take(at(gf.loc, i * nl * nl, nl, x, y));
+    take(at(gb.loc, i * nl * nl, nl, x, y));
+    for (size_t c = 0; c < gf.ctrl_node.size(); ++c)
+      if (gf.ctrl_node[c] == i) {
+        take(at(gf.ctrl, (int)c * nl * nl, nl, x, y));
+        take(at(gb.ctrl, (int)c * nl * nl, nl, x, y));
+      }
+    return re && im ? 3 : re ? 1 : im ? 2 : 0;
+  };
+  std::vector<std::vector<int>> out(cols.size());
+  for (int i = 0; i < N; ++i)
+    for (int x = 0; x < nl; ++x) {
+      int yr = x, yi = x;
+      for (int y : cols[(size_t)i * nl + x]) {
+        const int k = cls(i, x, y);
+        if (k == 3) return false;
+        if (k == 1) {
+          if (yr != x) return false;
+          yr = y;
+        } else if (k == 2) {
+          if (yi != x) return false;
+          yi = y;
+        }
+      }
+      if (i == N - 1 && yr != x && (x / NP) * (yr / NP) != 0) return false;   // cavity: g <-> r only
+      if (i == N - 1 && yi != x && (x / NP) * (yi / NP) != 2) return false;   // drive: e <-> r only
+      out[(size_t)i * nl + x] = {yr, yi};
+    }
+  cols.swap(out);
+  return true;
+}
+
 // Validation, a1 (structured H_eff = H - (i/2) sum_l L_l^dag L_l), a2 (spectral interval and
 // Chebyshev length), tile geometry and the scaled generator tables of both directions.
 kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
@@ -894,6 +949,10 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
       S = std::max(S, (int)cl.size());
     }
   if (S > KT_MAX_S) return fail(KT_ERR_UNSUPPORTED, "a node row has %d > %d off-diagonal entries", S, KT_MAX_S);
+  const bool fiber = (nl == 6 || nl == 9);
+  const bool acs = fiber && cavity_structure(gf, gb, lo_dl, lo_val, ra_dl, ra_val);
+  const bool ri = acs && S <= 2 && ri_classes(gf, gb, lo_val, ra_val, cols);
+  if (ri) S = 2;
   g.S = std::max(S, 1);
   int SH = 1;
   for (int c = 0; c < nc; ++c)
@@ -912,7 +971,6 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
     return fail(KT_ERR_ARG, "tile_traj must be a power of two <= 32");
   // fiber mapping (one thread per run of n_loc elements along the last node) for the compiled
   // local dimensions; otherwise the strided mapping with 4, 8 or 16 items per thread
-  const bool fiber = (nl == 6 || nl == 9);
   const int fiber_max_threads = 768;
   int Tsel = 0;
   // strided mapping: items per thread above 8 spill registers, so only when nothing else fits
@@ -945,8 +1003,11 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
     g.prefetch_chi = kt_smem_bytes(t, esz, true) <= 227 * 1024 ? 1 : 0;
   }
   if (fiber) {
-    // launcher codes: -nl fiber, -(100 + nl) cavity structure, -(200 + nl) the same with T = 1 compiled in
-    P.ept = cavity_structure(gf, gb, lo_dl, lo_val, ra_dl, ra_val) ? -((Tsel == 1 ? 200 : 100) + nl) : -nl;
+    // launcher codes -(100 v + nl): v = 0 fiber, 1 cavity structure, 2 the same with T = 1 compiled
+    // in, 3 cavity structure with real / imaginary couplings, 4 the same with T = 1 (n_loc = 9)
+    int v = 0;
+    if (acs) v = ri ? (nl == 9 && Tsel == 1 ? 4 : 3) : (nl == 9 && Tsel == 1 ? 2 : 1);
+    P.ept = -(100 * v + nl);
     g.nthreads = std::max(32, ((d / nl) * Tsel + 31) / 32 * 32);
   } else {
     const int items = d * Tsel;
@@ -968,6 +1029,7 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
       for (int x = 0; x < nl; ++x) {
         const std::vector<int> &cl = cols[(size_t)i * nl + x];
         for (size_t q = 0; q < cl.size(); ++q) {
+          if (cl[q] == x) continue;                  // empty slot
           const size_t e = (size_t)i * nls + x * g.S + q;
           im.dl[e] = cl[q] - x;
           const cd v = at(gen.loc, i * nl * nl, nl, x, cl[q]) / r;
@@ -982,6 +1044,7 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
       for (int x = 0; x < nl; ++x) {
         const std::vector<int> &cl = cols[(size_t)i * nl + x];
         for (size_t q = 0; q < cl.size(); ++q) {
+          if (cl[q] == x) continue;
           const cd v = at(gen.ctrl, c * nl * nl, nl, x, cl[q]) / r;
           im.cslot[(size_t)c * nls + x * g.S + q] = KtCplx{v.real(), v.imag()};
         }
