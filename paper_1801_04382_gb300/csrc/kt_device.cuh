@@ -194,17 +194,44 @@ enum { TI_ACT = 0, TI_BUSY, TI_CH, TI_NJ, TI_J0, TI_J1, TI_J2, TI_J3, TI_J4, TI_
 // --------------------------------------------------------------------------------------
 // Per-trajectory block reduction: every thread holds NV partial sums of its trajectory
 // (tau = tid % T); sums over lanes of equal tau by shuffles, then over warps in a fixed
-// order.  Result in out[tau*NV + v].  Deterministic.
+// order.  Result in out[tau*NV + v].  Deterministic (FP64 throughout).
+// For NV a power of two the first shuffle levels transpose: at offset o a lane sends half of its
+// live values to its partner and adds the partner's other half, so each level halves the live
+// values (8 values over 5 levels: 9 additions per lane instead of 40 -- FP64 runs at 1/64 of the
+// FP32 rate on this GPU).  Slot q of lane l then holds value q + idx(l), idx from the lane bits of
+// the transposing levels; the remaining levels add plainly.
 template <int NV>
 __device__ __forceinline__ void reduce_tau(double (&v)[NV], const KtGeom &g, double *red, double *out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  for (int o = 16; o >= g.T; o >>= 1) {
+  int o = 16, live = NV, idx = 0, tmask = 0;
+  if constexpr (NV > 1 && (NV & (NV - 1)) == 0) {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    for (int h = NV / 2; h >= 1; h >>= 1) {
+      if (o >= g.T) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int q = 0; q < h; ++q) {
+          const double send = up ? v[q] : v[q + h];
+          const double keep = up ? v[q + h] : v[q];
+          v[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+        if (up) idx += h;
+        tmask |= o;
+        live = h;
+        o >>= 1;
+      }
+    }
   }
-  if (lane < g.T) {
+  for (; o >= g.T; o >>= 1) {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) red[(warp * g.T + lane) * 8 + q] = v[q];
+    for (int q = 0; q < NV; ++q)
+      if (q < live) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  }
+  if (((lane & ~(g.T - 1)) & ~tmask) == 0) {
+    const int tau = lane & (g.T - 1);
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+      if (q < live) red[(warp * g.T + tau) * 8 + q + idx] = v[q];
   }
   __syncthreads();
   for (int t = threadIdx.x; t < g.T * NV; t += blockDim.x) {
@@ -1145,18 +1172,41 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
   for (int c = 0; c < g.n_ctrl; ++c) {
     const int node = g.ctrl_node[c];
     R s = 0;
+    if (NL > 0 && node != g.n_nodes - 1) {
+      // fiber mapping, control on another node: one factor row serves the whole fiber
+      if (it.ok(0)) {
+        const int base = (c * g.n_loc + ((it.dig(0) >> (4 * node)) & 15)) * g.SH;
+        C h[EPT];
 #pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-      if (!it.ok(q)) continue;
-      const int xi = (it.dig(q) >> (4 * node)) & 15;
-      const int base = (c * g.n_loc + xi) * g.SH;
-      C h = mkc((R)0, (R)0);
-      for (int e = 0; e < g.SH; ++e) {
-        const C w = hv[base + e];
-        if (w.x != (R)0 || w.y != (R)0) h = cfma(w, A[it.item(q) + sm.hc_off[base + e]], h);
+        for (int q = 0; q < EPT; ++q) h[q] = mkc((R)0, (R)0);
+        for (int e = 0; e < g.SH; ++e) {
+          const C w = hv[base + e];
+          if (w.x != (R)0 || w.y != (R)0) {
+            const int off = sm.hc_off[base + e];
+#pragma unroll
+            for (int q = 0; q < EPT; ++q) h[q] = cfma(w, A[it.item(q) + off], h[q]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+          const C x = chi[it.item(q)];
+          s += x.x * h[q].y - x.y * h[q].x;       // Im(conj(chi) * h)
+        }
       }
-      const C x = chi[it.item(q)];
-      s += x.x * h.y - x.y * h.x;       // Im(conj(chi) * h)
+    } else {
+#pragma unroll
+      for (int q = 0; q < EPT; ++q) {
+        if (!it.ok(q)) continue;
+        const int xi = (it.dig(q) >> (4 * node)) & 15;
+        const int base = (c * g.n_loc + xi) * g.SH;
+        C h = mkc((R)0, (R)0);
+        for (int e = 0; e < g.SH; ++e) {
+          const C w = hv[base + e];
+          if (w.x != (R)0 || w.y != (R)0) h = cfma(w, A[it.item(q) + sm.hc_off[base + e]], h);
+        }
+        const C x = chi[it.item(q)];
+        s += x.x * h.y - x.y * h.x;       // Im(conj(chi) * h)
+      }
     }
     v[c] = (double)s;
   }
