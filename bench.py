@@ -40,6 +40,10 @@ import synth_inputs as si  # noqa: E402
 
 METRIC = "Krotov iters/s and traj·steps/s, FP32-mixed vs FP64 path, % of HBM roofline"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of each interval kernel at
+# this workload's launch size (1024 trajectories, d = 6561, FP32-mixed), from one ncu capture of the
+# current kernels; None where no capture of the current kernel exists.
+NCU_TRAFFIC_PER_LAUNCH = {"bwd": 53.92e6 + 9.62e6, "fwd": None}
 SM_COUNT, FP32_LANES = 152, 128
 
 
@@ -417,7 +421,8 @@ def run_ours(args, rank, world):
     hbm_achieved = bytes_per_iter * (iters_per_s / world) / 1e9
     kernel_bytes = (3 if fam == "fwd" else 2) * s_bytes * wl.d * wl.M
     roof = {"bound": "alu", "kernel": f"{fam}_kernel", "achieved": achieved, "peak": fp32_peak,
-            "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+            "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+            "traffic": NCU_TRAFFIC_PER_LAUNCH.get(fam) if wl.precision == "fp32" else None,
             "avg_launch_ms": avg_s * 1e3, "launches": f_n,
             "flops_per_launch": flops_per_launch, "algorithmic_bytes_per_launch": kernel_bytes,
             "hbm_gbs_of_kernel": kernel_bytes / avg_s / 1e9,

@@ -187,3 +187,22 @@ def test_update_before_backward_is_a_state_error():
             p.forward(True)
         with pytest.raises(KrotovError, match="KT_ERR_STATE"):
             p.backward()
+
+
+def test_full_size_launch_sampled():
+    """The benchmark's launch configuration -- d = 6561, 1024 trajectories, FP32-mixed, one CTA per
+    trajectory, co-state checkpoints (every 3 of 4 intervals, so one segment is recomputed) -- over a
+    short window (dt = 0.01); trajectories start in the paper's initial state except the first 32,
+    which start in random full-space states and jump.  F, the pulse update and every jump-free
+    trajectory's state against the oracle."""
+    wl = si.CONFIGS["cfg5_d6561"]
+    nt = 4
+    c = setup(wl.n_nodes, wl.n_cav, wl.dt * nt, nt, wl.M, wl.guess_amp, wl.seed, 1, random_init=True)
+    m = om.build_model(wl.n_nodes, wl.n_cav)
+    psi0 = np.repeat(m.psi0[None, :], wl.M, axis=0)
+    psi0[:32] = c["psi0"][:32]
+    c["psi0"] = psi0
+    gpu = run_gpu(c, "fp32", ckpt=3)
+    assert gpu["info"].tile_traj == 1 and gpu["info"].n_tiles == wl.M
+    _, res = run_oracle(c)
+    compare(c, gpu, res, 3e-5, 1e-5, 1e-4, 1e-4, margin_min=1e-5)
