@@ -9,11 +9,15 @@ intervals, synthetic seeded inputs (guess pulse sin^2 of amplitude 1, uniforms f
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
     python bench.py --workload mix64 [--steps K] [--warmup W]
+    python bench.py --workload grad729 [--steps K] [--warmup W]
 
 --workload mix64 times the batch of 64 independent problems of mixed size (2, 3 and 4 nodes,
 d = 81 / 729 / 6561, 128..2048 trajectories, nt 1000 or 2000, kappa in [0.5, 2], FP32-mixed,
 seed 3); one step is one Krotov iteration of every problem, issued as one graph launch; the
 same problems iterated one after another (one graph launch each) are timed beside it.
+--workload grad729 times the exact gradient dJ_T/deps (frozen jump record) on the three-node
+chain (d = 729, 1024 trajectories, nt = 2000, FP32-mixed, seed 2): one step is a forward sweep
+that keeps the states plus the gradient sweep.
 
 N > 1 (under torchrun): every rank optimises an independent problem (its own seed); there is
 no data-path collective ("weak" scaling).  --impl reference times the FP64 CPU oracle on a
@@ -308,6 +312,90 @@ def run_mix(args, rank, world):
     return 0
 
 
+def run_grad(args, rank, world):
+    """Gradient evaluations per second on the three-node workload."""
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU (GB300); the CUDA path has no CPU fallback")
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1801_04382_gb300 import Problem, cascaded_chain
+    wl = si.CONFIGS["cfg3_d729"]
+    wl = wl.with_(seed=wl.seed + 1000 * rank)
+    net = cascaded_chain(wl.n_nodes, wl.n_cav, wl.delta, wl.g, wl.kappa)
+    eps0 = si.guess_pulses(net.n_ctrl, wl.nt, wl.T, wl.guess_amp)
+    S = si.shape_functions(net.n_ctrl, wl.nt, wl.T)
+    lam = np.full(net.n_ctrl, wl.lam)
+    U = si.uniforms(wl.seed, 1 + args.warmup + args.steps, wl.M, wl.draws_per_traj)
+    stream = torch.cuda.current_stream()
+    prob = Problem(net, wl.T, wl.nt, wl.M, eps0, S, lam, U, precision=wl.precision,
+                   ckpt_interval=wl.ckpt_interval, stream=stream)
+    info = prob.info
+    for _ in range(args.warmup):
+        prob.forward(False, stream=stream, keep_for_gradient=True)
+        prob.gradient(stream=stream)
+    clk_path = os.path.join(tempfile.gettempdir(), f"kt_clocks_{os.getpid()}.csv")
+    proc, fh = clocks_start(clk_path)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    prob.set_profiling(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        prob.forward(False, stream=stream, keep_for_gradient=True)
+        grad = prob.gradient(stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_step = reduce_max(ev0.elapsed_time(ev1) / args.steps, dist, "cuda")
+    prof = prob.profile()
+    prob.set_profiling(False)
+    clocks = clocks_stop(proc, fh, clk_path, local)
+    peaks, peak_src = measured_peaks()
+    clk_max = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = SM_COUNT * FP32_LANES * 2 * clk_max * 1e6 / 1e12
+    K = info.cheb_terms
+    nnz = avg_row_nonzeros(net)
+    # per control a 2d-dimensional propagation: the state's and the derivative's recurrences, plus
+    # the control factor (one entry per row) applied to the state in every term
+    g_ms, g_n = prof["grad"]
+    flops_grad = net.n_ctrl * K * (2 * (8.0 * nnz + 12.0) + 8.0) * wl.d * wl.M
+    achieved = flops_grad / (g_ms / max(g_n, 1) / 1000.0) / 1e12
+    per_s = world * 1000.0 / ms_step
+    line = {
+        "metric": METRIC, "value": per_s, "unit": "gradient evaluations/s (forward sweep + gradient sweep)",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic",
+        "config": {"workload": "cfg3_d729 gradient", "d": wl.d, "M": wl.M, "nt": wl.nt, "dt": wl.dt,
+                   "precision": "FP32-mixed", "ckpt_interval": wl.ckpt_interval, "cheb_terms": K,
+                   "tile_traj": info.tile_traj, "l2": "inputs larger than L2 (forward states kept for the "
+                   f"gradient, {info.device_bytes / 1e9:.1f} GB)", "parallelism": f"replicas{world}"},
+        "traj_steps_per_s": per_s * 2 * wl.M * wl.nt,
+        "roofline": {"bound": "alu", "kernel": "grad_kernel", "achieved": achieved, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                     "avg_launch_ms": g_ms / max(g_n, 1), "launches": g_n, "flops_per_launch": flops_grad,
+                     "peak_source": f"FP32 FFMA: {SM_COUNT} SMs x {FP32_LANES} lanes x 2 x {clk_max:.0f} MHz"},
+        "kernels": {f"{k}_kernel": {"launches": n, "total_ms": ms, "avg_ms": ms / max(n, 1)}
+                    for k, (ms, n) in prof.items() if n > 0},
+        "max_abs_gradient": float(np.abs(grad).max()),
+        "gpu_launches": int(sum(n for _, n in prof.values())),
+        "clocks": clocks,
+    }
+    prob.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -445,7 +533,7 @@ def run_ours(args, rank, world):
         "e2e": {"value": world * 1000.0 / e2e_ms, "unit": "Krotov iters/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "kernels": {f"{k}_kernel": {"launches": n, "total_ms": ms, "avg_ms": ms / max(n, 1)}
-                    for k, (ms, n) in prof.items()},
+                    for k, (ms, n) in prof.items() if n > 0},
         "gpu_launches": int(prof["fwd"][1] + prof["bwd"][1] + 4 * args.steps),
         "clocks": clocks,
     }
@@ -471,7 +559,7 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-comparison", action="store_true")
-    ap.add_argument("--workload", choices=["cfg5", "mix64"], default="cfg5")
+    ap.add_argument("--workload", choices=["cfg5", "mix64", "grad729"], default="cfg5")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -479,6 +567,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "mix64":
         return run_mix(args, rank, world)
+    if args.workload == "grad729":
+        return run_grad(args, rank, world)
     return run_ours(args, rank, world)
 
 

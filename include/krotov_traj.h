@@ -195,11 +195,12 @@ KT_API kt_status krotov_set_uniforms(kt_problem *p, const double *uniforms, int 
  * around every launch (on = 1), e.g. to derive each kernel's average duration during a
  * benchmark.  Turning it on or off clears the totals.  krotov_get_profile returns, per family
  * (KT_PROF_FWD: forward interval kernel incl. the pulse update; KT_PROF_BWD: backward interval
- * kernel incl. checkpoint recompute; KT_PROF_OTHER: reserved), the summed milliseconds and
+ * kernel incl. checkpoint recompute and the gradient's forward replay; KT_PROF_GRAD: gradient
+ * kernel of krotov_gradient), the summed milliseconds and
  * the launch count since profiling was turned on; arrays of KT_PROF_FAMILIES entries. */
 #define KT_PROF_FWD 0
 #define KT_PROF_BWD 1
-#define KT_PROF_OTHER 2
+#define KT_PROF_GRAD 2
 #define KT_PROF_FAMILIES 3
 KT_API kt_status krotov_set_profiling(kt_problem *p, int on);
 KT_API kt_status krotov_get_profile(kt_problem *p, double *ms_out, long long *launches_out);

@@ -24,7 +24,7 @@
 #define KT_PROF_FAMILIES 3
 #define KT_PROF_FWD 0
 #define KT_PROF_BWD 1
-#define KT_PROF_OTHER 2
+#define KT_PROF_GRAD 2
 #endif
 
 // Device status word values (first error wins); mirror kt_status.

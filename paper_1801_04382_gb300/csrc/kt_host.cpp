@@ -489,15 +489,21 @@ kt_status gradient_sweep(kt_problem *p, cudaStream_t st) {
         b.cursor = p->fcursor;
         b.forward_replay = 1;
         b.jcount = p->jcount[prev];
+        kt_status s = prof_begin(p, KT_PROF_BWD, st);
+        if (s != KT_OK) return s;
         KT_CUDA(kt_launch_bwd(p->fp64, p->ept, p->g, p->im_fwd, p->ops, b, st));
+        if ((s = prof_end(p, st)) != KT_OK) return s;
       }
     }
     for (int j = seg_b; j >= seg_a + 1; --j) {
       ga.j = j;
       ga.psi_prev = psi_at(p, j - 1, seg_a);
       ga.chi_t = p->chi_run[j & 1];
+      kt_status s = prof_begin(p, KT_PROF_GRAD, st);
+      if (s != KT_OK) return s;
       KT_CUDA(kt_launch_grad(p->fp64, p->grad_ept, p->g1, p->g.T, p->g.tile_elems, p->im_fwd, p->im_bwd, p->ops, ga, st));
-      kt_status s = launch_bwd_step(p, j, p->chi_run[j & 1], p->chi_run[(j - 1) & 1], st);
+      if ((s = prof_end(p, st)) != KT_OK) return s;
+      s = launch_bwd_step(p, j, p->chi_run[j & 1], p->chi_run[(j - 1) & 1], st);
       if (s != KT_OK) return s;
     }
     seg_b = seg_a;

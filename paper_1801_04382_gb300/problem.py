@@ -161,12 +161,13 @@ class Problem:
         _capi.check(self._lib.krotov_set_profiling(self._h, int(bool(on))), "krotov_set_profiling")
 
     def profile(self):
-        """{family: (total_ms, launches)} for 'fwd' and 'bwd' interval kernels since profiling was enabled."""
+        """{family: (total_ms, launches)} for the 'fwd' and 'bwd' interval kernels and the 'grad' kernel
+        since profiling was enabled."""
         ms = np.zeros(3)
         n = np.zeros(3, dtype=np.int64)
         _capi.check(self._lib.krotov_get_profile(self._h, _ptr(ms), n.ctypes.data_as(ct.POINTER(ct.c_longlong))),
                     "krotov_get_profile")
-        return {"fwd": (float(ms[0]), int(n[0])), "bwd": (float(ms[1]), int(n[1]))}
+        return {"fwd": (float(ms[0]), int(n[0])), "bwd": (float(ms[1]), int(n[1])), "grad": (float(ms[2]), int(n[2]))}
 
     def get_info(self):
         info = _capi.Info()

@@ -78,3 +78,41 @@ def test_autograd_function_matches_central_differences_at_kappa_zero():
             Jm = float(trajectory_functional(torch.tensor(em), p))
             fd = (Jp - Jm) / (2 * h)
             assert fd == pytest.approx(g[i, j], rel=1e-6, abs=1e-11)
+
+
+def test_gradient_full_size_launch_fd_and_precisions():
+    """The three-node gradient workload's launch size (d = 729, 1024 trajectories, one CTA per
+    trajectory in the gradient kernel) over a shorter window (nt = 200, dt = 0.025) at kappa = 0 --
+    no jumps, so the free-running functional is the frozen-record one: the FP64 gradient against
+    central differences (h = 1e-4) at 20 random slots, and the FP32-mixed gradient against the FP64
+    one within 2e-3 of max |dJ_T/deps| (complex64 states and co-states over 200 intervals)."""
+    N, nc = 3, 2
+    wl = si.CONFIGS["cfg3_d729"]
+    nt, M = 200, wl.M
+    T = wl.dt * nt
+    eps, S, lam, U, psi0 = _case(N, nc, T, nt, M, 30.0, wl.seed, kappa=0.0)
+    net = cascaded_chain(N, nc, kappa=0.0)
+    grads = {}
+    for prec in ("fp64", "fp32"):
+        with Problem(net, T, nt, M, eps, S, lam, U, psi0_batch=psi0, precision=prec) as p:
+            p.forward(keep_for_gradient=True)
+            assert sum(len(r) for r in p.records()) == 0
+            grads[prec] = p.gradient()
+            if prec != "fp64":
+                continue
+            rng = np.random.default_rng(1)
+            h = 1e-4
+            for _ in range(20):
+                i, j = int(rng.integers(N)), int(rng.integers(nt))
+                ep = eps.copy()
+                ep[i, j] += h
+                em = eps.copy()
+                em[i, j] -= h
+                p.set_pulses(ep)
+                Jp = 1.0 - p.forward(False)
+                p.set_pulses(em)
+                Jm = 1.0 - p.forward(False)
+                fd = (Jp - Jm) / (2 * h)
+                assert fd == pytest.approx(grads["fp64"][i, j], rel=1e-6, abs=1e-11), (i, j)
+    scale = np.abs(grads["fp64"]).max()
+    assert np.abs(grads["fp32"] - grads["fp64"]).max() <= 2e-3 * scale
