@@ -106,8 +106,117 @@ __device__ void aug_run(const KtGeom &g, const KtGenImage &im, const Smem &sm, c
   }
 }
 
-template <typename R, int EPT>
-__global__ void __launch_bounds__(EPT == 4 ? 256 : 1024)
+// Fiber form of (H_c / r) v for the thread's fiber (tile width 1): a control on the last node
+// takes row q of its factor for element q, a control on another node one row for the whole fiber.
+// Same entries and order as hc_item.
+template <typename R, int NL>
+__device__ __forceinline__ void hc_fiber(const KtGeom &g, const Smem &sm, int c, const typename C2<R>::T *v, int base,
+                                         uint32_t fdig, R invr, typename C2<R>::T (&h)[NL]) {
+  typedef typename C2<R>::T C;
+  const C *hv = (const C *)sm.hc_val;
+  const int node = g.ctrl_node[c];
+#pragma unroll
+  for (int q = 0; q < NL; ++q) h[q] = mkc((R)0, (R)0);
+  if (node == g.n_nodes - 1) {
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      const int b = (c * g.n_loc + q) * g.SH;
+      for (int e = 0; e < g.SH; ++e) {
+        const C w = hv[b + e];
+        if (w.x != (R)0 || w.y != (R)0) h[q] = cfma(w, v[base + q + sm.hc_off[b + e]], h[q]);
+      }
+    }
+  } else {
+    const int b = (c * g.n_loc + ((fdig >> (4 * node)) & 15)) * g.SH;
+    for (int e = 0; e < g.SH; ++e) {
+      const C w = hv[b + e];
+      if (w.x != (R)0 || w.y != (R)0) {
+        const int off = sm.hc_off[b + e];
+#pragma unroll
+        for (int q = 0; q < NL; ++q) h[q] = cfma(w, v[base + off + q], h[q]);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NL; ++q) h[q] = mkc(h[q].x * invr, h[q].y * invr);
+}
+
+// aug_run in the fiber mapping with tile width 1, for the cavity structure with real / imaginary
+// coupling classes: the same two recurrences, Ghat applied by apply_acs.
+template <typename R, int NC, class IT>
+__device__ void aug_run_acs(const KtGeom &g, const KtGenImage &im, const Smem &sm, const IT &it, int K, int c,
+                            typename C2<R>::T *Dbuf, typename C2<R>::T (&acc)[3 * (NC + 1)]) {
+  typedef typename C2<R>::T C;
+  constexpr int NL = 3 * (NC + 1);
+  C *A = (C *)sm.bufA, *B = (C *)sm.bufB, *Cb = (C *)sm.bufC, *D = Dbuf;
+  const C *cf = (const C *)sm.coef;
+  const C *dg = (const C *)sm.diag;
+  const R invr = (R)(1.0 / g.r);
+  const bool ok = it.ok(0);
+  const int base = it.item(0);
+  const uint32_t fdig = it.dig(0);
+  const int last = g.n_nodes - 1;
+  C Df = mkc((R)0, (R)0);
+  for (int i = 0; i < last; ++i) {
+    const C v = dg[i * NL + ((fdig >> (4 * i)) & 15)];
+    Df.x += v.x;
+    Df.y += v.y;
+  }
+#pragma unroll
+  for (int q = 0; q < NL; ++q) {
+    acc[q] = mkc((R)0, (R)0);
+    if (ok) Cb[base + q] = mkc((R)0, (R)0);   // y_0 = 0
+  }
+  if (K < 2) { __syncthreads(); return; }
+  C v[NL], t[NL], h[NL];
+  if (ok) {
+#pragma unroll
+    for (int q = 0; q < NL; ++q) v[q] = A[base + q];
+    apply_acs<R, NC, 1, true>(g, im, sm, A, base, fdig, Df, v, t);      // z_1 = Ghat z_0
+    hc_fiber<R, NL>(g, sm, c, A, base, fdig, invr, h);                // y_1 = Hhat z_0
+    const C c1 = cf[1];
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      B[base + q] = t[q];
+      D[base + q] = h[q];
+      acc[q] = cfma(c1, h[q], acc[q]);
+    }
+  }
+  __syncthreads();
+  C *Pz = A, *Qz = B, *Py = Cb, *Qy = D;
+  for (int k = 2; k < K; ++k) {
+    if (ok) {
+      const C ak = cf[k];
+#pragma unroll
+      for (int q = 0; q < NL; ++q) v[q] = Qz[base + q];
+      apply_acs<R, NC, 1, true>(g, im, sm, Qz, base, fdig, Df, v, t);
+      hc_fiber<R, NL>(g, sm, c, Qz, base, fdig, invr, h);
+#pragma unroll
+      for (int q = 0; q < NL; ++q) {
+        const C oz = Pz[base + q];
+        Pz[base + q] = mkc(t[q].x + t[q].x - oz.x, t[q].y + t[q].y - oz.y);
+        v[q] = Qy[base + q];
+      }
+      apply_acs<R, NC, 1, true>(g, im, sm, Qy, base, fdig, Df, v, t);
+#pragma unroll
+      for (int q = 0; q < NL; ++q) {
+        const C ty = mkc(t[q].x + h[q].x, t[q].y + h[q].y);
+        const C oy = Py[base + q];
+        const C ny = mkc(ty.x + ty.x - oy.x, ty.y + ty.y - oy.y);
+        Py[base + q] = ny;
+        acc[q] = cfma(ak, ny, acc[q]);
+      }
+    }
+    __syncthreads();
+    C *t1 = Pz; Pz = Qz; Qz = t1;
+    C *t2 = Py; Py = Qy; Qy = t2;
+  }
+}
+
+// NL = 0: strided items (EPT per thread); NL = 9 with ACS = 4: fiber mapping, tile width 1,
+// cavity structure with real / imaginary coupling classes.
+template <typename R, int EPT, int NL, int ACS>
+__global__ void __launch_bounds__(NL > 0 ? 96 : (EPT == 4 ? 256 : 1024), NL > 0 ? 5 : 1)
     grad_kernel(KtGeom g, int T_layout, int tel, KtGenImage imf, KtGenImage imb, KtOps ops, GradArgs a) {
   typedef typename C2<R>::T C;
   extern __shared__ __align__(16) char smem_raw[];
@@ -131,8 +240,8 @@ __global__ void __launch_bounds__(EPT == 4 ? 256 : 1024)
   }
   __syncthreads();
   const int m = sm.tin[TI_NJ];
-  Items<EPT, 0> it;
-  load_items<EPT, 0>(g, ops, it);
+  Items<EPT, NL> it;
+  load_items<EPT, NL>(g, ops, it);
   const C *psi_t = (const C *)a.psi_prev;
   const C *chi_t = (const C *)a.chi_t;
   // piece boundaries s_0 = 0 < s_1 < ... < s_m < s_{m+1} = dt
@@ -194,7 +303,8 @@ __global__ void __launch_bounds__(EPT == 4 ? 256 : 1024)
       for (int qq = 0; qq < EPT; ++qq)
         if (it.ok(qq)) A[it.item(qq)] = zq[qq];
       __syncthreads();
-      aug_run<R, EPT>(g, imf, sm, it, g.K, c, D, acc);
+      if constexpr (ACS == 4) aug_run_acs<R, NL / 3 - 1>(g, imf, sm, it, g.K, c, D, acc);
+      else aug_run<R, EPT>(g, imf, sm, it, g.K, c, D, acc);
       double sacc = 0.0;
 #pragma unroll
       for (int qq = 0; qq < EPT; ++qq)
@@ -232,17 +342,17 @@ __global__ void __launch_bounds__(EPT == 4 ? 256 : 1024)
   if (threadIdx.x == 0) *a.counter = 0u;
 }
 
-template <typename R, int EPT>
+template <typename R, int EPT, int NL, int ACS>
 static cudaError_t launch_grad_t(const KtGeom &g1, int T_layout, int tel, const KtGenImage &imf,
                                  const KtGenImage &imb, const KtOps &ops, const GradArgs &a, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(grad_kernel<R, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(grad_kernel<R, EPT, NL, ACS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const size_t smem = grad_carve(g1, sizeof(typename C2<R>::T), nullptr, nullptr, nullptr);
-  grad_kernel<R, EPT><<<g1.M, g1.nthreads, smem, st>>>(g1, T_layout, tel, imf, imb, ops, a);
+  grad_kernel<R, EPT, NL, ACS><<<g1.M, g1.nthreads, smem, st>>>(g1, T_layout, tel, imf, imb, ops, a);
   return cudaGetLastError();
 }
 
@@ -256,13 +366,15 @@ cudaError_t kt_launch_grad(int fp64, int ept, const KtGeom &g1, int T_layout, in
                            const KtGenImage &imb, const KtOps &ops, const GradArgs &a, cudaStream_t st) {
   if (fp64) {
     switch (ept) {
-      case 4: return kt::launch_grad_t<double, 4>(g1, T_layout, tel, imf, imb, ops, a, st);
-      case 8: return kt::launch_grad_t<double, 8>(g1, T_layout, tel, imf, imb, ops, a, st);
+      case 4: return kt::launch_grad_t<double, 4, 0, 0>(g1, T_layout, tel, imf, imb, ops, a, st);
+      case 8: return kt::launch_grad_t<double, 8, 0, 0>(g1, T_layout, tel, imf, imb, ops, a, st);
+      case -409: return kt::launch_grad_t<double, 9, 9, 4>(g1, T_layout, tel, imf, imb, ops, a, st);
     }
   } else {
     switch (ept) {
-      case 4: return kt::launch_grad_t<float, 4>(g1, T_layout, tel, imf, imb, ops, a, st);
-      case 8: return kt::launch_grad_t<float, 8>(g1, T_layout, tel, imf, imb, ops, a, st);
+      case 4: return kt::launch_grad_t<float, 4, 0, 0>(g1, T_layout, tel, imf, imb, ops, a, st);
+      case 8: return kt::launch_grad_t<float, 8, 0, 0>(g1, T_layout, tel, imf, imb, ops, a, st);
+      case -409: return kt::launch_grad_t<float, 9, 9, 4>(g1, T_layout, tel, imf, imb, ops, a, st);
     }
   }
   return cudaErrorInvalidValue;

@@ -430,10 +430,18 @@ kt_status grad_setup(kt_problem *p, cudaStream_t st) {
   g1.M_pad = p->M;
   g1.tile_elems = (g1.d + 3) / 4 * 4;
   g1.prefetch_chi = 0;
-  // 4 items per thread up to 256 threads, else 8 up to 1024 (the compiled gradient kernels)
-  int ept = (g1.d + 3) / 4 <= 256 ? 4 : 8;
-  if ((g1.d + ept - 1) / ept > 1024) return fail(KT_ERR_UNSUPPORTED, "dimension too large for the gradient kernel");
-  g1.nthreads = std::max(32, ((g1.d + ept - 1) / ept + 31) / 32 * 32);
+  // cavity structure with real / imaginary coupling classes, n_loc = 9, up to 96 fibers (the
+  // compiled block size): one thread per last-node fiber; otherwise 4 items per thread up to 256
+  // threads, else 8 up to 1024
+  int ept;
+  if ((p->ept == -309 || p->ept == -409) && g1.d / 9 <= 96) {
+    ept = -409;
+    g1.nthreads = std::max(32, (g1.d / 9 + 31) / 32 * 32);
+  } else {
+    ept = (g1.d + 3) / 4 <= 256 ? 4 : 8;
+    if ((g1.d + ept - 1) / ept > 1024) return fail(KT_ERR_UNSUPPORTED, "dimension too large for the gradient kernel");
+    g1.nthreads = std::max(32, ((g1.d + ept - 1) / ept + 31) / 32 * 32);
+  }
   if (kt_grad_smem_bytes(g1, (int)p->esz) > 227 * 1024)
     return fail(KT_ERR_UNSUPPORTED, "the gradient needs four state buffers of d = %d in shared memory (%s)", g1.d,
                 p->fp64 ? "use FP32-mixed" : "too large");
