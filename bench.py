@@ -10,6 +10,7 @@ intervals, synthetic seeded inputs (guess pulse sin^2 of amplitude 1, uniforms f
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
     python bench.py --workload mix64 [--steps K] [--warmup W]
     python bench.py --workload grad729 [--steps K] [--warmup W]
+    python bench.py --workload noise
 
 --workload mix64 times the batch of 64 independent problems of mixed size (2, 3 and 4 nodes,
 d = 81 / 729 / 6561, 128..2048 trajectories, nt 1000 or 2000, kappa in [0.5, 2], FP32-mixed,
@@ -18,6 +19,9 @@ same problems iterated one after another (one graph launch each) are timed besid
 --workload grad729 times the exact gradient dJ_T/deps (frozen jump record) on the three-node
 chain (d = 729, 1024 trajectories, nt = 2000, FP32-mixed, seed 2): one step is a forward sweep
 that keeps the states plus the gradient sweep.
+--workload noise measures the pulse noise nu_i (Eq. noise) after 10 Krotov iterations on the
+two-node chain (d = 81, nt = 1000, guess amplitude 20 so that a quarter of the trajectories jump,
+FP32-mixed) for M = 8 ... 1024 trajectories and fits nu_i ~ M^b (the paper finds b = -1/2).
 
 N > 1 (under torchrun): every rank optimises an independent problem (its own seed); there is
 no data-path collective ("weak" scaling).  --impl reference times the FP64 CPU oracle on a
@@ -396,6 +400,48 @@ def run_grad(args, rank, world):
     return 0
 
 
+def run_noise(args, rank, world):
+    """Pulse noise nu_i versus the number of trajectories (Fig. 4 experiment, independent trajectories)."""
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU (GB300); the CUDA path has no CPU fallback")
+    if rank != 0:
+        return 0
+    from paper_1801_04382_gb300 import Problem, cascaded_chain
+    wl = si.CONFIGS["cfg2_d81"]
+    amp, n_iter = 20.0, 10
+    net = cascaded_chain(wl.n_nodes, wl.n_cav, wl.delta, wl.g, wl.kappa)
+    eps0 = si.guess_pulses(net.n_ctrl, wl.nt, wl.T, amp)
+    S = si.shape_functions(net.n_ctrl, wl.nt, wl.T)
+    lam = np.full(net.n_ctrl, wl.lam)
+    stream = torch.cuda.current_stream()
+    Ms = [8, 16, 32, 64, 128, 256, 512, 1024]
+    rows = []
+    for M in Ms:
+        U = si.uniforms(wl.seed, n_iter + 1, M, wl.draws_per_traj)
+        with Problem(net, wl.T, wl.nt, M, eps0, S, lam, U, precision="fp32", stream=stream) as p:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            p.forward(False, stream=stream)
+            e0.record(stream)
+            JT, _ = p.update(n_iter, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            nu = p.pulse_noise(stream=stream)
+            jumped = float(np.mean([len(r) > 0 for r in p.records()]))
+            rows.append({"M": M, "nu": nu.tolist(), "final_JT": float(JT[-1]), "jumped_fraction": jumped,
+                         "iters_per_s": n_iter * 1000.0 / e0.elapsed_time(e1)})
+    logM = np.log(np.array(Ms, dtype=np.float64))
+    slopes = [float(np.polyfit(logM, np.log([r["nu"][i] for r in rows]), 1)[0]) for i in range(net.n_ctrl)]
+    line = {"metric": "pulse noise nu_i(M) (Eq. noise), fitted exponent of M", "value": float(np.mean(slopes)),
+            "unit": "exponent b of nu ~ M^b (paper: -1/2)", "n_gpus": 1, "higher_is_better": False,
+            "data": "synthetic", "dtype": "c64+f64",
+            "config": {"workload": f"{wl.name} model, guess amplitude {amp}, {n_iter} iterations, FP32-mixed",
+                       "d": wl.d, "nt": wl.nt, "M": Ms},
+            "slopes": slopes, "runs": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -559,7 +605,7 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-comparison", action="store_true")
-    ap.add_argument("--workload", choices=["cfg5", "mix64", "grad729"], default="cfg5")
+    ap.add_argument("--workload", choices=["cfg5", "mix64", "grad729", "noise"], default="cfg5")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -569,6 +615,8 @@ def main():
         return run_mix(args, rank, world)
     if args.workload == "grad729":
         return run_grad(args, rank, world)
+    if args.workload == "noise":
+        return run_noise(args, rank, world)
     return run_ours(args, rank, world)
 
 

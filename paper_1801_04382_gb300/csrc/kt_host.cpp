@@ -172,6 +172,7 @@ struct kt_problem {
   int *status = nullptr;
 
   int *pass = nullptr;          // device [3]: next uniforms row, rows held, row of the running pass
+  double *nu = nullptr;         // device [KT_MAX_CTRL]: pulse noise (krotov_pulse_noise)
   double *eps_base = nullptr;   // the pulse buffer eps_old pointed to at init (keys the graphs)
   bool have_fwd = false, have_bwd = false, have_deps = false;
   int final_buf = 0;
@@ -1499,6 +1500,21 @@ KT_API kt_status krotov_gradient(kt_problem *p, double *dJ_out, void *stream) {
   kt_status s = gradient_sweep(p, st);
   if (s != KT_OK) return s;
   KT_CUDA(cudaMemcpyAsync(dJ_out, p->dgrad, sizeof(double) * p->g.n_ctrl * p->nt, cudaMemcpyDeviceToHost, st));
+  KT_CUDA(cudaStreamSynchronize(st));
+  return KT_OK;
+}
+
+KT_API kt_status krotov_pulse_noise(kt_problem *p, double *nu_out, void *stream) {
+  if (!p || !nu_out) return fail(KT_ERR_ARG, "NULL argument");
+  if (p->nt < 5) return fail(KT_ERR_ARG, "the five-point smoothing needs nt >= 5");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nc = p->g.n_ctrl;
+  if (!p->nu) {
+    kt_status s = dev_alloc(p, (void **)&p->nu, KT_MAX_CTRL * sizeof(double));
+    if (s != KT_OK) return s;
+  }
+  KT_CUDA(kt_launch_pulse_noise(p->eps_old, nc, p->nt, p->g.dt, p->nu, st));
+  KT_CUDA(cudaMemcpyAsync(nu_out, p->nu, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
   KT_CUDA(cudaStreamSynchronize(st));
   return KT_OK;
 }

@@ -60,9 +60,48 @@ __global__ void chi_boundary_kernel(KtGeom g, KtOps ops, const KtCplx *tau, C *c
   }
 }
 
+// Noise of the pulse (Eq. noise): nu_c = sum_j |eps_cj - smooth_cj| dt, smooth = five-point cubic
+// Savitzky-Golay smoothing -- the least-squares cubic through the five samples around j (the first
+// or last five at the two ends) evaluated at j.  Weights x 70 of that fit at window positions
+// 0, 1, 2 (3 and 4 mirror them); position 2 is the published centred convolute (-3,12,17,12,-3)/35.
+__constant__ double sg5_w[3][5] = {{69, 4, -6, 4, -1}, {4, 54, 24, -16, 4}, {-6, 24, 34, 24, -6}};
+
+// One block per control; fixed-order FP64 reduction.
+__global__ void pulse_noise_kernel(const double *eps, int nt, double dt, double *nu) {
+  __shared__ double red[32];
+  const int c = blockIdx.x;
+  const double *e = eps + (size_t)c * nt;
+  double s = 0.0;
+  for (int j = threadIdx.x; j < nt; j += blockDim.x) {
+    int start, pos;
+    if (j < 2) { start = 0; pos = j; }
+    else if (j >= nt - 2) { start = nt - 5; pos = 4 - (nt - 1 - j); }
+    else { start = j - 2; pos = 2; }
+    double sm = 0.0;
+    for (int q = 0; q < 5; ++q) {
+      const double w = pos <= 2 ? sg5_w[pos][q] : sg5_w[4 - pos][4 - q];
+      sm += w * e[start + q];
+    }
+    s += fabs(e[j] - sm / 70.0) * dt;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    nu[c] = t;
+  }
+}
+
 }  // namespace kt
 
 using namespace kt;
+
+cudaError_t kt_launch_pulse_noise(const double *eps, int n_ctrl, int nt, double dt, double *nu, cudaStream_t st) {
+  pulse_noise_kernel<<<n_ctrl, 256, 0, st>>>(eps, nt, dt, nu);
+  return cudaGetLastError();
+}
 
 size_t kt_smem_bytes(const KtGeom &g, int elem_bytes, bool with_chi_buffer) {
   return carve(g, elem_bytes, nullptr, nullptr, with_chi_buffer);

@@ -395,3 +395,39 @@ def test_gradient_matches_free_running_fd_at_kappa_zero():
         Fm = mcwf.fidelity(mcwf.forward_pass(m, em, wl.T, U[0], psi0).psi_T, m.psi_tgt)[1]
         fd = -(Fp - Fm) / (2 * h)
         assert fd == pytest.approx(grad[i, j], rel=1e-6, abs=1e-11)
+
+
+# ---------------------------------------------------------------- noise measure (Eq. noise)
+def test_savitzky_golay_reproduces_cubics_and_published_weights():
+    """A cubic least-squares smoother leaves any cubic unchanged (nu = 0), and its centred
+    five-point weights are the published convolute (-3, 12, 17, 12, -3)/35."""
+    from oracle import noise
+    t = np.linspace(-1.0, 2.0, 40)
+    cubic = 0.3 - 1.2 * t + 0.7 * t ** 2 + 0.25 * t ** 3
+    np.testing.assert_allclose(noise.savitzky_golay_cubic5(cubic), cubic, rtol=0, atol=1e-12)
+    assert noise.pulse_noise(cubic[None, :], 0.1)[0] <= 1e-11
+    for k in range(5):
+        e = np.zeros(11)
+        e[3 + k] = 1.0
+        assert noise.savitzky_golay_cubic5(e)[5] == pytest.approx([-3, 12, 17, 12, -3][4 - k] / 35.0, abs=1e-14)
+
+
+def test_savitzky_golay_matches_scipy_interp_mode():
+    from scipy.signal import savgol_filter
+    from oracle import noise
+    y = np.random.default_rng(3).normal(size=57)
+    np.testing.assert_allclose(noise.savitzky_golay_cubic5(y), savgol_filter(y, 5, 3, mode="interp"),
+                               rtol=0, atol=1e-12)
+
+
+def test_noise_of_white_noise_scales_and_power_law_fit():
+    """nu is linear in the noise amplitude and the log-log fit recovers an exact power law."""
+    from oracle import noise
+    rng = np.random.default_rng(4)
+    base = np.sin(np.linspace(0, np.pi, 400)) ** 2
+    w = rng.normal(size=400)
+    n1 = noise.pulse_noise((base + 1e-3 * w)[None, :], 0.05)[0]
+    n2 = noise.pulse_noise((base + 2e-3 * w)[None, :], 0.05)[0]
+    assert n2 / n1 == pytest.approx(2.0, rel=1e-3)
+    M = np.array([4, 16, 64, 256])
+    assert noise.fit_power_law(M, 3.0 / np.sqrt(M)) == pytest.approx(-0.5, abs=1e-12)
