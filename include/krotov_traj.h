@@ -185,12 +185,14 @@ KT_API kt_status krotov_get_states(kt_problem *p, double *psi_out);
  * j a checkpoint. */
 KT_API kt_status krotov_get_costate(kt_problem *p, int j, double *chi_out);
 
-/* Noise of the current pulse (Eq. noise): nu_out[c] = sum_j |eps_cj - smooth_cj| dt for each
- * control (host output [n_ctrl]), smooth = five-point cubic Savitzky-Golay smoothing (the
+/* Noise of the current pulse (Eq. noise): nu_out[c] = sum_j |e_cj - smooth_cj| dt for each control
+ * (host output [n_ctrl]), e = eps, or eps - ref when ref (host [n_ctrl][nt], nullable) is given --
+ * e.g. ref = the guess pulse measures the noise of the accumulated update without the smoothing
+ * residual of a smooth guess.  smooth = five-point cubic Savitzky-Golay smoothing (the
  * least-squares cubic through the five samples centred on j, or the first / last five at the two
  * ends, evaluated at j).  Computed on the device from the device-resident pulse; needs nt >= 5
  * (KT_ERR_ARG otherwise).  Synchronises `stream`. */
-KT_API kt_status krotov_pulse_noise(kt_problem *p, double *nu_out, void *stream);
+KT_API kt_status krotov_pulse_noise(kt_problem *p, const double *ref, double *nu_out, void *stream);
 
 /* Replace the uniform random numbers (host array [n_passes][M][draws_per_traj], 1 <= n_passes
  * <= the value given at init, draws as at init); later passes cycle through these n_passes rows,

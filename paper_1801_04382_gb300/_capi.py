@@ -65,7 +65,7 @@ SIGNATURES = {
     "krotov_get_costate": (ct.c_int, [ct.c_void_p, ct.c_int, dp]),
     "krotov_get_info": (ct.c_int, [ct.c_void_p, ct.POINTER(Info)]),
     "krotov_set_uniforms": (ct.c_int, [ct.c_void_p, dp, ct.c_int, ct.c_void_p]),
-    "krotov_pulse_noise": (ct.c_int, [ct.c_void_p, dp, ct.c_void_p]),
+    "krotov_pulse_noise": (ct.c_int, [ct.c_void_p, dp, dp, ct.c_void_p]),
     "krotov_set_profiling": (ct.c_int, [ct.c_void_p, ct.c_int]),
     "krotov_get_profile": (ct.c_int, [ct.c_void_p, dp, ct.POINTER(ct.c_longlong)]),
     "krotov_free": (None, [ct.c_void_p]),

@@ -173,6 +173,7 @@ struct kt_problem {
 
   int *pass = nullptr;          // device [3]: next uniforms row, rows held, row of the running pass
   double *nu = nullptr;         // device [KT_MAX_CTRL]: pulse noise (krotov_pulse_noise)
+  double *nu_ref = nullptr;     // device [n_ctrl][nt]: its reference pulse
   double *eps_base = nullptr;   // the pulse buffer eps_old pointed to at init (keys the graphs)
   bool have_fwd = false, have_bwd = false, have_deps = false;
   int final_buf = 0;
@@ -1504,16 +1505,19 @@ KT_API kt_status krotov_gradient(kt_problem *p, double *dJ_out, void *stream) {
   return KT_OK;
 }
 
-KT_API kt_status krotov_pulse_noise(kt_problem *p, double *nu_out, void *stream) {
+KT_API kt_status krotov_pulse_noise(kt_problem *p, const double *ref, double *nu_out, void *stream) {
   if (!p || !nu_out) return fail(KT_ERR_ARG, "NULL argument");
   if (p->nt < 5) return fail(KT_ERR_ARG, "the five-point smoothing needs nt >= 5");
   cudaStream_t st = (cudaStream_t)stream;
   const int nc = p->g.n_ctrl;
+  const size_t n = (size_t)nc * p->nt;
   if (!p->nu) {
     kt_status s = dev_alloc(p, (void **)&p->nu, KT_MAX_CTRL * sizeof(double));
+    if (s == KT_OK) s = dev_alloc(p, (void **)&p->nu_ref, n * sizeof(double));
     if (s != KT_OK) return s;
   }
-  KT_CUDA(kt_launch_pulse_noise(p->eps_old, nc, p->nt, p->g.dt, p->nu, st));
+  if (ref) KT_CUDA(cudaMemcpyAsync(p->nu_ref, ref, n * sizeof(double), cudaMemcpyHostToDevice, st));
+  KT_CUDA(kt_launch_pulse_noise(p->eps_old, ref ? p->nu_ref : nullptr, nc, p->nt, p->g.dt, p->nu, st));
   KT_CUDA(cudaMemcpyAsync(nu_out, p->nu, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
   KT_CUDA(cudaStreamSynchronize(st));
   return KT_OK;

@@ -72,8 +72,9 @@ cudaError_t kt_launch_init_pass(const KtGeom &g, const double *U, int *pass, dou
                                 cudaStream_t st);
 // pass[0] = 0, pass[1] = n_passes
 cudaError_t kt_launch_pass_reset(int *pass, int n_passes, cudaStream_t st);
-// nu[c] = noise of pulse c (five-point cubic Savitzky-Golay residual, integrated), nt >= 5
-cudaError_t kt_launch_pulse_noise(const double *eps, int n_ctrl, int nt, double dt, double *nu, cudaStream_t st);
+// nu[c] = noise of pulse c minus ref (nullable) (five-point cubic Savitzky-Golay residual, integrated), nt >= 5
+cudaError_t kt_launch_pulse_noise(const double *eps, const double *ref, int n_ctrl, int nt, double dt, double *nu,
+                                  cudaStream_t st);
 cudaError_t kt_launch_cursor_seek(const KtGeom &g, const int *rec_step, const int *jcount, int upto,
                                   int *cursor, cudaStream_t st);
 // cursor[k] = first record of trajectory k with interval >= from (jcount[k] if none)

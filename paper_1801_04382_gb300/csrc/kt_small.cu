@@ -67,10 +67,13 @@ __global__ void chi_boundary_kernel(KtGeom g, KtOps ops, const KtCplx *tau, C *c
 __constant__ double sg5_w[3][5] = {{69, 4, -6, 4, -1}, {4, 54, 24, -16, 4}, {-6, 24, 34, 24, -6}};
 
 // One block per control; fixed-order FP64 reduction.
-__global__ void pulse_noise_kernel(const double *eps, int nt, double dt, double *nu) {
+// With ref != NULL the noise of eps - ref (e.g. of the accumulated update) is measured.
+__global__ void pulse_noise_kernel(const double *eps, const double *ref, int nt, double dt, double *nu) {
   __shared__ double red[32];
   const int c = blockIdx.x;
   const double *e = eps + (size_t)c * nt;
+  const double *rf = ref ? ref + (size_t)c * nt : nullptr;
+  auto val = [&](int j) { return rf ? e[j] - rf[j] : e[j]; };
   double s = 0.0;
   for (int j = threadIdx.x; j < nt; j += blockDim.x) {
     int start, pos;
@@ -80,9 +83,9 @@ __global__ void pulse_noise_kernel(const double *eps, int nt, double dt, double 
     double sm = 0.0;
     for (int q = 0; q < 5; ++q) {
       const double w = pos <= 2 ? sg5_w[pos][q] : sg5_w[4 - pos][4 - q];
-      sm += w * e[start + q];
+      sm += w * val(start + q);
     }
-    s += fabs(e[j] - sm / 70.0) * dt;
+    s += fabs(val(j) - sm / 70.0) * dt;
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -98,8 +101,9 @@ __global__ void pulse_noise_kernel(const double *eps, int nt, double dt, double 
 
 using namespace kt;
 
-cudaError_t kt_launch_pulse_noise(const double *eps, int n_ctrl, int nt, double dt, double *nu, cudaStream_t st) {
-  pulse_noise_kernel<<<n_ctrl, 256, 0, st>>>(eps, nt, dt, nu);
+cudaError_t kt_launch_pulse_noise(const double *eps, const double *ref, int n_ctrl, int nt, double dt, double *nu,
+                                  cudaStream_t st) {
+  pulse_noise_kernel<<<n_ctrl, 256, 0, st>>>(eps, ref, nt, dt, nu);
   return cudaGetLastError();
 }
 

@@ -150,11 +150,13 @@ class Problem:
         _capi.check(self._lib.krotov_get_costate(self._h, int(j), _ptr(out)), "krotov_get_costate")
         return out[..., 0] + 1j * out[..., 1]
 
-    def pulse_noise(self, stream=None) -> np.ndarray:
-        """nu_c = integral |eps_c - smooth(eps_c)| dt of the current pulse (five-point cubic
-        Savitzky-Golay smoothing), [n_ctrl]."""
+    def pulse_noise(self, ref=None, stream=None) -> np.ndarray:
+        """nu_c = integral |e_c - smooth(e_c)| dt with e = current pulse (minus ``ref`` [n_ctrl, nt]
+        when given), five-point cubic Savitzky-Golay smoothing; [n_ctrl]."""
         out = np.zeros(self.n_ctrl)
-        _capi.check(self._lib.krotov_pulse_noise(self._h, _ptr(out), _stream_handle(stream)), "krotov_pulse_noise")
+        r = _c(ref) if ref is not None else None
+        _capi.check(self._lib.krotov_pulse_noise(self._h, _ptr(r), _ptr(out), _stream_handle(stream)),
+                    "krotov_pulse_noise")
         return out
 
     def set_uniforms(self, uniforms, stream=None) -> None:

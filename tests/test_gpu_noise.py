@@ -23,7 +23,11 @@ def test_pulse_noise_matches_oracle(precision):
                  psi0_batch=si.random_states(109, M, (3 * (nc + 1)) ** N)) as p:
         p.update(3)
         nu = p.pulse_noise()
-        eps = p.pulses()
-        ref = noise.pulse_noise(eps, T / nt)
-    assert np.all(ref > 0)
-    np.testing.assert_allclose(nu, ref, rtol=0, atol=16 * np.finfo(float).eps * np.abs(eps).max() * T)
+        nu_upd = p.pulse_noise(ref=eps)
+        pulse = p.pulses()
+    tol = 16 * np.finfo(float).eps * np.abs(pulse).max() * T
+    want = noise.pulse_noise(pulse, T / nt)
+    want_upd = noise.pulse_noise(pulse - eps, T / nt)
+    assert np.all(want > 0) and np.all(want_upd > 0)
+    np.testing.assert_allclose(nu, want, rtol=0, atol=tol)
+    np.testing.assert_allclose(nu_upd, want_upd, rtol=0, atol=tol)
