@@ -437,13 +437,17 @@ def run_noise(args, rank, world):
     slopes = [float(np.polyfit(logM, np.log([r["nu"][i] for r in rows]), 1)[0]) for i in range(net.n_ctrl)]
     slopes_upd = [float(np.polyfit(logM, np.log([r["nu_update"][i] for r in rows]), 1)[0])
                   for i in range(net.n_ctrl)]
+    big = [i for i, M in enumerate(Ms) if M >= 128]
+    slopes_tail = [float(np.polyfit(logM[big], np.log([rows[k]["nu_update"][i] for k in big]), 1)[0])
+                   for i in range(net.n_ctrl)]
     line = {"metric": "pulse noise nu_i(M) (Eq. noise) of the accumulated update, fitted exponent of M",
             "value": float(np.mean(slopes_upd)),
             "unit": "exponent b of nu ~ M^b (paper: -1/2)", "n_gpus": 1, "higher_is_better": False,
             "data": "synthetic", "dtype": "c64+f64",
             "config": {"workload": f"{wl.name} model, guess amplitude {amp}, {n_iter} iterations, FP32-mixed",
                        "d": wl.d, "nt": wl.nt, "M": Ms},
-            "slopes_update": slopes_upd, "slopes_pulse": slopes, "runs": rows}
+            "slopes_update": slopes_upd, "slopes_update_M_ge_128": slopes_tail, "slopes_pulse": slopes,
+            "runs": rows}
     print(json.dumps(line), flush=True)
     return 0
 
