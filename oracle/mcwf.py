@@ -11,6 +11,9 @@ Follows, step by step and in the paper's order:
       Delta eps_i(t) = S_i(t) / (M lambda_i) sum_k Im <chi_k^(0)(t)| H_i |Psi_k^(1)(t)>
   with chi_k^(0)(T) = tau_k |Psi_tgt> and tau_k the overlap of Eq. (functional_traj).
 * Sec. 2.2, Eq. (krotov_functional): J = J_T + sum_i lambda_i/S_i int Delta eps_i^2 dt.
+* Sec. 2.3, Eq. (cross_traj_update), the cross-trajectory variant:
+      Delta eps_i(t) = S_i(t) / (M^2 lambda_i) sum_{k,k'} Im[<xi_k^(0)(t)|H_i|Psi_k'^(1)(t)> <Psi_k'^(1)(t)|xi_k^(0)(t)>]
+  with xi_k^(0)(T) = |Psi_tgt> propagated backward like chi_k (along trajectory k's record).
 
 Readings of points the paper leaves open (each listed with this build's design notes):
 the state is not renormalised between jumps and is renormalised after each jump; a jump
@@ -102,16 +105,24 @@ def _step_with_jumps(prop: StepPropagator, Ls: list, psi: np.ndarray, dt: float,
         s0 = s0 + hi
 
 
+def cross_overlap(xi: np.ndarray, psi: np.ndarray, Hc: np.ndarray) -> float:
+    """sum_{k,k'} Im[<xi_k|Hc|psi_k'> <psi_k'|xi_k>] for xi, psi [M, d] (Eq. cross_traj_update)."""
+    A = np.conj(xi) @ (psi @ Hc.T).T          # A[k, k'] = <xi_k|Hc|psi_k'>
+    G = np.conj(xi) @ psi.T                   # G[k, k'] = <xi_k|psi_k'>, so <psi_k'|xi_k> = conj(G)
+    return float(np.sum(np.imag(A * np.conj(G))))
+
+
 def forward_pass(model, eps: np.ndarray, T: float, U_pass: np.ndarray, psi0: np.ndarray,
                  chi: np.ndarray = None, shape: np.ndarray = None, lam: np.ndarray = None,
-                 keep_states: bool = False, max_jumps: int = None) -> ForwardResult:
+                 keep_states: bool = False, max_jumps: int = None, cross: bool = False) -> ForwardResult:
     """One forward MCWF sweep over all M trajectories.
 
     Without ``chi`` the pulse ``eps`` is used as is.  With ``chi`` ([nt+1, M, d], the
     co-states of the previous backward sweep) the Krotov update is applied sequentially:
     before interval j is propagated, Delta eps_ij is formed from all trajectories' states
     at t_{j-1} and the new value eps_ij + Delta eps_ij is used for that interval.
-    ``psi0`` is [d] (same initial state for every trajectory) or [M, d].
+    ``psi0`` is [d] (same initial state for every trajectory) or [M, d].  With ``cross`` the
+    co-states are the xi_k of Eq. (cross_traj_update) and the update is the cross-trajectory one.
     """
     n_ctrl, nt = eps.shape
     M = U_pass.shape[0]
@@ -128,6 +139,10 @@ def forward_pass(model, eps: np.ndarray, T: float, U_pass: np.ndarray, psi0: np.
     for j in range(1, nt + 1):
         if chi is not None:
             for i in range(n_ctrl):
+                if cross:
+                    g = cross_overlap(chi[j - 1], psi, model.Hc[i])
+                    deps[i, j - 1] = shape[i, j - 1] / (lam[i] * M * M) * g
+                    continue
                 hpsi = psi @ model.Hc[i].T          # rows: Hc_i psi_k
                 g = np.sum(np.imag(np.sum(np.conj(chi[j - 1]) * hpsi, axis=1)))
                 deps[i, j - 1] = shape[i, j - 1] / (lam[i] * M) * g
@@ -213,11 +228,14 @@ class OptimizationResult:
 
 
 def optimize(model, eps0: np.ndarray, T: float, U: np.ndarray, shape: np.ndarray, lam: np.ndarray,
-             n_iter: int, psi0=None, keep: bool = False) -> OptimizationResult:
-    """Independent-trajectory Krotov: guess pass 0, then n_iter x [backward; updating forward].
+             n_iter: int, psi0=None, keep: bool = False, update: str = "independent") -> OptimizationResult:
+    """Trajectory Krotov: guess pass 0, then n_iter x [backward; updating forward].
 
-    Forward pass p reads uniforms U[p]; iteration n uses the records of pass n-1.
+    Forward pass p reads uniforms U[p]; iteration n uses the records of pass n-1.  ``update``:
+    "independent" (Eq. independent_traj_update, chi_k(T) = tau_k |tgt>) or "cross"
+    (Eq. cross_traj_update, xi_k(T) = |tgt>).
     """
+    cross = update == "cross"
     psi0 = model.psi0 if psi0 is None else psi0
     nt = eps0.shape[1]
     dt = T / nt
@@ -228,8 +246,9 @@ def optimize(model, eps0: np.ndarray, T: float, U: np.ndarray, shape: np.ndarray
         res.forward.append(fw)
     eps = eps0.copy()
     for n in range(1, n_iter + 1):
-        chi = backward_pass(model, eps, T, tau[:, None] * model.psi_tgt[None, :], fw.records)
-        fw = forward_pass(model, eps, T, U[n], psi0, chi=chi, shape=shape, lam=lam)
+        boundary = np.ones_like(tau) if cross else tau
+        chi = backward_pass(model, eps, T, boundary[:, None] * model.psi_tgt[None, :], fw.records)
+        fw = forward_pass(model, eps, T, U[n], psi0, chi=chi, shape=shape, lam=lam, cross=cross)
         eps = fw.eps
         tau, F = fidelity(fw.psi_T, model.psi_tgt)
         res.JT.append(1.0 - F)

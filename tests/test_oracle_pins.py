@@ -431,3 +431,37 @@ def test_noise_of_white_noise_scales_and_power_law_fit():
     assert n2 / n1 == pytest.approx(2.0, rel=1e-3)
     M = np.array([4, 16, 64, 256])
     assert noise.fit_power_law(M, 3.0 / np.sqrt(M)) == pytest.approx(-0.5, abs=1e-12)
+
+
+# ---------------------------------------------------------------- cross-trajectory update
+def test_cross_overlap_is_the_trace_of_the_two_projectors():
+    """sum_{k,k'} <xi_k|H|psi_k'><psi_k'|xi_k> = tr(H R Pi) with R = sum |psi><psi|, Pi = sum |xi><xi|:
+    fixes which factor carries k and which k' (a transposed operand changes the value)."""
+    rng = np.random.default_rng(11)
+    M, d = 5, 7
+    xi = rng.normal(size=(M, d)) + 1j * rng.normal(size=(M, d))
+    psi = rng.normal(size=(M, d)) + 1j * rng.normal(size=(M, d))
+    H = rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))
+    H = H + H.conj().T
+    R = sum(np.outer(p, p.conj()) for p in psi)
+    Pi = sum(np.outer(x, x.conj()) for x in xi)
+    assert mcwf.cross_overlap(xi, psi, H) == pytest.approx(np.imag(np.trace(H @ R @ Pi)), rel=1e-12)
+    swapped = float(np.sum(np.imag((np.conj(xi) @ (psi @ H.T).T).T * np.conj(np.conj(xi) @ psi.T))))
+    assert abs(swapped - np.imag(np.trace(H @ R @ Pi))) > 1e-3
+
+
+def test_cross_update_equals_independent_for_one_closed_trajectory_at_t0():
+    """M = 1, kappa = 0: <psi(t_0)|xi(t_0)> = <psi(T)|tgt> = conj(tau) (norm 1), so the first
+    interval's cross update equals the independent one; later intervals differ."""
+    m = om.build_model(2, 1, kappa=0.0)
+    nt, T = 30, 3.0
+    eps = si.guess_pulses(2, nt, T, 20.0)
+    S = si.shape_functions(2, nt, T)
+    lam = np.full(2, 10.0)
+    U = si.uniforms(0, 2, 1, 9)
+    a = mcwf.optimize(m, eps, T, U, S, lam, 1, keep=True)
+    b = mcwf.optimize(m, eps, T, U, S, lam, 1, keep=True, update="cross")
+    da, db = a.forward[1].deps, b.forward[1].deps
+    assert np.abs(da[:, 0]).max() > 1e-8
+    np.testing.assert_allclose(db[:, 0], da[:, 0], rtol=1e-10, atol=1e-18)
+    assert np.abs(db - da).max() > 1e-6 * np.abs(da).max()
