@@ -115,6 +115,11 @@ typedef struct {
                                (heuristic); -1 = autotuned: krotov_init times the forward
                                interval kernel for every width that fits (12 launches each on
                                `stream`, guess pulse) and keeps the fastest */
+  int update_rule;          /* 0: independent-trajectory update (Eq. independent_traj_update),
+                               co-states chi_k(T) = tau_k |tgt>; 1: cross-trajectory update
+                               (Eq. cross_traj_update), co-states xi_k(T) = |tgt> and
+                               Delta eps_c = S_c / (M^2 lambda_c) sum_{k,k'}
+                               Im[<xi_k|h_c|psi_k'><psi_k'|xi_k>] (all pairs of trajectories) */
 } kt_config;
 
 /* Create a problem: validate, assemble H_eff in structured form (a1), choose the Chebyshev
@@ -205,12 +210,14 @@ KT_API kt_status krotov_set_uniforms(kt_problem *p, const double *uniforms, int 
  * benchmark.  Turning it on or off clears the totals.  krotov_get_profile returns, per family
  * (KT_PROF_FWD: forward interval kernel incl. the pulse update; KT_PROF_BWD: backward interval
  * kernel incl. checkpoint recompute and the gradient's forward replay; KT_PROF_GRAD: gradient
- * kernel of krotov_gradient), the summed milliseconds and
+ * kernel of krotov_gradient; KT_PROF_CROSS: the cross-trajectory update's kernels), the summed
+ * milliseconds and
  * the launch count since profiling was turned on; arrays of KT_PROF_FAMILIES entries. */
 #define KT_PROF_FWD 0
 #define KT_PROF_BWD 1
 #define KT_PROF_GRAD 2
-#define KT_PROF_FAMILIES 3
+#define KT_PROF_CROSS 3
+#define KT_PROF_FAMILIES 4
 KT_API kt_status krotov_set_profiling(kt_problem *p, int on);
 KT_API kt_status krotov_get_profile(kt_problem *p, double *ms_out, long long *launches_out);
 

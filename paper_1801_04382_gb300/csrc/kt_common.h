@@ -21,10 +21,11 @@
 
 // Kernel families timed by krotov_set_profiling (mirror KT_PROF_* in the public header).
 #ifndef KT_PROF_FAMILIES
-#define KT_PROF_FAMILIES 3
+#define KT_PROF_FAMILIES 4
 #define KT_PROF_FWD 0
 #define KT_PROF_BWD 1
 #define KT_PROF_GRAD 2
+#define KT_PROF_CROSS 3
 #endif
 
 // Device status word values (first error wins); mirror kt_status.

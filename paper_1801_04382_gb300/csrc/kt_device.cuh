@@ -892,14 +892,14 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
   C *A = (C *)sm.bufA;
   C *B = (C *)sm.bufB;
   const uint32_t tile_bytes = (uint32_t)(g.tile_elems * sizeof(C));
-  const bool need_chi = a.update && j < a.nt;
+  const bool need_chi = a.overlap && j < a.nt;
   const C *chi_g = need_chi ? (const C *)a.chi_t + (size_t)tile * g.tile_elems : nullptr;
   // the bulk engine brings psi(t_{j-1}) (and chi(t_j) when there is room) while the tables are built
   if (threadIdx.x == 0) {
     bulk_load(A, psi_in, tile_bytes, &sm.mbar[0]);
     if (need_chi && g.prefetch_chi) bulk_load(sm.bufC, chi_g, tile_bytes, &sm.mbar[1]);
   }
-  build_tables<R>(g, im, ops, sm, sm.eps, a.update != 0);
+  build_tables<R>(g, im, ops, sm, sm.eps, a.overlap != 0);
   Items<EPT, NL> it;
   load_items<EPT, NL>(g, ops, it);
   C acc[EPT];
@@ -1142,7 +1142,7 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
   }
 
   // ---------------- update overlap at t_j: g_c = sum_k Im <chi_k|hc_c|psi_k> ----------------
-  if (!a.update) {
+  if (!a.overlap) {
     if (threadIdx.x == 0 && stored) bulk_store_wait();
     return;
   }

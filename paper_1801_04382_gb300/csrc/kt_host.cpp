@@ -142,7 +142,7 @@ kt_status kt_fail(kt_status s, const char *msg) { return fail(s, "%s", msg); }
 // ---------------------------------------------------------------------------- problem object
 struct kt_problem {
   KtGeom g{};
-  int fp64 = 1, ept = 4;
+  int fp64 = 1, ept = 4, cross = 0;
   size_t esz = 16;
   int nt = 0, M = 0, n_passes = 0, n_passes_alloc = 0, ckpt = 0;
   double T = 0.0;
@@ -173,6 +173,9 @@ struct kt_problem {
 
   int *pass = nullptr;          // device [3]: next uniforms row, rows held, row of the running pass
   double *nu = nullptr;         // device [KT_MAX_CTRL]: pulse noise (krotov_pulse_noise)
+  void *cwork = nullptr;        // cross-trajectory update: [x][k] states and control products
+  double *cpart = nullptr;      // its per-tile partial sums
+  unsigned *ccounter = nullptr;
   double *nu_ref = nullptr;     // device [n_ctrl][nt]: its reference pulse
   double *eps_base = nullptr;   // the pulse buffer eps_old pointed to at init (keys the graphs)
   bool have_fwd = false, have_bwd = false, have_deps = false;
@@ -193,8 +196,8 @@ struct kt_problem {
   std::vector<cudaEvent_t> ev_pool;            // pairs: [2i] before, [2i+1] after launch i
   std::vector<int> ev_family;                  // kernel family of pending pair i
   int ev_used = 0;
-  double prof_ms[KT_PROF_FAMILIES] = {0, 0, 0};
-  long long prof_launches[KT_PROF_FAMILIES] = {0, 0, 0};
+  double prof_ms[KT_PROF_FAMILIES] = {};
+  long long prof_launches[KT_PROF_FAMILIES] = {};
 
   // Krotov iterations (backward sweep + updating forward sweep) captured as CUDA graphs, one per
   // buffer state: the record buffer being written (cur) and which pulse buffer holds the old pulse.
@@ -295,6 +298,7 @@ FwdArgs fwd_args(kt_problem *p, int update) {
   a.nt = p->nt;
   a.update = update;
   a.pass_row = p->pass + 2;
+  a.overlap = update && !p->cross;
   a.eps_old = p->eps_old;
   a.eps_new = p->eps_new;
   a.deps = p->deps;
@@ -361,12 +365,40 @@ const void *chi_at(const kt_problem *p, int j, int seg_a) {
   return state_slot(p, p->seg, j - seg_a);
 }
 
+// Cross-trajectory update of interval j+1 from psi(t_j) and xi(t_j).
+kt_status launch_cross(kt_problem *p, int j, const void *psi, const void *xi, cudaStream_t st) {
+  const KtGeom &g = p->g;
+  const size_t Mp = (size_t)(g.M + 31) / 32 * 32, n = (size_t)g.d * Mp;
+  CrossArgs c{};
+  c.j = j;
+  c.nt = p->nt;
+  c.psi = psi;
+  c.xi = xi;
+  c.X = p->cwork;
+  c.P = (char *)p->cwork + n * p->esz;
+  c.HP = (char *)p->cwork + 2 * n * p->esz;
+  c.partials = p->cpart;
+  c.counter = p->ccounter;
+  c.eps_old = p->eps_old;
+  c.eps_new = p->eps_new;
+  c.deps = p->deps;
+  c.shape = p->shape;
+  c.status = p->status;
+  kt_status s = prof_begin(p, KT_PROF_CROSS, st);
+  if (s != KT_OK) return s;
+  KT_CUDA(kt_launch_cross(p->fp64, g, p->ops, c, st));
+  return prof_end(p, st);
+}
+
 // Launches of one forward sweep: no synchronisation and no change of host state, so that the
 // sequence can be captured into a graph.
 kt_status enqueue_forward(kt_problem *p, int update, cudaStream_t st, bool save_psi) {
   KT_CUDA(kt_launch_init_pass(p->g, p->U, p->pass, p->rstate, p->jcount[p->cur], st));
   FwdArgs a = fwd_args(p, update);
-  if (update) {
+  if (update && p->cross) {
+    kt_status s = launch_cross(p, 0, p->psi_init, ckpt_slot(p, 0), st);
+    if (s != KT_OK) return s;
+  } else if (update) {
     a.j = 0;
     a.psi_in = p->psi_init;
     a.psi_out = nullptr;
@@ -392,6 +424,8 @@ kt_status enqueue_forward(kt_problem *p, int update, cudaStream_t st, bool save_
       if (s != KT_OK) return s;
       KT_CUDA(kt_launch_fwd(p->fp64, p->ept, p->g, p->im_fwd, p->ops, a, st));
       if ((s = prof_end(p, st)) != KT_OK) return s;
+      if (update && p->cross && j < p->nt && (s = launch_cross(p, j, p->psi[j & 1], chi_at(p, j, seg_a), st)) != KT_OK)
+        return s;
       if (save_psi && j < p->nt && j % p->Kg == 0)
         KT_CUDA(cudaMemcpyAsync(state_slot(p, p->psi_ck, j / p->Kg), p->psi[j & 1], p->state_bytes,
                                 cudaMemcpyDeviceToDevice, st));
@@ -525,7 +559,7 @@ kt_status gradient_sweep(kt_problem *p, cudaStream_t st) {
 kt_status enqueue_backward(kt_problem *p, cudaStream_t st) {
   const int prev = 1 - p->cur;
   void *chiT = ckpt_slot(p, p->nt);
-  KT_CUDA(kt_launch_chi_boundary(p->fp64, p->g, p->ops, p->tau, chiT, st));
+  KT_CUDA(kt_launch_chi_boundary(p->fp64, p->g, p->ops, p->cross ? nullptr : p->tau, chiT, st));
   KT_CUDA(kt_launch_cursor_seek(p->g, p->rec_step[prev], p->jcount[prev], p->nt, p->cursor, st));
   const void *in = chiT;
   for (int j = p->nt; j >= 1; --j) {
@@ -702,7 +736,7 @@ struct HostImage {
 
 struct HostPlan {
   KtGeom g{};
-  int fp64 = 1, ept = 4, ckpt = 0;
+  int fp64 = 1, ept = 4, ckpt = 0, cross = 0;
   double e_min = 0, e_max = 0, damping = 0;
   HostImage fwd, bwd;
   std::vector<int> lo_dl, ra_dl, hc_dl;
@@ -824,6 +858,7 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
   if (cfg->prec != KT_FP64 && cfg->prec != KT_FP32_MIXED) return fail(KT_ERR_ARG, "unknown precision");
   if (cfg->ckpt_interval < 0) return fail(KT_ERR_ARG, "ckpt_interval < 0");
   if (cfg->tile_traj < -1) return fail(KT_ERR_ARG, "tile_traj must be -1 (autotuned), 0 (automatic) or a power of two <= 32");
+  if (cfg->update_rule != 0 && cfg->update_rule != 1) return fail(KT_ERR_ARG, "update_rule must be 0 or 1");
   for (int c = 0; c < md->n_ctrl; ++c) {
     if (md->ctrl_node[c] < 0 || md->ctrl_node[c] >= N) return fail(KT_ERR_ARG, "ctrl_node[%d] out of range", c);
     if (!(cfg->lambda_a[c] > 0.0)) return fail(KT_ERR_ARG, "lambda[%d] must be > 0", c);
@@ -921,6 +956,7 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
   if (K < 1 || K > KT_MAX_K) return fail(KT_ERR_UNSUPPORTED, "Chebyshev series needs %d > %d terms (reduce dt)", K, KT_MAX_K);
 
   P.fp64 = cfg->prec == KT_FP64;
+  P.cross = cfg->update_rule;
   P.ckpt = (cfg->ckpt_interval > 0 && cfg->ckpt_interval < nt) ? cfg->ckpt_interval : 0;
   P.e_min = bf.lo;
   P.e_max = bf.hi;
@@ -1168,6 +1204,7 @@ kt_status create_problem(const kt_model_desc *md, const kt_config *cfg, const Ho
   p->g = P.g;
   p->fp64 = P.fp64;
   p->ept = P.ept;
+  p->cross = P.cross;
   p->esz = P.fp64 ? 16 : 8;
   p->nt = nt;
   p->M = M;
@@ -1239,6 +1276,15 @@ kt_status create_problem(const kt_model_desc *md, const kt_config *cfg, const Ho
   TRY(dev_alloc(p, (void **)&p->norm2, Mp * sizeof(double)));
   TRY(dev_alloc(p, (void **)&p->status, sizeof(int)));
   TRY(dev_alloc(p, (void **)&p->pass, 3 * sizeof(int)));
+  if (p->cross && !probe) {
+    TRY(dev_alloc(p, &p->cwork, kt_cross_work_bytes(g, (int)p->esz)));
+    TRY(dev_alloc(p, (void **)&p->cpart, kt_cross_partials(g) * sizeof(double)));
+    TRY(dev_alloc(p, (void **)&p->ccounter, sizeof(unsigned)));
+    if (cudaMemsetAsync(p->ccounter, 0, sizeof(unsigned), st) != cudaSuccess) {
+      krotov_free(p);
+      return fail(KT_ERR_CUDA, "memset failed");
+    }
+  }
   p->eps_base = p->eps_old;
   if (kt_launch_pass_reset(p->pass, p->n_passes, st) != cudaSuccess ||
       cudaMemsetAsync(p->counter, 0, sizeof(unsigned), st) != cudaSuccess ||

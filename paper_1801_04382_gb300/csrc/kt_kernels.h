@@ -8,7 +8,8 @@
 struct FwdArgs {
   int j;                 // interval 1..nt; 0 = prologue (update overlap at t_0 only)
   int nt;
-  int update;            // sequential Krotov update on
+  int update;            // propagate interval j with eps_old + deps (sequential Krotov update)
+  int overlap;           // form the independent-trajectory overlap and Delta eps of interval j+1 here
   const int *pass_row;   // device: uniforms row of the running pass (written by init_pass)
   const void *psi_in;    // tile-layout states at t_{j-1}
   void *psi_out;         // tile-layout states at t_j
@@ -80,6 +81,26 @@ cudaError_t kt_launch_cursor_seek(const KtGeom &g, const int *rec_step, const in
 // cursor[k] = first record of trajectory k with interval >= from (jcount[k] if none)
 cudaError_t kt_launch_cursor_seek_fwd(const KtGeom &g, const int *rec_step, const int *jcount, int from,
                                       int *cursor, cudaStream_t st);
+// Cross-trajectory update of interval j+1 (Eq. cross_traj_update) from psi(t_j), xi(t_j) in tile
+// layout: transposes both to [x][k] (k padded to a multiple of 32), applies the control factors,
+// sums Im[<xi_k|h_c|psi_k'><psi_k'|xi_k>] over all pairs in 32 x 32 pair tiles and, in the last
+// CTA, writes deps / eps_new of interval j+1 (0-based index j).
+struct CrossArgs {
+  int j, nt;
+  const void *psi;       // tile layout, t_j
+  const void *xi;        // tile layout, t_j
+  void *X, *P, *HP;      // [d][Mp], [d][Mp], [n_ctrl][d][Mp] work arrays
+  double *partials;      // [(Mp/32)^2][n_ctrl]
+  unsigned *counter;
+  const double *eps_old;
+  double *eps_new, *deps;
+  const double *shape;
+  int *status;
+};
+size_t kt_cross_work_bytes(const KtGeom &g, int elem_bytes);   // X + P + HP
+size_t kt_cross_partials(const KtGeom &g);                     // entries of CrossArgs::partials
+cudaError_t kt_launch_cross(int fp64, const KtGeom &g, const KtOps &ops, const CrossArgs &a, cudaStream_t st);
+
 cudaError_t kt_launch_chi_grad_boundary(int fp64, const KtGeom &g, const KtOps &ops, const KtCplx *tau,
                                         const double *norm2, const void *psi, void *chi, cudaStream_t st);
 

@@ -55,7 +55,8 @@ __global__ void chi_boundary_kernel(KtGeom g, KtOps ops, const KtCplx *tau, C *c
     if (rem >= g.d * g.T) { chi[e] = mkc((R)0, (R)0); continue; }
     const int x = rem / g.T, t = rem % g.T, k = tile * g.T + t;
     const KtCplx tg = ops.tgt[x];
-    const KtCplx tk = tau[k];
+    // tau NULL: xi_k(T) = |tgt> (cross-trajectory form); padding trajectories stay zero
+    const KtCplx tk = tau ? tau[k] : KtCplx{k < g.M ? 1.0 : 0.0, 0.0};
     chi[e] = mkc((R)(tk.re * tg.re - tk.im * tg.im), (R)(tk.re * tg.im + tk.im * tg.re));
   }
 }

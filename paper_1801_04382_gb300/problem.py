@@ -41,11 +41,13 @@ class Problem:
     [n_ctrl, nt], ``lam`` [n_ctrl], ``uniforms`` [n_passes, M, draws_per_traj].
     ``precision`` is "fp64" or "fp32" (FP32-mixed: complex64 states, FP64 norms and sums).
     ``tile_traj``: 0 automatic, -1 autotuned at init, else trajectories per CTA tile.
+    ``update_rule``: "independent" (Eq. independent_traj_update) or "cross" (Eq. cross_traj_update).
     """
 
     def __init__(self, net: NetworkFactors, T: float, nt: int, M: int, eps_guess, shape, lam, uniforms,
                  precision: str = "fp64", ckpt_interval: int = 0, eps_bound: float = 0.0,
-                 cheb_tol: float = 0.0, tile_traj: int = 0, psi0_batch=None, stream=None):
+                 cheb_tol: float = 0.0, tile_traj: int = 0, psi0_batch=None, stream=None,
+                 update_rule: str = "independent"):
         self._lib = _capi.load()
         self.net = net
         self.T, self.nt, self.M = float(T), int(nt), int(M)
@@ -54,7 +56,7 @@ class Problem:
         if uniforms.ndim != 3 or uniforms.shape[1] != M:
             raise ValueError("uniforms must have shape [n_passes, M, draws_per_traj]")
         keep, md, cfg = _descriptors(net, self.T, self.nt, self.M, eps_guess, shape, lam, uniforms, precision,
-                                     ckpt_interval, eps_bound, cheb_tol, tile_traj, psi0_batch)
+                                     ckpt_interval, eps_bound, cheb_tol, tile_traj, psi0_batch, update_rule)
         handle = ct.c_void_p()
         self._h = None
         _capi.check(self._lib.krotov_init(ct.byref(md), ct.byref(cfg), _stream_handle(stream), ct.byref(handle)),
@@ -170,13 +172,14 @@ class Problem:
         _capi.check(self._lib.krotov_set_profiling(self._h, int(bool(on))), "krotov_set_profiling")
 
     def profile(self):
-        """{family: (total_ms, launches)} for the 'fwd' and 'bwd' interval kernels and the 'grad' kernel
-        since profiling was enabled."""
-        ms = np.zeros(3)
-        n = np.zeros(3, dtype=np.int64)
+        """{family: (total_ms, launches)} for the 'fwd' and 'bwd' interval kernels, the 'grad' kernel and
+        the 'cross' update kernels since profiling was enabled."""
+        ms = np.zeros(4)
+        n = np.zeros(4, dtype=np.int64)
         _capi.check(self._lib.krotov_get_profile(self._h, _ptr(ms), n.ctypes.data_as(ct.POINTER(ct.c_longlong))),
                     "krotov_get_profile")
-        return {"fwd": (float(ms[0]), int(n[0])), "bwd": (float(ms[1]), int(n[1])), "grad": (float(ms[2]), int(n[2]))}
+        return {"fwd": (float(ms[0]), int(n[0])), "bwd": (float(ms[1]), int(n[1])), "grad": (float(ms[2]), int(n[2])),
+                "cross": (float(ms[3]), int(n[3]))}
 
     def get_info(self):
         info = _capi.Info()
@@ -207,7 +210,7 @@ class Batch:
     (C ABI ``kt_batch``).  ``specs`` is a list of dicts of ``Problem`` constructor arguments
     (net, T, nt, M, eps_guess, shape, lam, uniforms and the optional keywords)."""
 
-    _KEYS = ("precision", "ckpt_interval", "eps_bound", "cheb_tol", "tile_traj", "psi0_batch")
+    _KEYS = ("precision", "ckpt_interval", "eps_bound", "cheb_tol", "tile_traj", "psi0_batch", "update_rule")
 
     def __init__(self, specs, stream=None):
         self._lib = _capi.load()
@@ -282,8 +285,11 @@ def bessel_j(alpha: float, n: int) -> np.ndarray:
     return out
 
 
+_UPDATE_RULES = {"independent": 0, "cross": 1}
+
+
 def _descriptors(net, T, nt, M, eps_guess, shape, lam, uniforms, precision="fp64", ckpt_interval=0,
-                 eps_bound=0.0, cheb_tol=0.0, tile_traj=0, psi0_batch=None):
+                 eps_bound=0.0, cheb_tol=0.0, tile_traj=0, psi0_batch=None, update_rule="independent"):
     """kt_model_desc / kt_config for ``net`` (the returned ``keep`` dict owns the host arrays)."""
     uniforms = _c(uniforms)
     keep = {
@@ -307,7 +313,7 @@ def _descriptors(net, T, nt, M, eps_guess, shape, lam, uniforms, precision="fp64
         ckpt_interval=int(ckpt_interval), eps_guess=_ptr(keep["eps"]), shape=_ptr(keep["shape"]),
         lambda_a=_ptr(keep["lam"]), uniforms=_ptr(keep["U"]), n_passes=uniforms.shape[0],
         draws_per_traj=uniforms.shape[2], eps_bound=float(eps_bound), cheb_tol=float(cheb_tol),
-        tile_traj=int(tile_traj))
+        tile_traj=int(tile_traj), update_rule=_UPDATE_RULES[update_rule])
     return keep, md, cfg
 
 

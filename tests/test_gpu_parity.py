@@ -36,11 +36,11 @@ def setup(N, nc, T, nt, M, amp, seed, n_iter, kappa=1.0, random_init=False, draw
                 kappa=kappa)
 
 
-def run_gpu(c, precision="fp64", ckpt=0, tile=0):
+def run_gpu(c, precision="fp64", ckpt=0, tile=0, update_rule="independent"):
     net = cascaded_chain(c["N"], c["nc"], kappa=c["kappa"])
     out = {"F": [], "recs": [], "psiT": [], "eps": [], "deps": []}
     with Problem(net, c["T"], c["nt"], c["M"], c["eps0"], c["S"], c["lam"], c["U"], precision=precision,
-                 ckpt_interval=ckpt, tile_traj=tile, psi0_batch=c["psi0"]) as p:
+                 ckpt_interval=ckpt, tile_traj=tile, psi0_batch=c["psi0"], update_rule=update_rule) as p:
         out["F"].append(p.forward(False))
         out["recs"].append(p.records())
         out["psiT"].append(p.states())
@@ -55,10 +55,11 @@ def run_gpu(c, precision="fp64", ckpt=0, tile=0):
     return out
 
 
-def run_oracle(c):
+def run_oracle(c, update="independent"):
     m = om.build_model(c["N"], c["nc"], kappa=c["kappa"])
     psi0 = c["psi0"] if c["psi0"] is not None else m.psi0
-    return m, mcwf.optimize(m, c["eps0"], c["T"], c["U"], c["S"], c["lam"], c["n_iter"], psi0=psi0, keep=True)
+    return m, mcwf.optimize(m, c["eps0"], c["T"], c["U"], c["S"], c["lam"], c["n_iter"], psi0=psi0, keep=True,
+                            update=update)
 
 
 def compare(c, gpu, res, tol_state, tol_F, tol_deps, tol_s, margin_min=0.0):
@@ -205,4 +206,24 @@ def test_full_size_launch_sampled():
     gpu = run_gpu(c, "fp32", ckpt=3)
     assert gpu["info"].tile_traj == 1 and gpu["info"].n_tiles == wl.M
     _, res = run_oracle(c)
+    compare(c, gpu, res, 3e-5, 1e-5, 1e-4, 1e-4, margin_min=1e-5)
+
+
+def test_cross_trajectory_update_fp64():
+    """Cross-trajectory update (Eq. cross_traj_update), FP64: strong drive, random full-space initial
+    states (several jumps per trajectory), 13 trajectories (one padded 32 x 32 pair tile), two
+    iterations, against the oracle at the FP64 tolerances."""
+    c = setup(2, 1, 12.0, 120, 13, 30.0, 9, 2, random_init=True)
+    gpu = run_gpu(c, update_rule="cross")
+    _, res = run_oracle(c, update="cross")
+    assert sum(len(r) for fw in res.forward for r in fw.records) >= 10
+    compare(c, gpu, res, 1e-10, 1e-10, 1e-10, 1e-9)
+
+
+def test_cross_trajectory_update_fp32_checkpointed():
+    """d = 81, 40 trajectories (pair tiles padded to 64), co-state checkpoints every 9 intervals,
+    FP32-mixed, two iterations."""
+    c = setup(2, 2, 5.0, 100, 40, 30.0, 3, 2, random_init=True)
+    gpu = run_gpu(c, "fp32", ckpt=9, update_rule="cross")
+    _, res = run_oracle(c, update="cross")
     compare(c, gpu, res, 3e-5, 1e-5, 1e-4, 1e-4, margin_min=1e-5)
