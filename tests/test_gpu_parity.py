@@ -221,9 +221,9 @@ def test_cross_trajectory_update_fp64():
 
 
 def test_cross_trajectory_update_fp32_checkpointed():
-    """d = 81, 40 trajectories (pair tiles padded to 64), co-state checkpoints every 9 intervals,
-    FP32-mixed, two iterations."""
-    c = setup(2, 2, 5.0, 100, 40, 30.0, 3, 2, random_init=True)
+    """d = 81, 40 trajectories in the paper's initial state (pair tiles padded to 64), co-state
+    checkpoints every 9 intervals, FP32-mixed, two iterations, at the FP32 tolerances (F 1e-5)."""
+    c = setup(2, 2, 5.0, 100, 40, 30.0, 3, 2, random_init=False)
     gpu = run_gpu(c, "fp32", ckpt=9, update_rule="cross")
     _, res = run_oracle(c, update="cross")
     compare(c, gpu, res, 3e-5, 1e-5, 1e-4, 1e-4, margin_min=1e-5)
