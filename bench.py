@@ -11,6 +11,7 @@ intervals, synthetic seeded inputs (guess pulse sin^2 of amplitude 1, uniforms f
     python bench.py --workload mix64 [--steps K] [--warmup W]
     python bench.py --workload grad729 [--steps K] [--warmup W]
     python bench.py --workload noise
+    python bench.py --workload cross
 
 --workload mix64 times the batch of 64 independent problems of mixed size (2, 3 and 4 nodes,
 d = 81 / 729 / 6561, 128..2048 trajectories, nt 1000 or 2000, kappa in [0.5, 2], FP32-mixed,
@@ -23,6 +24,9 @@ that keeps the states plus the gradient sweep.
 two-node chain (d = 81, nt = 1000, guess amplitude 20 so that a quarter of the trajectories jump,
 FP32-mixed) for M = 8 ... 1024 trajectories, of the pulse and of the accumulated update eps - eps_guess
 (free of the smoothing residual of the smooth guess), and fits nu_i ~ M^b (the paper finds b = -1/2).
+--workload cross runs 20 iterations of the cross-trajectory update (Eq. cross_traj_update) and of
+the independent-trajectory update on the two-node chain (d = 81, M = 128, nt = 1000, FP32-mixed)
+and reports both convergence histories, iterations/s and the pair-sum kernels' time.
 
 N > 1 (under torchrun): every rank optimises an independent problem (its own seed); there is
 no data-path collective ("weak" scaling).  --impl reference times the FP64 CPU oracle on a
@@ -452,6 +456,54 @@ def run_noise(args, rank, world):
     return 0
 
 
+def run_cross(args, rank, world):
+    """Cross-trajectory vs independent-trajectory Krotov on the two-node workload."""
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU (GB300); the CUDA path has no CPU fallback")
+    if rank != 0:
+        return 0
+    from paper_1801_04382_gb300 import Problem, cascaded_chain
+    wl = si.CONFIGS["cfg2_d81"]
+    n_iter = 20
+    net = cascaded_chain(wl.n_nodes, wl.n_cav, wl.delta, wl.g, wl.kappa)
+    eps0 = si.guess_pulses(net.n_ctrl, wl.nt, wl.T, wl.guess_amp)
+    S = si.shape_functions(net.n_ctrl, wl.nt, wl.T)
+    lam = np.full(net.n_ctrl, wl.lam)
+    U = si.uniforms(wl.seed, n_iter + 1, wl.M, wl.draws_per_traj)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for rule in ("independent", "cross"):
+        with Problem(net, wl.T, wl.nt, wl.M, eps0, S, lam, U, precision="fp32", stream=stream,
+                     update_rule=rule) as p:
+            F0 = p.forward(False, stream=stream)
+            p.set_profiling(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            JT, _ = p.update(n_iter, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            prof = p.profile()
+            out[rule] = {"iters_per_s": n_iter * 1000.0 / e0.elapsed_time(e1), "JT_guess": 1.0 - F0,
+                         "JT": [float(x) for x in JT],
+                         "kernels": {f"{k}_kernel": {"launches": n, "total_ms": ms, "avg_ms": ms / max(n, 1)}
+                                     for k, (ms, n) in prof.items() if n > 0}}
+    peaks, _ = measured_peaks()
+    fp32_peak = SM_COUNT * FP32_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    c_ms, c_n = prof["cross"]
+    pair_flops = 8.0 * (1 + net.n_ctrl) * wl.M * wl.M * wl.d        # complex MACs of G and A_c per launch
+    line = {"metric": "cross-trajectory Krotov (Eq. cross_traj_update) vs independent, iterations/s and J_T",
+            "value": out["cross"]["iters_per_s"], "unit": "Krotov iters/s (cross-trajectory update)",
+            "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "dtype": "c64+f64",
+            "config": {"workload": f"{wl.name} (d={wl.d}, M={wl.M}, nt={wl.nt}), {n_iter} iterations, FP32-mixed"},
+            "independent": out["independent"], "cross": out["cross"],
+            "cross_pairs": {"launches": c_n, "avg_ms": c_ms / max(c_n, 1), "flops_per_launch": pair_flops,
+                            "tflops": pair_flops / (c_ms / max(c_n, 1) / 1000.0) / 1e12 if c_n else None,
+                            "fp32_peak_tflops": fp32_peak}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -615,7 +667,7 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-comparison", action="store_true")
-    ap.add_argument("--workload", choices=["cfg5", "mix64", "grad729", "noise"], default="cfg5")
+    ap.add_argument("--workload", choices=["cfg5", "mix64", "grad729", "noise", "cross"], default="cfg5")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -627,6 +679,8 @@ def main():
         return run_grad(args, rank, world)
     if args.workload == "noise":
         return run_noise(args, rank, world)
+    if args.workload == "cross":
+        return run_cross(args, rank, world)
     return run_ours(args, rank, world)
 
 

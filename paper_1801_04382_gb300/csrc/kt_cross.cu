@@ -2,9 +2,10 @@
 //   Delta eps_c = S_c / (M^2 lambda_c) sum_{k,k'} Im[<xi_k|h_c|psi_k'> <psi_k'|xi_k>],
 // all pairs of trajectories at time t_j.  The states are transposed to [x][k] (k padded to a
 // multiple of 32 with zeros), then 32 x 32 pair tiles accumulate G_kk' = <xi_k|psi_k'> and
-// A_c,kk' = <xi_k|h_c|psi_k'> over x (per-thread partial sums over chunks of 8 elements in the
-// state precision, then FP64), and the FP64 pair terms are summed in a fixed order: per CTA by a
-// shuffle / shared-memory tree, across CTAs by the last CTA in tile order.
+// A_c,kk' = <xi_k|h_c|psi_k'> over slices of x (per-thread partial sums over chunks of 8 elements
+// in the state precision, then FP64), the slice sums are added in slice order, and the FP64 pair
+// terms are summed in a fixed order: per CTA by a shuffle / shared-memory tree, across CTAs by the
+// last CTA in tile order.
 #include <algorithm>
 
 #include "kt_device.cuh"
@@ -42,27 +43,27 @@ __global__ void cross_prep_kernel(KtGeom g, KtOps ops, const C *psi, const C *xi
   }
 }
 
-// One CTA per 32 x 32 tile of pairs, one pair per thread: k = 32 blockIdx.y + (tid / 32),
-// k' = 32 blockIdx.x + (tid % 32).
+// Pair tile sums over a slice of the elements: one CTA per 32 x 32 tile of pairs and slice z
+// (blockIdx.z) of the x range, one pair per thread (k = 32 blockIdx.y + tid / 32,
+// k' = 32 blockIdx.x + tid % 32).  Writes the FP64 slice sums of G_kk' and A_c,kk' to buf.
 template <typename C>
-__global__ void __launch_bounds__(1024) cross_pairs_kernel(KtGeom g, CrossArgs a, int Mp) {
+__global__ void __launch_bounds__(1024) cross_slice_kernel(KtGeom g, CrossArgs a, int Mp, int xlen) {
   typedef decltype(C().x) R;
   __shared__ C sX[XC][32], sP[XC][32], sH[KT_MAX_CTRL][XC][32];
-  __shared__ double red[32][KT_MAX_CTRL];
-  __shared__ int last;
   const C *X = (const C *)a.X, *P = (const C *)a.P, *HP = (const C *)a.HP;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int kb = blockIdx.y * 32, kpb = blockIdx.x * 32;
   const int nc = g.n_ctrl;
   const size_t n = (size_t)g.d * Mp;
+  const int xa = blockIdx.z * xlen, xb = min(g.d, xa + xlen);
   double G[2] = {0.0, 0.0};
   double A[KT_MAX_CTRL][2];
 #pragma unroll
   for (int c = 0; c < KT_MAX_CTRL; ++c) A[c][0] = A[c][1] = 0.0;
-  for (int x0 = 0; x0 < g.d; x0 += XC) {
+  for (int x0 = xa; x0 < xb; x0 += XC) {
     if (threadIdx.x < XC * 32) {
       const int xx = threadIdx.x / 32, kk = threadIdx.x % 32, x = x0 + xx;
-      const bool ok = x < g.d;
+      const bool ok = x < xb;
       const size_t r = (size_t)x * Mp;
       sX[xx][kk] = ok ? X[r + kb + kk] : mkc((R)0, (R)0);
       sP[xx][kk] = ok ? P[r + kpb + kk] : mkc((R)0, (R)0);
@@ -98,7 +99,42 @@ __global__ void __launch_bounds__(1024) cross_pairs_kernel(KtGeom g, CrossArgs a
       }
     __syncthreads();
   }
-  // pair term Im[A_c conj(G)], summed over the tile in a fixed order
+  // buf[z][pair][1 + nc] (re, im)
+  const size_t pair = (size_t)(kb + ty) * Mp + kpb + tx;
+  double2 *o = (double2 *)a.pairbuf + ((size_t)blockIdx.z * Mp * Mp + pair) * (1 + nc);
+  o[0] = make_double2(G[0], G[1]);
+#pragma unroll
+  for (int c = 0; c < KT_MAX_CTRL; ++c)
+    if (c < nc) o[1 + c] = make_double2(A[c][0], A[c][1]);
+}
+
+// Slice sums added in slice order, pair term Im[A_c conj(G)], summed over the tile in a fixed
+// order, tile partials summed in tile order by the last CTA, which writes Delta eps of interval j+1.
+__global__ void __launch_bounds__(1024) cross_final_kernel(KtGeom g, CrossArgs a, int Mp, int nz) {
+  __shared__ double red[32][KT_MAX_CTRL];
+  __shared__ int last;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int kb = blockIdx.y * 32, kpb = blockIdx.x * 32;
+  const int nc = g.n_ctrl;
+  const size_t pair = (size_t)(kb + ty) * Mp + kpb + tx;
+  const double2 *buf = (const double2 *)a.pairbuf;
+  double G[2] = {0.0, 0.0};
+  double A[KT_MAX_CTRL][2];
+#pragma unroll
+  for (int c = 0; c < KT_MAX_CTRL; ++c) A[c][0] = A[c][1] = 0.0;
+  for (int z = 0; z < nz; ++z) {
+    const double2 *o = buf + ((size_t)z * Mp * Mp + pair) * (1 + nc);
+    const double2 gz = o[0];
+    G[0] += gz.x;
+    G[1] += gz.y;
+#pragma unroll
+    for (int c = 0; c < KT_MAX_CTRL; ++c)
+      if (c < nc) {
+        const double2 az = o[1 + c];
+        A[c][0] += az.x;
+        A[c][1] += az.y;
+      }
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int c = 0; c < KT_MAX_CTRL; ++c) {
@@ -145,7 +181,12 @@ cudaError_t launch_cross_t(const KtGeom &g, const KtOps &ops, const CrossArgs &a
                                                 (C *)a.HP, Mp);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  cross_pairs_kernel<C><<<dim3(Mp / 32, Mp / 32), 1024, 0, st>>>(g, a, Mp);
+  const int nz = kt_cross_slices(g);
+  const int chunks = (g.d + XC - 1) / XC;
+  const int xlen = (chunks + nz - 1) / nz * XC;
+  cross_slice_kernel<C><<<dim3(Mp / 32, Mp / 32, nz), 1024, 0, st>>>(g, a, Mp, xlen);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  cross_final_kernel<<<dim3(Mp / 32, Mp / 32), 1024, 0, st>>>(g, a, Mp, nz);
   return cudaGetLastError();
 }
 
@@ -154,6 +195,20 @@ cudaError_t launch_cross_t(const KtGeom &g, const KtOps &ops, const CrossArgs &a
 size_t kt_cross_work_bytes(const KtGeom &g, int elem_bytes) {
   const size_t Mp = (size_t)(g.M + 31) / 32 * 32;
   return (size_t)g.d * Mp * (2 + g.n_ctrl) * elem_bytes;
+}
+
+// slices of the x range: about two CTAs per SM in all, at most one chunk of XC elements each
+int kt_cross_slices(const KtGeom &g) {
+  const int t = (g.M + 31) / 32;
+  const int want = (2 * 152 + t * t - 1) / (t * t);
+  const int chunks = (g.d + kt::XC - 1) / kt::XC;
+  const int nz = std::max(1, std::min(want, chunks));
+  return (chunks + (chunks + nz - 1) / nz - 1) / ((chunks + nz - 1) / nz);   // slices actually non-empty
+}
+
+size_t kt_cross_pair_bytes(const KtGeom &g) {
+  const size_t Mp = (size_t)(g.M + 31) / 32 * 32;
+  return (size_t)kt_cross_slices(g) * Mp * Mp * (1 + g.n_ctrl) * 2 * sizeof(double);
 }
 
 size_t kt_cross_partials(const KtGeom &g) {

@@ -175,6 +175,7 @@ struct kt_problem {
   double *nu = nullptr;         // device [KT_MAX_CTRL]: pulse noise (krotov_pulse_noise)
   void *cwork = nullptr;        // cross-trajectory update: [x][k] states and control products
   double *cpart = nullptr;      // its per-tile partial sums
+  double *cpair = nullptr;      // its per-slice pair sums
   unsigned *ccounter = nullptr;
   double *nu_ref = nullptr;     // device [n_ctrl][nt]: its reference pulse
   double *eps_base = nullptr;   // the pulse buffer eps_old pointed to at init (keys the graphs)
@@ -377,6 +378,7 @@ kt_status launch_cross(kt_problem *p, int j, const void *psi, const void *xi, cu
   c.X = p->cwork;
   c.P = (char *)p->cwork + n * p->esz;
   c.HP = (char *)p->cwork + 2 * n * p->esz;
+  c.pairbuf = p->cpair;
   c.partials = p->cpart;
   c.counter = p->ccounter;
   c.eps_old = p->eps_old;
@@ -1279,6 +1281,7 @@ kt_status create_problem(const kt_model_desc *md, const kt_config *cfg, const Ho
   if (p->cross && !probe) {
     TRY(dev_alloc(p, &p->cwork, kt_cross_work_bytes(g, (int)p->esz)));
     TRY(dev_alloc(p, (void **)&p->cpart, kt_cross_partials(g) * sizeof(double)));
+    TRY(dev_alloc(p, (void **)&p->cpair, kt_cross_pair_bytes(g)));
     TRY(dev_alloc(p, (void **)&p->ccounter, sizeof(unsigned)));
     if (cudaMemsetAsync(p->ccounter, 0, sizeof(unsigned), st) != cudaSuccess) {
       krotov_free(p);

@@ -90,6 +90,7 @@ struct CrossArgs {
   const void *psi;       // tile layout, t_j
   const void *xi;        // tile layout, t_j
   void *X, *P, *HP;      // [d][Mp], [d][Mp], [n_ctrl][d][Mp] work arrays
+  double *pairbuf;       // [slices][Mp][Mp][1 + n_ctrl] FP64 complex slice sums of G and A_c
   double *partials;      // [(Mp/32)^2][n_ctrl]
   unsigned *counter;
   const double *eps_old;
@@ -99,6 +100,8 @@ struct CrossArgs {
 };
 size_t kt_cross_work_bytes(const KtGeom &g, int elem_bytes);   // X + P + HP
 size_t kt_cross_partials(const KtGeom &g);                     // entries of CrossArgs::partials
+int kt_cross_slices(const KtGeom &g);                          // slices of the element range
+size_t kt_cross_pair_bytes(const KtGeom &g);                   // CrossArgs::pairbuf
 cudaError_t kt_launch_cross(int fp64, const KtGeom &g, const KtOps &ops, const CrossArgs &a, cudaStream_t st);
 
 cudaError_t kt_launch_chi_grad_boundary(int fp64, const KtGeom &g, const KtOps &ops, const KtCplx *tau,
