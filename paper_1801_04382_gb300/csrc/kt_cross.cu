@@ -2,10 +2,10 @@
 //   Delta eps_c = S_c / (M^2 lambda_c) sum_{k,k'} Im[<xi_k|h_c|psi_k'> <psi_k'|xi_k>],
 // all pairs of trajectories at time t_j.  The states are transposed to [x][k] (k padded to a
 // multiple of 32 with zeros), then 32 x 32 pair tiles accumulate G_kk' = <xi_k|psi_k'> and
-// A_c,kk' = <xi_k|h_c|psi_k'> over slices of x (per-thread partial sums over chunks of 8 elements
-// in the state precision, then FP64), the slice sums are added in slice order, and the FP64 pair
-// terms are summed in a fixed order: per CTA by a shuffle / shared-memory tree, across CTAs by the
-// last CTA in tile order.
+// A_c,kk' = <xi_k|h_c|psi_k'> over slices of x in the state precision (like every per-trajectory
+// partial sum of the FP32-mixed path), the slice sums are added in slice order, and the pair terms
+// Im[A conj(G)] -- the cross-trajectory sum -- are formed and summed in FP64 in a fixed order: per
+// CTA by a shuffle / shared-memory tree, across CTAs by the last CTA in tile order.
 #include <algorithm>
 
 #include "kt_device.cuh"
@@ -45,7 +45,8 @@ __global__ void cross_prep_kernel(KtGeom g, KtOps ops, const C *psi, const C *xi
 
 // Pair tile sums over a slice of the elements: one CTA per 32 x 32 tile of pairs and slice z
 // (blockIdx.z) of the x range, one pair per thread (k = 32 blockIdx.y + tid / 32,
-// k' = 32 blockIdx.x + tid % 32).  Writes the FP64 slice sums of G_kk' and A_c,kk' to buf.
+// k' = 32 blockIdx.x + tid % 32).  Writes the slice sums of G_kk' and A_c,kk' to
+// buf[tile][z][1 + n_ctrl][1024] (coalesced).
 template <typename C>
 __global__ void __launch_bounds__(1024) cross_slice_kernel(KtGeom g, CrossArgs a, int Mp, int xlen) {
   typedef decltype(C().x) R;
@@ -56,10 +57,10 @@ __global__ void __launch_bounds__(1024) cross_slice_kernel(KtGeom g, CrossArgs a
   const int nc = g.n_ctrl;
   const size_t n = (size_t)g.d * Mp;
   const int xa = blockIdx.z * xlen, xb = min(g.d, xa + xlen);
-  double G[2] = {0.0, 0.0};
-  double A[KT_MAX_CTRL][2];
+  R G[2] = {0, 0};
+  R A[KT_MAX_CTRL][2];
 #pragma unroll
-  for (int c = 0; c < KT_MAX_CTRL; ++c) A[c][0] = A[c][1] = 0.0;
+  for (int c = 0; c < KT_MAX_CTRL; ++c) A[c][0] = A[c][1] = 0;
   for (int x0 = xa; x0 < xb; x0 += XC) {
     if (threadIdx.x < XC * 32) {
       const int xx = threadIdx.x / 32, kk = threadIdx.x % 32, x = x0 + xx;
@@ -89,57 +90,57 @@ __global__ void __launch_bounds__(1024) cross_slice_kernel(KtGeom g, CrossArgs a
           ai[c] += xv.x * hv.y - xv.y * hv.x;
         }
     }
-    G[0] += (double)gr;
-    G[1] += (double)gi;
+    G[0] += gr;
+    G[1] += gi;
 #pragma unroll
     for (int c = 0; c < KT_MAX_CTRL; ++c)
       if (c < nc) {
-        A[c][0] += (double)ar[c];
-        A[c][1] += (double)ai[c];
+        A[c][0] += ar[c];
+        A[c][1] += ai[c];
       }
     __syncthreads();
   }
-  // buf[z][pair][1 + nc] (re, im)
-  const size_t pair = (size_t)(kb + ty) * Mp + kpb + tx;
-  double2 *o = (double2 *)a.pairbuf + ((size_t)blockIdx.z * Mp * Mp + pair) * (1 + nc);
-  o[0] = make_double2(G[0], G[1]);
+  const size_t tile = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+  C *o = (C *)a.pairbuf + ((tile * gridDim.z + blockIdx.z) * (1 + nc)) * 1024 + threadIdx.x;
+  o[0] = mkc(G[0], G[1]);
 #pragma unroll
   for (int c = 0; c < KT_MAX_CTRL; ++c)
-    if (c < nc) o[1 + c] = make_double2(A[c][0], A[c][1]);
+    if (c < nc) o[(1 + c) * 1024] = mkc(A[c][0], A[c][1]);
 }
 
 // Slice sums added in slice order, pair term Im[A_c conj(G)], summed over the tile in a fixed
 // order, tile partials summed in tile order by the last CTA, which writes Delta eps of interval j+1.
-__global__ void __launch_bounds__(1024) cross_final_kernel(KtGeom g, CrossArgs a, int Mp, int nz) {
+template <typename C>
+__global__ void __launch_bounds__(1024) cross_final_kernel(KtGeom g, CrossArgs a, int nz) {
+  typedef decltype(C().x) R;
   __shared__ double red[32][KT_MAX_CTRL];
   __shared__ int last;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int kb = blockIdx.y * 32, kpb = blockIdx.x * 32;
   const int nc = g.n_ctrl;
-  const size_t pair = (size_t)(kb + ty) * Mp + kpb + tx;
-  const double2 *buf = (const double2 *)a.pairbuf;
-  double G[2] = {0.0, 0.0};
-  double A[KT_MAX_CTRL][2];
+  const size_t tile0 = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+  const C *buf = (const C *)a.pairbuf + tile0 * nz * (1 + nc) * 1024 + threadIdx.x;
+  R Gr = 0, Gi = 0;
+  R A[KT_MAX_CTRL][2];
 #pragma unroll
-  for (int c = 0; c < KT_MAX_CTRL; ++c) A[c][0] = A[c][1] = 0.0;
+  for (int c = 0; c < KT_MAX_CTRL; ++c) A[c][0] = A[c][1] = 0;
   for (int z = 0; z < nz; ++z) {
-    const double2 *o = buf + ((size_t)z * Mp * Mp + pair) * (1 + nc);
-    const double2 gz = o[0];
-    G[0] += gz.x;
-    G[1] += gz.y;
+    const C *o = buf + (size_t)z * (1 + nc) * 1024;
+    const C gz = o[0];
+    Gr += gz.x;
+    Gi += gz.y;
 #pragma unroll
     for (int c = 0; c < KT_MAX_CTRL; ++c)
       if (c < nc) {
-        const double2 az = o[1 + c];
+        const C az = o[(1 + c) * 1024];
         A[c][0] += az.x;
         A[c][1] += az.y;
       }
   }
+  const double G[2] = {(double)Gr, (double)Gi};
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int c = 0; c < KT_MAX_CTRL; ++c) {
     if (c >= nc) break;
-    double v = A[c][1] * G[0] - A[c][0] * G[1];
+    double v = (double)A[c][1] * G[0] - (double)A[c][0] * G[1];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) red[warp][c] = v;
   }
@@ -186,7 +187,7 @@ cudaError_t launch_cross_t(const KtGeom &g, const KtOps &ops, const CrossArgs &a
   const int xlen = (chunks + nz - 1) / nz * XC;
   cross_slice_kernel<C><<<dim3(Mp / 32, Mp / 32, nz), 1024, 0, st>>>(g, a, Mp, xlen);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  cross_final_kernel<<<dim3(Mp / 32, Mp / 32), 1024, 0, st>>>(g, a, Mp, nz);
+  cross_final_kernel<C><<<dim3(Mp / 32, Mp / 32), 1024, 0, st>>>(g, a, nz);
   return cudaGetLastError();
 }
 
@@ -208,7 +209,7 @@ int kt_cross_slices(const KtGeom &g) {
 
 size_t kt_cross_pair_bytes(const KtGeom &g) {
   const size_t Mp = (size_t)(g.M + 31) / 32 * 32;
-  return (size_t)kt_cross_slices(g) * Mp * Mp * (1 + g.n_ctrl) * 2 * sizeof(double);
+  return (size_t)kt_cross_slices(g) * Mp * Mp * (1 + g.n_ctrl) * 2 * sizeof(double);   // complex128 bound
 }
 
 size_t kt_cross_partials(const KtGeom &g) {
