@@ -120,6 +120,9 @@ typedef struct {
                                (Eq. cross_traj_update), co-states xi_k(T) = |tgt> and
                                Delta eps_c = S_c / (M^2 lambda_c) sum_{k,k'}
                                Im[<xi_k|h_c|psi_k'><psi_k'|xi_k>] (all pairs of trajectories) */
+  int jump_scheme;          /* 0: jump times located by bisection of the norm, several jumps per
+                               interval possible (Sec. 2.1); 1: the first-order scheme of Sec. 2.1,
+                               at most one jump per interval, applied at its end (s* = dt) */
 } kt_config;
 
 /* Create a problem: validate, assemble H_eff in structured form (a1), choose the Chebyshev

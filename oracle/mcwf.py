@@ -65,8 +65,13 @@ class JumpRecordFull(RuntimeError):
 
 
 def _step_with_jumps(prop: StepPropagator, Ls: list, psi: np.ndarray, dt: float, j: int,
-                     state: dict, u_row: np.ndarray, max_jumps: int, records: list) -> np.ndarray:
-    """Advance one trajectory over one interval [t_{j-1}, t_j] with MCWF jumps."""
+                     state: dict, u_row: np.ndarray, max_jumps: int, records: list,
+                     first_order: bool = False) -> np.ndarray:
+    """Advance one trajectory over one interval [t_{j-1}, t_j] with MCWF jumps.
+
+    ``first_order``: the alternative scheme of Sec. 2.1 with at most one jump per time step -- the
+    jump found at the end of the interval is applied there (s* = dt), without locating its time.
+    """
     s0 = 0.0
     start = psi
     while True:
@@ -76,7 +81,7 @@ def _step_with_jumps(prop: StepPropagator, Ls: list, psi: np.ndarray, dt: float,
             state["margin"] = min(state["margin"], n_end - state["r"])
             return phi
         # a jump happens in (s0, dt]: locate it by bisection on the norm
-        lo, hi = 0.0, dt - s0
+        lo, hi = (dt - s0 if first_order else 0.0), dt - s0
         it = 0
         while hi - lo > BISECT_REL_TOL * dt and it < BISECT_MAX_IT:
             mid = 0.5 * (lo + hi)
@@ -114,7 +119,8 @@ def cross_overlap(xi: np.ndarray, psi: np.ndarray, Hc: np.ndarray) -> float:
 
 def forward_pass(model, eps: np.ndarray, T: float, U_pass: np.ndarray, psi0: np.ndarray,
                  chi: np.ndarray = None, shape: np.ndarray = None, lam: np.ndarray = None,
-                 keep_states: bool = False, max_jumps: int = None, cross: bool = False) -> ForwardResult:
+                 keep_states: bool = False, max_jumps: int = None, cross: bool = False,
+                 first_order: bool = False) -> ForwardResult:
     """One forward MCWF sweep over all M trajectories.
 
     Without ``chi`` the pulse ``eps`` is used as is.  With ``chi`` ([nt+1, M, d], the
@@ -159,7 +165,7 @@ def forward_pass(model, eps: np.ndarray, T: float, U_pass: np.ndarray, psi0: np.
                 new[k] = full[k]
             else:
                 new[k] = _step_with_jumps(prop, Ls, psi[k], dt, j, states[k], U_pass[k],
-                                          max_jumps, records[k])
+                                          max_jumps, records[k], first_order)
         psi = new
         if keep_states:
             psi_t.append(psi.copy())
@@ -228,7 +234,8 @@ class OptimizationResult:
 
 
 def optimize(model, eps0: np.ndarray, T: float, U: np.ndarray, shape: np.ndarray, lam: np.ndarray,
-             n_iter: int, psi0=None, keep: bool = False, update: str = "independent") -> OptimizationResult:
+             n_iter: int, psi0=None, keep: bool = False, update: str = "independent",
+             first_order: bool = False) -> OptimizationResult:
     """Trajectory Krotov: guess pass 0, then n_iter x [backward; updating forward].
 
     Forward pass p reads uniforms U[p]; iteration n uses the records of pass n-1.  ``update``:
@@ -239,7 +246,7 @@ def optimize(model, eps0: np.ndarray, T: float, U: np.ndarray, shape: np.ndarray
     psi0 = model.psi0 if psi0 is None else psi0
     nt = eps0.shape[1]
     dt = T / nt
-    fw = forward_pass(model, eps0, T, U[0], psi0)
+    fw = forward_pass(model, eps0, T, U[0], psi0, first_order=first_order)
     tau, F = fidelity(fw.psi_T, model.psi_tgt)
     res = OptimizationResult(eps=eps0.copy(), JT=[1.0 - F])
     if keep:
@@ -248,7 +255,8 @@ def optimize(model, eps0: np.ndarray, T: float, U: np.ndarray, shape: np.ndarray
     for n in range(1, n_iter + 1):
         boundary = np.ones_like(tau) if cross else tau
         chi = backward_pass(model, eps, T, boundary[:, None] * model.psi_tgt[None, :], fw.records)
-        fw = forward_pass(model, eps, T, U[n], psi0, chi=chi, shape=shape, lam=lam, cross=cross)
+        fw = forward_pass(model, eps, T, U[n], psi0, chi=chi, shape=shape, lam=lam, cross=cross,
+                          first_order=first_order)
         eps = fw.eps
         tau, F = fidelity(fw.psi_T, model.psi_tgt)
         res.JT.append(1.0 - F)

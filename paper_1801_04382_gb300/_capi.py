@@ -38,7 +38,7 @@ class Config(ct.Structure):
         ("ckpt_interval", ct.c_int), ("eps_guess", dp), ("shape", dp), ("lambda_a", dp),
         ("uniforms", dp), ("n_passes", ct.c_int), ("draws_per_traj", ct.c_int),
         ("eps_bound", ct.c_double), ("cheb_tol", ct.c_double), ("tile_traj", ct.c_int),
-        ("update_rule", ct.c_int),
+        ("update_rule", ct.c_int), ("jump_scheme", ct.c_int),
     ]
 
 

@@ -85,6 +85,7 @@ struct KtGeom {
   int K;                             // Chebyshev terms of a full step
   int max_jumps, draws;              // jump cap and uniforms per trajectory and pass
   int prefetch_chi;                  // forward kernel keeps a third tile buffer for chi(t_j)
+  int first_order;                   // jump scheme: 0 jump times by bisection, 1 at most one jump per interval, at its end
   int stride[KT_MAX_NODES];          // element stride of node i (n_loc^(N-1-i))
   int ctrl_node[KT_MAX_CTRL];
   double lam[KT_MAX_CTRL];

@@ -960,7 +960,8 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
         sm.tin[TI_ACT * g.T + t] = act;
         sm.tsc[TS_R * g.T + t] = r;
         sm.tsc[TS_S0 * g.T + t] = 0.0;
-        sm.tsc[TS_LO * g.T + t] = 0.0;
+        // first-order scheme: the bracket starts closed at dt, the jump is applied at the end
+        sm.tsc[TS_LO * g.T + t] = g.first_order ? g.dt : 0.0;
         sm.tsc[TS_HI * g.T + t] = g.dt;
         sm.tin[TI_CH * g.T + t] = 0;                     // bisection iteration counter
         if (act) atomicAdd(&sm.flag[0], 1);
@@ -1078,8 +1079,8 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
           if (sm.tsc[TS_NRM * g.T + t] > sm.tsc[TS_R * g.T + t]) done = 1;
           else {
             atomicAdd(&sm.flag[2], 1);      // another jump inside the remainder
-            sm.tsc[TS_LO * g.T + t] = 0.0;
             sm.tsc[TS_HI * g.T + t] = g.dt - sm.tsc[TS_S0 * g.T + t];
+            sm.tsc[TS_LO * g.T + t] = g.first_order ? sm.tsc[TS_HI * g.T + t] : 0.0;
             sm.tin[TI_CH * g.T + t] = 0;
           }
         }

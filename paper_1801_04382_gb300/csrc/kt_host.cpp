@@ -861,6 +861,7 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
   if (cfg->ckpt_interval < 0) return fail(KT_ERR_ARG, "ckpt_interval < 0");
   if (cfg->tile_traj < -1) return fail(KT_ERR_ARG, "tile_traj must be -1 (autotuned), 0 (automatic) or a power of two <= 32");
   if (cfg->update_rule != 0 && cfg->update_rule != 1) return fail(KT_ERR_ARG, "update_rule must be 0 or 1");
+  if (cfg->jump_scheme != 0 && cfg->jump_scheme != 1) return fail(KT_ERR_ARG, "jump_scheme must be 0 or 1");
   for (int c = 0; c < md->n_ctrl; ++c) {
     if (md->ctrl_node[c] < 0 || md->ctrl_node[c] >= N) return fail(KT_ERR_ARG, "ctrl_node[%d] out of range", c);
     if (!(cfg->lambda_a[c] > 0.0)) return fail(KT_ERR_ARG, "lambda[%d] must be > 0", c);
@@ -974,6 +975,7 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
   g.n_pairs = (int)gf.pairs.size();
   g.K = K;
   g.max_jumps = (cfg->draws_per_traj - 1) / 2;   // 0: any jump is reported as KT_ERR_RECORD_FULL
+  g.first_order = cfg->jump_scheme;
   g.draws = cfg->draws_per_traj;
   g.dt = dt;
   g.eps_bound = E;

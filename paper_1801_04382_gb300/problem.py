@@ -42,12 +42,13 @@ class Problem:
     ``precision`` is "fp64" or "fp32" (FP32-mixed: complex64 states, FP64 norms and sums).
     ``tile_traj``: 0 automatic, -1 autotuned at init, else trajectories per CTA tile.
     ``update_rule``: "independent" (Eq. independent_traj_update) or "cross" (Eq. cross_traj_update).
+    ``jump_scheme``: "bisection" (exact jump times) or "first_order" (at most one jump per interval).
     """
 
     def __init__(self, net: NetworkFactors, T: float, nt: int, M: int, eps_guess, shape, lam, uniforms,
                  precision: str = "fp64", ckpt_interval: int = 0, eps_bound: float = 0.0,
                  cheb_tol: float = 0.0, tile_traj: int = 0, psi0_batch=None, stream=None,
-                 update_rule: str = "independent"):
+                 update_rule: str = "independent", jump_scheme: str = "bisection"):
         self._lib = _capi.load()
         self.net = net
         self.T, self.nt, self.M = float(T), int(nt), int(M)
@@ -56,7 +57,8 @@ class Problem:
         if uniforms.ndim != 3 or uniforms.shape[1] != M:
             raise ValueError("uniforms must have shape [n_passes, M, draws_per_traj]")
         keep, md, cfg = _descriptors(net, self.T, self.nt, self.M, eps_guess, shape, lam, uniforms, precision,
-                                     ckpt_interval, eps_bound, cheb_tol, tile_traj, psi0_batch, update_rule)
+                                     ckpt_interval, eps_bound, cheb_tol, tile_traj, psi0_batch, update_rule,
+                                     jump_scheme)
         handle = ct.c_void_p()
         self._h = None
         _capi.check(self._lib.krotov_init(ct.byref(md), ct.byref(cfg), _stream_handle(stream), ct.byref(handle)),
@@ -210,7 +212,8 @@ class Batch:
     (C ABI ``kt_batch``).  ``specs`` is a list of dicts of ``Problem`` constructor arguments
     (net, T, nt, M, eps_guess, shape, lam, uniforms and the optional keywords)."""
 
-    _KEYS = ("precision", "ckpt_interval", "eps_bound", "cheb_tol", "tile_traj", "psi0_batch", "update_rule")
+    _KEYS = ("precision", "ckpt_interval", "eps_bound", "cheb_tol", "tile_traj", "psi0_batch", "update_rule",
+             "jump_scheme")
 
     def __init__(self, specs, stream=None):
         self._lib = _capi.load()
@@ -286,10 +289,12 @@ def bessel_j(alpha: float, n: int) -> np.ndarray:
 
 
 _UPDATE_RULES = {"independent": 0, "cross": 1}
+_JUMP_SCHEMES = {"bisection": 0, "first_order": 1}
 
 
 def _descriptors(net, T, nt, M, eps_guess, shape, lam, uniforms, precision="fp64", ckpt_interval=0,
-                 eps_bound=0.0, cheb_tol=0.0, tile_traj=0, psi0_batch=None, update_rule="independent"):
+                 eps_bound=0.0, cheb_tol=0.0, tile_traj=0, psi0_batch=None, update_rule="independent",
+                 jump_scheme="bisection"):
     """kt_model_desc / kt_config for ``net`` (the returned ``keep`` dict owns the host arrays)."""
     uniforms = _c(uniforms)
     keep = {
@@ -313,7 +318,7 @@ def _descriptors(net, T, nt, M, eps_guess, shape, lam, uniforms, precision="fp64
         ckpt_interval=int(ckpt_interval), eps_guess=_ptr(keep["eps"]), shape=_ptr(keep["shape"]),
         lambda_a=_ptr(keep["lam"]), uniforms=_ptr(keep["U"]), n_passes=uniforms.shape[0],
         draws_per_traj=uniforms.shape[2], eps_bound=float(eps_bound), cheb_tol=float(cheb_tol),
-        tile_traj=int(tile_traj), update_rule=_UPDATE_RULES[update_rule])
+        tile_traj=int(tile_traj), update_rule=_UPDATE_RULES[update_rule], jump_scheme=_JUMP_SCHEMES[jump_scheme])
     return keep, md, cfg
 
 

@@ -36,11 +36,12 @@ def setup(N, nc, T, nt, M, amp, seed, n_iter, kappa=1.0, random_init=False, draw
                 kappa=kappa)
 
 
-def run_gpu(c, precision="fp64", ckpt=0, tile=0, update_rule="independent"):
+def run_gpu(c, precision="fp64", ckpt=0, tile=0, update_rule="independent", jump_scheme="bisection"):
     net = cascaded_chain(c["N"], c["nc"], kappa=c["kappa"])
     out = {"F": [], "recs": [], "psiT": [], "eps": [], "deps": []}
     with Problem(net, c["T"], c["nt"], c["M"], c["eps0"], c["S"], c["lam"], c["U"], precision=precision,
-                 ckpt_interval=ckpt, tile_traj=tile, psi0_batch=c["psi0"], update_rule=update_rule) as p:
+                 ckpt_interval=ckpt, tile_traj=tile, psi0_batch=c["psi0"], update_rule=update_rule,
+                 jump_scheme=jump_scheme) as p:
         out["F"].append(p.forward(False))
         out["recs"].append(p.records())
         out["psiT"].append(p.states())
@@ -55,11 +56,11 @@ def run_gpu(c, precision="fp64", ckpt=0, tile=0, update_rule="independent"):
     return out
 
 
-def run_oracle(c, update="independent"):
+def run_oracle(c, update="independent", first_order=False):
     m = om.build_model(c["N"], c["nc"], kappa=c["kappa"])
     psi0 = c["psi0"] if c["psi0"] is not None else m.psi0
     return m, mcwf.optimize(m, c["eps0"], c["T"], c["U"], c["S"], c["lam"], c["n_iter"], psi0=psi0, keep=True,
-                            update=update)
+                            update=update, first_order=first_order)
 
 
 def compare(c, gpu, res, tol_state, tol_F, tol_deps, tol_s, margin_min=0.0):
@@ -227,3 +228,21 @@ def test_cross_trajectory_update_fp32_checkpointed():
     gpu = run_gpu(c, "fp32", ckpt=9, update_rule="cross")
     _, res = run_oracle(c, update="cross")
     compare(c, gpu, res, 3e-5, 1e-5, 1e-4, 1e-4, margin_min=1e-5)
+
+
+def test_first_order_jump_scheme_fp64():
+    """First-order jump scheme (Sec. 2.1): at most one jump per interval, applied at its end
+    (s* = dt).  Strong drive and random full-space initial states, two iterations, FP64."""
+    c = setup(2, 1, 12.0, 120, 13, 30.0, 9, 2, random_init=True)
+    gpu = run_gpu(c, jump_scheme="first_order")
+    _, res = run_oracle(c, first_order=True)
+    dt = c["T"] / c["nt"]
+    n = 0
+    for recs in gpu["recs"]:
+        for rk in recs:
+            steps = [r[0] for r in rk]
+            assert len(steps) == len(set(steps))
+            assert all(r[1] == dt for r in rk)
+            n += len(rk)
+    assert n >= 10
+    compare(c, gpu, res, 1e-10, 1e-10, 1e-10, 1e-9)

@@ -465,3 +465,31 @@ def test_cross_update_equals_independent_for_one_closed_trajectory_at_t0():
     assert np.abs(da[:, 0]).max() > 1e-8
     np.testing.assert_allclose(db[:, 0], da[:, 0], rtol=1e-10, atol=1e-18)
     assert np.abs(db - da).max() > 1e-6 * np.abs(da).max()
+
+
+# ---------------------------------------------------------------- first-order jump scheme
+def test_first_order_jump_lands_at_the_end_of_the_interval_containing_the_exact_time():
+    """Same decaying cavity as the closed-form pin: with at most one jump per step, decided at the
+    end of the step, the jump of trajectory k is recorded in interval ceil(t*/dt) at s* = dt, with
+    c = 1/||L psi(t_j)|| = 1/sqrt(2 kappa exp(-2 kappa t_j))."""
+    kappa = 0.8
+    m = om.build_model(1, 1, g=0.0, kappa=kappa)
+    psi0 = np.zeros(m.d, dtype=complex)
+    psi0[om.basis_index(1, [om.G], [1])] = 1.0
+    T, nt, M = 4.0, 40, 16
+    U = si.uniforms(11, 1, M, 3)
+    fw = mcwf.forward_pass(m, np.zeros((1, nt)), T, U[0], psi0, first_order=True)
+    dt = T / nt
+    n_jumped = 0
+    for k in range(M):
+        t_star = -math.log(U[0, k, 0]) / (2 * kappa)
+        j = math.ceil(t_star / dt)
+        if j <= nt:
+            n_jumped += 1
+            assert len(fw.records[k]) == 1
+            rec = fw.records[k][0]
+            assert rec.step == j and rec.s == dt
+            assert rec.c == pytest.approx(1.0 / math.sqrt(2 * kappa * math.exp(-2 * kappa * j * dt)), rel=1e-9)
+        else:
+            assert len(fw.records[k]) == 0
+    assert n_jumped >= 5
