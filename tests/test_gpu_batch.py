@@ -22,25 +22,27 @@ from paper_1801_04382_gb300 import Batch, Problem, cascaded_chain
 pytestmark = pytest.mark.gpu
 
 
-def spec(N, nc, T, nt, M, amp, seed, n_passes, kappa=1.0, precision="fp64", ckpt=0, random_init=True, tile=0):
+def spec(N, nc, T, nt, M, amp, seed, n_passes, kappa=1.0, precision="fp64", ckpt=0, random_init=True, tile=0,
+         update_rule="independent", jump_scheme="bisection"):
     draws = 1 + 2 * N * (1 + nc)
     d = (3 * (nc + 1)) ** N
     return dict(net=cascaded_chain(N, nc, kappa=kappa), T=T, nt=nt, M=M,
                 eps_guess=si.guess_pulses(N, nt, T, amp), shape=si.shape_functions(N, nt, T),
                 lam=np.full(N, 10.0), uniforms=si.uniforms(seed, n_passes, M, draws), precision=precision,
-                ckpt_interval=ckpt, tile_traj=tile,
+                ckpt_interval=ckpt, tile_traj=tile, update_rule=update_rule, jump_scheme=jump_scheme,
                 psi0_batch=si.random_states(seed + 100, M, d) if random_init else None)
 
 
 def problem(sp):
-    kw = {k: sp[k] for k in ("precision", "ckpt_interval", "tile_traj", "psi0_batch")}
+    kw = {k: sp[k] for k in ("precision", "ckpt_interval", "tile_traj", "psi0_batch", "update_rule", "jump_scheme")}
     return Problem(sp["net"], sp["T"], sp["nt"], sp["M"], sp["eps_guess"], sp["shape"], sp["lam"], sp["uniforms"],
                    **kw)
 
 
-@pytest.mark.parametrize("ckpt", [0, 7])
-def test_graph_iterations_match_sweeps(ckpt):
-    sp = spec(2, 1, 12.0, 120, 13, 30.0, 9, 4, ckpt=ckpt)
+@pytest.mark.parametrize("ckpt,rule,scheme", [(0, "independent", "bisection"), (7, "independent", "bisection"),
+                                              (7, "cross", "bisection"), (0, "independent", "first_order")])
+def test_graph_iterations_match_sweeps(ckpt, rule, scheme):
+    sp = spec(2, 1, 12.0, 120, 13, 30.0, 9, 4, ckpt=ckpt, update_rule=rule, jump_scheme=scheme)
     with problem(sp) as a, problem(sp) as b:
         a.forward(False)
         F_a, eps_a, rec_a = [], [], []
@@ -72,7 +74,8 @@ def mixed_specs():
     return [spec(2, 1, 12.0, 120, 13, 30.0, 9, 3, kappa=1.0),
             spec(2, 2, 5.0, 100, 40, 30.0, 3, 3, kappa=0.7, precision="fp32", ckpt=9),
             spec(3, 2, 0.5, 20, 6, 30.0, 2, 3, kappa=1.6, precision="fp32"),
-            spec(2, 2, 5.0, 100, 7, 30.0, 5, 3, kappa=1.9, random_init=False)]
+            spec(2, 2, 5.0, 100, 7, 30.0, 5, 3, kappa=1.9, random_init=False),
+            spec(2, 1, 12.0, 120, 9, 30.0, 4, 3, kappa=1.2, update_rule="cross", jump_scheme="first_order")]
 
 
 def test_batch_matches_problems_alone():
