@@ -64,3 +64,28 @@ def test_average_row_nonzeros_of_four_node_chain():
     """d = 6561 chain: 1 (diagonal) + 4 x 10/9 node off-diagonals + 6 pairs x 4/9 = 8.11."""
     net = pm.cascaded_chain(4, 2)
     assert bench.avg_row_nonzeros(net) == pytest.approx(1 + 4 * 10 / 9 + 6 * 4 / 9)
+
+
+def test_batch_mix_is_seeded_and_fits_its_memory_budget():
+    """The 64-problem mix: deterministic for a seed, sizes in the stated ranges, and the co-state
+    checkpointing chosen so that the batch holds at most the budget."""
+    import synth_inputs as si
+    a, b = si.batch_mix(seed=3), si.batch_mix(seed=3)
+    assert a == b and len(a) == 64
+    for w in a:
+        assert w.n_nodes in (2, 3, 4) and w.n_cav == 2
+        assert w.M in (128, 256, 512, 1024, 2048) and w.nt in (1000, 2000)
+        assert 0.5 <= w.kappa <= 2.0 and w.precision == "fp32"
+    held = sum(si.costate_bytes(w) + 4 * w.M * w.d * 8 for w in a)
+    assert held <= 150e9
+    assert any(w.ckpt_interval > 0 for w in a) and any(w.ckpt_interval == 0 for w in a)
+    small = si.batch_mix(seed=3, hbm_budget=1e15)
+    assert all(w.ckpt_interval == 0 for w in small)
+
+
+def test_costate_bytes_counts_checkpoints_and_segment():
+    import synth_inputs as si
+    w = si.CONFIGS["cfg5_d6561"]
+    state = w.M * w.d * 8
+    assert si.costate_bytes(w) == (5000 // 100 + 1 + 100 + 1) * state
+    assert si.costate_bytes(w.with_(ckpt_interval=0)) == 5001 * state
