@@ -643,14 +643,43 @@ __device__ __forceinline__ typename C2<R>::T lind_item(const KtGeom &g, const Kt
 // every coupling inside a thread's fiber (which runs over the last node) has a position known
 // at compile time: the fiber's own T_k stays in registers and the last node's factor and the
 // pair hops that raise or lower its photon number become register-indexed FMAs.
+// The fiber's rows of the other nodes' factors (at most three other nodes on the fiber path: the
+// fiber of the last node holds n_loc^(N-1) <= 736 threads' worth of the tile), loaded once per
+// Chebyshev series: element offsets of the real and imaginary slot and their coefficients.
+template <typename R>
+struct RowCache {
+  int off0[3], off1[3];
+  R a[3], b[3];
+};
+
+template <typename R, int NL>
+__device__ __forceinline__ void load_rows(const KtGeom &g, const Smem &sm, uint32_t fdig, RowCache<R> &rc) {
+  typedef typename C2<R>::T C;
+  const C *lv = (const C *)sm.loc_val;
+  const int last = g.n_nodes - 1;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    rc.off0[i] = rc.off1[i] = 0;
+    rc.a[i] = rc.b[i] = (R)0;
+    if (i < last) {
+      const int e0 = (i * NL + ((fdig >> (4 * i)) & 15)) * 2;
+      rc.off0[i] = sm.loc_off[e0];
+      rc.off1[i] = sm.loc_off[e0 + 1];
+      rc.a[i] = lv[e0].x;
+      rc.b[i] = lv[e0 + 1].y;
+    }
+  }
+}
+
 // RI: the couplings are purely real or imaginary by class (host check: node rows hold
 // [real, imaginary] slots, last-node cavity real and drive imaginary, pair coefficients imaginary,
-// ladder values real), applied with two FMAs each.
-template <typename R, int NC, int TT, bool RI>
+// ladder values real), applied with two FMAs each.  CACHE: the other nodes' rows come from rc
+// (registers) instead of the shared tables.
+template <typename R, int NC, int TT, bool RI, bool CACHE>
 __device__ __forceinline__ void apply_acs(const KtGeom &g, const KtGenImage &im, const Smem &sm,
                                           const typename C2<R>::T *__restrict__ v, int base, uint32_t fdig,
                                           typename C2<R>::T Df, const typename C2<R>::T (&vk)[3 * (NC + 1)],
-                                          typename C2<R>::T (&out)[3 * (NC + 1)]) {
+                                          typename C2<R>::T (&out)[3 * (NC + 1)], const RowCache<R> &rc) {
   typedef typename C2<R>::T C;
   constexpr int NP = NC + 1, NL = 3 * NP;
   const C *lv = (const C *)sm.loc_val;
@@ -691,7 +720,7 @@ __device__ __forceinline__ void apply_acs(const KtGeom &g, const KtGenImage &im,
     }
   }
   // other nodes: one row per fiber, each entry one neighbouring fiber
-  if constexpr (RI) {
+  if constexpr (RI && !CACHE) {
     for (int i = 0; i < last; ++i) {
       const int e0 = (i * NL + ((fdig >> (4 * i)) & 15)) * 2;
       const int off0 = sm.loc_off[e0], off1 = sm.loc_off[e0 + 1];
@@ -704,6 +733,18 @@ __device__ __forceinline__ void apply_acs(const KtGeom &g, const KtGenImage &im,
         const R b = lv[e0 + 1].y;
 #pragma unroll
         for (int q = 0; q < NL; ++q) out[q] = ifma(b, v[base + off1 + q * T], out[q]);
+      }
+    }
+  } else if constexpr (RI) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      if (rc.off0[i]) {
+#pragma unroll
+        for (int q = 0; q < NL; ++q) out[q] = rfma(rc.a[i], v[base + rc.off0[i] + q * T], out[q]);
+      }
+      if (rc.off1[i]) {
+#pragma unroll
+        for (int q = 0; q < NL; ++q) out[q] = ifma(rc.b[i], v[base + rc.off1[i] + q * T], out[q]);
       }
     }
   } else {
@@ -782,7 +823,7 @@ __device__ __forceinline__ void apply_acs(const KtGeom &g, const KtGenImage &im,
   }
 }
 
-template <typename R, int NC, int TT, bool RI, class IT>
+template <typename R, int NC, int TT, bool RI, bool CACHE, class IT>
 __device__ void cheb_run_acs(const KtGeom &g, const KtGenImage &im, const Smem &sm, const IT &it,
                              int K, typename C2<R>::T (&acc)[3 * (NC + 1)]) {
   typedef typename C2<R>::T C;
@@ -803,6 +844,10 @@ __device__ void cheb_run_acs(const KtGeom &g, const KtGenImage &im, const Smem &
     Df.x += v.x;
     Df.y += v.y;
   }
+  RowCache<R> rc;
+  if constexpr (RI && CACHE) {
+    if (ok) load_rows<R, NL>(g, sm, fdig, rc);
+  }
   C vk[NL];
   const C c0 = cf[tau];
 #pragma unroll
@@ -813,7 +858,7 @@ __device__ void cheb_run_acs(const KtGeom &g, const KtGenImage &im, const Smem &
   if (K == 1) { __syncthreads(); return; }
   C t[NL];
   if (ok) {
-    apply_acs<R, NC, TT, RI>(g, im, sm, A, base, fdig, Df, vk, t);
+    apply_acs<R, NC, TT, RI, CACHE>(g, im, sm, A, base, fdig, Df, vk, t, rc);
     const C c1 = cf[T + tau];
 #pragma unroll
     for (int q = 0; q < NL; ++q) {
@@ -828,7 +873,7 @@ __device__ void cheb_run_acs(const KtGeom &g, const KtGenImage &im, const Smem &
   for (int k = 2; k < K; ++k) {
     if (ok) {
       const C a = cf[k * T + tau];
-      apply_acs<R, NC, TT, RI>(g, im, sm, Q, base, fdig, Df, vk, t);
+      apply_acs<R, NC, TT, RI, CACHE>(g, im, sm, Q, base, fdig, Df, vk, t, rc);
 #pragma unroll
       for (int q = 0; q < NL; ++q) {
         const C old = P[base + q * T];
@@ -843,11 +888,11 @@ __device__ void cheb_run_acs(const KtGeom &g, const KtGenImage &im, const Smem &
   }
 }
 
-template <typename R, int EPT, int NL, int ACS, class IT>
+template <typename R, int EPT, int NL, int ACS, bool CACHE, class IT>
 __device__ __forceinline__ void cheb_dispatch(const KtGeom &g, const KtGenImage &im, const Smem &sm,
                                               const IT &it, int K, typename C2<R>::T (&acc)[EPT]) {
   // ACS: 1 cavity structure, 2 the same with T = 1, 3 with real / imaginary couplings, 4 both
-  if constexpr (ACS) cheb_run_acs<R, NL / 3 - 1, (ACS == 2 || ACS == 4) ? 1 : 0, (ACS >= 3)>(g, im, sm, it, K, acc);
+  if constexpr (ACS) cheb_run_acs<R, NL / 3 - 1, (ACS == 2 || ACS == 4) ? 1 : 0, (ACS >= 3), CACHE>(g, im, sm, it, K, acc);
   else if constexpr (NL > 0) cheb_run_fiber<R, NL>(g, im, sm, it, K, acc);
   else cheb_run<R, EPT>(g, im, sm, it, K, acc);
 }
@@ -861,7 +906,7 @@ __device__ __forceinline__ void cheb_dispatch(const KtGeom &g, const KtGenImage 
 enum { PH_MAIN = 0, PH_BISECT, PH_SSTAR, PH_REST, PH_DONE };
 
 template <typename R, int EPT, int NL, int ACS>
-__global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) fwd_kernel(KtGeom g, KtGenImage im, KtOps ops, FwdArgs a) {
+__global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) fwd_kernel(KtGeom g, KtGenImage im, KtOps ops, FwdArgs a) {
   typedef typename C2<R>::T C;
   extern __shared__ __align__(16) char smem_raw[];
   Smem sm;
@@ -943,7 +988,7 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
     }
     if (phase != PH_MAIN) load_tile<R, EPT>(g, it, psi_out, A);   // the main round's tile came by bulk copy
     __syncthreads();
-    cheb_dispatch<R, EPT, NL, ACS>(g, im, sm, it, g.K, acc);
+    cheb_dispatch<R, EPT, NL, ACS, true>(g, im, sm, it, g.K, acc);   // rows cached: measured faster here
     norms<R, EPT>(g, sm, it, acc);
 
     // ---- consume the result
@@ -1262,7 +1307,7 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
 // the forward generator's, pieces run forwards (s_1, s_2 - s_1, ..., dt - s_m) and each is
 // followed by c L of its jump -- the frozen-record map U_j of the gradient (no bisection).
 template <typename R, int EPT, int NL, int ACS>
-__global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) bwd_kernel(KtGeom g, KtGenImage im, KtOps ops, BwdArgs a) {
+__global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) bwd_kernel(KtGeom g, KtGenImage im, KtOps ops, BwdArgs a) {
   typedef typename C2<R>::T C;
   extern __shared__ __align__(16) char smem_raw[];
   Smem sm;
@@ -1341,7 +1386,7 @@ __global__ void __launch_bounds__(NL > 0 ? 768 : (sizeof(R) == 8 ? 512 : 1024)) 
     for (int q = 0; q < EPT; ++q)
       if (it.ok(q)) A[it.item(q)] = B[it.item(q)];
     __syncthreads();
-    cheb_dispatch<R, EPT, NL, ACS>(g, im, sm, it, g.K, acc);
+    cheb_dispatch<R, EPT, NL, ACS, false>(g, im, sm, it, g.K, acc);   // rows from the tables: measured faster here
     if (rnd == rounds) break;
 #pragma unroll
     for (int q = 0; q < EPT; ++q)

@@ -169,10 +169,12 @@ __device__ void aug_run_acs(const KtGeom &g, const KtGenImage &im, const Smem &s
   }
   if (K < 2) { __syncthreads(); return; }
   C v[NL], t[NL], h[NL];
+  RowCache<R> rc;
+  if (ok) load_rows<R, NL>(g, sm, fdig, rc);
   if (ok) {
 #pragma unroll
     for (int q = 0; q < NL; ++q) v[q] = A[base + q];
-    apply_acs<R, NC, 1, true>(g, im, sm, A, base, fdig, Df, v, t);      // z_1 = Ghat z_0
+    apply_acs<R, NC, 1, true, true>(g, im, sm, A, base, fdig, Df, v, t, rc);      // z_1 = Ghat z_0
     hc_fiber<R, NL>(g, sm, c, A, base, fdig, invr, h);                // y_1 = Hhat z_0
     const C c1 = cf[1];
 #pragma unroll
@@ -189,7 +191,7 @@ __device__ void aug_run_acs(const KtGeom &g, const KtGenImage &im, const Smem &s
       const C ak = cf[k];
 #pragma unroll
       for (int q = 0; q < NL; ++q) v[q] = Qz[base + q];
-      apply_acs<R, NC, 1, true>(g, im, sm, Qz, base, fdig, Df, v, t);
+      apply_acs<R, NC, 1, true, true>(g, im, sm, Qz, base, fdig, Df, v, t, rc);
       hc_fiber<R, NL>(g, sm, c, Qz, base, fdig, invr, h);
 #pragma unroll
       for (int q = 0; q < NL; ++q) {
@@ -197,7 +199,7 @@ __device__ void aug_run_acs(const KtGeom &g, const KtGenImage &im, const Smem &s
         Pz[base + q] = mkc(t[q].x + t[q].x - oz.x, t[q].y + t[q].y - oz.y);
         v[q] = Qy[base + q];
       }
-      apply_acs<R, NC, 1, true>(g, im, sm, Qy, base, fdig, Df, v, t);
+      apply_acs<R, NC, 1, true, true>(g, im, sm, Qy, base, fdig, Df, v, t, rc);
 #pragma unroll
       for (int q = 0; q < NL; ++q) {
         const C ty = mkc(t[q].x + h[q].x, t[q].y + h[q].y);

@@ -1027,7 +1027,7 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
     return fail(KT_ERR_ARG, "tile_traj must be a power of two <= 32");
   // fiber mapping (one thread per run of n_loc elements along the last node) for the compiled
   // local dimensions; otherwise the strided mapping with 4, 8 or 16 items per thread
-  const int fiber_max_threads = 768;
+  const int fiber_max_threads = 736;   // the fiber kernels' launch bound
   int Tsel = 0;
   // strided mapping: items per thread above 8 spill registers, so only when nothing else fits
   const long long max_items = ((long long)d > 8LL * maxthr) ? 16LL * maxthr : 8LL * maxthr;
