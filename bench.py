@@ -56,7 +56,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of each interval kernel at
 # this workload's launch size (1024 trajectories, d = 6561, FP32-mixed), from one ncu capture of the
 # current kernels; None where no capture of the current kernel exists.
-NCU_TRAFFIC_PER_LAUNCH = {"bwd": 53.92e6 + 9.62e6, "fwd": None}
+NCU_TRAFFIC_PER_LAUNCH = {"bwd": (53.89e6 + 10.16e6 + 53.95e6 + 6.23e6) / 2, "fwd": None}
 SM_COUNT, FP32_LANES = 152, 128
 
 
