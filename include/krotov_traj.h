@@ -226,11 +226,16 @@ KT_API kt_status krotov_get_profile(kt_problem *p, double *ms_out, long long *la
 
 /* Sizes chosen at init: max jumps per pass, Chebyshev terms per step, tile width, tiles,
  * threads per CTA, and the spectral interval [e_min, e_max] of the forward generator's
- * Hermitian part. */
+ * Hermitian part; passes = completed forward sweeps since the uniforms were last uploaded (pass
+ * p used row p mod n_passes), which lets a run be resumed bit-identically: a new problem with the
+ * saved pulse, the same eps_bound and the uniform rows from passes - 1 on repeats the last forward
+ * sweep exactly. */
 typedef struct {
   int d, max_jumps, cheb_terms, tile_traj, n_tiles, threads;
   double e_min, e_max, damping;
   long long device_bytes;
+  long long passes;
+  double eps_bound;         /* the pulse bound the spectral estimate used (given or automatic) */
 } kt_info;
 KT_API kt_status krotov_get_info(kt_problem *p, kt_info *info);
 

@@ -46,7 +46,8 @@ class Info(ct.Structure):
     _fields_ = [
         ("d", ct.c_int), ("max_jumps", ct.c_int), ("cheb_terms", ct.c_int), ("tile_traj", ct.c_int),
         ("n_tiles", ct.c_int), ("threads", ct.c_int), ("e_min", ct.c_double), ("e_max", ct.c_double),
-        ("damping", ct.c_double), ("device_bytes", ct.c_longlong),
+        ("damping", ct.c_double), ("device_bytes", ct.c_longlong), ("passes", ct.c_longlong),
+        ("eps_bound", ct.c_double),
     ]
 
 

@@ -172,6 +172,7 @@ struct kt_problem {
   int *status = nullptr;
 
   int *pass = nullptr;          // device [3]: next uniforms row, rows held, row of the running pass
+  long long passes = 0;         // completed forward sweeps since the uniforms were uploaded
   double *nu = nullptr;         // device [KT_MAX_CTRL]: pulse noise (krotov_pulse_noise)
   void *cwork = nullptr;        // cross-trajectory update: [x][k] states and control products
   double *cpart = nullptr;      // its per-tile partial sums
@@ -438,6 +439,7 @@ kt_status enqueue_forward(kt_problem *p, int update, cudaStream_t st, bool save_
 
 // Host bookkeeping of a completed forward sweep.
 void commit_forward(kt_problem *p, int update, bool save_psi) {
+  p->passes++;
   p->final_buf = p->nt & 1;
   if (update) {
     std::swap(p->eps_old, p->eps_new);
@@ -1583,6 +1585,7 @@ KT_API kt_status krotov_set_uniforms(kt_problem *p, const double *uniforms, int 
   KT_CUDA(cudaMemcpyAsync(p->U, uniforms, n * sizeof(double), cudaMemcpyHostToDevice, st));
   KT_CUDA(kt_launch_pass_reset(p->pass, n_passes, st));
   p->n_passes = n_passes;
+  p->passes = 0;
   return KT_OK;
 }
 
@@ -1618,6 +1621,8 @@ KT_API kt_status krotov_get_info(kt_problem *p, kt_info *info) {
   info->e_max = p->e_max;
   info->damping = p->damping;
   info->device_bytes = (long long)p->bytes;
+  info->passes = p->passes;
+  info->eps_bound = p->g.eps_bound;
   return KT_OK;
 }
 

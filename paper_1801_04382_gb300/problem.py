@@ -183,6 +183,15 @@ class Problem:
         return {"fwd": (float(ms[0]), int(n[0])), "bwd": (float(ms[1]), int(n[1])), "grad": (float(ms[2]), int(n[2])),
                 "cross": (float(ms[3]), int(n[3]))}
 
+    def checkpoint(self) -> dict:
+        """What resumes this optimisation bit-identically: the current pulse, the pulse bound of the
+        spectral estimate and the number of completed forward sweeps (pass p used uniforms row p).
+        Resume with ``Problem(..., eps_guess=ck["eps"], eps_bound=ck["eps_bound"],
+        uniforms=U[ck["passes"] - 1:])``, one ``forward()`` (it repeats the last sweep exactly, jump
+        records included) and ``update()`` as before."""
+        info = self.get_info()
+        return {"eps": self.pulses(), "eps_bound": float(info.eps_bound), "passes": int(info.passes)}
+
     def get_info(self):
         info = _capi.Info()
         _capi.check(self._lib.krotov_get_info(self._h, ct.byref(info)), "krotov_get_info")

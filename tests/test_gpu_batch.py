@@ -117,3 +117,28 @@ def test_autotuned_tile_matches_oracle():
         dmax = np.abs(res.forward[1].deps).max()
         assert abs(JT[0] - res.JT[1]) <= 1e-10
         assert np.abs(p.deps() - res.forward[1].deps).max() <= 1e-10 * dmax
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_checkpoint_resume_is_bit_identical(precision):
+    """Optimise 3 iterations in one go, or 1 iteration, checkpoint, and resume in a new problem
+    for 2 more: identical J_T, pulses and jump records."""
+    sp = spec(2, 1, 12.0, 120, 13, 30.0, 9, 5, precision=precision)
+    with problem(sp) as a:
+        a.forward(False)
+        JT_a, _ = a.update(3)
+        eps_a, rec_a = a.pulses(), a.records()
+    with problem(sp) as b:
+        b.forward(False)
+        b.update(1)
+        ck = b.checkpoint()
+    assert ck["passes"] == 2
+    sp2 = dict(sp, eps_guess=ck["eps"], uniforms=sp["uniforms"][ck["passes"] - 1:])
+    kw = {k: sp2[k] for k in ("precision", "ckpt_interval", "tile_traj", "psi0_batch", "update_rule", "jump_scheme")}
+    with Problem(sp2["net"], sp2["T"], sp2["nt"], sp2["M"], sp2["eps_guess"], sp2["shape"], sp2["lam"],
+                 sp2["uniforms"], eps_bound=ck["eps_bound"], **kw) as c:
+        c.forward(False)
+        JT_c, _ = c.update(2)
+        assert np.array_equal(JT_c, JT_a[1:])
+        assert np.array_equal(c.pulses(), eps_a)
+        assert c.records() == rec_a
