@@ -180,7 +180,7 @@ struct kt_problem {
   unsigned *ccounter = nullptr;
   double *nu_ref = nullptr;     // device [n_ctrl][nt]: its reference pulse
   double *eps_base = nullptr;   // the pulse buffer eps_old pointed to at init (keys the graphs)
-  bool have_fwd = false, have_bwd = false, have_deps = false;
+  bool have_fwd = false, have_bwd = false;
   int final_buf = 0;
 
   // gradient (krotov_gradient): forward states kept every Kg intervals, replayed per segment
@@ -441,10 +441,7 @@ kt_status enqueue_forward(kt_problem *p, int update, cudaStream_t st, bool save_
 void commit_forward(kt_problem *p, int update, bool save_psi) {
   p->passes++;
   p->final_buf = p->nt & 1;
-  if (update) {
-    std::swap(p->eps_old, p->eps_new);
-    p->have_deps = true;
-  }
+  if (update) std::swap(p->eps_old, p->eps_new);
   p->cur = 1 - p->cur;          // the records just written become the "last completed" ones
   p->have_fwd = true;
   p->have_bwd = false;
