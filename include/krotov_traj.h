@@ -7,7 +7,10 @@
  * trajectories are propagated forward under the non-Hermitian effective Hamiltonian
  * (Sec. 2.1), co-states are propagated backward under its adjoint, and the pulse is updated
  * sequentially in time from the cross-trajectory sum of Im<chi_k|dH/deps_i|psi_k>
- * (Eq. independent_traj_update).
+ * (Eq. independent_traj_update), or, with kt_config.update_rule = 1, from the sum over all pairs
+ * of trajectories of Eq. cross_traj_update.  Also: the exact gradient of the trajectory
+ * functional (krotov_gradient), Krotov iterations as CUDA graph launches (krotov_update),
+ * batches of independent problems (krotov_init_batch), the pulse noise measure of Eq. noise.
  *
  * General conventions
  *  - All pointers in the descriptors are HOST pointers; the library copies what it needs at
