@@ -115,16 +115,18 @@ def basis_index(n_cav: int, atoms, photons) -> int:
     return idx
 
 
-def build_model(n_nodes: int, n_cav: int, delta: float = 100.0, g: float = 1.0,
+def build_model(n_nodes: int, n_cav: int, delta: float = 100.0, g: complex = 1.0,
                 kappa: float = 1.0) -> DenseModel:
-    """Cascaded chain of ``n_nodes`` atom-cavity nodes (paper Sec. 3.1)."""
+    """Cascaded chain of ``n_nodes`` atom-cavity nodes (paper Sec. 3.1).  A complex g = |g| e^(i phi)
+    couples g sigma_rg a + conj(g) sigma_gr a^dag (a phase the paper's real g = 1 does not have,
+    used to exercise complex couplings)."""
     loc = local_operators(n_cav)
     d = (3 * (n_cav + 1)) ** n_nodes
     sparse = d > SPARSE_ABOVE      # same operators, stored sparse so that d = 6561 fits in memory
     H0 = sp.csr_matrix((d, d), dtype=np.complex128) if sparse else np.zeros((d, d), dtype=np.complex128)
     a_full = [embed(loc["a"], i, n_nodes, sparse) for i in range(n_nodes)]
-    h0_node = (-delta * loc["Pi_r"] - (g * g / delta) * loc["n"]
-               + g * (loc["sigma_rg"] @ loc["a"] + (loc["sigma_rg"] @ loc["a"]).conj().T))
+    h0_node = (-delta * loc["Pi_r"] - (abs(g) ** 2 / delta) * loc["n"]
+               + g * (loc["sigma_rg"] @ loc["a"]) + np.conj(g) * (loc["sigma_rg"] @ loc["a"]).conj().T)
     for i in range(n_nodes):
         H0 = H0 + embed(h0_node, i, n_nodes, sparse)
     for i in range(n_nodes):

@@ -58,7 +58,7 @@ def _full_index(n_loc: int, digits) -> int:
     return x
 
 
-def cascaded_chain(n_nodes: int, n_cav: int, delta: float = 100.0, g: float = 1.0,
+def cascaded_chain(n_nodes: int, n_cav: int, delta: float = 100.0, g: complex = 1.0,
                    kappa: float = 1.0) -> NetworkFactors:
     nl = 3 * (n_cav + 1)
     a = np.zeros((nl, nl), dtype=np.complex128)
@@ -69,14 +69,14 @@ def cascaded_chain(n_nodes: int, n_cav: int, delta: float = 100.0, g: float = 1.
             x = _loc(n_cav, atom, n)
             if n >= 1:
                 a[_loc(n_cav, atom, n - 1), x] = math.sqrt(n)          # a |n> = sqrt(n) |n-1>
-            h[x, x] += -(g * g / delta) * n
+            h[x, x] += -(abs(g) ** 2 / delta) * n
             if atom == ATOM_R:
                 h[x, x] += -delta
     for n in range(1, n_cav + 1):
-        # g |r, n-1><g, n| sqrt(n)  (|r><g| a)  and its Hermitian conjugate
+        # g |r, n-1><g, n| sqrt(n)  (|r><g| a)  and its Hermitian conjugate (g may carry a phase)
         r_, g_ = _loc(n_cav, ATOM_R, n - 1), _loc(n_cav, ATOM_G, n)
         h[r_, g_] += g * math.sqrt(n)
-        h[g_, r_] += g * math.sqrt(n)
+        h[g_, r_] += np.conj(g) * math.sqrt(n)
     for n in range(n_cav + 1):
         r_, e_ = _loc(n_cav, ATOM_R, n), _loc(n_cav, ATOM_E, n)
         hc[r_, e_] += 0.5j

@@ -12,6 +12,8 @@ Tolerances (stated per result):
   The jump time is compared in the norm that defines it (Sec. 2.1, step 3): the norm decays at
   rate ||L psi(s*)||^2 = 1/c^2 there, so a norm discrepancy delta shifts s* by delta c^2.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -245,4 +247,38 @@ def test_first_order_jump_scheme_fp64():
             assert all(r[1] == dt for r in rk)
             n += len(rk)
     assert n >= 10
+    compare(c, gpu, res, 1e-10, 1e-10, 1e-10, 1e-9)
+
+
+@pytest.mark.parametrize("nc", [1, 2])
+def test_complex_coupling_takes_the_complex_cavity_path(nc):
+    """A cavity coupling with a phase (g = e^{i pi/5}) is neither real nor imaginary, so the library
+    keeps the complex form of the cavity-structure kernels; FP64 stress case against the oracle
+    built with the same complex g."""
+    g = complex(math.cos(math.pi / 5), math.sin(math.pi / 5))
+    c = setup(2, nc, 12.0 if nc == 1 else 5.0, 120 if nc == 1 else 100, 13, 30.0, 9, 2, random_init=True)
+    net = cascaded_chain(2, nc, g=g)
+    out = {"F": [], "recs": [], "psiT": [], "eps": [], "deps": []}
+    with Problem(net, c["T"], c["nt"], c["M"], c["eps0"], c["S"], c["lam"], c["U"], psi0_batch=c["psi0"]) as p:
+        out["F"].append(p.forward(False))
+        out["recs"].append(p.records())
+        out["psiT"].append(p.states())
+        for _ in range(c["n_iter"]):
+            p.backward()
+            out["F"].append(p.forward(True))
+            out["recs"].append(p.records())
+            out["psiT"].append(p.states())
+            out["eps"].append(p.pulses())
+            out["deps"].append(p.deps())
+    m = om.build_model(2, nc, g=g)
+    res = mcwf.optimize(m, c["eps0"], c["T"], c["U"], c["S"], c["lam"], c["n_iter"], psi0=c["psi0"], keep=True)
+    compare(c, out, res, 1e-10, 1e-10, 1e-10, 1e-9)
+
+
+def test_cavity_cutoff_three_takes_the_strided_path():
+    """Cavity cutoff 3 (n_loc = 12, d = 144): no fiber kernel is compiled for n_loc = 12, so the
+    generic strided mapping runs; FP64 stress case against the oracle."""
+    c = setup(2, 3, 4.0, 40, 13, 30.0, 9, 2, random_init=True)
+    gpu = run_gpu(c)
+    _, res = run_oracle(c)
     compare(c, gpu, res, 1e-10, 1e-10, 1e-10, 1e-9)
