@@ -493,3 +493,21 @@ def test_first_order_jump_lands_at_the_end_of_the_interval_containing_the_exact_
         else:
             assert len(fw.records[k]) == 0
     assert n_jumped >= 5
+
+
+def test_complex_coupling_is_a_photon_number_gauge_of_the_real_one():
+    """With g = |g| e^{i phi}, H_eff = V H_eff(|g|) V^dag for V = exp(-i phi N_phot) (N_phot the
+    total photon number): the phase only rotates a, which the cascade hops a_j^dag a_i, L^dag L
+    and the drive do not see.  A dropped conjugate or a wrong |g|^2 breaks the identity."""
+    phi = 0.7
+    gc = 1.3 * complex(math.cos(phi), math.sin(phi))
+    mc = om.build_model(2, 2, g=gc)
+    mr = om.build_model(2, 2, g=1.3)
+    nl, NP = 9, 3
+    x = np.arange(nl * nl)
+    nph = (x // nl) % NP + (x % nl) % NP          # local index = atom * (n_cav + 1) + n
+    V = np.diag(np.exp(-1j * phi * nph))
+    eps = np.array([0.4, -0.9])
+    Hc, Hr = mc.Heff(eps), mr.Heff(eps)
+    np.testing.assert_allclose(Hc, V @ Hr @ V.conj().T, rtol=0, atol=1e-12 * np.abs(Hr).max())
+    assert np.abs(Hc - Hr).max() > 0.1                # the phase is really there
