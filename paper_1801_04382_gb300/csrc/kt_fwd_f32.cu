@@ -6,12 +6,10 @@ namespace kt {
 template <typename R, int EPT, int NL, int ACS>
 static cudaError_t launch_fwd_t(const KtGeom &g, const KtGenImage &im, const KtOps &ops, const FwdArgs &a, size_t smem,
                                 cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(fwd_kernel<R, EPT, NL, ACS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  // once per instantiation; a function-local static is initialised thread-safely
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(fwd_kernel<R, EPT, NL, ACS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (attr != cudaSuccess) return attr;
   fwd_kernel<R, EPT, NL, ACS><<<g.n_tiles, g.nthreads, smem, st>>>(g, im, ops, a);
   return cudaGetLastError();
 }
