@@ -511,3 +511,71 @@ def test_complex_coupling_is_a_photon_number_gauge_of_the_real_one():
     Hc, Hr = mc.Heff(eps), mr.Heff(eps)
     np.testing.assert_allclose(Hc, V @ Hr @ V.conj().T, rtol=0, atol=1e-12 * np.abs(Hr).max())
     assert np.abs(Hc - Hr).max() > 0.1                # the phase is really there
+
+
+# ---------------------------------------------------------------- density-matrix Krotov
+def test_density_backward_map_is_the_adjoint():
+    """<<P(t_j)|rho(t_j)>> is the same at every t_j under one pulse (fixes E^dag, not E^T or E)."""
+    from oracle import density as od
+    m = om.build_model(1, 1)
+    nt, T = 12, 3.0
+    eps = si.guess_pulses(1, nt, T, 20.0)
+    rho = ol.propagate_rho(m, eps, T, np.outer(m.psi0, m.psi0.conj()), dense=True, keep=True)
+    P = od.backward_P(m, eps, T, np.outer(m.psi_tgt, m.psi_tgt.conj()))
+    pair = [np.trace(P[j].conj().T @ rho[j]) for j in range(nt + 1)]
+    np.testing.assert_allclose(pair, pair[-1], rtol=1e-11, atol=1e-13)
+
+
+def test_density_update_is_the_first_order_descent_direction():
+    """Delta u_1 = -S / (lambda dt) dJ_T/du_1 to first order in dt (central differences of J_T
+    from the density-matrix propagation): fixes the sign and the factor of Eq. krotovupdate with
+    dL/du rho = [H, rho] and dE/du = -i dt [H, .] to first order."""
+    from oracle import density as od
+    m = om.build_model(1, 1)
+    nt, T = 400, 4.0
+    dt = T / nt
+    eps = si.guess_pulses(1, nt, T, 20.0)
+    S = np.ones((1, nt))
+    lam = np.array([2.0])
+    rho0 = np.outer(m.psi0, m.psi0.conj())
+    P = od.backward_P(m, eps, T, np.outer(m.psi_tgt, m.psi_tgt.conj()))
+    _, deps, _ = od.forward_update(m, eps, T, rho0, P, S, lam)
+    h = 1e-5
+    ep, em = eps.copy(), eps.copy()
+    ep[0, 0] += h
+    em[0, 0] -= h
+    Jp = od.functional(m, ol.propagate_rho(m, ep, T, rho0, dense=True))
+    Jm = od.functional(m, ol.propagate_rho(m, em, T, rho0, dense=True))
+    grad = (Jp - Jm) / (2 * h)
+    assert abs(grad) > 1e-8
+    assert deps[0, 0] == pytest.approx(-S[0, 0] / (lam[0] * dt) * grad, rel=2e-2)
+
+
+def test_density_update_is_twice_the_trajectory_update_for_a_closed_pure_state():
+    """kappa = 0, pure initial state: P(t) = |xi><xi|, rho = |psi><psi|, and Im<<P|[H, rho]>> =
+    2 Im[<xi|H|psi><psi|xi>] = 2 Im<chi|H|psi> at t_0 (chi = tau xi, <psi_0|xi(t_0)> = conj(tau));
+    so the first interval's density-matrix update is twice the one-trajectory update."""
+    from oracle import density as od
+    m = om.build_model(1, 1, kappa=0.0)
+    nt, T = 40, 4.0
+    eps = si.guess_pulses(1, nt, T, 20.0)
+    S = si.shape_functions(1, nt, T)
+    lam = np.full(1, 10.0)
+    psi0 = si.random_states(5, 1, m.d)[0]
+    rho0 = np.outer(psi0, psi0.conj())
+    P = od.backward_P(m, eps, T, np.outer(m.psi_tgt, m.psi_tgt.conj()))
+    _, d_dm, _ = od.forward_update(m, eps, T, rho0, P, S, lam)
+    res = mcwf.optimize(m, eps, T, si.uniforms(0, 2, 1, 5), S, lam, 1, psi0=psi0, keep=True)
+    d_traj = res.forward[1].deps
+    assert abs(d_traj[0, 0]) > 1e-10
+    np.testing.assert_allclose(d_dm[:, 0], 2.0 * d_traj[:, 0], rtol=1e-8, atol=1e-16)
+
+
+def test_density_krotov_is_monotone_with_dissipation():
+    """The density-matrix functional is linear in rho and the dynamics linear in u, so first-order
+    Krotov lowers J_T at every iteration, here with cavity decay (kappa = 1)."""
+    from oracle import density as od
+    m = om.build_model(1, 1)
+    nt, T = 40, 4.0
+    JT, _ = od.optimize_dm(m, si.guess_pulses(1, nt, T, 20.0), T, si.shape_functions(1, nt, T), np.array([5.0]), 4)
+    assert np.all(np.diff(JT) < 0.0)
