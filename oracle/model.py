@@ -116,10 +116,15 @@ def basis_index(n_cav: int, atoms, photons) -> int:
 
 
 def build_model(n_nodes: int, n_cav: int, delta: float = 100.0, g: complex = 1.0,
-                kappa: float = 1.0) -> DenseModel:
+                kappa: float = 1.0, lindblad: str = "collective") -> DenseModel:
     """Cascaded chain of ``n_nodes`` atom-cavity nodes (paper Sec. 3.1).  A complex g = |g| e^(i phi)
     couples g sigma_rg a + conj(g) sigma_gr a^dag (a phase the paper's real g = 1 does not have,
-    used to exercise complex couplings)."""
+    used to exercise complex couplings).
+
+    ``lindblad``: "collective" -- the paper's single operator L = sqrt(2 kappa) sum_i a_i;
+    "local" -- one operator per node, L_i = sqrt(2 kappa) a_i (the field leaving each cavity
+    detected separately; not the paper's network, used to exercise the channel choice of Sec. 2.1
+    with several Lindblad operators)."""
     loc = local_operators(n_cav)
     d = (3 * (n_cav + 1)) ** n_nodes
     sparse = d > SPARSE_ABOVE      # same operators, stored sparse so that d = 6561 fits in memory
@@ -135,7 +140,12 @@ def build_model(n_nodes: int, n_cav: int, delta: float = 100.0, g: complex = 1.0
             H0 = H0 + (-1j * kappa) * (a_full[j].conj().T @ a_full[i])
     hc_node = 0.5j * (loc["sigma_re"] - loc["sigma_re"].conj().T)
     Hc = [embed(hc_node, i, n_nodes, sparse) for i in range(n_nodes)]
-    L = [np.sqrt(2.0 * kappa) * reduce(lambda x, y: x + y, a_full)]
+    if lindblad == "collective":
+        L = [np.sqrt(2.0 * kappa) * reduce(lambda x, y: x + y, a_full)]
+    elif lindblad == "local":
+        L = [np.sqrt(2.0 * kappa) * a_i for a_i in a_full]
+    else:
+        raise ValueError("lindblad must be 'collective' or 'local'")
     psi0 = np.zeros(d, dtype=np.complex128)
     psi0[basis_index(n_cav, [E] + [G] * (n_nodes - 1), [0] * n_nodes)] = 1.0
     tgt = np.zeros(d, dtype=np.complex128)

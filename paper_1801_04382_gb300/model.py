@@ -59,7 +59,12 @@ def _full_index(n_loc: int, digits) -> int:
 
 
 def cascaded_chain(n_nodes: int, n_cav: int, delta: float = 100.0, g: complex = 1.0,
-                   kappa: float = 1.0) -> NetworkFactors:
+                   kappa: float = 1.0, lindblad: str = "collective") -> NetworkFactors:
+    """``lindblad``: "collective" -- the network's single output L = sqrt(2 kappa) sum_i a_i;
+    "local" -- one operator per node, L_i = sqrt(2 kappa) a_i (every cavity's output detected on its
+    own, n_lind = n_nodes)."""
+    if lindblad not in ("collective", "local"):
+        raise ValueError("lindblad must be 'collective' or 'local'")
     nl = 3 * (n_cav + 1)
     a = np.zeros((nl, nl), dtype=np.complex128)
     h = np.zeros((nl, nl), dtype=np.complex128)
@@ -103,6 +108,7 @@ def cascaded_chain(n_nodes: int, n_cav: int, delta: float = 100.0, g: complex = 
         a_local=a,
         pair_dst=np.array(pd, dtype=np.int32), pair_src=np.array(ps, dtype=np.int32),
         pair_coef=np.array(pc, dtype=np.complex128),
-        lind_coef=np.full((1, n_nodes), math.sqrt(2.0 * kappa), dtype=np.complex128),
+        lind_coef=(np.full((1, n_nodes), math.sqrt(2.0 * kappa), dtype=np.complex128) if lindblad == "collective"
+                   else math.sqrt(2.0 * kappa) * np.eye(n_nodes, dtype=np.complex128)),
         psi0=psi0, psi_tgt=tgt,
     )

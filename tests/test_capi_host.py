@@ -128,18 +128,21 @@ def test_model_builder_matches_paper_structure():
     assert abs(np.linalg.norm(net.psi_tgt) - 1.0) < 1e-15
 
 
-@pytest.mark.parametrize("N,nc,kappa,g", [(2, 1, 1.0, 1.0), (2, 2, 0.7, 1.0), (3, 1, 1.3, 1.0), (1, 2, 1.0, 1.0),
-                                          (2, 2, 1.0, complex(0.8, 0.6)), (2, 3, 1.0, 1.0)])
-def test_structured_generator_tables_match_dense_heff(lib, N, nc, kappa, g):
+@pytest.mark.parametrize("N,nc,kappa,g,lind", [(2, 1, 1.0, 1.0, "collective"), (2, 2, 0.7, 1.0, "collective"),
+                                               (3, 1, 1.3, 1.0, "collective"), (1, 2, 1.0, 1.0, "collective"),
+                                               (2, 2, 1.0, complex(0.8, 0.6), "collective"),
+                                               (2, 3, 1.0, 1.0, "collective"), (3, 2, 1.0, 1.0, "local")])
+def test_structured_generator_tables_match_dense_heff(lib, N, nc, kappa, g, lind):
     """The library's structured generator tables, expanded with the kernels' own indexing
     (digits, slot offsets, per-direction pair tables), equal the oracle's dense
     H_eff = H - (i/2) L^dag L (direction 0) and -H_eff^dag (direction 1, co-state propagation).
     Includes a complex cavity coupling (tables of the complex cavity-structure path) and cavity
-    cutoff 3 (tables of the strided path)."""
+    cutoff 3 (tables of the strided path), and one Lindblad operator per node (no L^dag L cross
+    terms: the cascade keeps both hop directions)."""
     from oracle import model as om
     from paper_1801_04382_gb300.problem import generator_dense
-    net = pm.cascaded_chain(N, nc, kappa=kappa, g=g)
-    m = om.build_model(N, nc, kappa=kappa, g=g)
+    net = pm.cascaded_chain(N, nc, kappa=kappa, g=g, lindblad=lind)
+    m = om.build_model(N, nc, kappa=kappa, g=g, lindblad=lind)
     nt, T, M = 8, 1.0, 3
     rng = np.random.default_rng(N * 10 + nc)
     eps_guess = si.guess_pulses(N, nt, T, 2.0)

@@ -579,3 +579,92 @@ def test_density_krotov_is_monotone_with_dissipation():
     nt, T = 40, 4.0
     JT, _ = od.optimize_dm(m, si.guess_pulses(1, nt, T, 20.0), T, si.shape_functions(1, nt, T), np.array([5.0]), 4)
     assert np.all(np.diff(JT) < 0.0)
+
+
+# ---------------------------------------------------------------- Krotov's functional, channels, large-d adjoint
+def test_krotov_functional_is_stationary_at_the_first_interval_update():
+    """Krotov's update minimises J = J_T + sum_i lambda_i/S_i int Delta eps_i^2 dt (Eq.
+    krotov_functional) to first order: f(D) = J(eps + D e_i1) with the penalty of that one
+    interval is stationary at D = the oracle's Delta eps_i1 up to O(dt) (kappa = 0, one
+    trajectory, S != 1 and lambda differing between the controls).  f'(D) = dJ_T/deps_i1 +
+    2 lambda_i D dt / S_i: a penalty with lambda S, S / lambda, without dt or linear in D leaves a
+    derivative of the size of dJ_T/deps itself, or far larger.  The gap shrinks as dt -> 0."""
+    m = om.build_model(2, 1, delta=5.0, kappa=0.0)
+    lam = np.array([10.0, 3.0])
+    ratios = []
+    for nt in (400, 800):
+        T = 4.0
+        dt = T / nt
+        eps = si.guess_pulses(2, nt, T, 3.0) + 0.3
+        S = np.empty((2, nt))
+        S[0], S[1] = 0.37, 0.8
+        U = si.uniforms(0, 2, 1, 5)
+        psi0 = si.random_states(3, 1, m.d)[0]     # both nodes driven at t_0: both updates nonzero
+        fw0 = mcwf.forward_pass(m, eps, T, U[0], psi0)
+        tau, _ = mcwf.fidelity(fw0.psi_T, m.psi_tgt)
+        chi = mcwf.backward_pass(m, eps, T, tau[:, None] * m.psi_tgt[None, :], fw0.records)
+        fw1 = mcwf.forward_pass(m, eps, T, U[1], psi0, chi=chi, shape=S, lam=lam)
+        worst = 0.0
+        for i in range(2):
+            d_star = fw1.deps[i, 0]
+            assert abs(d_star) > 1e-9
+            h = 1e-4 * abs(d_star)
+
+            def f(D):
+                ep = eps.copy()
+                ep[i, 0] += D
+                JT = 1.0 - mcwf.fidelity(mcwf.forward_pass(m, ep, T, U[0], psi0).psi_T, m.psi_tgt)[1]
+                dmat = np.zeros_like(eps)
+                dmat[i, 0] = D
+                return mcwf.krotov_functional(JT, dmat, S, lam, dt)
+
+            slope = (f(d_star + h) - f(d_star - h)) / (2 * h)
+            # dJ_T/deps_i1 = -2 lambda_i D* dt / S_i at the stationary point: the scale of each term
+            scale = 2 * lam[i] * abs(d_star) * dt / S[i, 0]
+            worst = max(worst, abs(slope) / scale)
+        ratios.append(worst)
+    # measured 0.074 -> 0.037; lambda S in place of lambda / S stays near 0.8, no dt gives ~1e2
+    assert ratios[0] < 0.15
+    assert ratios[1] < 0.6 * ratios[0]
+
+
+def test_channel_choice_matches_integrated_channel_rates():
+    """Several Lindblad operators (Sec. 2.1: the jump goes to channel l with probability
+    proportional to <psi|L_l^dag L_l|psi>).  Two cavity modes coupled by the cascade hop
+    i kappa (a_0^dag a_1 - a_1^dag a_0), one photon shared as alpha |1,0> + beta |0,1>, atoms
+    decoupled (g = 0, eps = 0), one detector per cavity L_l = sqrt(2 kappa) a_l: the no-jump
+    amplitudes are c(t) = exp(-kappa t) R(kappa t) c(0) with R a rotation, and channel l fires
+    with total probability 2 kappa int_0^inf |c_l(t)|^2 dt = (3 alpha^2 + 2 alpha beta + beta^2)/4
+    for l = 0 (the rest for l = 1).  The chosen channels' frequency over 1500 trajectories
+    matches within the binomial 3 sigma; choosing the other channel, or by u alone, fails."""
+    m = om.build_model(2, 1, g=0.0, kappa=1.0, lindblad="local")
+    assert len(m.L) == 2
+    a2 = 0.3
+    al, be = math.sqrt(a2), math.sqrt(1.0 - a2)
+    psi0 = np.zeros(m.d, dtype=np.complex128)
+    psi0[om.basis_index(1, [0, 0], [1, 0])] = al
+    psi0[om.basis_index(1, [0, 0], [0, 1])] = be
+    M, nt, T = 1500, 40, 8.0                      # exp(-2 kappa T) ~ 1e-7: every trajectory jumps once
+    U = si.uniforms(21, 1, M, 5)
+    fw = mcwf.forward_pass(m, np.zeros((2, nt)), T, U[0], psi0)
+    assert all(len(r) == 1 for r in fw.records)
+    p0 = (3 * a2 + 2 * al * be + (1 - a2)) / 4
+    freq = np.mean([r[0].channel == 0 for r in fw.records])
+    assert abs(freq - p0) <= 3 * math.sqrt(p0 * (1 - p0) / M), (freq, p0)
+
+
+def test_backward_sweep_is_the_adjoint_at_d729():
+    """The pathwise co-state sweep on the three-node chain (d = 729), where the oracle propagates
+    with its Chebyshev series on -H_eff^dag instead of expm: <chi_k(t_j)|psi_k(t_j)> is the same
+    at every t_j along trajectories with jumps."""
+    m = om.build_model(3, 2)
+    nt, T, M = 20, 0.5, 3
+    eps = si.guess_pulses(3, nt, T, 30.0)
+    U = si.uniforms(2, 1, M, 1 + 2 * 9)
+    psi0 = si.random_states(102, M, m.d)
+    fw = mcwf.forward_pass(m, eps, T, U[0], psi0, keep_states=True)
+    assert sum(len(r) for r in fw.records) >= 1
+    chi_T = si.random_states(12, M, m.d)
+    chi = mcwf.backward_pass(m, eps, T, chi_T, fw.records)
+    ov = np.einsum("tkd,tkd->tk", chi.conj(), fw.psi_t)
+    assert np.abs(ov - ov[-1][None, :]).max() < 1e-11
