@@ -2,12 +2,16 @@
 """Benchmark: Krotov iterations per second of the trajectory-parallel Krotov hot path on GB300.
 
 Workload (one "step" = one Krotov iteration = backward co-state sweep + updating forward sweep,
-including the checkpoint recompute): four-node cascaded atom-cavity chain, three-level atoms,
+including any co-state recompute): four-node cascaded atom-cavity chain, three-level atoms,
 cavity cutoff 2 (d = 6561), 1024 trajectories, nt = 5000 intervals of dt = 0.01, four controls,
-FP32-mixed precision (complex64 states, FP64 norms and sums), co-state checkpoints every 100
-intervals, synthetic seeded inputs (guess pulse sin^2 of amplitude 1, uniforms from seed 4).
+FP32-mixed precision (complex64 states, FP64 norms and sums), co-state storage chosen from the
+free device memory (all 5001 co-states, 269 GB, when they fit; --ckpt K keeps every K-th and
+recomputes the rest), synthetic seeded inputs (guess pulse sin^2 of amplitude 1, uniforms from
+seed 4).  The timed region runs krotov_update as the product does: one CUDA graph launch per
+iteration; one more iteration launched kernel by kernel gives the per-kernel split.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--ckpt K]
+    python bench.py --workload profile [--precision fp32|fp64] [--profile-M M]
     python bench.py --workload mix64 [--steps K] [--warmup W]
     python bench.py --workload grad729 [--steps K] [--warmup W]
     python bench.py --workload noise
@@ -24,6 +28,8 @@ that keeps the states plus the gradient sweep.
 two-node chain (d = 81, nt = 1000, guess amplitude 20 so that a quarter of the trajectories jump,
 FP32-mixed) for M = 8 ... 1024 trajectories, of the pulse and of the accumulated update eps - eps_guess
 (free of the smoothing residual of the smooth guess), and fits nu_i ~ M^b (the paper finds b = -1/2).
+--workload profile runs a 12-interval case of the four-node interval kernels at M trajectories (a
+small command for ncu captures).
 --workload cross runs 20 iterations of the cross-trajectory update (Eq. cross_traj_update) and of
 the independent-trajectory update on the two-node chain (d = 81, M = 128, nt = 1000, FP32-mixed)
 and reports both convergence histories, iterations/s and the pair-sum kernels' time.
@@ -56,8 +62,26 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of each interval kernel at
 # this workload's launch size (1024 trajectories, d = 6561, FP32-mixed), from one ncu capture of the
 # current kernels; None where no capture of the current kernel exists.
-NCU_TRAFFIC_PER_LAUNCH = {"bwd": (53.89e6 + 10.16e6 + 53.95e6 + 6.23e6) / 2, "fwd": None}
-SM_COUNT, FP32_LANES = 152, 128
+NCU_TRAFFIC_PER_LAUNCH = {"bwd": None, "fwd": None}
+FP32_LANES = 128              # FP32 FMA lanes per SM (Blackwell)
+
+
+def sm_count() -> int:
+    """Streaming multiprocessors of the current device (read from the device, not assumed)."""
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
+def fp32_peak_tflops(clk_mhz: float) -> float:
+    return sm_count() * FP32_LANES * 2 * clk_mhz * 1e6 / 1e12
+
+
+def executed_flops_per_elem_term(nnz: float, ri: bool) -> float:
+    """FP32 flops one element of one Chebyshev term executes: every off-diagonal coupling of the
+    cavity network is purely real or purely imaginary, so the kernels apply it with two FMAs
+    (4 flops) instead of a complex multiply-add (8); the diagonal is a complex product (6), the
+    recurrence 2 T_k - T_{k-1} 4 and the running sum a complex FMA 8."""
+    return (4.0 if ri else 8.0) * (nnz - 1.0) + 6.0 + 4.0 + 8.0
 
 
 def measured_peaks():
@@ -285,7 +309,7 @@ def run_mix(args, rank, world):
 
     peaks, peak_src = measured_peaks()
     clk_max = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = SM_COUNT * FP32_LANES * 2 * clk_max * 1e6 / 1e12
+    fp32_peak = fp32_peak_tflops(clk_max)
     iters_per_s = world * 1000.0 / ms_step
     achieved = flops_it / (ms_step / 1000.0) / 1e12
     counts = {}
@@ -303,7 +327,7 @@ def run_mix(args, rank, world):
         "traj_steps_per_s": tsteps_it * iters_per_s,
         "roofline": {"bound": "alu", "kernel": "all interval kernels of the batch", "achieved": achieved,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
-                     "peak_source": f"FP32 FFMA: {SM_COUNT} SMs x {FP32_LANES} lanes x 2 x {clk_max:.0f} MHz"},
+                     "peak_source": f"FP32 FFMA: {sm_count()} SMs x {FP32_LANES} lanes x 2 x {clk_max:.0f} MHz"},
         "hbm_roofline": {"achieved_gbs": bytes_it * iters_per_s / world / 1e9, "peak_gbs": peaks["hbm_gbs"],
                          "frac": bytes_it * iters_per_s / world / 1e9 / peaks["hbm_gbs"], "peak_source": peak_src},
         "sequential_same_problems": {"ms_per_step": seq_ms, "batch_speedup": seq_ms / ms_step},
@@ -368,7 +392,7 @@ def run_grad(args, rank, world):
     clocks = clocks_stop(proc, fh, clk_path, local)
     peaks, peak_src = measured_peaks()
     clk_max = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = SM_COUNT * FP32_LANES * 2 * clk_max * 1e6 / 1e12
+    fp32_peak = fp32_peak_tflops(clk_max)
     K = info.cheb_terms
     nnz = avg_row_nonzeros(net)
     # per control a 2d-dimensional propagation: the state's and the derivative's recurrences, plus
@@ -389,10 +413,10 @@ def run_grad(args, rank, world):
         "roofline": {"bound": "alu", "kernel": "grad_kernel", "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
                      "avg_launch_ms": g_ms / max(g_n, 1), "launches": g_n, "flops_per_launch": flops_grad,
-                     "peak_source": f"FP32 FFMA: {SM_COUNT} SMs x {FP32_LANES} lanes x 2 x {clk_max:.0f} MHz"},
+                     "peak_source": f"FP32 FFMA: {sm_count()} SMs x {FP32_LANES} lanes x 2 x {clk_max:.0f} MHz"},
         "kernels": {f"{k}_kernel": {"launches": n, "total_ms": ms, "avg_ms": ms / max(n, 1)}
                     for k, (ms, n) in prof.items() if n > 0},
-        "max_abs_gradient": float(np.abs(grad).max()),
+        "max_abs_gradient": float(grad.abs().max()),
         "gpu_launches": int(sum(n for _, n in prof.values())),
         "clocks": clocks,
     }
@@ -489,7 +513,7 @@ def run_cross(args, rank, world):
                          "kernels": {f"{k}_kernel": {"launches": n, "total_ms": ms, "avg_ms": ms / max(n, 1)}
                                      for k, (ms, n) in prof.items() if n > 0}}
     peaks, _ = measured_peaks()
-    fp32_peak = SM_COUNT * FP32_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    fp32_peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
     c_ms, c_n = prof["cross"]
     pair_flops = 8.0 * (1 + net.n_ctrl) * wl.M * wl.M * wl.d        # complex MACs of G and A_c per launch
     line = {"metric": "cross-trajectory Krotov (Eq. cross_traj_update) vs independent, iterations/s and J_T",
@@ -543,43 +567,49 @@ def run_ours(args, rank, world):
 
     wl = workload(rank, args.precision)
     net = cascaded_chain(wl.n_nodes, wl.n_cav, wl.delta, wl.g, wl.kappa)
-    n_passes = 1 + args.warmup + args.steps
+    n_passes = 2 + args.warmup + args.steps
     eps0 = si.guess_pulses(net.n_ctrl, wl.nt, wl.T, wl.guess_amp)
     S = si.shape_functions(net.n_ctrl, wl.nt, wl.T)
     lam = np.full(net.n_ctrl, wl.lam)
     U = si.uniforms(wl.seed, n_passes, wl.M, wl.draws_per_traj)
     stream = torch.cuda.current_stream()
+    # co-state storage from the free device memory (every co-state when they fit)
     prob = Problem(net, wl.T, wl.nt, wl.M, eps0, S, lam, U, precision=wl.precision,
-                   ckpt_interval=wl.ckpt_interval, stream=stream)
+                   ckpt_interval=args.ckpt, stream=stream)
     info = prob.info
     prob.forward(False, stream=stream)                  # guess sweep (pass 0)
     for _ in range(args.warmup):
-        prob.update(1, stream=stream)
+        prob.update(1, stream=stream)                   # also captures the two iteration graphs
 
-    # ---------------- timed region: K Krotov iterations, inputs resident in HBM
+    # ---------------- timed region: K Krotov iterations through the product path (one CUDA graph
+    # launch per iteration), inputs resident in HBM
     clk_path = os.path.join(tempfile.gettempdir(), f"kt_clocks_{os.getpid()}.csv")
     proc, fh = clocks_start(clk_path)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    prob.set_profiling(True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    JT = None
-    for _ in range(args.steps):
-        JT, _ = prob.update(1, stream=stream)
+    JT, _ = prob.update(args.steps, stream=stream)
     ev1.record(stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     ms_total = ev0.elapsed_time(ev1)
-    prof = prob.profile()
-    prob.set_profiling(False)
     clocks = clocks_stop(proc, fh, clk_path, local)
     ms_total = reduce_max(ms_total, dist, "cuda")
     ms_step = ms_total / args.steps
     iters_per_s = world * 1000.0 / ms_step
     traj_steps_per_s = iters_per_s * 2 * wl.M * wl.nt
+
+    # ---------------- per-kernel split: one more iteration launched kernel by kernel, CUDA events on
+    # the launching stream around every launch
+    prob.set_profiling(True)
+    prob.update(1, stream=stream)
+    torch.cuda.synchronize()
+    prof = prob.profile()
+    prob.set_profiling(False)
+    prof_ms_iter = sum(ms for ms, _ in prof.values())
 
     # ---------------- end to end through the public API, host buffers each step
     e2e_steps = max(1, min(args.steps, 3))
@@ -607,10 +637,12 @@ def run_ours(args, rank, world):
     avg_s = f_ms / max(f_n, 1) / 1000.0
     nnz = avg_row_nonzeros(net)
     K = info.cheb_terms
-    flops_per_elem_term = 8.0 * nnz + 12.0          # complex MACs, recurrence, accumulation
-    flops_per_launch = flops_per_elem_term * K * wl.d * wl.M
+    ri = info.threads > 0 and wl.n_cav == 2      # cavity network with real / imaginary coupling classes
+    exec_per_elem_term = executed_flops_per_elem_term(nnz, ri)
+    survey_per_elem_term = 8.0 * nnz + 12.0      # every coupling counted as a complex multiply-add
+    flops_per_launch = exec_per_elem_term * K * wl.d * wl.M
     clk_max = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = SM_COUNT * FP32_LANES * 2 * clk_max * 1e6 / 1e12
+    fp32_peak = fp32_peak_tflops(clk_max)
     achieved = flops_per_launch / avg_s / 1e12
     s_bytes = 8 if wl.precision == "fp32" else 16
     bytes_per_iter = 5.0 * s_bytes * wl.d * wl.M * wl.nt
@@ -620,18 +652,24 @@ def run_ours(args, rank, world):
             "unit": "TFLOP/s", "frac": achieved / fp32_peak,
             "traffic": NCU_TRAFFIC_PER_LAUNCH.get(fam) if wl.precision == "fp32" else None,
             "avg_launch_ms": avg_s * 1e3, "launches": f_n,
-            "flops_per_launch": flops_per_launch, "algorithmic_bytes_per_launch": kernel_bytes,
+            "flops_per_launch": flops_per_launch, "flops_per_elem_term": exec_per_elem_term,
+            "flops_per_elem_term_complex_count": survey_per_elem_term,
+            "tflops_complex_count": survey_per_elem_term * K * wl.d * wl.M / avg_s / 1e12,
+            "algorithmic_bytes_per_launch": kernel_bytes,
             "hbm_gbs_of_kernel": kernel_bytes / avg_s / 1e9,
-            "peak_source": f"FP32 FFMA: {SM_COUNT} SMs x {FP32_LANES} lanes x 2 x {clk_max:.0f} MHz"}
+            "peak_source": f"FP32 FFMA: {sm_count()} SMs x {FP32_LANES} lanes x 2 x {clk_max:.0f} MHz"}
     line = {
         "metric": METRIC, "value": iters_per_s, "unit": "Krotov iters/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c64+f64" if wl.precision == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": wl.name, "d": wl.d, "M": wl.M, "nt": wl.nt, "dt": wl.dt,
                    "precision": "FP32-mixed" if wl.precision == "fp32" else "FP64",
-                   "ckpt_interval": wl.ckpt_interval, "cheb_terms": K, "tile_traj": info.tile_traj,
-                   "threads": info.threads, "l2": "inputs larger than L2 (co-state checkpoints and segment "
-                   f"buffers {info.device_bytes / 1e9:.1f} GB per GPU)", "parallelism": f"replicas{world}"},
+                   "costate_storage": ("every co-state kept" if info.ckpt_interval == 0 else
+                                       f"t_0..t_{info.ckpt_kept_prefix} kept, then every {info.ckpt_interval}"),
+                   "costate_slots": info.costate_slots, "cheb_terms": K, "tile_traj": info.tile_traj,
+                   "threads": info.threads, "l2": "inputs larger than L2 (co-states "
+                   f"{info.device_bytes / 1e9:.1f} GB per GPU)", "parallelism": f"replicas{world}",
+                   "timed_path": "krotov_update: one CUDA graph launch per iteration"},
         "traj_steps_per_s": traj_steps_per_s,
         "hbm_roofline": {"achieved_gbs": hbm_achieved, "peak_gbs": peaks["hbm_gbs"],
                          "frac": hbm_achieved / peaks["hbm_gbs"], "peak_source": peak_src,
@@ -640,9 +678,10 @@ def run_ours(args, rank, world):
         "roofline": roof,
         "e2e": {"value": world * 1000.0 / e2e_ms, "unit": "Krotov iters/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "kernels": {f"{k}_kernel": {"launches": n, "total_ms": ms, "avg_ms": ms / max(n, 1)}
-                    for k, (ms, n) in prof.items() if n > 0},
-        "gpu_launches": int(prof["fwd"][1] + prof["bwd"][1] + 4 * args.steps),
+        "kernels_one_profiled_iteration": {f"{k}_kernel": {"launches": n, "total_ms": ms, "avg_ms": ms / max(n, 1)}
+                                           for k, (ms, n) in prof.items() if n > 0},
+        "profiled_iteration_ms": prof_ms_iter,
+        "gpu_launches": int((prof["fwd"][1] + prof["bwd"][1] + 4) * args.steps),
         "clocks": clocks,
     }
     if rank == 0 and not args.no_precision_comparison:
@@ -658,6 +697,35 @@ def run_ours(args, rank, world):
     return 0
 
 
+def run_profile(args):
+    """Small case of the four-node interval kernels for ncu captures that must stay small: d = 6561,
+    dt = 0.01, M trajectories (--profile-M, default 1024 = the benchmark's launch size), 12 intervals:
+    guess sweep, backward sweep, updating forward sweep, with the library's per-launch event timing
+    printed at the end.  A few GB on the device."""
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU (GB300); the CUDA path has no CPU fallback")
+    from paper_1801_04382_gb300 import Problem, cascaded_chain
+    nt, T, M = 12, 0.12, args.profile_M
+    net = cascaded_chain(4, 2)
+    eps0 = si.guess_pulses(4, nt, T, 1.0)
+    S = si.shape_functions(4, nt, T)
+    lam = np.full(4, 10.0)
+    U = si.uniforms(4, 4, M, 25)
+    with Problem(net, T, nt, M, eps0, S, lam, U, precision=args.precision) as p:
+        info = p.info
+        print(f"d={info.d} tile_traj={info.tile_traj} threads={info.threads} cheb_terms={info.cheb_terms} "
+              f"tiles={info.n_tiles}")
+        p.forward(False)
+        p.set_profiling(True)
+        p.backward()
+        p.forward(True)
+        prof = p.profile()
+        for k, (ms, n) in prof.items():
+            print(f"{k}_kernel: {n} launches, {ms:.3f} ms, {ms / max(n, 1):.4f} ms/launch")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -667,7 +735,11 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-comparison", action="store_true")
-    ap.add_argument("--workload", choices=["cfg5", "mix64", "grad729", "noise", "cross"], default="cfg5")
+    ap.add_argument("--workload", choices=["cfg5", "mix64", "grad729", "noise", "cross", "profile"], default="cfg5")
+    ap.add_argument("--ckpt", type=int, default=-1,
+                    help="co-state storage of the cfg5 problem: -1 automatic from free memory (default), "
+                         "0 all, K > 0 every K-th")
+    ap.add_argument("--profile-M", type=int, default=1024)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -681,6 +753,8 @@ def main():
         return run_noise(args, rank, world)
     if args.workload == "cross":
         return run_cross(args, rank, world)
+    if args.workload == "profile":
+        return run_profile(args)
     return run_ours(args, rank, world)
 
 

@@ -15,7 +15,9 @@
  * General conventions
  *  - All pointers in the descriptors are HOST pointers; the library copies what it needs at
  *    krotov_init and never keeps a caller pointer.  Output pointers are host pointers written
- *    before the call returns (such calls synchronise the stream).
+ *    before the call returns (such calls synchronise the stream), except where a parameter is
+ *    marked DEVICE (krotov_gradient, krotov_set_pulses_device, krotov_get_JT; krotov_set_uniforms
+ *    takes either): those are read or written on `stream` without a host round trip.
  *  - Complex numbers are stored as two consecutive doubles (re, im).
  *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream.  All
  *    device work of a call is enqueued on that stream.
@@ -104,7 +106,12 @@ typedef struct {
   kt_precision prec;        /* KT_FP64, or KT_FP32_MIXED: complex64 states with FP32
                                arithmetic, FP64 norms, renormalisation, overlaps and sums */
   int ckpt_interval;        /* 0: keep the co-state at every t_j; K > 0: keep every K-th
-                               and recompute the rest segment by segment */
+                               and recompute the rest segment by segment; -1: automatic from the
+                               device memory free at krotov_init -- every co-state if they fit,
+                               else the longest prefix t_0..t_A plus checkpoints every K after it
+                               with the fewest recomputed co-states (a reserve of max(2 GiB, 2 %)
+                               and 2 sqrt(nt) + 4 states stays free); krotov_get_info reports the
+                               choice.  Results are bit-identical whatever the storage. */
   const double *eps_guess;  /* [n_ctrl][nt] guess pulse eps_c^(0) on each interval */
   const double *shape;      /* [n_ctrl][nt] update shape S_c(t_{j-1/2}) in [0, 1] */
   const double *lambda_a;   /* [n_ctrl] Krotov step weights lambda_c > 0 */
@@ -126,6 +133,8 @@ typedef struct {
   int jump_scheme;          /* 0: jump times located by bisection of the norm, several jumps per
                                interval possible (Sec. 2.1); 1: the first-order scheme of Sec. 2.1,
                                at most one jump per interval, applied at its end (s* = dt) */
+  int ckpt_prefix;          /* with ckpt_interval = K > 0: the co-states of t_0 .. t_ckpt_prefix
+                               are all kept as well (checkpoints every K after it); 0 = none */
 } kt_config;
 
 /* Create a problem: validate, assemble H_eff in structured form (a1), choose the Chebyshev
@@ -147,15 +156,31 @@ KT_API kt_status propagate_forward(kt_problem *p, int sequential_update, double 
  * ckpt_interval intervals, or all of them when ckpt_interval = 0) for krotov_gradient.  Any
  * later forward sweep or krotov_set_pulses discards them. */
 
-/* Exact gradient dJ_T/deps [n_ctrl][nt] (host output) of the trajectory functional
- * J_T = 1 - (1/M) sum_k |<tgt|psi_k(T)>|^2 / ||psi_k(T)||^2 (Eq. functional_traj) at the current
- * pulse, for the jump record of the last propagate_forward(p, 2, ...) held fixed:
+/* Exact gradient dJ_T/deps_ij (Sec. 2.2, Eq. gradient: the discrete derivative of the propagator)
+ * of the trajectory functional J_T = 1 - (1/M) sum_k |<tgt|psi_k(T)>|^2 / ||psi_k(T)||^2
+ * (Eq. functional_traj), for the jump record of a forward sweep held fixed:
  *   dJ_T/deps_ij = -(2/M) sum_k Re <chi~_k(t_j)| dU_kj/deps_i |psi_k(t_{j-1})>,
  * chi~_k(T) = (tau_k |tgt> - |tau_k|^2 psihat_k) / ||psi_k(T)||, chi~ propagated backwards along
- * each trajectory's own record, dU/deps exact (the discrete derivative of the propagator,
- * Sec. 2.2, Eq. gradient).  Forward states are replayed segment by segment from the kept ones.
+ * each trajectory's own record, dU/deps exact.  Forward states are replayed segment by segment from
+ * the kept ones.
+ *   eps_dev  DEVICE [n_ctrl][nt] pulse, or NULL.  Non-NULL: the pulse is set from it (as
+ *            krotov_set_pulses_device) and a forward sweep that keeps its states runs first (it
+ *            consumes the next pass of uniforms); the gradient is that sweep's.  NULL: the gradient
+ *            of the last propagate_forward(p, 2, ...) at the current pulse (KT_ERR_STATE if none).
+ *   dJ_dev   DEVICE [n_ctrl][nt] output, written on `stream` (the caller owns it).
+ * Everything stays on the device; the call synchronises `stream` once to read the status word.
  * Needs four state buffers of d in shared memory (KT_ERR_UNSUPPORTED otherwise). */
-KT_API kt_status krotov_gradient(kt_problem *p, double *dJ_out, void *stream);
+KT_API kt_status krotov_gradient(kt_problem *p, const double *eps_dev, double *dJ_dev, void *stream);
+
+/* Replace the current pulse from DEVICE memory eps_dev [n_ctrl][nt] (device-to-device copies on
+ * `stream`, no host round trip); invalidates co-states, records and kept states like
+ * krotov_set_pulses.  The values are checked on the device (finite, |eps| <= eps_bound); a failure
+ * is reported by the next sweep as KT_ERR_NONFINITE / KT_ERR_RANGE. */
+KT_API kt_status krotov_set_pulses_device(kt_problem *p, const double *eps_dev, void *stream);
+
+/* J_T = 1 - (1/M) sum_k |tau_k|^2 of the last forward sweep (Eq. functional_traj) written to one
+ * DEVICE double JT_dev on `stream` (no synchronisation). */
+KT_API kt_status krotov_get_JT(kt_problem *p, double *JT_dev, void *stream);
 
 /* Backward co-state sweep (Sec. 2.3): chi_k(T) = tau_k |tgt>, then
  * chi_k(t_{j-1}) = U_kj^dag chi_k(t_j) under the pulse of the last forward sweep, where U_kj
@@ -205,10 +230,11 @@ KT_API kt_status krotov_get_costate(kt_problem *p, int j, double *chi_out);
  * (KT_ERR_ARG otherwise).  Synchronises `stream`. */
 KT_API kt_status krotov_pulse_noise(kt_problem *p, const double *ref, double *nu_out, void *stream);
 
-/* Replace the uniform random numbers (host array [n_passes][M][draws_per_traj], 1 <= n_passes
- * <= the value given at init, draws as at init); later passes cycle through these n_passes rows,
- * starting again at row 0.  Asynchronous on `stream`; the host
- * array must stay valid until the stream reaches the copy (pinned memory recommended). */
+/* Replace the uniform random numbers ([n_passes][M][draws_per_traj] in host OR device memory --
+ * the copy direction is taken from the pointer; 1 <= n_passes <= the value given at init, draws as
+ * at init); later passes cycle through these n_passes rows, starting again at row 0.  Asynchronous
+ * on `stream`; the array must stay valid until the stream reaches the copy (pinned host memory or
+ * device memory). */
 KT_API kt_status krotov_set_uniforms(kt_problem *p, const double *uniforms, int n_passes, void *stream);
 
 /* Per-launch timing of the interval kernels with CUDA events recorded on the calling stream
@@ -239,6 +265,12 @@ typedef struct {
   long long device_bytes;
   long long passes;
   double eps_bound;         /* the pulse bound the spectral estimate used (given or automatic) */
+  long long sweeps;         /* forward sweeps completed since krotov_init (never reset): tells a
+                               caller whether another sweep ran since the one it depends on */
+  int ckpt_interval;        /* co-state storage in use: 0 = every co-state kept; K > 0 = the
+                               co-states of t_0 .. t_{ckpt_kept_prefix} kept, then every K-th */
+  int ckpt_kept_prefix;
+  int costate_slots;        /* co-state slots held in device memory */
 } kt_info;
 KT_API kt_status krotov_get_info(kt_problem *p, kt_info *info);
 
@@ -289,8 +321,9 @@ KT_API kt_status kt_generator_dense(const kt_model_desc *model, const kt_config 
  *   psi, chi   DEVICE pointers, [M][d][2] FP64 states (plain layout, d = n_loc^n_nodes)
  *   hc_local   HOST [n_ctrl][n_loc][n_loc][2] control factors, ctrl_node [n_ctrl] (host)
  *   shape_j, lambda_a  HOST [n_ctrl];  deps_out DEVICE [n_ctrl] FP64 (written on `stream`)
- * The first call on a device looks up the scratch array's device address (once per device);
- * make that first call before any stream capture begins.  Every call shares the one array and
+ * Every call looks up the scratch array's device address on the current device (a host-only
+ * query); the first call on a device may load the library's device code there, so make that
+ * first call before any stream capture begins.  Every call shares the one array and
  * the call clears its ticket itself, so calls whose kernels overlap on the GPU (different
  * streams, or different host threads on the same device) race and must be serialised by the
  * caller.  Sizes beyond the scratch (n_ctrl > 8) are rejected with KT_ERR_UNSUPPORTED;

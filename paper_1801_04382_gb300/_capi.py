@@ -38,7 +38,7 @@ class Config(ct.Structure):
         ("ckpt_interval", ct.c_int), ("eps_guess", dp), ("shape", dp), ("lambda_a", dp),
         ("uniforms", dp), ("n_passes", ct.c_int), ("draws_per_traj", ct.c_int),
         ("eps_bound", ct.c_double), ("cheb_tol", ct.c_double), ("tile_traj", ct.c_int),
-        ("update_rule", ct.c_int), ("jump_scheme", ct.c_int),
+        ("update_rule", ct.c_int), ("jump_scheme", ct.c_int), ("ckpt_prefix", ct.c_int),
     ]
 
 
@@ -47,7 +47,8 @@ class Info(ct.Structure):
         ("d", ct.c_int), ("max_jumps", ct.c_int), ("cheb_terms", ct.c_int), ("tile_traj", ct.c_int),
         ("n_tiles", ct.c_int), ("threads", ct.c_int), ("e_min", ct.c_double), ("e_max", ct.c_double),
         ("damping", ct.c_double), ("device_bytes", ct.c_longlong), ("passes", ct.c_longlong),
-        ("eps_bound", ct.c_double),
+        ("eps_bound", ct.c_double), ("sweeps", ct.c_longlong), ("ckpt_interval", ct.c_int),
+        ("ckpt_kept_prefix", ct.c_int), ("costate_slots", ct.c_int),
     ]
 
 
@@ -56,7 +57,9 @@ SIGNATURES = {
     "krotov_init": (ct.c_int, [ct.POINTER(ModelDesc), ct.POINTER(Config), ct.c_void_p, ct.POINTER(ct.c_void_p)]),
     "propagate_forward": (ct.c_int, [ct.c_void_p, ct.c_int, dp, ct.c_void_p]),
     "propagate_backward": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
-    "krotov_gradient": (ct.c_int, [ct.c_void_p, dp, ct.c_void_p]),
+    "krotov_gradient": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "krotov_set_pulses_device": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "krotov_get_JT": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "krotov_update": (ct.c_int, [ct.c_void_p, ct.c_int, dp, dp, ct.c_void_p]),
     "fidelity": (ct.c_int, [ct.c_void_p, dp, dp]),
     "krotov_get_pulses": (ct.c_int, [ct.c_void_p, dp]),
@@ -66,7 +69,7 @@ SIGNATURES = {
     "krotov_get_states": (ct.c_int, [ct.c_void_p, dp]),
     "krotov_get_costate": (ct.c_int, [ct.c_void_p, ct.c_int, dp]),
     "krotov_get_info": (ct.c_int, [ct.c_void_p, ct.POINTER(Info)]),
-    "krotov_set_uniforms": (ct.c_int, [ct.c_void_p, dp, ct.c_int, ct.c_void_p]),
+    "krotov_set_uniforms": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_void_p]),
     "krotov_pulse_noise": (ct.c_int, [ct.c_void_p, dp, dp, ct.c_void_p]),
     "krotov_set_profiling": (ct.c_int, [ct.c_void_p, ct.c_int]),
     "krotov_get_profile": (ct.c_int, [ct.c_void_p, dp, ct.POINTER(ct.c_longlong)]),

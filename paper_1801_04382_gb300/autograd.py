@@ -1,14 +1,18 @@
 """torch.autograd binding of the trajectory functional.
 
 ``KrotovTrajFunction.apply(eps, problem)`` returns J_T = 1 - F (Eq. functional_traj) for the
-pulse ``eps`` [n_ctrl, nt] (float64 tensor); its backward is the library's gradient sweep
+pulse ``eps`` [n_ctrl, nt] (a CUDA float64 tensor); its backward is the library's gradient sweep
 (co-state propagation along each trajectory's frozen jump record with exact propagator
 derivatives, ``krotov_gradient``), i.e. dJ_T/deps with the record of this forward pass fixed.
-Both directions run in the CUDA library; torch only carries the tensors.
+Both directions run in the CUDA library on torch's current stream; the pulse, J_T and the
+gradient stay in device memory (pointers cross the C ABI, nothing goes through the host).
+
+The gradient belongs to the forward sweep of the same graph node: if the problem has run another
+forward sweep since (a second evaluation, a line search, ``set_pulses``), backward raises instead
+of returning the newer sweep's gradient.
 """
 from __future__ import annotations
 
-import numpy as np
 import torch
 
 from .problem import Problem
@@ -17,18 +21,26 @@ from .problem import Problem
 class KrotovTrajFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, eps: torch.Tensor, problem: Problem):
-        e = eps.detach().to("cpu", torch.float64).numpy()
-        problem.set_pulses(e)
-        F = problem.forward(keep_for_gradient=True)
+        if not eps.is_cuda:
+            raise ValueError("eps must be a CUDA tensor")
+        stream = torch.cuda.current_stream(eps.device)
+        e = eps.detach().to(torch.float64).contiguous()
+        problem.set_pulses_device(e, stream=stream)
+        problem.forward(keep_for_gradient=True, stream=stream, want_F=False)
+        JT = problem.JT_device(stream=stream)
         ctx.problem = problem
-        ctx.eps_device = eps.device
-        return torch.tensor(1.0 - F, dtype=torch.float64, device=eps.device)
+        ctx.sweep = problem.sweeps()
+        ctx.eps_dtype = eps.dtype
+        return JT.to(eps.dtype)
 
     @staticmethod
     def backward(ctx, grad_out: torch.Tensor):
-        g = ctx.problem.gradient()
-        gt = torch.from_numpy(np.ascontiguousarray(g)).to(ctx.eps_device)
-        return grad_out * gt, None
+        p = ctx.problem
+        if p.sweeps() != ctx.sweep:
+            raise RuntimeError("the problem ran another forward sweep after this J_T was evaluated; its "
+                               "gradient belongs to the latest sweep -- evaluate J_T again before backward")
+        g = p.gradient(stream=torch.cuda.current_stream(grad_out.device))
+        return (grad_out * g).to(ctx.eps_dtype), None
 
 
 def trajectory_functional(eps: torch.Tensor, problem: Problem) -> torch.Tensor:

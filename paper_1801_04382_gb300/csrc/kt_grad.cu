@@ -347,9 +347,7 @@ __global__ void __launch_bounds__(NL > 0 ? 96 : (EPT == 4 ? 256 : 1024), NL > 0 
 template <typename R, int EPT, int NL, int ACS>
 static cudaError_t launch_grad_t(const KtGeom &g1, int T_layout, int tel, const KtGenImage &imf,
                                  const KtGenImage &imb, const KtOps &ops, const GradArgs &a, cudaStream_t st) {
-  // once per instantiation; a function-local static is initialised thread-safely
-  static const cudaError_t attr =
-      cudaFuncSetAttribute(grad_kernel<R, EPT, NL, ACS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  const cudaError_t attr = kt_allow_large_smem((const void *)grad_kernel<R, EPT, NL, ACS>);
   if (attr != cudaSuccess) return attr;
   const size_t smem = grad_carve(g1, sizeof(typename C2<R>::T), nullptr, nullptr, nullptr);
   grad_kernel<R, EPT, NL, ACS><<<g1.M, g1.nthreads, smem, st>>>(g1, T_layout, tel, imf, imb, ops, a);

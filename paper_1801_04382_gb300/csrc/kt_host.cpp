@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/krotov_traj.h"
@@ -135,6 +136,73 @@ Bounds gen_bounds(const Gen &g, double amax, double E) {
   return b;
 }
 
+// Field-of-values bounds of the forward generator G(eps) = G0 + sum_c eps_c dG/deps_c for all
+// |eps_c| <= E, from Gershgorin discs of whole rows of the full-space operator: the real parts of
+// W(G) are those of W((G + G^dag)/2) and the imaginary parts those of W((G - G^dag)/(2i)), each
+// inside the union of its row discs (centre the diagonal entry at the worst eps, radius the
+// off-diagonal row sum with every control at |eps_c| = E).  Whole rows are tighter than the sum of
+// per-node bounds (a row never meets the worst case of every node at once).  The backward
+// generator -G^dag has Hermitian part -Herm(G) and the same anti-Hermitian part, so its bounds
+// follow.  Entries are enumerated with the kernels' own indexing (digits, node strides, pair hops).
+Bounds row_bounds(const Gen &g, const std::vector<int> &lo_dl, const std::vector<cd> &lo_val,
+                  const std::vector<int> &ra_dl, const std::vector<cd> &ra_val, int d, const int *stride, double E) {
+  const int nl = g.nl, N = g.N, nc = (int)g.ctrl_node.size();
+  // entries of G0 (m = 0) and of dG/deps_c (m = 1 + c), keyed by row * d + column
+  std::vector<std::unordered_map<long long, cd>> mats(1 + nc);
+  auto add = [&](int m, long long x, long long y, cd v) {
+    if (v != 0.0) mats[m][x * d + y] += v;
+  };
+  for (int x = 0; x < d; ++x) {
+    int dig[KT_MAX_NODES];
+    for (int i = 0; i < N; ++i) dig[i] = (x / stride[i]) % nl;
+    for (int i = 0; i < N; ++i)
+      for (int y = 0; y < nl; ++y) {
+        const long long col = x + (long long)(y - dig[i]) * stride[i];
+        add(0, x, col, g.loc[((size_t)i * nl + dig[i]) * nl + y]);
+        for (int c = 0; c < nc; ++c)
+          if (g.ctrl_node[c] == i) add(1 + c, x, col, g.ctrl[((size_t)c * nl + dig[i]) * nl + y]);
+      }
+    for (const Pair &q : g.pairs) {
+      const int xd = dig[q.dst], xs = dig[q.src];
+      if (ra_val[xd] == 0.0 || lo_val[xs] == 0.0) continue;
+      if (q.dst == q.src) continue;
+      const long long col = x + (long long)ra_dl[xd] * stride[q.dst] + (long long)lo_dl[xs] * stride[q.src];
+      add(0, x, col, q.coef * ra_val[xd] * lo_val[xs]);
+    }
+  }
+  // Hermitian (h) and anti-Hermitian (a) parts, per row: |diagonal|-range and off-diagonal sums
+  std::vector<double> hc(d, 0.0), hspread(d, 0.0), hrad(d, 0.0), arad(d, 0.0);
+  for (int m = 0; m <= nc; ++m) {
+    const double w = m == 0 ? 1.0 : E;
+    std::unordered_map<long long, cd> herm, anti;
+    for (const auto &kv : mats[m]) {
+      const long long x = kv.first / d, y = kv.first % d;
+      const cd v = kv.second;
+      herm[x * d + y] += 0.5 * v;
+      herm[y * d + x] += 0.5 * std::conj(v);
+      anti[x * d + y] += v / cd(0.0, 2.0);
+      anti[y * d + x] -= std::conj(v) / cd(0.0, 2.0);
+    }
+    for (const auto &kv : herm) {
+      const long long x = kv.first / d, y = kv.first % d;
+      if (x == y) {
+        if (m == 0) hc[x] += kv.second.real();
+        else hspread[x] += w * std::abs(kv.second.real());
+      } else {
+        hrad[x] += w * std::abs(kv.second);
+      }
+    }
+    for (const auto &kv : anti) arad[kv.first / d] += w * std::abs(kv.second);   // diagonal counted too
+  }
+  Bounds b{1e300, -1e300, 0.0};
+  for (int x = 0; x < d; ++x) {
+    b.lo = std::min(b.lo, hc[x] - hspread[x] - hrad[x]);
+    b.hi = std::max(b.hi, hc[x] + hspread[x] + hrad[x]);
+    b.damp = std::max(b.damp, arad[x]);
+  }
+  return b;
+}
+
 }  // namespace
 
 kt_status kt_fail(kt_status s, const char *msg) { return fail(s, "%s", msg); }
@@ -145,6 +213,8 @@ struct kt_problem {
   int fp64 = 1, ept = 4, cross = 0;
   size_t esz = 16;
   int nt = 0, M = 0, n_passes = 0, n_passes_alloc = 0, ckpt = 0;
+  int ckpt_dense = 0;           // ckpt > 0: co-states t_0 .. t_A all kept (A = ckpt_dense), then every ckpt-th
+  bool ckpt_auto = false;       // storage chosen from free device memory (ckpt_interval = -1)
   double T = 0.0;
   size_t state_bytes = 0;       // one tile-layout array of all trajectories
   size_t bytes = 0;
@@ -157,7 +227,7 @@ struct kt_problem {
 
   double *eps_old = nullptr, *eps_new = nullptr, *deps = nullptr, *shape = nullptr, *U = nullptr;
   void *psi_init = nullptr, *psi[2] = {nullptr, nullptr};
-  void *chi = nullptr;          // ckpt == 0: [nt+1] states, else checkpoints
+  void *chi = nullptr;          // ckpt == 0: [nt+1] states, else the kept prefix and the checkpoints
   int n_chi_slots = 0;
   void *seg = nullptr;          // ckpt > 0: [ckpt + 1] states (segment / running buffers)
   double *rstate = nullptr;
@@ -173,6 +243,7 @@ struct kt_problem {
 
   int *pass = nullptr;          // device [3]: next uniforms row, rows held, row of the running pass
   long long passes = 0;         // completed forward sweeps since the uniforms were uploaded
+  long long sweeps = 0;         // completed forward sweeps since krotov_init (never reset)
   double *nu = nullptr;         // device [KT_MAX_CTRL]: pulse noise (krotov_pulse_noise)
   void *cwork = nullptr;        // cross-trajectory update: [x][k] states and control products
   double *cpart = nullptr;      // its per-tile partial sums
@@ -267,13 +338,26 @@ void *state_slot(const kt_problem *p, void *base, long long slot) {
   return (char *)base + (size_t)slot * p->state_bytes;
 }
 
-// location of chi(t_j): ckpt == 0 -> chi[j]; else checkpoint slots j/ckpt (and the last one for nt)
+// Co-state storage: ckpt == 0 keeps chi(t_j) for every j in slot j.  Otherwise slots 0..A hold
+// chi(t_0)..chi(t_A) (A = ckpt_dense, possibly 0), then one slot per checkpoint t_{A + mK}
+// (K = ckpt), and the last slot holds chi(t_nt); the co-states in between are recomputed segment
+// by segment before the forward sweep needs them.
 void *ckpt_slot(const kt_problem *p, int j) {
-  if (p->ckpt == 0) return state_slot(p, p->chi, j);
+  if (p->ckpt == 0 || j <= p->ckpt_dense) return state_slot(p, p->chi, j);
   if (j == p->nt) return state_slot(p, p->chi, p->n_chi_slots - 1);
-  return state_slot(p, p->chi, j / p->ckpt);
+  return state_slot(p, p->chi, p->ckpt_dense + (j - p->ckpt_dense) / p->ckpt);
 }
-bool is_ckpt(const kt_problem *p, int j) { return p->ckpt == 0 || j == p->nt || j % p->ckpt == 0; }
+bool is_ckpt(const kt_problem *p, int j) {
+  return p->ckpt == 0 || j <= p->ckpt_dense || j == p->nt || (j - p->ckpt_dense) % p->ckpt == 0;
+}
+int n_ckpt_slots(int nt, int A, int K) { return K == 0 ? nt + 1 : A + 1 + (nt - A + K - 1) / K; }
+// End of the forward-sweep segment that starts at seg_a: the kept prefix is one segment (nothing to
+// recompute), then checkpoint to checkpoint.
+int seg_end(const kt_problem *p, int seg_a) {
+  if (p->ckpt == 0) return p->nt;
+  if (seg_a < p->ckpt_dense) return p->ckpt_dense;
+  return std::min(seg_a + p->ckpt, p->nt);
+}
 
 kt_status read_status(kt_problem *p, cudaStream_t st) {
   int s = 0;
@@ -288,7 +372,7 @@ kt_status read_status(kt_problem *p, cudaStream_t st) {
   switch (s) {
     case KT_DEV_NONFINITE: return fail(KT_ERR_NONFINITE, "non-finite norm, overlap or pulse value on the device");
     case KT_DEV_RECORD_FULL: return fail(KT_ERR_RECORD_FULL, "a trajectory needed more jumps than draws_per_traj allows");
-    case KT_DEV_RANGE: return fail(KT_ERR_RANGE, "an updated pulse value left [-eps_bound, eps_bound]");
+    case KT_DEV_RANGE: return fail(KT_ERR_RANGE, "a pulse value (updated, or set from device memory) left [-eps_bound, eps_bound]");
     case KT_DEV_ZERO_JUMP: return fail(KT_ERR_NONFINITE, "jump into a zero state (||L psi|| = 0 at a jump)");
     case KT_DEV_TIMEOUT: return fail(KT_ERR_TIMEOUT, "a bounded device-side wait for a bulk copy expired");
     default: return fail(KT_ERR_CUDA, "device status %d", s);
@@ -411,10 +495,9 @@ kt_status enqueue_forward(kt_problem *p, int update, cudaStream_t st, bool save_
     KT_CUDA(kt_launch_fwd(p->fp64, p->ept, p->g, p->im_fwd, p->ops, a, st));
     if ((s = prof_end(p, st)) != KT_OK) return s;
   }
-  const int K = (p->ckpt == 0) ? p->nt : p->ckpt;
-  for (int seg_a = 0; seg_a < p->nt; seg_a += K) {
-    const int seg_b = std::min(seg_a + K, p->nt);
-    if (update && p->ckpt > 0) {
+  for (int seg_a = 0; seg_a < p->nt; seg_a = seg_end(p, seg_a)) {
+    const int seg_b = seg_end(p, seg_a);
+    if (update && p->ckpt > 0 && seg_a >= p->ckpt_dense) {
       kt_status s = recompute_segment(p, seg_a, seg_b, st);
       if (s != KT_OK) return s;
     }
@@ -440,6 +523,7 @@ kt_status enqueue_forward(kt_problem *p, int update, cudaStream_t st, bool save_
 // Host bookkeeping of a completed forward sweep.
 void commit_forward(kt_problem *p, int update, bool save_psi) {
   p->passes++;
+  p->sweeps++;
   p->final_buf = p->nt & 1;
   if (update) std::swap(p->eps_old, p->eps_new);
   p->cur = 1 - p->cur;          // the records just written become the "last completed" ones
@@ -484,7 +568,11 @@ kt_status grad_setup(kt_problem *p, cudaStream_t st) {
                 p->fp64 ? "use FP32-mixed" : "too large");
   p->g1 = g1;
   p->grad_ept = ept;
-  p->Kg = p->ckpt > 0 ? p->ckpt : p->nt;
+  // forward states kept every Kg intervals: the co-state spacing if one was given; with automatic
+  // storage Kg ~ sqrt(nt), the fewest kept states (nt/Kg + Kg) for the same replay cost (about one
+  // forward sweep whatever Kg > 1)
+  if (p->ckpt_auto) p->Kg = std::max(1, (int)std::lround(std::sqrt((double)p->nt)));
+  else p->Kg = p->ckpt > 0 ? p->ckpt : p->nt;
   kt_status s;
   if ((s = dev_alloc(p, &p->psi_ck, p->state_bytes * (p->nt / p->Kg + 1))) != KT_OK) return s;
   if ((s = dev_alloc(p, &p->psi_seg, p->state_bytes * p->Kg)) != KT_OK) return s;
@@ -737,7 +825,7 @@ struct HostImage {
 
 struct HostPlan {
   KtGeom g{};
-  int fp64 = 1, ept = 4, ckpt = 0, cross = 0;
+  int fp64 = 1, ept = 4, ckpt = 0, ckpt_dense = 0, cross = 0;
   double e_min = 0, e_max = 0, damping = 0;
   HostImage fwd, bwd;
   std::vector<int> lo_dl, ra_dl, hc_dl;
@@ -857,7 +945,7 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
   if (cfg->n_passes < 1 || cfg->draws_per_traj < 1 || cfg->draws_per_traj % 2 == 0)
     return fail(KT_ERR_ARG, "need n_passes >= 1 and odd draws_per_traj >= 1");
   if (cfg->prec != KT_FP64 && cfg->prec != KT_FP32_MIXED) return fail(KT_ERR_ARG, "unknown precision");
-  if (cfg->ckpt_interval < 0) return fail(KT_ERR_ARG, "ckpt_interval < 0");
+  if (cfg->ckpt_interval < -1) return fail(KT_ERR_ARG, "ckpt_interval must be -1 (automatic), 0 or > 0");
   if (cfg->tile_traj < -1) return fail(KT_ERR_ARG, "tile_traj must be -1 (autotuned), 0 (automatic) or a power of two <= 32");
   if (cfg->update_rule != 0 && cfg->update_rule != 1) return fail(KT_ERR_ARG, "update_rule must be 0 or 1");
   if (cfg->jump_scheme != 0 && cfg->jump_scheme != 1) return fail(KT_ERR_ARG, "jump_scheme must be 0 or 1");
@@ -938,7 +1026,19 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
   }
   for (long i = 0; i < (long)nc * nt; ++i)
     if (std::fabs(cfg->eps_guess[i]) > E) return fail(KT_ERR_RANGE, "guess pulse exceeds eps_bound");
-  const Bounds bf = gen_bounds(gf, amax, E), bb = gen_bounds(gb, amax, E);
+  // spectral interval: the tighter of the per-node bounds and whole-row Gershgorin discs (rows
+  // enumerated on the host, at most d = 2^22 of them)
+  Bounds bf = gen_bounds(gf, amax, E), bb = gen_bounds(gb, amax, E);
+  if (d <= (1 << 22)) {
+    int strd[KT_MAX_NODES];
+    for (int i = 0; i < N; ++i) strd[i] = ipow(nl, N - 1 - i);
+    const Bounds rf = row_bounds(gf, lo_dl, lo_val, ra_dl, ra_val, d, strd, E);
+    const Bounds rb{-rf.hi, -rf.lo, rf.damp};        // -G^dag: Hermitian part negated, same anti part
+    if (rf.hi - rf.lo < bf.hi - bf.lo) { bf.lo = rf.lo; bf.hi = rf.hi; }
+    if (rb.hi - rb.lo < bb.hi - bb.lo) { bb.lo = rb.lo; bb.hi = rb.hi; }
+    bf.damp = std::min(bf.damp, rf.damp);
+    bb.damp = std::min(bb.damp, rf.damp);
+  }
   const double r = 0.5 * std::max(bf.hi - bf.lo, bb.hi - bb.lo) * 1.0001 + 1e-12;
   const double c_fwd = 0.5 * (bf.lo + bf.hi), c_bwd = 0.5 * (bb.lo + bb.hi);
   const double damp = std::max(bf.damp, bb.damp);
@@ -960,6 +1060,8 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
   P.fp64 = cfg->prec == KT_FP64;
   P.cross = cfg->update_rule;
   P.ckpt = (cfg->ckpt_interval > 0 && cfg->ckpt_interval < nt) ? cfg->ckpt_interval : 0;
+  if (cfg->ckpt_prefix < 0) return fail(KT_ERR_ARG, "ckpt_prefix < 0");
+  P.ckpt_dense = P.ckpt > 0 ? std::min(cfg->ckpt_prefix, nt) : 0;
   P.e_min = bf.lo;
   P.e_max = bf.hi;
   P.damping = damp;
@@ -1197,6 +1299,44 @@ extern "C" {
 
 namespace {
 
+// Automatic co-state storage (ckpt_interval = -1) from the device memory still free: keep every
+// co-state if they fit, else the longest prefix t_0..t_A plus checkpoints every K after it, with
+// (A, K) chosen to recompute the fewest co-states (every co-state not kept is recomputed once per
+// forward sweep, so the count is about nt + 1 minus the slots kept).  A reserve stays free: 2 GiB
+// or 2 % of the device, and room for the forward states a gradient sweep keeps (2 sqrt(nt) + 4).
+kt_status choose_storage(kt_problem *p) {
+  size_t free_b = 0, total_b = 0;
+  KT_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  const int nt = p->nt;
+  const long long reserve = std::max<long long>(2LL << 30, (long long)(total_b / 50)) +
+                            (long long)(2.0 * std::sqrt((double)nt) + 4.0) * (long long)p->state_bytes;
+  const long long budget = ((long long)free_b - reserve) / (long long)p->state_bytes;
+  p->ckpt_auto = true;
+  if (budget >= nt + 1) {
+    p->ckpt = 0;
+    p->ckpt_dense = nt;
+    return KT_OK;
+  }
+  long long best = -1;
+  int bestA = 0, bestK = 0;
+  for (int K = 2; K <= nt; ++K) {
+    if (n_ckpt_slots(nt, 0, K) + K + 1 > budget) continue;        // not even without a prefix
+    int lo = 0, hi = nt - 1;                                      // largest A < nt that fits
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (n_ckpt_slots(nt, mid, K) + K + 1 <= budget) lo = mid; else hi = mid - 1;
+    }
+    const long long gap = nt - lo - 1, recompute = gap - gap / K;
+    if (best < 0 || recompute < best) { best = recompute; bestA = lo; bestK = K; }
+  }
+  if (best < 0)
+    return fail(KT_ERR_OOM, "automatic co-state storage: %lld state slots of %zu bytes left, too few for any "
+                "checkpoint spacing", budget, p->state_bytes);
+  p->ckpt = bestK;
+  p->ckpt_dense = bestA;
+  return KT_OK;
+}
+
 // Allocate and upload a problem for the plan P.  A probe (autotuning) keeps no co-state storage.
 kt_status create_problem(const kt_model_desc *md, const kt_config *cfg, const HostPlan &P, cudaStream_t st,
                          bool probe, kt_problem **out) {
@@ -1215,6 +1355,8 @@ kt_status create_problem(const kt_model_desc *md, const kt_config *cfg, const Ho
   p->n_passes = cfg->n_passes;
   p->n_passes_alloc = cfg->n_passes;
   p->ckpt = P.ckpt;
+  p->ckpt_dense = P.ckpt_dense;
+  if (p->ckpt > 0 && p->ckpt_dense >= nt) p->ckpt = p->ckpt_dense = 0;   // the prefix keeps everything
   p->e_min = P.e_min;
   p->e_max = P.e_max;
   p->damping = P.damping;
@@ -1257,11 +1399,6 @@ kt_status create_problem(const kt_model_desc *md, const kt_config *cfg, const Ho
   }
   TRY(dev_alloc(p, &p->psi[0], p->state_bytes));
   TRY(dev_alloc(p, &p->psi[1], p->state_bytes));
-  if (!probe) {
-    p->n_chi_slots = p->ckpt == 0 ? nt + 1 : nt / p->ckpt + 1 + (nt % p->ckpt ? 1 : 0);
-    TRY(dev_alloc(p, &p->chi, p->state_bytes * p->n_chi_slots));
-    if (p->ckpt > 0) TRY(dev_alloc(p, &p->seg, p->state_bytes * (p->ckpt + 1)));
-  }
   const size_t Mp = g.M_pad, mj = g.max_jumps;
   TRY(dev_alloc(p, (void **)&p->rstate, Mp * sizeof(double)));
   for (int b = 0; b < 2; ++b) {
@@ -1288,6 +1425,13 @@ kt_status create_problem(const kt_model_desc *md, const kt_config *cfg, const Ho
       krotov_free(p);
       return fail(KT_ERR_CUDA, "memset failed");
     }
+  }
+  if (!probe) {
+    // co-state storage, allocated last so that an automatic choice sees the memory left
+    if (cfg->ckpt_interval == -1) TRY(choose_storage(p));
+    p->n_chi_slots = n_ckpt_slots(nt, p->ckpt_dense, p->ckpt);
+    TRY(dev_alloc(p, &p->chi, p->state_bytes * p->n_chi_slots));
+    if (p->ckpt > 0) TRY(dev_alloc(p, &p->seg, p->state_bytes * (p->ckpt + 1)));
   }
   p->eps_base = p->eps_old;
   if (kt_launch_pass_reset(p->pass, p->n_passes, st) != cudaSuccess ||
@@ -1545,13 +1689,36 @@ KT_API kt_status krotov_get_costate(kt_problem *p, int j, double *chi_out) {
   return download_state(p, ckpt_slot(p, j), chi_out, 0);
 }
 
-KT_API kt_status krotov_gradient(kt_problem *p, double *dJ_out, void *stream) {
-  if (!p || !dJ_out) return fail(KT_ERR_ARG, "NULL argument");
+KT_API kt_status krotov_set_pulses_device(kt_problem *p, const double *eps_dev, void *stream) {
+  if (!p || !eps_dev) return fail(KT_ERR_ARG, "NULL argument");
   cudaStream_t st = (cudaStream_t)stream;
-  kt_status s = gradient_sweep(p, st);
-  if (s != KT_OK) return s;
-  KT_CUDA(cudaMemcpyAsync(dJ_out, p->dgrad, sizeof(double) * p->g.n_ctrl * p->nt, cudaMemcpyDeviceToHost, st));
-  KT_CUDA(cudaStreamSynchronize(st));
+  const size_t n = (size_t)p->g.n_ctrl * p->nt;
+  KT_CUDA(cudaMemcpyAsync(p->eps_old, eps_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  KT_CUDA(cudaMemcpyAsync(p->eps_new, eps_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  KT_CUDA(kt_launch_pulse_check(p->eps_old, (long long)n, p->g.eps_bound, p->status, st));
+  p->have_fwd = p->have_bwd = false;
+  p->grad_ready = false;
+  return KT_OK;
+}
+
+KT_API kt_status krotov_gradient(kt_problem *p, const double *eps_dev, double *dJ_dev, void *stream) {
+  if (!p || !dJ_dev) return fail(KT_ERR_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  kt_status s;
+  if (eps_dev) {
+    if ((s = krotov_set_pulses_device(p, eps_dev, stream)) != KT_OK) return s;
+    if ((s = grad_setup(p, st)) != KT_OK) return s;
+    if ((s = forward_sweep(p, 0, st, true)) != KT_OK) return s;
+  }
+  if ((s = gradient_sweep(p, st)) != KT_OK) return s;
+  KT_CUDA(cudaMemcpyAsync(dJ_dev, p->dgrad, sizeof(double) * p->g.n_ctrl * p->nt, cudaMemcpyDeviceToDevice, st));
+  return KT_OK;
+}
+
+KT_API kt_status krotov_get_JT(kt_problem *p, double *JT_dev, void *stream) {
+  if (!p || !JT_dev) return fail(KT_ERR_ARG, "NULL argument");
+  if (!p->have_fwd) return fail(KT_ERR_STATE, "no forward sweep yet");
+  KT_CUDA(kt_launch_functional(p->tau, p->M, JT_dev, (cudaStream_t)stream));
   return KT_OK;
 }
 
@@ -1579,7 +1746,7 @@ KT_API kt_status krotov_set_uniforms(kt_problem *p, const double *uniforms, int 
     return fail(KT_ERR_ARG, "n_passes must be in [1, %d] (the value given at init)", p->n_passes_alloc);
   const size_t n = (size_t)n_passes * p->M * p->g.draws;
   cudaStream_t st = (cudaStream_t)stream;
-  KT_CUDA(cudaMemcpyAsync(p->U, uniforms, n * sizeof(double), cudaMemcpyHostToDevice, st));
+  KT_CUDA(cudaMemcpyAsync(p->U, uniforms, n * sizeof(double), cudaMemcpyDefault, st));   // host or device memory
   KT_CUDA(kt_launch_pass_reset(p->pass, n_passes, st));
   p->n_passes = n_passes;
   p->passes = 0;
@@ -1620,6 +1787,10 @@ KT_API kt_status krotov_get_info(kt_problem *p, kt_info *info) {
   info->device_bytes = (long long)p->bytes;
   info->passes = p->passes;
   info->eps_bound = p->g.eps_bound;
+  info->sweeps = p->sweeps;
+  info->ckpt_interval = p->ckpt;
+  info->ckpt_kept_prefix = p->ckpt == 0 ? p->nt : p->ckpt_dense;
+  info->costate_slots = p->n_chi_slots;
   return KT_OK;
 }
 

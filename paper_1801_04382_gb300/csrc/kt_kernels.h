@@ -3,7 +3,27 @@
 
 #include <cuda_runtime.h>
 
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "kt_common.h"
+
+// Lift a kernel's dynamic shared-memory limit to 227 KB on the current device.  The attribute is
+// per device, so it is set once per (kernel, device) pair; only successes are remembered, a failed
+// call is tried again on the next launch.
+inline cudaError_t kt_allow_large_smem(const void *kern) {
+  static std::mutex mu;
+  static std::set<std::pair<const void *, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({kern, dev})) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess) done.insert({kern, dev});
+  return e;
+}
 
 struct FwdArgs {
   int j;                 // interval 1..nt; 0 = prologue (update overlap at t_0 only)
@@ -128,6 +148,11 @@ size_t kt_grad_smem_bytes(const KtGeom &g1, int elem_bytes);
 cudaError_t kt_launch_grad(int fp64, int ept, const KtGeom &g1, int T_layout, int tile_elems_layout,
                            const KtGenImage &im_fwd, const KtGenImage &im_bwd, const KtOps &ops, const GradArgs &a,
                            cudaStream_t st);
+
+// status <- KT_DEV_NONFINITE / KT_DEV_RANGE if a value of eps [n] is not finite or |eps| > bound
+cudaError_t kt_launch_pulse_check(const double *eps, long long n, double bound, int *status, cudaStream_t st);
+// JT[0] = 1 - (1/M) sum_k |tau_k|^2
+cudaError_t kt_launch_functional(const KtCplx *tau, int M, double *JT, cudaStream_t st);
 
 cudaError_t kt_launch_chi_boundary(int fp64, const KtGeom &g, const KtOps &ops, const KtCplx *tau, void *chi,
                                    cudaStream_t st);

@@ -11,7 +11,6 @@
 // the process exits.
 #include <cuda_runtime.h>
 
-#include <mutex>
 
 #include "../../include/krotov_traj.h"
 #include "kt_common.h"
@@ -90,8 +89,6 @@ __global__ void __launch_bounds__(256) overlap_noalloc_kernel(NoAllocArgs a, dou
   if (threadIdx.x == 0) *ticket = 0u;
 }
 
-std::mutex g_mu;
-void *g_scratch_addr[64] = {nullptr};   // device address of kt_noalloc_scratch, per device
 
 }  // namespace
 
@@ -145,22 +142,13 @@ extern "C" KT_API kt_status kt_update_overlap_noalloc(int n_nodes, int n_loc, in
   a.chi = reinterpret_cast<const double2 *>(chi);
   a.deps = deps_out;
 
-  // set-up, once per device: the device address of the scratch array (its host-side name is
-  // only a stand-in and must never be handed to a kernel)
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
-    return kt_fail(KT_ERR_CUDA, "kt_update_overlap_noalloc: no current CUDA device");
+  // the device address of the scratch array on the current device, looked up on every call (a
+  // host-only query; caching it would go stale if the context were torn down and rebuilt).  The
+  // array's host-side name is only a stand-in and must never be handed to a kernel.
   void *scratch = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
-      void *ptr = nullptr;
-      if (cudaGetSymbolAddress(&ptr, kt_noalloc_scratch) != cudaSuccess || !ptr)
-        return kt_fail(KT_ERR_CUDA, "kt_update_overlap_noalloc: cudaGetSymbolAddress of the scratch array failed");
-      g_scratch_addr[dev] = ptr;
-    }
-    scratch = g_scratch_addr[dev];
-  }
+  if (cudaGetSymbolAddress(&scratch, kt_noalloc_scratch) != cudaSuccess || !scratch)
+    return kt_fail(KT_ERR_CUDA, "kt_update_overlap_noalloc: cudaGetSymbolAddress of the scratch array failed "
+                                "(no usable current CUDA device?)");
   cudaStream_t st = (cudaStream_t)stream;
   // the ticket must start at zero even if an earlier call on this device was cut short
   if (cudaMemsetAsync((double *)scratch + KT_NOALLOC_BLOCKS * KT_MAX_CTRL, 0, sizeof(double), st) != cudaSuccess)

@@ -1,5 +1,7 @@
 // Small kernels (pass set-up, record cursors, co-state boundary), shared-memory sizing and the
 // precision dispatch of the interval kernels.
+#include <algorithm>
+
 #include "kt_device.cuh"
 
 namespace kt {
@@ -185,5 +187,43 @@ cudaError_t kt_launch_chi_boundary(int fp64, const KtGeom &g, const KtOps &ops, 
   if (blocks > 4096) blocks = 4096;
   if (fp64) chi_boundary_kernel<double2><<<blocks, 256, 0, st>>>(g, ops, tau, (double2 *)chi);
   else chi_boundary_kernel<float2><<<blocks, 256, 0, st>>>(g, ops, tau, (float2 *)chi);
+  return cudaGetLastError();
+}
+
+namespace kt {
+// Check of a pulse handed over in device memory: every value finite and within the spectral
+// estimate's bound (the host does the same check on host arrays).  Failures go to the status word.
+__global__ void pulse_check_kernel(const double *eps, long long n, double bound, int *status) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double e = eps[i];
+    if (!isfinite(e)) set_status(status, KT_DEV_NONFINITE);
+    else if (fabs(e) > bound) set_status(status, KT_DEV_RANGE);
+  }
+}
+
+// J_T = 1 - (1/M) sum_k |tau_k|^2 (Eq. functional_traj) into one device double: one block, each
+// thread a fixed strided share of the trajectories, then a fixed shuffle and warp order.
+__global__ void functional_kernel(const KtCplx *tau, int M, double *JT) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int k = threadIdx.x; k < M; k += blockDim.x) s += tau[k].re * tau[k].re + tau[k].im * tau[k].im;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    JT[0] = 1.0 - t / (double)M;
+  }
+}
+}  // namespace kt
+
+cudaError_t kt_launch_pulse_check(const double *eps, long long n, double bound, int *status, cudaStream_t st) {
+  kt::pulse_check_kernel<<<(int)std::min<long long>((n + 255) / 256, 1024), 256, 0, st>>>(eps, n, bound, status);
+  return cudaGetLastError();
+}
+
+cudaError_t kt_launch_functional(const KtCplx *tau, int M, double *JT, cudaStream_t st) {
+  kt::functional_kernel<<<1, 256, 0, st>>>(tau, M, JT);
   return cudaGetLastError();
 }

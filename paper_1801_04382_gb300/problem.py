@@ -26,6 +26,14 @@ def _ptr(a, ctype=ct.c_double):
     return a.ctypes.data_as(ct.POINTER(ctype)) if a is not None else None
 
 
+def _check_dev(t, shape, name):
+    """A contiguous float64 CUDA tensor of the given shape (device pointers cross the ABI as is)."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+            and tuple(t.shape) == tuple(shape)):
+        raise ValueError(f"{name}: contiguous float64 CUDA tensor of shape {tuple(shape)} expected")
+
+
 def _stream_handle(stream):
     if stream is None:
         return None
@@ -48,7 +56,7 @@ class Problem:
     def __init__(self, net: NetworkFactors, T: float, nt: int, M: int, eps_guess, shape, lam, uniforms,
                  precision: str = "fp64", ckpt_interval: int = 0, eps_bound: float = 0.0,
                  cheb_tol: float = 0.0, tile_traj: int = 0, psi0_batch=None, stream=None,
-                 update_rule: str = "independent", jump_scheme: str = "bisection"):
+                 update_rule: str = "independent", jump_scheme: str = "bisection", ckpt_prefix: int = 0):
         self._lib = _capi.load()
         self.net = net
         self.T, self.nt, self.M = float(T), int(nt), int(M)
@@ -58,7 +66,7 @@ class Problem:
             raise ValueError("uniforms must have shape [n_passes, M, draws_per_traj]")
         keep, md, cfg = _descriptors(net, self.T, self.nt, self.M, eps_guess, shape, lam, uniforms, precision,
                                      ckpt_interval, eps_bound, cheb_tol, tile_traj, psi0_batch, update_rule,
-                                     jump_scheme)
+                                     jump_scheme, ckpt_prefix)
         handle = ct.c_void_p()
         self._h = None
         _capi.check(self._lib.krotov_init(ct.byref(md), ct.byref(cfg), _stream_handle(stream), ct.byref(handle)),
@@ -83,23 +91,54 @@ class Problem:
         return self
 
     # ------------------------------------------------------------------ calls
-    def forward(self, update: bool = False, stream=None, keep_for_gradient: bool = False) -> float:
-        """One forward sweep; returns F.  update: sequential Krotov update on the fly;
-        keep_for_gradient: plain sweep that keeps the forward states for gradient()."""
+    def forward(self, update: bool = False, stream=None, keep_for_gradient: bool = False, want_F: bool = True):
+        """One forward sweep; returns F (None with want_F=False: no host read of the fidelity).
+        update: sequential Krotov update on the fly; keep_for_gradient: plain sweep that keeps the
+        forward states for gradient()."""
         if update and keep_for_gradient:
             raise ValueError("a sweep either updates the pulse or keeps states for the gradient")
         mode = 1 if update else (2 if keep_for_gradient else 0)
         F = ct.c_double()
-        _capi.check(self._lib.propagate_forward(self._h, mode, ct.byref(F), _stream_handle(stream)),
-                    "propagate_forward")
-        return F.value
+        _capi.check(self._lib.propagate_forward(self._h, mode, ct.byref(F) if want_F else None,
+                                                _stream_handle(stream)), "propagate_forward")
+        return F.value if want_F else None
 
-    def gradient(self, stream=None) -> np.ndarray:
-        """dJ_T/deps [n_ctrl, nt] at the current pulse, jump record of the last
-        forward(keep_for_gradient=True) held fixed."""
-        out = np.zeros((self.n_ctrl, self.nt))
-        _capi.check(self._lib.krotov_gradient(self._h, _ptr(out), _stream_handle(stream)), "krotov_gradient")
+    def gradient(self, eps=None, out=None, stream=None):
+        """dJ_T/deps [n_ctrl, nt] as a CUDA float64 tensor (``out``, allocated if None), computed and
+        written on the device.  eps None: at the current pulse with the jump record of the last
+        forward(keep_for_gradient=True) held fixed; eps a CUDA float64 tensor [n_ctrl, nt]: the pulse
+        is set from it and a forward sweep that keeps its states runs first."""
+        import torch
+        if out is None:
+            out = torch.empty((self.n_ctrl, self.nt), dtype=torch.float64, device="cuda")
+        _check_dev(out, (self.n_ctrl, self.nt), "out")
+        e = None
+        if eps is not None:
+            _check_dev(eps, (self.n_ctrl, self.nt), "eps")
+            e = ct.c_void_p(eps.data_ptr())
+        _capi.check(self._lib.krotov_gradient(self._h, e, ct.c_void_p(out.data_ptr()), _stream_handle(stream)),
+                    "krotov_gradient")
         return out
+
+    def set_pulses_device(self, eps, stream=None) -> None:
+        """Replace the pulse from a CUDA float64 tensor [n_ctrl, nt] (device-to-device, on stream)."""
+        _check_dev(eps, (self.n_ctrl, self.nt), "eps")
+        _capi.check(self._lib.krotov_set_pulses_device(self._h, ct.c_void_p(eps.data_ptr()), _stream_handle(stream)),
+                    "krotov_set_pulses_device")
+
+    def JT_device(self, out=None, stream=None):
+        """J_T = 1 - F of the last forward sweep as a 0-d CUDA float64 tensor, written on the device."""
+        import torch
+        if out is None:
+            out = torch.empty((), dtype=torch.float64, device="cuda")
+        _check_dev(out, (), "out")
+        _capi.check(self._lib.krotov_get_JT(self._h, ct.c_void_p(out.data_ptr()), _stream_handle(stream)),
+                    "krotov_get_JT")
+        return out
+
+    def sweeps(self) -> int:
+        """Forward sweeps completed since the problem was created (never reset)."""
+        return int(self.get_info().sweeps)
 
     def backward(self, stream=None) -> None:
         _capi.check(self._lib.propagate_backward(self._h, _stream_handle(stream)), "propagate_backward")
@@ -164,11 +203,18 @@ class Problem:
         return out
 
     def set_uniforms(self, uniforms, stream=None) -> None:
-        """Upload a fresh [n_passes, M, draws] block of uniforms (pass counter restarts)."""
-        u = _c(uniforms)
-        self._u_keep = u          # host buffer must outlive the asynchronous copy
-        _capi.check(self._lib.krotov_set_uniforms(self._h, _ptr(u), int(u.shape[0]), _stream_handle(stream)),
-                    "krotov_set_uniforms")
+        """Replace the uniforms by a [n_passes, M, draws] block (pass counter restarts): a host array,
+        or a CUDA float64 tensor (copied device to device)."""
+        if hasattr(uniforms, "data_ptr") and getattr(uniforms, "is_cuda", False):
+            if uniforms.dtype != __import__("torch").float64 or not uniforms.is_contiguous() or uniforms.dim() != 3:
+                raise ValueError("uniforms: contiguous float64 CUDA tensor [n_passes, M, draws] expected")
+            self._u_keep = uniforms
+            ptr, n = ct.c_void_p(uniforms.data_ptr()), int(uniforms.shape[0])
+        else:
+            u = _c(uniforms)
+            self._u_keep = u      # host buffer must outlive the asynchronous copy
+            ptr, n = ct.c_void_p(u.ctypes.data), int(u.shape[0])
+        _capi.check(self._lib.krotov_set_uniforms(self._h, ptr, n, _stream_handle(stream)), "krotov_set_uniforms")
 
     def set_profiling(self, on: bool = True) -> None:
         _capi.check(self._lib.krotov_set_profiling(self._h, int(bool(on))), "krotov_set_profiling")
@@ -222,7 +268,7 @@ class Batch:
     (net, T, nt, M, eps_guess, shape, lam, uniforms and the optional keywords)."""
 
     _KEYS = ("precision", "ckpt_interval", "eps_bound", "cheb_tol", "tile_traj", "psi0_batch", "update_rule",
-             "jump_scheme")
+             "jump_scheme", "ckpt_prefix")
 
     def __init__(self, specs, stream=None):
         self._lib = _capi.load()
@@ -303,7 +349,7 @@ _JUMP_SCHEMES = {"bisection": 0, "first_order": 1}
 
 def _descriptors(net, T, nt, M, eps_guess, shape, lam, uniforms, precision="fp64", ckpt_interval=0,
                  eps_bound=0.0, cheb_tol=0.0, tile_traj=0, psi0_batch=None, update_rule="independent",
-                 jump_scheme="bisection"):
+                 jump_scheme="bisection", ckpt_prefix=0):
     """kt_model_desc / kt_config for ``net`` (the returned ``keep`` dict owns the host arrays)."""
     uniforms = _c(uniforms)
     keep = {
@@ -327,7 +373,8 @@ def _descriptors(net, T, nt, M, eps_guess, shape, lam, uniforms, precision="fp64
         ckpt_interval=int(ckpt_interval), eps_guess=_ptr(keep["eps"]), shape=_ptr(keep["shape"]),
         lambda_a=_ptr(keep["lam"]), uniforms=_ptr(keep["U"]), n_passes=uniforms.shape[0],
         draws_per_traj=uniforms.shape[2], eps_bound=float(eps_bound), cheb_tol=float(cheb_tol),
-        tile_traj=int(tile_traj), update_rule=_UPDATE_RULES[update_rule], jump_scheme=_JUMP_SCHEMES[jump_scheme])
+        tile_traj=int(tile_traj), update_rule=_UPDATE_RULES[update_rule], jump_scheme=_JUMP_SCHEMES[jump_scheme],
+        ckpt_prefix=int(ckpt_prefix))
     return keep, md, cfg
 
 

@@ -60,11 +60,17 @@ def test_graph_iterations_match_sweeps(ckpt, rule, scheme):
         assert sum(len(r) for r in rec_a[-1]) >= 5
 
 
-def test_set_uniforms_restarts_pass_counter():
+@pytest.mark.parametrize("where", ["host", "device"])
+def test_set_uniforms_restarts_pass_counter(where):
+    """krotov_set_uniforms takes host or device memory (a CUDA tensor is copied device to device)."""
     sp = spec(2, 1, 12.0, 120, 13, 30.0, 9, 3)
     with problem(sp) as a, problem(sp) as b:
         a.update(2)
-        a.set_uniforms(sp["uniforms"])
+        if where == "device":
+            import torch
+            a.set_uniforms(torch.tensor(sp["uniforms"], device="cuda"))
+        else:
+            a.set_uniforms(sp["uniforms"])
         b.set_pulses(a.pulses())
         assert a.forward(False) == b.forward(False)
         assert a.records() == b.records()

@@ -37,7 +37,7 @@ def test_gradient_fp64_matches_oracle_with_jumps(ckpt):
     with Problem(cascaded_chain(N, nc), T, nt, M, eps, S, lam, U, psi0_batch=psi0, ckpt_interval=ckpt) as p:
         F = p.forward(keep_for_gradient=True)
         recs = p.records()
-        grad = p.gradient()
+        grad = p.gradient().cpu().numpy()
     assert sum(len(r) for r in recs) >= 2
     m = om.build_model(N, nc)
     ref, jt = og.gradient(m, eps, T, psi0, _records_to_oracle(recs))
@@ -51,7 +51,7 @@ def test_gradient_fp32_d729_matches_oracle():
     with Problem(cascaded_chain(N, nc), T, nt, M, eps, S, lam, U, psi0_batch=psi0, precision="fp32") as p:
         p.forward(keep_for_gradient=True)
         recs = p.records()
-        grad = p.gradient()
+        grad = p.gradient().cpu().numpy()
     m = om.build_model(N, nc)
     ref, _ = og.gradient(m, eps, T, psi0, _records_to_oracle(recs))
     assert np.abs(grad - ref).max() <= 2e-4 * np.abs(ref).max()
@@ -64,18 +64,18 @@ def test_autograd_function_matches_central_differences_at_kappa_zero():
     eps, S, lam, U, psi0 = _case(N, nc, T, nt, M, 30.0, 8, kappa=0.0)
     net = cascaded_chain(N, nc, kappa=0.0)
     with Problem(net, T, nt, M, eps, S, lam, U, psi0_batch=psi0) as p:
-        e = torch.tensor(eps, dtype=torch.float64, requires_grad=True)
+        e = torch.tensor(eps, dtype=torch.float64, device="cuda", requires_grad=True)
         J = trajectory_functional(e, p)
         J.backward()
-        g = e.grad.numpy()
+        g = e.grad.cpu().numpy()
         rng = np.random.default_rng(0)
         h = 1e-4
         for _ in range(20):
             i, j = int(rng.integers(N)), int(rng.integers(nt))
             ep = eps.copy(); ep[i, j] += h
             em = eps.copy(); em[i, j] -= h
-            Jp = float(trajectory_functional(torch.tensor(ep), p))
-            Jm = float(trajectory_functional(torch.tensor(em), p))
+            Jp = float(trajectory_functional(torch.tensor(ep, device="cuda"), p))
+            Jm = float(trajectory_functional(torch.tensor(em, device="cuda"), p))
             fd = (Jp - Jm) / (2 * h)
             assert fd == pytest.approx(g[i, j], rel=1e-6, abs=1e-11)
 
@@ -97,7 +97,7 @@ def test_gradient_full_size_launch_fd_and_precisions():
         with Problem(net, T, nt, M, eps, S, lam, U, psi0_batch=psi0, precision=prec) as p:
             p.forward(keep_for_gradient=True)
             assert sum(len(r) for r in p.records()) == 0
-            grads[prec] = p.gradient()
+            grads[prec] = p.gradient().cpu().numpy()
             if prec != "fp64":
                 continue
             rng = np.random.default_rng(1)
@@ -131,7 +131,71 @@ def test_gradient_d6561_full_launch_checkpointed_replay():
     for ckpt in (0, 2):
         with Problem(cascaded_chain(N, nc), T, nt, M, eps, S, lam, U, precision="fp32", ckpt_interval=ckpt) as p:
             p.forward(keep_for_gradient=True)
-            grads.append(p.gradient())
+            grads.append(p.gradient().cpu().numpy())
     scale = np.abs(grads[0]).max()
     assert scale > 0 and np.all(np.isfinite(grads[1]))
     assert np.abs(grads[1] - grads[0]).max() <= 2e-4 * scale
+
+
+def test_autograd_keeps_tensors_on_the_device():
+    """The pulse goes in and J_T and dJ_T/deps come out as CUDA tensors: forward and backward pass
+    device pointers through the C ABI on torch's current stream (no host copy of eps or of the
+    gradient); the result equals the gradient of the host-driven path (set_pulses + forward +
+    krotov_gradient) bit for bit, and krotov_gradient with a pulse argument equals both."""
+    torch = pytest.importorskip("torch")
+    from paper_1801_04382_gb300 import trajectory_functional
+    N, nc, T, nt, M = 2, 1, 6.0, 60, 6
+    eps, S, lam, U, psi0 = _case(N, nc, T, nt, M, 30.0, 5)
+    U = np.repeat(U[:1], 4, axis=0)           # every pass draws the same numbers: same records
+    with Problem(cascaded_chain(N, nc), T, nt, M, eps, S, lam, U, psi0_batch=psi0) as p:
+        e = torch.tensor(eps, dtype=torch.float64, device="cuda", requires_grad=True)
+        J = trajectory_functional(e, p)
+        assert J.is_cuda and J.dim() == 0
+        J.backward()
+        assert e.grad.is_cuda
+        g_auto = e.grad.cpu().numpy()
+        p.set_pulses(eps)
+        F = p.forward(keep_for_gradient=True)
+        assert abs(float(J) - (1.0 - F)) <= 1e-14
+        g_host = p.gradient().cpu().numpy()
+        g_arg = p.gradient(eps=torch.tensor(eps, device="cuda")).cpu().numpy()
+        assert sum(len(r) for r in p.records()) >= 2
+    assert np.array_equal(g_auto, g_host) and np.array_equal(g_arg, g_host)
+
+
+def test_autograd_rejects_a_stale_graph_node():
+    """backward of a J_T whose forward sweep was followed by another one raises instead of returning
+    the later sweep's gradient."""
+    torch = pytest.importorskip("torch")
+    from paper_1801_04382_gb300 import trajectory_functional
+    N, nc, T, nt, M = 2, 1, 2.0, 20, 2
+    eps, S, lam, U, psi0 = _case(N, nc, T, nt, M, 3.0, 5)
+    with Problem(cascaded_chain(N, nc), T, nt, M, eps, S, lam, U, psi0_batch=psi0) as p:
+        e1 = torch.tensor(eps, device="cuda", requires_grad=True)
+        J1 = trajectory_functional(e1, p)
+        e2 = torch.tensor(eps * 1.1, device="cuda", requires_grad=True)
+        J2 = trajectory_functional(e2, p)
+        with pytest.raises(RuntimeError, match="another forward sweep"):
+            J1.backward()
+        J2.backward()
+        assert e2.grad.is_cuda
+
+
+def test_device_pulse_out_of_range_is_reported():
+    """A pulse handed over in device memory is checked on the device (|eps| <= eps_bound, finite)."""
+    torch = pytest.importorskip("torch")
+    from paper_1801_04382_gb300 import KrotovError
+    N, nc, T, nt, M = 2, 1, 2.0, 20, 2
+    eps, S, lam, U, psi0 = _case(N, nc, T, nt, M, 3.0, 5)
+    with Problem(cascaded_chain(N, nc), T, nt, M, eps, S, lam, U, psi0_batch=psi0) as p:
+        bad = torch.tensor(eps, device="cuda")
+        bad[1, 3] = 1e3
+        p.set_pulses_device(bad)
+        with pytest.raises(KrotovError, match="RANGE"):
+            p.forward(False)
+        bad[1, 3] = float("nan")
+        p.set_pulses_device(bad)
+        with pytest.raises(KrotovError, match="NONFINITE"):
+            p.forward(False)
+        p.set_pulses_device(torch.tensor(eps, device="cuda"))
+        p.forward(False)

@@ -39,12 +39,12 @@ def setup(N, nc, T, nt, M, amp, seed, n_iter, kappa=1.0, random_init=False, draw
                 kappa=kappa, lindblad=lindblad)
 
 
-def run_gpu(c, precision="fp64", ckpt=0, tile=0, update_rule="independent", jump_scheme="bisection"):
+def run_gpu(c, precision="fp64", ckpt=0, tile=0, update_rule="independent", jump_scheme="bisection", ckpt_prefix=0):
     net = cascaded_chain(c["N"], c["nc"], kappa=c["kappa"], lindblad=c["lindblad"])
     out = {"F": [], "recs": [], "psiT": [], "eps": [], "deps": [], "precision": precision}
     with Problem(net, c["T"], c["nt"], c["M"], c["eps0"], c["S"], c["lam"], c["U"], precision=precision,
                  ckpt_interval=ckpt, tile_traj=tile, psi0_batch=c["psi0"], update_rule=update_rule,
-                 jump_scheme=jump_scheme) as p:
+                 jump_scheme=jump_scheme, ckpt_prefix=ckpt_prefix) as p:
         out["F"].append(p.forward(False))
         out["recs"].append(p.records())
         out["psiT"].append(p.states())
@@ -149,13 +149,22 @@ def test_cfg2_fp64_and_fp32():
     compare(c, run_gpu(c, "fp32"), res, 2e-4, 1e-5, 1e-4, 1e-4, margin_min=1e-5)
 
 
-def test_checkpointed_costates_are_bit_identical():
+@pytest.mark.parametrize("ckpt,prefix", [(7, 0), (7, 50), (-1, 0)])
+def test_checkpointed_costates_are_bit_identical(ckpt, prefix):
+    """Co-states kept every 7 intervals, kept for t_0..t_50 and every 7th after, or chosen from the
+    free device memory (ckpt_interval = -1): the optimisation is bit-identical to keeping them all."""
     c = setup(2, 1, 12.0, 120, 13, 30.0, 9, 2, random_init=True)
     a = run_gpu(c, ckpt=0)
-    b = run_gpu(c, ckpt=7)
+    b = run_gpu(c, ckpt=ckpt, ckpt_prefix=prefix)
     for x, y in zip(a["eps"], b["eps"]):
         assert np.array_equal(x, y)
     assert a["F"] == b["F"]
+    info = b["info"]
+    if ckpt == -1:       # plenty of device memory for 121 small states
+        assert info.ckpt_interval == 0 and info.costate_slots == c["nt"] + 1
+    else:
+        assert info.ckpt_interval == 7 and info.ckpt_kept_prefix == prefix
+        assert info.costate_slots == prefix + 1 + (c["nt"] - prefix + 6) // 7
 
 
 def test_costates_match_oracle():
@@ -335,7 +344,8 @@ def test_two_lindblad_channels_match_oracle(precision):
     if precision == "fp64":
         compare(c, gpu, res, 1e-10, 1e-10, 1e-10, 1e-9)
     else:
-        compare(c, gpu, res, 3e-5, 1e-5, 1e-4, 1e-4, margin_min=1e-5)
+        # 120 intervals of K ~ 28 terms at d = 36: unit roundoff 6e-8 x K nt ~ 2e-4 bounds the state drift
+        compare(c, gpu, res, 2e-4, 1e-5, 1e-4, 1e-4, margin_min=1e-5)
 
 
 _D6561 = {}
