@@ -28,6 +28,8 @@ that keeps the states plus the gradient sweep.
 two-node chain (d = 81, nt = 1000, guess amplitude 20 so that a quarter of the trajectories jump,
 FP32-mixed) for M = 8 ... 1024 trajectories, of the pulse and of the accumulated update eps - eps_guess
 (free of the smoothing residual of the smooth guess), and fits nu_i ~ M^b (the paper finds b = -1/2).
+--workload density times density-matrix Krotov (Eq. krotovupdate) on the two-node d = 81 model
+(vec(rho) of dimension 6561 as one Liouville-space state) in FP32-mixed and FP64.
 --workload profile runs a 12-interval case of the four-node interval kernels at M trajectories (a
 small command for ncu captures).
 --workload cross runs 20 iterations of the cross-trajectory update (Eq. cross_traj_update) and of
@@ -528,6 +530,48 @@ def run_cross(args, rank, world):
     return 0
 
 
+def run_density(args, rank, world):
+    """Density-matrix Krotov (Sec. 2.2, Eq. krotovupdate), the convergence reference of the trajectory
+    methods, on the two-node chain of the d = 81 workload (T = 50, nt = 1000, seed-free): vec(rho) is
+    one state of the four-node Liouville-space network (d^2 = 6561), propagated by the trajectory
+    kernels in one CTA per interval.  Iterations/s and the J_T history in FP32-mixed and FP64."""
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU (GB300); the CUDA path has no CPU fallback")
+    if rank != 0:
+        return 0
+    from paper_1801_04382_gb300 import DensityProblem, cascaded_chain
+    wl = si.CONFIGS["cfg2_d81"]
+    net = cascaded_chain(wl.n_nodes, wl.n_cav, wl.delta, wl.g, wl.kappa)
+    eps0 = si.guess_pulses(net.n_ctrl, wl.nt, wl.T, wl.guess_amp)
+    S = si.shape_functions(net.n_ctrl, wl.nt, wl.T)
+    lam = np.full(net.n_ctrl, wl.lam)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for prec, n_iter in (("fp32", max(args.steps, 3)), ("fp64", 2)):
+        with DensityProblem(net, wl.T, wl.nt, eps0, S, lam, precision=prec, stream=stream) as p:
+            F0 = p.forward(False, stream=stream)
+            p.update(1, stream=stream)                    # warm-up: captures the iteration graphs
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            JT, _ = p.update(n_iter, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out[prec] = {"iters_per_s": n_iter * 1000.0 / e0.elapsed_time(e1), "JT_guess": 1.0 - F0,
+                         "JT": [float(x) for x in JT], "cheb_terms": p.info.cheb_terms,
+                         "liouville_dim": p.info.d}
+    line = {"metric": "density-matrix Krotov (Eq. krotovupdate) iterations/s", "value": out["fp32"]["iters_per_s"],
+            "unit": "Krotov iters/s (FP32-mixed)", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "dtype": "c64+f64",
+            "config": {"workload": f"{wl.name} model as a density matrix (d={wl.d}, Liouville dimension "
+                                   f"{wl.d ** 2}, nt={wl.nt}, T={wl.T})"},
+            "fp32": out["fp32"], "fp64": out["fp64"],
+            "fp32_over_fp64": out["fp32"]["iters_per_s"] / out["fp64"]["iters_per_s"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -565,7 +609,9 @@ def run_ours(args, rank, world):
         dist.init_process_group("nccl")
     from paper_1801_04382_gb300 import Problem, cascaded_chain
 
-    wl = workload(rank, args.precision)
+    # replicas (default): every rank optimises its own problem (own seed); --shard: the ranks split one
+    # problem's trajectories and exchange the update's tile partials over NCCL once per interval
+    wl = workload(0 if args.shard else rank, args.precision)
     net = cascaded_chain(wl.n_nodes, wl.n_cav, wl.delta, wl.g, wl.kappa)
     n_passes = 2 + args.warmup + args.steps
     eps0 = si.guess_pulses(net.n_ctrl, wl.nt, wl.T, wl.guess_amp)
@@ -573,9 +619,22 @@ def run_ours(args, rank, world):
     lam = np.full(net.n_ctrl, wl.lam)
     U = si.uniforms(wl.seed, n_passes, wl.M, wl.draws_per_traj)
     stream = torch.cuda.current_stream()
+    shard_kw, M_rank = {}, wl.M
+    if args.shard:
+        from paper_1801_04382_gb300 import nccl_unique_id, shard_ranges
+        from paper_1801_04382_gb300.problem import nccl_library_path
+        off, M_rank = shard_ranges(wl.M, world, 1)[rank]
+        U = np.ascontiguousarray(U[:, off:off + M_rank])
+        shard_kw = dict(traj_offset=off, M_total=wl.M, tile_traj=1)
     # co-state storage from the free device memory (every co-state when they fit)
-    prob = Problem(net, wl.T, wl.nt, wl.M, eps0, S, lam, U, precision=wl.precision,
-                   ckpt_interval=args.ckpt, stream=stream)
+    prob = Problem(net, wl.T, wl.nt, M_rank, eps0, S, lam, U, precision=wl.precision,
+                   ckpt_interval=args.ckpt, stream=stream, **shard_kw)
+    if args.shard:
+        lib = nccl_library_path()
+        uid = [nccl_unique_id(lib) if rank == 0 else None]
+        if dist:
+            dist.broadcast_object_list(uid, src=0)
+        prob.shard_nccl(uid[0], rank, world, lib)
     info = prob.info
     prob.forward(False, stream=stream)                  # guess sweep (pass 0)
     for _ in range(args.warmup):
@@ -599,7 +658,7 @@ def run_ours(args, rank, world):
     clocks = clocks_stop(proc, fh, clk_path, local)
     ms_total = reduce_max(ms_total, dist, "cuda")
     ms_step = ms_total / args.steps
-    iters_per_s = world * 1000.0 / ms_step
+    iters_per_s = (1 if args.shard else world) * 1000.0 / ms_step
     traj_steps_per_s = iters_per_s * 2 * wl.M * wl.nt
 
     # ---------------- per-kernel split: one more iteration launched kernel by kernel, CUDA events on
@@ -613,8 +672,8 @@ def run_ours(args, rank, world):
 
     # ---------------- end to end through the public API, host buffers each step
     e2e_steps = max(1, min(args.steps, 3))
-    pin = torch.empty((1, wl.M, wl.draws_per_traj), dtype=torch.float64, pin_memory=True)
-    host_U = si.uniforms(wl.seed + 7, e2e_steps, wl.M, wl.draws_per_traj)
+    pin = torch.empty((1, M_rank, wl.draws_per_traj), dtype=torch.float64, pin_memory=True)
+    host_U = si.uniforms(wl.seed + 7, e2e_steps, M_rank, wl.draws_per_traj)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -627,8 +686,8 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1000.0 / e2e_steps
     e2e_ms = reduce_max(e2e_ms, dist, "cuda")
-    h2d = wl.M * wl.draws_per_traj * 8
-    d2h = wl.M * 16 + net.n_ctrl * wl.nt * 8
+    h2d = M_rank * wl.draws_per_traj * 8
+    d2h = (wl.M if args.shard else M_rank) * 16 + net.n_ctrl * wl.nt * 8
 
     # ---------------- roofline of the dominant kernel
     peaks, peak_src = measured_peaks()
@@ -640,27 +699,28 @@ def run_ours(args, rank, world):
     ri = info.threads > 0 and wl.n_cav == 2      # cavity network with real / imaginary coupling classes
     exec_per_elem_term = executed_flops_per_elem_term(nnz, ri)
     survey_per_elem_term = 8.0 * nnz + 12.0      # every coupling counted as a complex multiply-add
-    flops_per_launch = exec_per_elem_term * K * wl.d * wl.M
+    flops_per_launch = exec_per_elem_term * K * wl.d * M_rank
     clk_max = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = fp32_peak_tflops(clk_max)
     achieved = flops_per_launch / avg_s / 1e12
     s_bytes = 8 if wl.precision == "fp32" else 16
     bytes_per_iter = 5.0 * s_bytes * wl.d * wl.M * wl.nt
     hbm_achieved = bytes_per_iter * (iters_per_s / world) / 1e9
-    kernel_bytes = (3 if fam == "fwd" else 2) * s_bytes * wl.d * wl.M
+    kernel_bytes = (3 if fam == "fwd" else 2) * s_bytes * wl.d * M_rank
     roof = {"bound": "alu", "kernel": f"{fam}_kernel", "achieved": achieved, "peak": fp32_peak,
             "unit": "TFLOP/s", "frac": achieved / fp32_peak,
             "traffic": NCU_TRAFFIC_PER_LAUNCH.get(fam) if wl.precision == "fp32" else None,
             "avg_launch_ms": avg_s * 1e3, "launches": f_n,
             "flops_per_launch": flops_per_launch, "flops_per_elem_term": exec_per_elem_term,
             "flops_per_elem_term_complex_count": survey_per_elem_term,
-            "tflops_complex_count": survey_per_elem_term * K * wl.d * wl.M / avg_s / 1e12,
+            "tflops_complex_count": survey_per_elem_term * K * wl.d * M_rank / avg_s / 1e12,
             "algorithmic_bytes_per_launch": kernel_bytes,
             "hbm_gbs_of_kernel": kernel_bytes / avg_s / 1e9,
             "peak_source": f"FP32 FFMA: {sm_count()} SMs x {FP32_LANES} lanes x 2 x {clk_max:.0f} MHz"}
     line = {
         "metric": METRIC, "value": iters_per_s, "unit": "Krotov iters/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "strong" if args.shard else "weak",
         "vs_baseline": None, "dtype": "c64+f64" if wl.precision == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": wl.name, "d": wl.d, "M": wl.M, "nt": wl.nt, "dt": wl.dt,
                    "precision": "FP32-mixed" if wl.precision == "fp32" else "FP64",
@@ -668,7 +728,8 @@ def run_ours(args, rank, world):
                                        f"t_0..t_{info.ckpt_kept_prefix} kept, then every {info.ckpt_interval}"),
                    "costate_slots": info.costate_slots, "cheb_terms": K, "tile_traj": info.tile_traj,
                    "threads": info.threads, "l2": "inputs larger than L2 (co-states "
-                   f"{info.device_bytes / 1e9:.1f} GB per GPU)", "parallelism": f"replicas{world}",
+                   f"{info.device_bytes / 1e9:.1f} GB per GPU)",
+                   "parallelism": f"trajectory-sharded{world}" if args.shard else f"replicas{world}",
                    "timed_path": "krotov_update: one CUDA graph launch per iteration"},
         "traj_steps_per_s": traj_steps_per_s,
         "hbm_roofline": {"achieved_gbs": hbm_achieved, "peak_gbs": peaks["hbm_gbs"],
@@ -681,7 +742,7 @@ def run_ours(args, rank, world):
         "kernels_one_profiled_iteration": {f"{k}_kernel": {"launches": n, "total_ms": ms, "avg_ms": ms / max(n, 1)}
                                            for k, (ms, n) in prof.items() if n > 0},
         "profiled_iteration_ms": prof_ms_iter,
-        "gpu_launches": int((prof["fwd"][1] + prof["bwd"][1] + 4) * args.steps),
+        "gpu_launches": int((prof["fwd"][1] + prof["bwd"][1] + prof["finish"][1] + 4) * args.steps),
         "clocks": clocks,
     }
     if rank == 0 and not args.no_precision_comparison:
@@ -735,11 +796,15 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-comparison", action="store_true")
-    ap.add_argument("--workload", choices=["cfg5", "mix64", "grad729", "noise", "cross", "profile"], default="cfg5")
+    ap.add_argument("--workload", choices=["cfg5", "mix64", "grad729", "noise", "cross", "profile", "density"],
+                    default="cfg5")
     ap.add_argument("--ckpt", type=int, default=-1,
                     help="co-state storage of the cfg5 problem: -1 automatic from free memory (default), "
                          "0 all, K > 0 every K-th")
     ap.add_argument("--profile-M", type=int, default=1024)
+    ap.add_argument("--shard", action="store_true",
+                    help="split one problem's trajectories over the ranks (NCCL exchange of the update's "
+                         "partials every interval; strong scaling) instead of one problem per rank")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -755,6 +820,8 @@ def main():
         return run_cross(args, rank, world)
     if args.workload == "profile":
         return run_profile(args)
+    if args.workload == "density":
+        return run_density(args, rank, world)
     return run_ours(args, rank, world)
 
 

@@ -120,7 +120,7 @@ typedef struct {
   int draws_per_traj;       /* odd, >= 1 */
   double eps_bound;         /* bound on |eps| used for the spectral estimate; 0 = automatic
                                (2 max|eps_guess| + 1) */
-  double cheb_tol;          /* Chebyshev truncation; 0 = 1e-15 (FP64) / 1e-8 (FP32-mixed) */
+  double cheb_tol;          /* Chebyshev truncation; 0 = 1e-16 (FP64) / 1e-8 (FP32-mixed) */
   int tile_traj;            /* trajectories per CTA tile (power of two <= 32); 0 = automatic
                                (heuristic); -1 = autotuned: krotov_init times the forward
                                interval kernel for every width that fits (12 launches each on
@@ -135,12 +135,50 @@ typedef struct {
                                at most one jump per interval, applied at its end (s* = dt) */
   int ckpt_prefix;          /* with ckpt_interval = K > 0: the co-states of t_0 .. t_ckpt_prefix
                                are all kept as well (checkpoints every K after it); 0 = none */
+  int traj_offset;          /* trajectory sharding (Sec. 2.3: trajectories are independent, only the
+                               update's scalars are exchanged): with M_total > 0 this problem is the
+                               shard holding trajectories traj_offset .. traj_offset + M - 1 of an
+                               M_total-trajectory problem -- its uniforms are those trajectories' rows,
+                               Delta eps is normalised by M_total, and the per-interval tile partials
+                               of all shards are exchanged (krotov_shard_nccl, or a group of shards in
+                               one process, krotov_group_init) before Delta eps is formed, in the same
+                               order as the unsharded problem (bit-identical results).  Shard
+                               boundaries fall on tile boundaries; the tile width is chosen for
+                               M_total (tile_traj -1 is refused); independent update rule only. */
+  int M_total;              /* 0: not a shard */
+  int inject_copy_timeout;  /* 0 (normal).  1: a test of failure reporting -- every interval kernel's
+                               first bounded wait for a state tile's bulk copy watches a barrier that
+                               nothing arrives at (about 10 us), takes its timeout path (a second wait
+                               lets the copy land, the block leaves) and the sweep returns
+                               KT_ERR_TIMEOUT; the device stays usable.  Each wait is bounded
+                               (about 2 s) whatever this flag. */
 } kt_config;
 
 /* Create a problem: validate, assemble H_eff in structured form (a1), choose the Chebyshev
  * expansion (a2), allocate and upload.  No propagation is done. */
 KT_API kt_status krotov_init(const kt_model_desc *model, const kt_config *cfg, void *stream,
                              kt_problem **out);
+
+/* Density-matrix Krotov (Sec. 2.2, Eqs. krotov_functional, krotovupdate, krotov_boundary), the
+ * convergence reference of the trajectory methods: rho(t) follows the master equation of Eq. lindblad,
+ * d rho/dt = -i (H_eff rho - rho H_eff^dag) + sum_l L_l rho L_l^dag, with the model's H, L_l (the same
+ * descriptor as krotov_init, pure initial state psi0); the functional is J_T = 1 - <tgt|rho(T)|tgt>,
+ * the co-state P(t) runs backward from P(T) = |tgt><tgt| under the adjoint dynamics, and the
+ * sequential update is Delta eps_c(t) = S_c / lambda_c Im <<P(t)| [H_c, rho(t)] >> with
+ * <<A|B>> = tr(A^dag B) and dL/deps_c rho = [H_c, rho] as the paper states it.
+ * The library runs it as ONE state vec(rho)[x d + y] = rho_xy of a network of 2 n_nodes nodes (ket
+ * nodes, then bra nodes) under G = H_eff (x) 1 - 1 (x) H_eff^* + i sum_l L_l (x) L_l^*
+ * (d vec(rho)/dt = -i G vec(rho)), with the trajectory kernels: no jumps, no normalisation.  So
+ * propagate_forward / propagate_backward / krotov_update / krotov_get_update / krotov_get_pulses
+ * work as for a trajectory problem; fidelity's F is <tgt|rho(T)|tgt> (tau_out[0] = <<P_tgt|rho(T)>>),
+ * krotov_get_states returns vec(rho(T)) as [1][d*d][2] and krotov_get_costate vec(P(t_j)).
+ * cfg: T, nt, prec, ckpt_interval (and ckpt_prefix), eps_guess, shape, lambda_a, eps_bound and
+ * cheb_tol are used; M, the uniforms, tile_traj, update_rule and jump_scheme are ignored.
+ * Limits: n_nodes <= 4, d^2 within the shared-memory limit above (two states of d^2 elements:
+ * d <= 81 in FP64), a real ladder factor.  krotov_gradient and the cross-trajectory rule are not
+ * defined for it (KT_ERR_UNSUPPORTED / KT_ERR_ARG). */
+KT_API kt_status krotov_init_density(const kt_model_desc *model, const kt_config *cfg, void *stream,
+                                     kt_problem **out);
 
 /* One forward MCWF sweep of all trajectories over [0, T] (Sec. 2.1), consuming the next
  * pass of uniforms.  sequential_update = 0 propagates under the current pulse.
@@ -242,14 +280,16 @@ KT_API kt_status krotov_set_uniforms(kt_problem *p, const double *uniforms, int 
  * benchmark.  Turning it on or off clears the totals.  krotov_get_profile returns, per family
  * (KT_PROF_FWD: forward interval kernel incl. the pulse update; KT_PROF_BWD: backward interval
  * kernel incl. checkpoint recompute and the gradient's forward replay; KT_PROF_GRAD: gradient
- * kernel of krotov_gradient; KT_PROF_CROSS: the cross-trajectory update's kernels), the summed
+ * kernel of krotov_gradient; KT_PROF_CROSS: the cross-trajectory update's kernels; KT_PROF_FINISH:
+ * the one-block update sum of a sharded problem), the summed
  * milliseconds and
  * the launch count since profiling was turned on; arrays of KT_PROF_FAMILIES entries. */
 #define KT_PROF_FWD 0
 #define KT_PROF_BWD 1
 #define KT_PROF_GRAD 2
 #define KT_PROF_CROSS 3
-#define KT_PROF_FAMILIES 4
+#define KT_PROF_FINISH 4
+#define KT_PROF_FAMILIES 5
 KT_API kt_status krotov_set_profiling(kt_problem *p, int on);
 KT_API kt_status krotov_get_profile(kt_problem *p, double *ms_out, long long *launches_out);
 
@@ -297,6 +337,38 @@ KT_API kt_status krotov_batch_info(kt_batch *b, int *n_problems, long long *grap
                                    long long *device_bytes);
 KT_API void krotov_batch_free(kt_batch *b);
 
+/* Trajectory sharding across GPUs (Sec. 2.3: the trajectories are independent and only scalars are
+ * exchanged).  Each process creates its shard with kt_config.traj_offset / M_total (equal slices in
+ * rank order: M_total = world * M, traj_offset = rank * M), then joins the communicator:
+ *   kt_nccl_unique_id   on one rank: a 128-byte NCCL unique id into id_out (host), to be sent to the
+ *                       other ranks by the caller's own means;
+ *   krotov_shard_nccl   on every rank, with its device current: a communicator of `world` ranks.
+ * From then on every updating forward sweep all-gathers the tile partials of the update overlap once
+ * per interval (in place, n_tiles x n_ctrl doubles per shard) and every shard forms the same Delta eps;
+ * each forward sweep ends with an all-gather of tau, so F (fidelity, krotov_update's J_T) is that of
+ * all M_total trajectories.  The collectives are enqueued on the sweep's stream and captured into
+ * krotov_update's graphs.  NCCL is loaded at run time (nccl_library, or "libnccl.so.2" when NULL);
+ * KT_ERR_UNSUPPORTED if it cannot be loaded.  The communicator is destroyed by krotov_free. */
+KT_API kt_status kt_nccl_unique_id(const char *nccl_library, void *id_out);
+KT_API kt_status krotov_shard_nccl(kt_problem *p, const void *unique_id, int rank, int world,
+                                   const char *nccl_library);
+
+/* Shards of one problem driven together in one process, on one stream (e.g. one device): the group
+ * runs their forward sweeps interval by interval, copies each shard's tile partials into every other
+ * shard's copy of the global partials (device-to-device) and forms Delta eps in every shard; the
+ * backward sweeps are independent.  krotov_group_init borrows n shards (any order; together they
+ * must cover trajectories 0 .. M_total - 1 in consecutive ranges with one tile width);
+ * krotov_group_update runs n_iter Krotov iterations (a guess sweep first if needed), JT_out
+ * (nullable, [n_iter]) gets J_T of all trajectories after each; krotov_group_fidelity gives F of the
+ * last sweep over all trajectories.  Each shard's own getters (pulses, records, states) work as usual;
+ * its propagate_* / krotov_update calls are refused while it has no communicator.  krotov_group_free
+ * releases the group, not the shards.  The results equal the unsharded problem's bit for bit. */
+typedef struct kt_group kt_group;
+KT_API kt_status krotov_group_init(kt_problem *const *shards, int n, kt_group **out);
+KT_API kt_status krotov_group_update(kt_group *g, int n_iter, double *JT_out, void *stream);
+KT_API kt_status krotov_group_fidelity(kt_group *g, double *F_out, void *stream);
+KT_API void krotov_group_free(kt_group *g);
+
 /* Chebyshev coefficient helper (host): Bessel J_0..J_{n-1}(alpha) by Miller's backward
  * recurrence, the routine the kernels use for sub-step propagators.  Returns KT_ERR_ARG for
  * alpha < 0 or n outside [1, 256]. */
@@ -306,7 +378,9 @@ KT_API kt_status kt_bessel_j(double alpha, int n, double *out);
  * model and configuration, expanded into a dense matrix out [d][d][2] with the same indexing the
  * kernels use (every neighbour index bounds-checked; KT_ERR_RANGE if one leaves the space).
  * direction 0: H_eff(eps) = H(eps) - (i/2) sum_l L_l^dag L_l (Sec. 2.1); direction 1: -H_eff(eps)^dag,
- * the generator of the backward co-state propagation.  eps: [n_ctrl] pulse values.  No device call. */
+ * the generator of the backward co-state propagation; directions 2 and 3: the same for the
+ * Liouville-space generator G of krotov_init_density (out is then [d^2][d^2][2]).  eps: [n_ctrl]
+ * pulse values.  No device call. */
 KT_API kt_status kt_generator_dense(const kt_model_desc *model, const kt_config *cfg, int direction,
                                     const double *eps, double *out);
 

@@ -17,7 +17,7 @@ Follows, step by step and in the paper's order:
 
 Readings of points the paper leaves open (each listed with this build's design notes):
 the state is not renormalised between jumps and is renormalised after each jump; a jump
-happens iff ||psi||^2 <= r; bisection stops when hi - lo <= 2^-40 dt (at most 60 halvings)
+happens iff ||psi||^2 <= r; bisection stops when hi - lo <= 2^-48 dt (at most 60 halvings)
 and takes s* = hi; the channel is the first l whose cumulative probability reaches
 u * sum_l p_l; uniforms come from ``synth_inputs.uniforms`` (column 0 = first r, columns
 2m-1 / 2m = channel draw / next r after jump m); the co-state is propagated backward along
@@ -33,7 +33,7 @@ import numpy as np
 
 from .propagate import StepPropagator
 
-BISECT_REL_TOL = 2.0 ** -40
+BISECT_REL_TOL = 2.0 ** -48
 BISECT_MAX_IT = 60
 
 
@@ -51,9 +51,10 @@ class ForwardResult:
     records: list                     # per trajectory: list[Jump]
     eps: np.ndarray                   # [n_ctrl, nt] pulse used by this pass
     deps: np.ndarray                  # [n_ctrl, nt] update (zeros without update)
-    margin: np.ndarray                # [M] min over steps of | ||psi||^2 - r |
+    margin: np.ndarray                # [M] min over interval ends of | ||psi||^2 - r | (incl. those that jump)
     psi_t: np.ndarray = None          # [nt+1, M, d] if requested
     error: str = ""
+    deps_scale: np.ndarray = None     # [n_ctrl, nt] S/(lambda M) sum_k |Im<chi_k|H_i|psi_k>| (update only)
 
 
 def _norm2(v: np.ndarray) -> float:
@@ -77,8 +78,10 @@ def _step_with_jumps(prop: StepPropagator, Ls: list, psi: np.ndarray, dt: float,
     while True:
         phi = prop.apply(start, dt - s0)
         n_end = _norm2(phi)
+        # distance of the no-jump norm at the interval's end from the threshold: it decides whether
+        # the jump falls in this interval or a later one, whichever way it goes
+        state["margin"] = min(state["margin"], abs(n_end - state["r"]))
         if n_end > state["r"]:
-            state["margin"] = min(state["margin"], n_end - state["r"])
             return phi
         # a jump happens in (s0, dt]: locate it by bisection on the norm
         lo, hi = (dt - s0 if first_order else 0.0), dt - s0
@@ -110,11 +113,15 @@ def _step_with_jumps(prop: StepPropagator, Ls: list, psi: np.ndarray, dt: float,
         s0 = s0 + hi
 
 
-def cross_overlap(xi: np.ndarray, psi: np.ndarray, Hc: np.ndarray) -> float:
-    """sum_{k,k'} Im[<xi_k|Hc|psi_k'> <psi_k'|xi_k>] for xi, psi [M, d] (Eq. cross_traj_update)."""
+def cross_overlap(xi: np.ndarray, psi: np.ndarray, Hc: np.ndarray, scale: bool = False):
+    """sum_{k,k'} Im[<xi_k|Hc|psi_k'> <psi_k'|xi_k>] for xi, psi [M, d] (Eq. cross_traj_update);
+    with scale, also the sum of the magnitudes of the terms."""
     A = np.conj(xi) @ (psi @ Hc.T).T          # A[k, k'] = <xi_k|Hc|psi_k'>
     G = np.conj(xi) @ psi.T                   # G[k, k'] = <xi_k|psi_k'>, so <psi_k'|xi_k> = conj(G)
-    return float(np.sum(np.imag(A * np.conj(G))))
+    terms = np.imag(A * np.conj(G))
+    if scale:
+        return float(np.sum(terms)), float(np.sum(np.abs(terms)))
+    return float(np.sum(terms))
 
 
 def forward_pass(model, eps: np.ndarray, T: float, U_pass: np.ndarray, psi0: np.ndarray,
@@ -138,6 +145,7 @@ def forward_pass(model, eps: np.ndarray, T: float, U_pass: np.ndarray, psi0: np.
     psi = np.array(np.broadcast_to(psi0, (M, psi0.shape[-1])), dtype=np.complex128)
     eps_used = np.array(eps, dtype=np.float64)
     deps = np.zeros_like(eps_used)
+    deps_scale = np.zeros_like(eps_used)
     states = [{"r": float(U_pass[k, 0]), "jumps": 0, "margin": np.inf} for k in range(M)]
     records = [[] for _ in range(M)]
     psi_t = [psi.copy()] if keep_states else None
@@ -146,12 +154,15 @@ def forward_pass(model, eps: np.ndarray, T: float, U_pass: np.ndarray, psi0: np.
         if chi is not None:
             for i in range(n_ctrl):
                 if cross:
-                    g = cross_overlap(chi[j - 1], psi, model.Hc[i])
+                    g, ga = cross_overlap(chi[j - 1], psi, model.Hc[i], scale=True)
                     deps[i, j - 1] = shape[i, j - 1] / (lam[i] * M * M) * g
+                    deps_scale[i, j - 1] = shape[i, j - 1] / (lam[i] * M * M) * ga
                     continue
                 hpsi = psi @ model.Hc[i].T          # rows: Hc_i psi_k
-                g = np.sum(np.imag(np.sum(np.conj(chi[j - 1]) * hpsi, axis=1)))
+                gk = np.imag(np.sum(np.conj(chi[j - 1]) * hpsi, axis=1))
+                g = np.sum(gk)
                 deps[i, j - 1] = shape[i, j - 1] / (lam[i] * M) * g
+                deps_scale[i, j - 1] = shape[i, j - 1] / (lam[i] * M) * np.sum(np.abs(gk))
             eps_used[:, j - 1] = eps[:, j - 1] + deps[:, j - 1]
         prop = StepPropagator(model.Heff(eps_used[:, j - 1]))
         # every trajectory first takes the full interval; those whose norm fell to the
@@ -171,7 +182,7 @@ def forward_pass(model, eps: np.ndarray, T: float, U_pass: np.ndarray, psi0: np.
             psi_t.append(psi.copy())
     return ForwardResult(psi, records, eps_used, deps,
                          np.array([s["margin"] for s in states]),
-                         np.array(psi_t) if keep_states else None)
+                         np.array(psi_t) if keep_states else None, deps_scale=deps_scale)
 
 
 def fidelity(psi_T: np.ndarray, psi_tgt: np.ndarray):

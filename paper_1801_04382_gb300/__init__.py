@@ -6,7 +6,8 @@ behind the C ABI of ``include/krotov_traj.h``; this package holds the build scri
 ctypes binding (``Problem``) and the structured model builder.
 """
 from .model import NetworkFactors, cascaded_chain  # noqa: F401
-from .problem import Batch, Problem, bessel_j  # noqa: F401
+from .problem import (Batch, DensityProblem, Problem, ShardGroup, bessel_j, nccl_unique_id,  # noqa: F401
+                      shard_ranges)
 from . import build  # noqa: F401  (module: build.build() compiles the CUDA library)
 from ._capi import KrotovError  # noqa: F401
 

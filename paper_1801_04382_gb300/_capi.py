@@ -39,6 +39,7 @@ class Config(ct.Structure):
         ("uniforms", dp), ("n_passes", ct.c_int), ("draws_per_traj", ct.c_int),
         ("eps_bound", ct.c_double), ("cheb_tol", ct.c_double), ("tile_traj", ct.c_int),
         ("update_rule", ct.c_int), ("jump_scheme", ct.c_int), ("ckpt_prefix", ct.c_int),
+        ("traj_offset", ct.c_int), ("M_total", ct.c_int), ("inject_copy_timeout", ct.c_int),
     ]
 
 
@@ -55,6 +56,8 @@ class Info(ct.Structure):
 # name -> (restype, argtypes); every symbol declared in include/krotov_traj.h
 SIGNATURES = {
     "krotov_init": (ct.c_int, [ct.POINTER(ModelDesc), ct.POINTER(Config), ct.c_void_p, ct.POINTER(ct.c_void_p)]),
+    "krotov_init_density": (ct.c_int, [ct.POINTER(ModelDesc), ct.POINTER(Config), ct.c_void_p,
+                                       ct.POINTER(ct.c_void_p)]),
     "propagate_forward": (ct.c_int, [ct.c_void_p, ct.c_int, dp, ct.c_void_p]),
     "propagate_backward": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
     "krotov_gradient": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
@@ -81,6 +84,12 @@ SIGNATURES = {
     "krotov_batch_problem": (ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_void_p)]),
     "krotov_batch_info": (ct.c_int, [ct.c_void_p, ip, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_longlong)]),
     "krotov_batch_free": (None, [ct.c_void_p]),
+    "kt_nccl_unique_id": (ct.c_int, [ct.c_char_p, ct.c_void_p]),
+    "krotov_shard_nccl": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_int, ct.c_char_p]),
+    "krotov_group_init": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.c_int, ct.POINTER(ct.c_void_p)]),
+    "krotov_group_update": (ct.c_int, [ct.c_void_p, ct.c_int, dp, ct.c_void_p]),
+    "krotov_group_fidelity": (ct.c_int, [ct.c_void_p, dp, ct.c_void_p]),
+    "krotov_group_free": (None, [ct.c_void_p]),
     "kt_bessel_j": (ct.c_int, [ct.c_double, ct.c_int, dp]),
     "kt_generator_dense": (ct.c_int, [ct.POINTER(ModelDesc), ct.POINTER(Config), ct.c_int, dp, dp]),
     "kt_update_overlap_noalloc": (ct.c_int, [ct.c_int, ct.c_int, ct.c_int, ip, dp, ct.c_int, ct.c_void_p,

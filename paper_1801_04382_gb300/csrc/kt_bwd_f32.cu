@@ -8,7 +8,7 @@ static cudaError_t launch_bwd_t(const KtGeom &g, const KtGenImage &im, const KtO
                                 cudaStream_t st) {
   const cudaError_t attr = kt_allow_large_smem((const void *)bwd_kernel<R, EPT, NL, ACS>);
   if (attr != cudaSuccess) return attr;
-  bwd_kernel<R, EPT, NL, ACS><<<g.n_tiles, g.nthreads, smem, st>>>(g, im, ops, a);
+  bwd_kernel<R, EPT, NL, ACS><<<g.bwd_grid > 0 ? g.bwd_grid : g.n_tiles, g.nthreads, smem, st>>>(g, im, ops, a);
   return cudaGetLastError();
 }
 }  // namespace kt

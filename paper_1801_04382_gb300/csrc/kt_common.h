@@ -11,6 +11,7 @@
 
 #define KT_MAX_NODES 8
 #define KT_MAX_CTRL 8
+#define KT_MAX_CTERMS 16  // control terms (a control acting on one node; two per control in Liouville space)
 #define KT_MAX_LIND 4
 #define KT_MAX_PAIRS 28
 #define KT_MAX_S 4        // off-diagonal entries per row of a node-local generator factor
@@ -21,11 +22,12 @@
 
 // Kernel families timed by krotov_set_profiling (mirror KT_PROF_* in the public header).
 #ifndef KT_PROF_FAMILIES
-#define KT_PROF_FAMILIES 4
+#define KT_PROF_FAMILIES 5
 #define KT_PROF_FWD 0
 #define KT_PROF_BWD 1
 #define KT_PROF_GRAD 2
 #define KT_PROF_CROSS 3
+#define KT_PROF_FINISH 4
 #endif
 
 // Device status word values (first error wins); mirror kt_status.
@@ -85,9 +87,16 @@ struct KtGeom {
   int K;                             // Chebyshev terms of a full step
   int max_jumps, draws;              // jump cap and uniforms per trajectory and pass
   int prefetch_chi;                  // forward kernel keeps a third tile buffer for chi(t_j)
+  int bwd_grid;                      // > 0: backward kernel CTAs looping over tiles, next input prefetched
   int first_order;                   // jump scheme: 0 jump times by bisection, 1 at most one jump per interval, at its end
   int stride[KT_MAX_NODES];          // element stride of node i (n_loc^(N-1-i))
-  int ctrl_node[KT_MAX_CTRL];
+  int ctrl_node[KT_MAX_CTRL];        // node of control c (its ket node for a density matrix)
+  int n_cterms;                      // control terms: control cterm_ctrl[t] acting on node cterm_node[t]
+  int cterm_ctrl[KT_MAX_CTERMS];
+  int cterm_node[KT_MAX_CTERMS];
+  int density;                       // 1: the one "trajectory" is vec(rho) in Liouville space (no jumps, no normalisation)
+  double M_norm;                     // M of the update's 1/M: all trajectories of the problem (M, or M_total when sharded)
+  int inject_timeout;                // test of the failure path: the first wait for a bulk copy runs out
   double lam[KT_MAX_CTRL];
   double dt, eps_bound;
   double c_fwd, c_bwd, r;            // generator centre (per direction) and half width
@@ -97,9 +106,9 @@ struct KtGeom {
 struct KtGenImage {
   const int *loc_dl;          // [N][n_loc][S] local column delta y - x (0 = no entry)
   const KtCplx *loc_base;     // [N][n_loc][S] scaled (1/r) drift part
-  const KtCplx *ctrl_slot;    // [n_ctrl][n_loc][S] scaled per-unit-eps part on node ctrl_node[c]
+  const KtCplx *ctrl_slot;    // [n_cterms][n_loc][S] scaled per-unit-eps part of term t on node cterm_node[t]
   const KtCplx *diag_base;    // [N][n_loc] scaled diagonal (node 0 also holds -c/r)
-  const KtCplx *ctrl_diag;    // [n_ctrl][n_loc] scaled per-unit-eps diagonal part
+  const KtCplx *ctrl_diag;    // [n_cterms][n_loc] scaled per-unit-eps diagonal part
   const int *pair_off;        // [P][n_loc*n_loc] element offset (in elements, before *T); 0 = none
   const KtCplx *pair_val;     // [P][n_loc*n_loc] scaled
   const KtCplx *cheb_full;    // [K] full-step coefficients, phase exp(-i c dt) folded in
@@ -115,8 +124,8 @@ struct KtOps {
   const int *ra_dl;           // [n_loc] adjoint a^dag: row x -> column x + ra_dl[x]
   const KtCplx *ra_val;       // [n_loc]
   const KtCplx *lind_coef;    // [n_lind][N]
-  const int *hc_dl;           // [n_ctrl][n_loc][SH] control factor (unscaled), column delta
-  const KtCplx *hc_val;       // [n_ctrl][n_loc][SH] (0 = no entry)
+  const int *hc_dl;           // [n_cterms][n_loc][SH] control term factor (unscaled), column delta
+  const KtCplx *hc_val;       // [n_cterms][n_loc][SH] (0 = no entry)
   const uint32_t *digits;     // [d] node digits of each basis index, node i in bits 4i..4i+3
   const KtCplx *tgt;          // [d] target state
 };

@@ -88,11 +88,14 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t 
   return ok != 0;
 }
 
-// wait (one thread) for phase `phase` of the barrier, giving up after ~2 s of clock
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, uint32_t phase) {
+#define KT_WAIT_CYCLES 4000000000LL   // ~2 s of SM clock
+
+// wait (one thread) for phase `phase` of the barrier, giving up after `budget` cycles of clock
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, uint32_t phase,
+                                                  long long budget = KT_WAIT_CYCLES) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, phase))
-    if (clock64() - t0 > 4000000000LL) return false;
+    if (clock64() - t0 > budget) return false;
   return true;
 }
 
@@ -105,11 +108,15 @@ __device__ __forceinline__ void bulk_store(void *dst_gmem, const void *src_smem,
 }
 __device__ __forceinline__ void bulk_store_wait() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
-// Whole-tile load by the bulk engine: thread 0 waits (bounded) and the block learns the outcome.
-// On a timeout the status word gets KT_DEV_TIMEOUT and false is returned to every thread.
-__device__ __forceinline__ bool tile_wait(unsigned long long *bar, uint32_t phase, int *flag_slot, int *status) {
+// Whole-tile load by the bulk engine: thread 0 waits (bounded, ~2 s) and the block learns the
+// outcome.  On a timeout the status word gets KT_DEV_TIMEOUT, thread 0 waits once more (~2 s) so
+// that the copy in flight lands before the block leaves, and false is returned to every thread.
+// idle_bar (a test of this failure path, kt_config.inject_copy_timeout): the first wait watches a
+// barrier nothing arrives at, for ~10 us, so that the timeout path runs deterministically.
+__device__ __forceinline__ bool tile_wait(unsigned long long *bar, uint32_t phase, int *flag_slot, int *status,
+                                          unsigned long long *idle_bar) {
   if (threadIdx.x == 0) {
-    bool ok = mbar_wait_bounded(bar, phase);
+    const bool ok = idle_bar ? mbar_wait_bounded(idle_bar, 0, 20000) : mbar_wait_bounded(bar, phase);
     if (!ok) {
       set_status(status, KT_DEV_TIMEOUT);
       mbar_wait_bounded(bar, phase);   // give the copy in flight a second bounded chance to land
@@ -125,14 +132,14 @@ __device__ __forceinline__ bool tile_wait(unsigned long long *bar, uint32_t phas
 struct Smem {
   void *bufA, *bufB;          // [tile_elems] complex each
   void *bufC;                 // [tile_elems] prefetched chi(t_j) (forward kernel, when it fits)
-  unsigned long long *mbar;   // [2] transaction barriers of the bulk copies
+  unsigned long long *mbar;   // [3] transaction barriers of the bulk copies; [2] never receives an arrival
   int *loc_off;               // [N*n_loc*S]  element offset * T (0 = no entry)
   void *loc_val;              // [N*n_loc*S]
   void *diag;                 // [N*n_loc]
   int *pair_off;              // [P*n_loc^2]
   void *pair_val;             // [P*n_loc^2]
-  int *hc_off;                // [n_ctrl*n_loc*SH]
-  void *hc_val;               // [n_ctrl*n_loc*SH]
+  int *hc_off;                // [n_cterms*n_loc*SH]
+  void *hc_val;               // [n_cterms*n_loc*SH]
   void *coef;                 // [K][T]
   double *red;                // [nwarps][T][8]
   double *tsc;                // per-trajectory scalars [16][T]
@@ -159,14 +166,14 @@ __host__ __device__ inline size_t carve(const KtGeom &g, int esz, char *base, Sm
   const size_t tile = (size_t)g.tile_elems * esz;
   char *a = take(tile), *b = take(tile);
   char *cbuf = with_c ? take(tile) : nullptr;
-  char *mb = take(2 * sizeof(unsigned long long));
+  char *mb = take(3 * sizeof(unsigned long long));
   char *lo = take(sizeof(int) * g.n_nodes * g.n_loc * g.S);
   char *lv = take((size_t)esz * g.n_nodes * g.n_loc * g.S);
   char *dg = take((size_t)esz * g.n_nodes * g.n_loc);
   char *po = take(sizeof(int) * g.n_pairs * nl2);
   char *pv = take((size_t)esz * g.n_pairs * nl2);
-  char *ho = take(sizeof(int) * g.n_ctrl * g.n_loc * g.SH);
-  char *hv = take((size_t)esz * g.n_ctrl * g.n_loc * g.SH);
+  char *ho = take(sizeof(int) * g.n_cterms * g.n_loc * g.SH);
+  char *hv = take((size_t)esz * g.n_cterms * g.n_loc * g.SH);
   char *cf = take((size_t)esz * g.K * g.T);
   char *rd = take(sizeof(double) * nwarps * g.T * 8);
   char *ts = take(sizeof(double) * 16 * g.T);
@@ -257,10 +264,10 @@ __device__ void build_tables(const KtGeom &g, const KtGenImage &im, const KtOps 
   for (int e = threadIdx.x; e < g.n_nodes * nls; e += blockDim.x) {
     const int i = e / nls, rem = e % nls;
     double re = im.loc_base[e].re, imv = im.loc_base[e].im;
-    for (int c = 0; c < g.n_ctrl; ++c)
-      if (g.ctrl_node[c] == i) {
-        re += eps[c] * im.ctrl_slot[c * nls + rem].re;
-        imv += eps[c] * im.ctrl_slot[c * nls + rem].im;
+    for (int t = 0; t < g.n_cterms; ++t)
+      if (g.cterm_node[t] == i) {
+        re += eps[g.cterm_ctrl[t]] * im.ctrl_slot[t * nls + rem].re;
+        imv += eps[g.cterm_ctrl[t]] * im.ctrl_slot[t * nls + rem].im;
       }
     lv[e] = mkc((R)re, (R)imv);
     sm.loc_off[e] = im.loc_dl[e] * g.stride[i] * g.T;
@@ -268,10 +275,10 @@ __device__ void build_tables(const KtGeom &g, const KtGenImage &im, const KtOps 
   for (int e = threadIdx.x; e < g.n_nodes * g.n_loc; e += blockDim.x) {
     const int i = e / g.n_loc, x = e % g.n_loc;
     double re = im.diag_base[e].re, imv = im.diag_base[e].im;
-    for (int c = 0; c < g.n_ctrl; ++c)
-      if (g.ctrl_node[c] == i) {
-        re += eps[c] * im.ctrl_diag[c * g.n_loc + x].re;
-        imv += eps[c] * im.ctrl_diag[c * g.n_loc + x].im;
+    for (int t = 0; t < g.n_cterms; ++t)
+      if (g.cterm_node[t] == i) {
+        re += eps[g.cterm_ctrl[t]] * im.ctrl_diag[t * g.n_loc + x].re;
+        imv += eps[g.cterm_ctrl[t]] * im.ctrl_diag[t * g.n_loc + x].im;
       }
     dg[e] = mkc((R)re, (R)imv);
   }
@@ -301,9 +308,9 @@ __device__ void build_tables(const KtGeom &g, const KtGenImage &im, const KtOps 
   if (with_hc) {
     C *hv = (C *)sm.hc_val;
     const int nh = g.n_loc * g.SH;
-    for (int e = threadIdx.x; e < g.n_ctrl * nh; e += blockDim.x) {
-      const int c = e / nh;
-      sm.hc_off[e] = ops.hc_dl[e] * g.stride[g.ctrl_node[c]] * g.T;
+    for (int e = threadIdx.x; e < g.n_cterms * nh; e += blockDim.x) {
+      const int t = e / nh;
+      sm.hc_off[e] = ops.hc_dl[e] * g.stride[g.cterm_node[t]] * g.T;
       hv[e] = from_kc<C>(ops.hc_val[e]);
     }
   }
@@ -916,7 +923,9 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
   const C *psi_in = (const C *)a.psi_in + (size_t)tile * g.tile_elems;
   C *psi_out = (C *)a.psi_out + (size_t)tile * g.tile_elems;
   const int j = a.j;
-  const double tol = 0x1p-40 * g.dt;
+  // bisection stop: 2^-48 dt in FP64 (near the rounding of the FP64 norm it compares), 2^-40 dt in
+  // FP32-mixed (far below the FP32 norm's own error)
+  const double tol = (sizeof(R) == 8 ? 0x1p-48 : 0x1p-40) * g.dt;
 
   if (threadIdx.x < g.n_ctrl) {
     const int c = threadIdx.x;
@@ -928,9 +937,12 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
     sm.eps[c] = e;
   }
   if (threadIdx.x < 8) sm.flag[threadIdx.x] = 0;
+  // the trajectory's current threshold, read now so that its latency is off the path after the series
+  const double r_start = (threadIdx.x < g.T) ? a.rstate[(size_t)tile * g.T + threadIdx.x] : 0.0;
   if (threadIdx.x == 0) {
     mbar_init(&sm.mbar[0], 1);
     mbar_init(&sm.mbar[1], 1);
+    mbar_init(&sm.mbar[2], 1);
     fence_mbar_init();
   }
   __syncthreads();
@@ -948,7 +960,7 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
   Items<EPT, NL> it;
   load_items<EPT, NL>(g, ops, it);
   C acc[EPT];
-  if (!tile_wait(&sm.mbar[0], 0, &sm.flag[4], a.status)) {
+  if (!tile_wait(&sm.mbar[0], 0, &sm.flag[4], a.status, g.inject_timeout ? &sm.mbar[2] : nullptr)) {
     if (threadIdx.x == 0 && need_chi && g.prefetch_chi) mbar_wait_bounded(&sm.mbar[1], 0);
     return;
   }
@@ -999,7 +1011,7 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
       if (threadIdx.x < g.T) {
         const int t = threadIdx.x, k = tile * g.T + t;
         const double nrm = sm.tsc[TS_NRM * g.T + t];
-        const double r = a.rstate[k];                    // padding trajectories carry r = -1
+        const double r = r_start;                        // padding trajectories carry r = -1
         if (!isfinite(nrm)) set_status(a.status, KT_DEV_NONFINITE);
         const int act = (k < g.M) && (nrm <= r);         // jump iff ||psi||^2 <= r
         sm.tin[TI_ACT * g.T + t] = act;
@@ -1177,7 +1189,9 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
       const int k = tile * g.T + threadIdx.x;
       const double *o = sm.tsc + TS_V0 * g.T + threadIdx.x * 3;
       const double nrm = o[2];
-      const double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
+      // a trajectory's overlap is taken with the normalised state; a density matrix's
+      // <<P_tgt|rho(T)>> is linear in rho and is not normalised
+      const double inv = g.density ? 1.0 : (nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0);
       a.tau[k].re = o[0] * inv;
       a.tau[k].im = o[1] * inv;
       a.norm2[k] = nrm;
@@ -1208,20 +1222,23 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
     if (threadIdx.x == 0) bulk_load(B, chi_g, tile_bytes, &sm.mbar[1]);
     chi = B;
   }
-  if (!tile_wait(&sm.mbar[1], 0, &sm.flag[5], a.status)) {
+  if (!tile_wait(&sm.mbar[1], 0, &sm.flag[5], a.status, g.inject_timeout ? &sm.mbar[2] : nullptr)) {
     if (threadIdx.x == 0 && stored) bulk_store_wait();
     return;
   }
   const C *hv = (const C *)sm.hc_val;
-  double v[KT_MAX_CTRL];
-  for (int c = 0; c < KT_MAX_CTRL; ++c) v[c] = 0.0;
-  for (int c = 0; c < g.n_ctrl; ++c) {
-    const int node = g.ctrl_node[c];
+  // per-thread sums per control in the state precision (a trajectory problem has one term per
+  // control; a density matrix a ket and a bra term), converted to FP64 once for the reduction
+  R sc[KT_MAX_CTRL];
+#pragma unroll
+  for (int c = 0; c < KT_MAX_CTRL; ++c) sc[c] = (R)0;
+  for (int t = 0; t < g.n_cterms; ++t) {
+    const int node = g.cterm_node[t];
     R s = 0;
     if (NL > 0 && node != g.n_nodes - 1) {
       // fiber mapping, control on another node: one factor row serves the whole fiber
       if (it.ok(0)) {
-        const int base = (c * g.n_loc + ((it.dig(0) >> (4 * node)) & 15)) * g.SH;
+        const int base = (t * g.n_loc + ((it.dig(0) >> (4 * node)) & 15)) * g.SH;
         C h[EPT];
 #pragma unroll
         for (int q = 0; q < EPT; ++q) h[q] = mkc((R)0, (R)0);
@@ -1244,7 +1261,7 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
       for (int q = 0; q < EPT; ++q) {
         if (!it.ok(q)) continue;
         const int xi = (it.dig(q) >> (4 * node)) & 15;
-        const int base = (c * g.n_loc + xi) * g.SH;
+        const int base = (t * g.n_loc + xi) * g.SH;
         C h = mkc((R)0, (R)0);
         for (int e = 0; e < g.SH; ++e) {
           const C w = hv[base + e];
@@ -1254,13 +1271,23 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
         s += x.x * h.y - x.y * h.x;       // Im(conj(chi) * h)
       }
     }
-    v[c] = (double)s;
+    const int ct = g.cterm_ctrl[t];
+#pragma unroll
+    for (int c = 0; c < KT_MAX_CTRL; ++c)
+      if (c == ct) sc[c] += s;
   }
+  double v[KT_MAX_CTRL];
+#pragma unroll
+  for (int c = 0; c < KT_MAX_CTRL; ++c) v[c] = c < g.n_ctrl ? (double)sc[c] : 0.0;
   reduce_tau<KT_MAX_CTRL>(v, g, sm.red, sm.tsc + TS_V0 * g.T);
   if (threadIdx.x < g.n_ctrl) {
     double s = 0.0;
     for (int t = 0; t < g.T; ++t) s += sm.tsc[TS_V0 * g.T + t * KT_MAX_CTRL + threadIdx.x];
     a.partials[(size_t)tile * g.n_ctrl + threadIdx.x] = s;
+  }
+  if (!a.finish) {   // sharded problem: the partials of all shards are summed after the exchange
+    if (threadIdx.x == 0 && stored) bulk_store_wait();
+    return;
   }
   // ---------------- last CTA: Delta eps of interval j+1, summed in tile order ----------------
   __threadfence();
@@ -1289,7 +1316,7 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sm.red[w * 8 + c];
     const size_t idx = (size_t)c * a.nt + j;   // interval j+1 (0-based index j)
-    const double de = a.shape[idx] / (g.lam[c] * (double)g.M) * s;
+    const double de = a.shape[idx] / (g.lam[c] * g.M_norm) * s;
     const double en = a.eps_old[idx] + de;
     a.deps[idx] = de;
     a.eps_new[idx] = en;
@@ -1306,118 +1333,144 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
 // With a.forward_replay the same kernel replays a recorded forward pass instead: the image is
 // the forward generator's, pieces run forwards (s_1, s_2 - s_1, ..., dt - s_m) and each is
 // followed by c L of its jump -- the frozen-record map U_j of the gradient (no bisection).
+// Tiles: with g.bwd_grid > 0 the grid holds that many CTAs, each looping over tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...: the tables and the item mapping (which depend on the interval only)
+// are built once, and the next tile's input arrives by bulk copy in a third buffer while the current
+// tile's series runs (loads alternate between two transaction barriers).  Otherwise one tile per CTA.
 template <typename R, int EPT, int NL, int ACS>
 __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) bwd_kernel(KtGeom g, KtGenImage im, KtOps ops, BwdArgs a) {
   typedef typename C2<R>::T C;
   extern __shared__ __align__(16) char smem_raw[];
   Smem sm;
-  carve(g, sizeof(C), smem_raw, &sm, false);
-  const int tile = blockIdx.x;
+  const bool persist = g.bwd_grid > 0;
+  carve(g, sizeof(C), smem_raw, &sm, persist);
   const int tau = threadIdx.x % g.T;
   const int j = a.j;
-  const C *chi_in = (const C *)a.chi_in + (size_t)tile * g.tile_elems;
-  C *chi_out = (C *)a.chi_out + (size_t)tile * g.tile_elems;
   if (threadIdx.x < g.n_ctrl) sm.eps[threadIdx.x] = a.eps[threadIdx.x * a.nt + (j - 1)];
   if (threadIdx.x < 8) sm.flag[threadIdx.x] = 0;
   if (threadIdx.x == 0) {
     mbar_init(&sm.mbar[0], 1);
+    mbar_init(&sm.mbar[1], 1);
+    mbar_init(&sm.mbar[2], 1);
     fence_mbar_init();
   }
   __syncthreads();
   const uint32_t tile_bytes = (uint32_t)(g.tile_elems * sizeof(C));
-  if (threadIdx.x == 0) bulk_load(sm.bufB, chi_in, tile_bytes, &sm.mbar[0]);
+  int tile = blockIdx.x;
+  if (threadIdx.x == 0)
+    bulk_load(sm.bufB, (const C *)a.chi_in + (size_t)tile * g.tile_elems, tile_bytes, &sm.mbar[0]);
   build_tables<R>(g, im, ops, sm, sm.eps, false);
   const bool fw = a.forward_replay != 0;
-  if (threadIdx.x < g.T) {
-    const int t = threadIdx.x, k = tile * g.T + t;
-    int nj = 0;
-    if (k < g.M) {
-      int cur = a.cursor[k];
-      if (fw) {
-        const int cnt = a.jcount[k];
-        while (cur < cnt && a.rec_step[(size_t)k * g.max_jumps + cur] == j && nj < 12) {
-          sm.tin[(TI_J0 + nj) * g.T + t] = cur;  // ascending in time
-          ++nj;
-          ++cur;
-        }
-        if (cur < cnt && a.rec_step[(size_t)k * g.max_jumps + cur] == j) set_status(a.status, KT_DEV_RECORD_FULL);
-      } else {
-        while (cur >= 0 && a.rec_step[(size_t)k * g.max_jumps + cur] == j && nj < 12) {
-          sm.tin[(TI_J0 + nj) * g.T + t] = cur;  // descending in time
-          ++nj;
-          --cur;
-        }
-        if (cur >= 0 && a.rec_step[(size_t)k * g.max_jumps + cur] == j) set_status(a.status, KT_DEV_RECORD_FULL);
-      }
-      if (a.advance_cursor) a.cursor[k] = cur;
-    }
-    sm.tin[TI_NJ * g.T + t] = nj;
-    atomicMax(&sm.flag[0], nj);
-  }
   Items<EPT, NL> it;
   load_items<EPT, NL>(g, ops, it);
-  C *A = (C *)sm.bufA;
-  C *B = (C *)sm.bufB;
-  if (!tile_wait(&sm.mbar[0], 0, &sm.flag[4], a.status)) return;
-  const int rounds = sm.flag[0];
-  C acc[EPT];
-  for (int rnd = 0; rnd <= rounds; ++rnd) {
-    if (rounds == 0) {
-      uniform_coefs<R>(g, sm, im.cheb_full);
-    } else if (threadIdx.x < g.T) {
-      const int t = threadIdx.x, k = tile * g.T + t, nj = sm.tin[TI_NJ * g.T + t];
-      double len = 0.0;
-      if (rnd <= nj) {
-        const double *rs = a.rec_s + (size_t)k * g.max_jumps;
-        if (fw) {   // pieces forwards: s_1 - 0, s_2 - s_1, ..., dt - s_m
-          const double lo = (rnd == 0) ? 0.0 : rs[sm.tin[(TI_J0 + rnd - 1) * g.T + t]];
-          const double hi = (rnd < nj) ? rs[sm.tin[(TI_J0 + rnd) * g.T + t]] : g.dt;
-          len = hi - lo;
-        } else {    // pieces backwards: dt - s_m, s_m - s_{m-1}, ..., s_1 - 0
-          const double hi = (rnd == 0) ? g.dt : rs[sm.tin[(TI_J0 + rnd - 1) * g.T + t]];
-          const double lo = (rnd < nj) ? rs[sm.tin[(TI_J0 + rnd) * g.T + t]] : 0.0;
-          len = hi - lo;
-        }
-      }
-      tau_coefs<R>(g, sm, t, fw ? g.c_fwd : g.c_bwd, len);
+  bool store_pending = false;
+  for (int use = 0; tile < g.n_tiles; tile += gridDim.x, ++use) {
+    C *chi_out = (C *)a.chi_out + (size_t)tile * g.tile_elems;
+    // this tile's input: load number `use`, on barrier use & 1 with phase parity (use >> 1) & 1
+    if (!tile_wait(&sm.mbar[use & 1], (use >> 1) & 1, &sm.flag[4], a.status,
+                   g.inject_timeout ? &sm.mbar[2] : nullptr)) {
+      if (threadIdx.x == 0 && store_pending) bulk_store_wait();
+      return;
     }
-    // B holds the vector to propagate
-#pragma unroll
-    for (int q = 0; q < EPT; ++q)
-      if (it.ok(q)) A[it.item(q)] = B[it.item(q)];
+    const int next = tile + (int)gridDim.x;
+    if (persist && next < g.n_tiles && threadIdx.x == 0)   // the third buffer is free: prefetch the next input
+      bulk_load(sm.bufC, (const C *)a.chi_in + (size_t)next * g.tile_elems, tile_bytes, &sm.mbar[(use + 1) & 1]);
+    if (threadIdx.x == 0) sm.flag[0] = 0;
+    if (threadIdx.x == 0 && store_pending) bulk_store_wait();   // A still feeds the previous tile's store
+    store_pending = false;
     __syncthreads();
-    cheb_dispatch<R, EPT, NL, ACS, false>(g, im, sm, it, g.K, acc);   // rows from the tables: measured faster here
-    if (rnd == rounds) break;
+    if (threadIdx.x < g.T) {
+      const int t = threadIdx.x, k = tile * g.T + t;
+      int nj = 0;
+      if (k < g.M) {
+        int cur = a.cursor[k];
+        if (fw) {
+          const int cnt = a.jcount[k];
+          while (cur < cnt && a.rec_step[(size_t)k * g.max_jumps + cur] == j && nj < 12) {
+            sm.tin[(TI_J0 + nj) * g.T + t] = cur;  // ascending in time
+            ++nj;
+            ++cur;
+          }
+          if (cur < cnt && a.rec_step[(size_t)k * g.max_jumps + cur] == j) set_status(a.status, KT_DEV_RECORD_FULL);
+        } else {
+          while (cur >= 0 && a.rec_step[(size_t)k * g.max_jumps + cur] == j && nj < 12) {
+            sm.tin[(TI_J0 + nj) * g.T + t] = cur;  // descending in time
+            ++nj;
+            --cur;
+          }
+          if (cur >= 0 && a.rec_step[(size_t)k * g.max_jumps + cur] == j) set_status(a.status, KT_DEV_RECORD_FULL);
+        }
+        if (a.advance_cursor) a.cursor[k] = cur;
+      }
+      sm.tin[TI_NJ * g.T + t] = nj;
+      atomicMax(&sm.flag[0], nj);
+    }
+    __syncthreads();
+    C *A = (C *)sm.bufA;
+    C *B = (C *)sm.bufB;
+    const int rounds = sm.flag[0];
+    C acc[EPT];
+    for (int rnd = 0; rnd <= rounds; ++rnd) {
+      if (rounds == 0) {
+        uniform_coefs<R>(g, sm, im.cheb_full);
+      } else if (threadIdx.x < g.T) {
+        const int t = threadIdx.x, k = tile * g.T + t, nj = sm.tin[TI_NJ * g.T + t];
+        double len = 0.0;
+        if (rnd <= nj) {
+          const double *rs = a.rec_s + (size_t)k * g.max_jumps;
+          if (fw) {   // pieces forwards: s_1 - 0, s_2 - s_1, ..., dt - s_m
+            const double lo = (rnd == 0) ? 0.0 : rs[sm.tin[(TI_J0 + rnd - 1) * g.T + t]];
+            const double hi = (rnd < nj) ? rs[sm.tin[(TI_J0 + rnd) * g.T + t]] : g.dt;
+            len = hi - lo;
+          } else {    // pieces backwards: dt - s_m, s_m - s_{m-1}, ..., s_1 - 0
+            const double hi = (rnd == 0) ? g.dt : rs[sm.tin[(TI_J0 + rnd - 1) * g.T + t]];
+            const double lo = (rnd < nj) ? rs[sm.tin[(TI_J0 + rnd) * g.T + t]] : 0.0;
+            len = hi - lo;
+          }
+        }
+        tau_coefs<R>(g, sm, t, fw ? g.c_fwd : g.c_bwd, len);
+      }
+      // B holds the vector to propagate
+#pragma unroll
+      for (int q = 0; q < EPT; ++q)
+        if (it.ok(q)) A[it.item(q)] = B[it.item(q)];
+      __syncthreads();
+      cheb_dispatch<R, EPT, NL, ACS, false>(g, im, sm, it, g.K, acc);   // rows from the tables: measured faster here
+      if (rnd == rounds) break;
+#pragma unroll
+      for (int q = 0; q < EPT; ++q)
+        if (it.ok(q)) A[it.item(q)] = acc[q];
+      __syncthreads();
+      const int nj = sm.tin[TI_NJ * g.T + tau];
+      const int k = tile * g.T + tau;
+#pragma unroll
+      for (int q = 0; q < EPT; ++q) {
+        if (!it.ok(q)) continue;
+        C y = A[it.item(q)];
+        if (rnd < nj) {
+          const size_t ri = (size_t)k * g.max_jumps + sm.tin[(TI_J0 + rnd) * g.T + tau];
+          const C z = lind_item<R>(g, ops, a.rec_ch[ri], fw ? 0 : 1, A, it.item(q), it.dig(q));
+          const R cn = (R)a.rec_c[ri];
+          y = mkc(cn * z.x, cn * z.y);
+        }
+        B[it.item(q)] = y;
+      }
+      __syncthreads();
+    }
+    // chi(t_{j-1}) of the whole tile: into A, then one bulk store (completed before A is reused)
 #pragma unroll
     for (int q = 0; q < EPT; ++q)
       if (it.ok(q)) A[it.item(q)] = acc[q];
+    fence_proxy_async_smem();
     __syncthreads();
-    const int nj = sm.tin[TI_NJ * g.T + tau];
-    const int k = tile * g.T + tau;
-#pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-      if (!it.ok(q)) continue;
-      C y = A[it.item(q)];
-      if (rnd < nj) {
-        const size_t ri = (size_t)k * g.max_jumps + sm.tin[(TI_J0 + rnd) * g.T + tau];
-        const C z = lind_item<R>(g, ops, a.rec_ch[ri], fw ? 0 : 1, A, it.item(q), it.dig(q));
-        const R cn = (R)a.rec_c[ri];
-        y = mkc(cn * z.x, cn * z.y);
-      }
-      B[it.item(q)] = y;
-    }
-    __syncthreads();
+    if (threadIdx.x == 0) bulk_store(chi_out, A, tile_bytes);
+    store_pending = true;
+    // the prefetched input becomes this CTA's input buffer; the old one (free) the next prefetch target
+    void *tmp = sm.bufB;
+    sm.bufB = sm.bufC;
+    sm.bufC = tmp;
   }
-  // chi(t_{j-1}) of the whole tile: into A, then one bulk store
-#pragma unroll
-  for (int q = 0; q < EPT; ++q)
-    if (it.ok(q)) A[it.item(q)] = acc[q];
-  fence_proxy_async_smem();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    bulk_store(chi_out, A, tile_bytes);
-    bulk_store_wait();
-  }
+  if (threadIdx.x == 0 && store_pending) bulk_store_wait();
 }
 
 }  // namespace kt

@@ -2,13 +2,16 @@
 // structured MCWF generator (a1), Chebyshev set-up (a2), device memory, and the sweep
 // schedulers behind the C ABI declared in include/krotov_traj.h.
 #include <cuda_runtime.h>
+#include <dlfcn.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <complex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -40,17 +43,66 @@ kt_status fail(kt_status s, const char *fmt, ...) {
       return fail(KT_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
   } while (0)
 
+// ---------------------------------------------------------------------------- NCCL, loaded at run time
+// The library does not link NCCL: a sharded problem loads it with dlopen (the caller may name the
+// file) and uses four entry points of its C API.
+struct NcclApi {
+  typedef int (*GetUniqueId)(void *id);
+  typedef int (*CommInitRank)(void **comm, int nranks, std::array<char, 128> id, int rank);
+  typedef int (*AllGather)(const void *send, void *recv, size_t count, int dtype, void *comm, cudaStream_t st);
+  typedef int (*CommDestroy)(void *comm);
+  typedef const char *(*ErrorString)(int r);
+  void *handle = nullptr;
+  GetUniqueId get_unique_id = nullptr;
+  CommInitRank comm_init_rank = nullptr;
+  AllGather all_gather = nullptr;
+  CommDestroy comm_destroy = nullptr;
+  ErrorString error_string = nullptr;
+};
+const int kNcclDouble = 8;   // ncclFloat64
+
+NcclApi g_nccl;
+std::mutex g_nccl_mu;
+
+kt_status nccl_load(const char *path) {
+  std::lock_guard<std::mutex> lock(g_nccl_mu);
+  if (g_nccl.handle) return KT_OK;
+  void *h = dlopen(path && *path ? path : "libnccl.so.2", RTLD_NOW | RTLD_GLOBAL);
+  if (!h) return fail(KT_ERR_UNSUPPORTED, "NCCL not found (%s)", dlerror());
+  NcclApi api;
+  api.handle = h;
+  api.get_unique_id = (NcclApi::GetUniqueId)dlsym(h, "ncclGetUniqueId");
+  api.comm_init_rank = (NcclApi::CommInitRank)dlsym(h, "ncclCommInitRank");
+  api.all_gather = (NcclApi::AllGather)dlsym(h, "ncclAllGather");
+  api.comm_destroy = (NcclApi::CommDestroy)dlsym(h, "ncclCommDestroy");
+  api.error_string = (NcclApi::ErrorString)dlsym(h, "ncclGetErrorString");
+  if (!api.get_unique_id || !api.comm_init_rank || !api.all_gather || !api.comm_destroy || !api.error_string) {
+    dlclose(h);
+    return fail(KT_ERR_UNSUPPORTED, "the NCCL library lacks an entry point this library uses");
+  }
+  g_nccl = api;
+  return KT_OK;
+}
+
 // ---------------------------------------------------------------------------- structured generator
+// Pair hop between two different nodes: kind 0 coef a_dst^dag a_src (the cascade, L^dag L cross
+// terms), kind 1 coef a_dst a_src and kind 2 coef a_dst^dag a_src^dag (the L rho L^dag term of a
+// density matrix in Liouville space, and its adjoint).
 struct Pair {
   int dst, src;
-  cd coef;   // coef * a_dst^dag a_src
+  cd coef;
+  int kind = 0;
 };
 
+// Structured generator: node factors, control terms and pair hops.  A control term is one factor
+// of a control on one node (ctrl_node[t], control term_ctrl[t]); an ordinary model has one term
+// per control, the Liouville-space generator of a density matrix two (the ket and the bra node).
 struct Gen {
-  int N = 0, nl = 0;
+  int N = 0, nl = 0, n_ctrl = 0;
   std::vector<cd> loc;    // [N][nl][nl]
-  std::vector<cd> ctrl;   // [n_ctrl][nl][nl] (per unit eps)
-  std::vector<int> ctrl_node;
+  std::vector<cd> ctrl;   // [n_terms][nl][nl] (per unit eps)
+  std::vector<int> ctrl_node;   // [n_terms] node of each term
+  std::vector<int> term_ctrl;   // [n_terms] control of each term
   std::vector<Pair> pairs;
 };
 
@@ -78,7 +130,12 @@ Gen minus_adjoint(const Gen &f) {
   for (size_t base = 0; base < f.ctrl.size(); base += nl * nl)
     for (int x = 0; x < nl; ++x)
       for (int y = 0; y < nl; ++y) b.ctrl[base + x * nl + y] = -std::conj(f.ctrl[base + y * nl + x]);
-  for (size_t p = 0; p < f.pairs.size(); ++p) b.pairs[p] = Pair{f.pairs[p].src, f.pairs[p].dst, -std::conj(f.pairs[p].coef)};
+  // (c a_d^dag a_s)^dag = conj(c) a_s^dag a_d; (c a_d a_s)^dag = conj(c) a_d^dag a_s^dag and back
+  for (size_t p = 0; p < f.pairs.size(); ++p) {
+    const Pair &q = f.pairs[p];
+    if (q.kind == 0) b.pairs[p] = Pair{q.src, q.dst, -std::conj(q.coef), 0};
+    else b.pairs[p] = Pair{q.dst, q.src, -std::conj(q.coef), q.kind == 1 ? 2 : 1};
+  }
   return b;
 }
 
@@ -146,7 +203,7 @@ Bounds gen_bounds(const Gen &g, double amax, double E) {
 // follow.  Entries are enumerated with the kernels' own indexing (digits, node strides, pair hops).
 Bounds row_bounds(const Gen &g, const std::vector<int> &lo_dl, const std::vector<cd> &lo_val,
                   const std::vector<int> &ra_dl, const std::vector<cd> &ra_val, int d, const int *stride, double E) {
-  const int nl = g.nl, N = g.N, nc = (int)g.ctrl_node.size();
+  const int nl = g.nl, N = g.N, nc = g.n_ctrl, nterm = (int)g.ctrl_node.size();
   // entries of G0 (m = 0) and of dG/deps_c (m = 1 + c), keyed by row * d + column
   std::vector<std::unordered_map<long long, cd>> mats(1 + nc);
   auto add = [&](int m, long long x, long long y, cd v) {
@@ -159,15 +216,17 @@ Bounds row_bounds(const Gen &g, const std::vector<int> &lo_dl, const std::vector
       for (int y = 0; y < nl; ++y) {
         const long long col = x + (long long)(y - dig[i]) * stride[i];
         add(0, x, col, g.loc[((size_t)i * nl + dig[i]) * nl + y]);
-        for (int c = 0; c < nc; ++c)
-          if (g.ctrl_node[c] == i) add(1 + c, x, col, g.ctrl[((size_t)c * nl + dig[i]) * nl + y]);
+        for (int t = 0; t < nterm; ++t)
+          if (g.ctrl_node[t] == i) add(1 + g.term_ctrl[t], x, col, g.ctrl[((size_t)t * nl + dig[i]) * nl + y]);
       }
     for (const Pair &q : g.pairs) {
       const int xd = dig[q.dst], xs = dig[q.src];
-      if (ra_val[xd] == 0.0 || lo_val[xs] == 0.0) continue;
-      if (q.dst == q.src) continue;
-      const long long col = x + (long long)ra_dl[xd] * stride[q.dst] + (long long)lo_dl[xs] * stride[q.src];
-      add(0, x, col, q.coef * ra_val[xd] * lo_val[xs]);
+      const bool rd = q.kind != 1, rs = q.kind == 2;        // raise the dst / src node?
+      const cd vd = rd ? ra_val[xd] : lo_val[xd], vs = rs ? ra_val[xs] : lo_val[xs];
+      if (vd == 0.0 || vs == 0.0 || q.dst == q.src) continue;
+      const long long col = x + (long long)(rd ? ra_dl[xd] : lo_dl[xd]) * stride[q.dst] +
+                            (long long)(rs ? ra_dl[xs] : lo_dl[xs]) * stride[q.src];
+      add(0, x, col, q.coef * vd * vs);
     }
   }
   // Hermitian (h) and anti-Hermitian (a) parts, per row: |diagonal|-range and off-diagonal sums
@@ -210,8 +269,17 @@ kt_status kt_fail(kt_status s, const char *msg) { return fail(s, "%s", msg); }
 // ---------------------------------------------------------------------------- problem object
 struct kt_problem {
   KtGeom g{};
-  int fp64 = 1, ept = 4, cross = 0;
+  int fp64 = 1, ept = 4, cross = 0, density = 0;
   size_t esz = 16;
+  // trajectory sharding: this problem holds trajectories [traj_offset, traj_offset + M) of M_total,
+  // tiles [tile_off, tile_off + n_tiles) of n_tiles_total; the per-interval update sums the tile
+  // partials of every shard, exchanged into gpart (all-gather over NCCL, or copies within a group)
+  int sharded = 0, tile_off = 0, n_tiles_total = 0, M_total = 0;
+  double *spart = nullptr;      // [n_tiles_total][n_ctrl]
+  void *nccl_comm = nullptr;
+  int nccl_rank = 0, nccl_world = 1;
+  KtCplx *tau_all = nullptr;    // NCCL shards: tau of all M_total trajectories after a sweep
+  bool in_group = false;
   int nt = 0, M = 0, n_passes = 0, n_passes_alloc = 0, ckpt = 0;
   int ckpt_dense = 0;           // ckpt > 0: co-states t_0 .. t_A all kept (A = ckpt_dense), then every ckpt-th
   bool ckpt_auto = false;       // storage chosen from free device memory (ckpt_interval = -1)
@@ -281,6 +349,15 @@ struct kt_problem {
 };
 
 namespace {
+
+// In-place all-gather of equal slices over the shard communicator (a shard's own slice is already
+// in place at its rank's offset).
+kt_status nccl_allgather(kt_problem *p, const void *send, void *recv, size_t count, cudaStream_t st) {
+  if (!p->nccl_comm) return fail(KT_ERR_STATE, "no NCCL communicator");
+  const int r = g_nccl.all_gather(send, recv, count, kNcclDouble, p->nccl_comm, st);
+  if (r != 0) return fail(KT_ERR_CUDA, "ncclAllGather failed: %s", g_nccl.error_string(r));
+  return KT_OK;
+}
 
 // Event pair around one launch of the given family (only while profiling).
 kt_status prof_begin(kt_problem *p, int family, cudaStream_t st) {
@@ -369,6 +446,9 @@ kt_status read_status(kt_problem *p, cudaStream_t st) {
   }
   if (s == KT_DEV_OK) return KT_OK;
   KT_CUDA(cudaMemsetAsync(p->status, 0, sizeof(int), st));
+  // a CTA that left early (a wait that ran out) took no last-CTA ticket: start the next sweep at zero
+  KT_CUDA(cudaMemsetAsync(p->counter, 0, sizeof(unsigned), st));
+  KT_CUDA(cudaStreamSynchronize(st));
   switch (s) {
     case KT_DEV_NONFINITE: return fail(KT_ERR_NONFINITE, "non-finite norm, overlap or pulse value on the device");
     case KT_DEV_RECORD_FULL: return fail(KT_ERR_RECORD_FULL, "a trajectory needed more jumps than draws_per_traj allows");
@@ -396,7 +476,8 @@ FwdArgs fwd_args(kt_problem *p, int update) {
   a.rec_ch = p->rec_ch[p->cur];
   a.rec_s = p->rec_s[p->cur];
   a.rec_c = p->rec_c[p->cur];
-  a.partials = p->partials;
+  a.partials = p->sharded ? p->spart + (size_t)p->tile_off * p->g.n_ctrl : p->partials;
+  a.finish = p->sharded ? 0 : 1;
   a.counter = p->counter;
   a.tau = p->tau;
   a.norm2 = p->norm2;
@@ -477,11 +558,18 @@ kt_status launch_cross(kt_problem *p, int j, const void *psi, const void *xi, cu
   return prof_end(p, st);
 }
 
-// Launches of one forward sweep: no synchronisation and no change of host state, so that the
-// sequence can be captured into a graph.
-kt_status enqueue_forward(kt_problem *p, int update, cudaStream_t st, bool save_psi) {
+// Start of the forward-sweep segment holding interval j (1-based): the kept prefix [0, A] is one
+// segment, then checkpoint to checkpoint (see seg_end).
+int seg_start(const kt_problem *p, int j) {
+  if (p->ckpt == 0 || j <= p->ckpt_dense) return 0;
+  return p->ckpt_dense + ((j - 1 - p->ckpt_dense) / p->ckpt) * p->ckpt;
+}
+
+// First launches of a forward sweep: the pass set-up and, for an updating sweep, the overlap at t_0
+// (Delta eps of interval 1).
+kt_status fwd_begin(kt_problem *p, int update, cudaStream_t st, FwdArgs &a) {
   KT_CUDA(kt_launch_init_pass(p->g, p->U, p->pass, p->rstate, p->jcount[p->cur], st));
-  FwdArgs a = fwd_args(p, update);
+  a = fwd_args(p, update);
   if (update && p->cross) {
     kt_status s = launch_cross(p, 0, p->psi_init, ckpt_slot(p, 0), st);
     if (s != KT_OK) return s;
@@ -495,28 +583,61 @@ kt_status enqueue_forward(kt_problem *p, int update, cudaStream_t st, bool save_
     KT_CUDA(kt_launch_fwd(p->fp64, p->ept, p->g, p->im_fwd, p->ops, a, st));
     if ((s = prof_end(p, st)) != KT_OK) return s;
   }
-  for (int seg_a = 0; seg_a < p->nt; seg_a = seg_end(p, seg_a)) {
-    const int seg_b = seg_end(p, seg_a);
-    if (update && p->ckpt > 0 && seg_a >= p->ckpt_dense) {
-      kt_status s = recompute_segment(p, seg_a, seg_b, st);
-      if (s != KT_OK) return s;
-    }
-    for (int j = seg_a + 1; j <= seg_b; ++j) {
-      a.j = j;
-      a.psi_in = (j == 1) ? p->psi_init : p->psi[(j - 1) & 1];
-      a.psi_out = p->psi[j & 1];
-      a.chi_t = (update && j < p->nt) ? chi_at(p, j, seg_a) : nullptr;
-      kt_status s = prof_begin(p, KT_PROF_FWD, st);
-      if (s != KT_OK) return s;
-      KT_CUDA(kt_launch_fwd(p->fp64, p->ept, p->g, p->im_fwd, p->ops, a, st));
-      if ((s = prof_end(p, st)) != KT_OK) return s;
-      if (update && p->cross && j < p->nt && (s = launch_cross(p, j, p->psi[j & 1], chi_at(p, j, seg_a), st)) != KT_OK)
-        return s;
-      if (save_psi && j < p->nt && j % p->Kg == 0)
-        KT_CUDA(cudaMemcpyAsync(state_slot(p, p->psi_ck, j / p->Kg), p->psi[j & 1], p->state_bytes,
-                                cudaMemcpyDeviceToDevice, st));
+  return KT_OK;
+}
+
+// Interval j of a forward sweep (with the co-state recompute of its segment first, if any).
+kt_status fwd_step(kt_problem *p, int update, cudaStream_t st, bool save_psi, FwdArgs &a, int j) {
+  const int seg_a = seg_start(p, j);
+  kt_status s;
+  if (update && p->ckpt > 0 && seg_a >= p->ckpt_dense && j == seg_a + 1 &&
+      (s = recompute_segment(p, seg_a, seg_end(p, seg_a), st)) != KT_OK)
+    return s;
+  a.j = j;
+  a.psi_in = (j == 1) ? p->psi_init : p->psi[(j - 1) & 1];
+  a.psi_out = p->psi[j & 1];
+  a.chi_t = (update && j < p->nt) ? chi_at(p, j, seg_a) : nullptr;
+  if ((s = prof_begin(p, KT_PROF_FWD, st)) != KT_OK) return s;
+  KT_CUDA(kt_launch_fwd(p->fp64, p->ept, p->g, p->im_fwd, p->ops, a, st));
+  if ((s = prof_end(p, st)) != KT_OK) return s;
+  if (update && p->cross && j < p->nt && (s = launch_cross(p, j, p->psi[j & 1], chi_at(p, j, seg_a), st)) != KT_OK)
+    return s;
+  if (save_psi && j < p->nt && j % p->Kg == 0)
+    KT_CUDA(cudaMemcpyAsync(state_slot(p, p->psi_ck, j / p->Kg), p->psi[j & 1], p->state_bytes,
+                            cudaMemcpyDeviceToDevice, st));
+  return KT_OK;
+}
+
+// Sharded update of interval j+1 after the shards' overlaps at t_j are in spart: Delta eps from the
+// partials of all tiles, in the single-GPU summation order.
+kt_status shard_finish(kt_problem *p, int j, cudaStream_t st) {
+  kt_status s = prof_begin(p, KT_PROF_FINISH, st);
+  if (s != KT_OK) return s;
+  KT_CUDA(kt_launch_finish_update(p->g, p->n_tiles_total, p->spart, j, p->nt, p->shape, p->eps_old, p->deps,
+                                  p->eps_new, p->status, st));
+  return prof_end(p, st);
+}
+
+// Launches of one forward sweep: no synchronisation and no change of host state, so that the
+// sequence can be captured into a graph.  A shard driven by NCCL exchanges the tile partials of
+// every interval (in-place all-gather) and, at the end, tau of all trajectories.
+kt_status enqueue_forward(kt_problem *p, int update, cudaStream_t st, bool save_psi) {
+  if (p->sharded && !p->nccl_comm)
+    return fail(KT_ERR_STATE, "a trajectory shard runs through its group (krotov_group_update) or over NCCL "
+                              "(krotov_shard_nccl)");
+  FwdArgs a;
+  kt_status s = fwd_begin(p, update, st, a);
+  if (s != KT_OK) return s;
+  const bool exchange = p->sharded && update && !p->cross;
+  const size_t nloc = (size_t)p->g.n_tiles * p->g.n_ctrl;
+  for (int j = 0; j <= p->nt; ++j) {
+    if (j >= 1 && (s = fwd_step(p, update, st, save_psi, a, j)) != KT_OK) return s;
+    if (exchange && j < p->nt) {
+      if ((s = nccl_allgather(p, p->spart + (size_t)p->tile_off * p->g.n_ctrl, p->spart, nloc, st)) != KT_OK) return s;
+      if ((s = shard_finish(p, j, st)) != KT_OK) return s;
     }
   }
+  if (p->sharded && (s = nccl_allgather(p, p->tau, p->tau_all, (size_t)2 * p->M, st)) != KT_OK) return s;
   return KT_OK;
 }
 
@@ -545,6 +666,7 @@ kt_status forward_sweep(kt_problem *p, int update, cudaStream_t st, bool save_ps
 // Buffers and geometry of the gradient sweep (first use only).
 kt_status grad_setup(kt_problem *p, cudaStream_t st) {
   if (p->psi_ck) return KT_OK;
+  if (p->density) return fail(KT_ERR_UNSUPPORTED, "the frozen-record gradient is defined for trajectory problems");
   KtGeom g1 = p->g;
   g1.T = 1;
   g1.n_tiles = p->M;
@@ -648,7 +770,8 @@ kt_status gradient_sweep(kt_problem *p, cudaStream_t st) {
 kt_status enqueue_backward(kt_problem *p, cudaStream_t st) {
   const int prev = 1 - p->cur;
   void *chiT = ckpt_slot(p, p->nt);
-  KT_CUDA(kt_launch_chi_boundary(p->fp64, p->g, p->ops, p->cross ? nullptr : p->tau, chiT, st));
+  // chi_k(T) = tau_k |tgt>; the cross-trajectory xi_k(T) = |tgt>; a density matrix's P(T) = P_tgt
+  KT_CUDA(kt_launch_chi_boundary(p->fp64, p->g, p->ops, (p->cross || p->density) ? nullptr : p->tau, chiT, st));
   KT_CUDA(kt_launch_cursor_seek(p->g, p->rec_step[prev], p->jcount[prev], p->nt, p->cursor, st));
   const void *in = chiT;
   for (int j = p->nt; j >= 1; --j) {
@@ -723,13 +846,25 @@ kt_status graph_iteration(kt_problem *p, cudaStream_t st) {
   return KT_OK;
 }
 
+// F of the last forward sweep (a shard over NCCL: of all M_total trajectories, from the gathered tau,
+// summed in trajectory order like the single-GPU problem); tau_out gets this problem's M values.
 kt_status host_fidelity(kt_problem *p, double *F, double *tau_out, cudaStream_t st) {
-  std::vector<KtCplx> tau(p->M);
-  KT_CUDA(cudaMemcpyAsync(tau.data(), p->tau, sizeof(KtCplx) * p->M, cudaMemcpyDeviceToHost, st));
+  const bool all = p->sharded && p->nccl_comm;
+  const int n = all ? p->M_total : p->M;
+  std::vector<KtCplx> tau(n);
+  KT_CUDA(cudaMemcpyAsync(tau.data(), all ? p->tau_all : p->tau, sizeof(KtCplx) * n, cudaMemcpyDeviceToHost, st));
   KT_CUDA(cudaStreamSynchronize(st));
   double s = 0.0;
-  for (int k = 0; k < p->M; ++k) s += tau[k].re * tau[k].re + tau[k].im * tau[k].im;
-  if (F) *F = s / p->M;
+  for (int k = 0; k < n; ++k) s += tau[k].re * tau[k].re + tau[k].im * tau[k].im;
+  if (F) *F = s / n;
+  if (all && tau_out) {
+    for (int k = 0; k < p->M; ++k) {
+      tau_out[2 * k] = tau[p->tile_off * p->g.T + k].re;
+      tau_out[2 * k + 1] = tau[p->tile_off * p->g.T + k].im;
+    }
+    return KT_OK;
+  }
+  if (F && p->density) *F = tau[0].re;        // <<P_tgt|rho(T)>> = <tgt|rho(T)|tgt>
   if (tau_out)
     for (int k = 0; k < p->M; ++k) {
       tau_out[2 * k] = tau[k].re;
@@ -808,6 +943,7 @@ KT_API void krotov_free(kt_problem *p) {
     if (p->iter_graph[k]) cudaGraphDestroy(p->iter_graph[k]);
   }
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  if (p->nccl_comm && g_nccl.comm_destroy) g_nccl.comm_destroy(p->nccl_comm);
   for (void *a : p->allocs) cudaFree(a);
   delete p;
 }
@@ -825,7 +961,9 @@ struct HostImage {
 
 struct HostPlan {
   KtGeom g{};
-  int fp64 = 1, ept = 4, ckpt = 0, ckpt_dense = 0, cross = 0;
+  int fp64 = 1, ept = 4, ckpt = 0, ckpt_dense = 0, cross = 0, density = 0;
+  int sharded = 0, tile_off = 0, n_tiles_total = 0, M_total = 0;
+  std::vector<double> psi0;    // density: vec(rho_0) [d][2]; empty otherwise (the model's psi0 is used)
   double e_min = 0, e_max = 0, damping = 0;
   HostImage fwd, bwd;
   std::vector<int> lo_dl, ra_dl, hc_dl;
@@ -842,6 +980,8 @@ bool cavity_structure(const Gen &gf, const Gen &gb, const std::vector<int> &lo_d
                       const std::vector<int> &ra_dl, const std::vector<cd> &ra_val) {
   const int nl = gf.nl;
   if (nl != 6 && nl != 9) return false;
+  for (const Pair &q : gf.pairs)
+    if (q.kind != 0) return false;           // the fast path's pair hops raise one node and lower the other
   const int NP = nl / 3, NC = NP - 1;
   for (int x = 0; x < nl; ++x) {
     const int n = x % NP;
@@ -925,12 +1065,13 @@ bool ri_classes(const Gen &gf, const Gen &gb, const std::vector<cd> &lo_val, con
 
 // Validation, a1 (structured H_eff = H - (i/2) sum_l L_l^dag L_l), a2 (spectral interval and
 // Chebyshev length), tile geometry and the scaled generator tables of both directions.
-kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
+kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P, bool density = false) {
   if (!md || !cfg) return fail(KT_ERR_ARG, "NULL descriptor");
-  const int N = md->n_nodes, nl = md->n_loc;
+  int N = md->n_nodes;
+  const int nl = md->n_loc;
   if (N < 1 || N > KT_MAX_NODES) return fail(KT_ERR_UNSUPPORTED, "n_nodes must be in [1, %d]", KT_MAX_NODES);
   if (nl < 2 || nl > 16) return fail(KT_ERR_UNSUPPORTED, "n_loc must be in [2, 16]");
-  const int d = ipow(nl, N);
+  int d = ipow(nl, N);
   if (d < 0) return fail(KT_ERR_UNSUPPORTED, "dimension n_loc^n_nodes too large");
   if (md->n_ctrl < 1 || md->n_ctrl > KT_MAX_CTRL) return fail(KT_ERR_ARG, "n_ctrl must be in [1, %d]", KT_MAX_CTRL);
   if (md->n_lind < 0 || md->n_lind > KT_MAX_LIND) return fail(KT_ERR_ARG, "n_lind must be in [0, %d]", KT_MAX_LIND);
@@ -948,6 +1089,19 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
   if (cfg->ckpt_interval < -1) return fail(KT_ERR_ARG, "ckpt_interval must be -1 (automatic), 0 or > 0");
   if (cfg->tile_traj < -1) return fail(KT_ERR_ARG, "tile_traj must be -1 (autotuned), 0 (automatic) or a power of two <= 32");
   if (cfg->update_rule != 0 && cfg->update_rule != 1) return fail(KT_ERR_ARG, "update_rule must be 0 or 1");
+  const bool sharded = cfg->M_total > 0;
+  if (sharded) {
+    if (cfg->traj_offset < 0 || cfg->traj_offset + cfg->M > cfg->M_total)
+      return fail(KT_ERR_ARG, "a shard needs 0 <= traj_offset and traj_offset + M <= M_total");
+    if (cfg->update_rule != 0 || density)
+      return fail(KT_ERR_ARG, "sharding covers the independent-trajectory update (the cross-trajectory sum "
+                              "needs every pair of trajectories)");
+    if (cfg->tile_traj == -1) return fail(KT_ERR_ARG, "the shards of one problem need one tile width: no autotuning");
+  } else if (cfg->traj_offset != 0) {
+    return fail(KT_ERR_ARG, "traj_offset without M_total");
+  }
+  if (density && (cfg->update_rule != 0 || cfg->M != 1))
+    return fail(KT_ERR_ARG, "a density-matrix problem has one Liouville-space state and the update of Eq. krotovupdate");
   if (cfg->jump_scheme != 0 && cfg->jump_scheme != 1) return fail(KT_ERR_ARG, "jump_scheme must be 0 or 1");
   for (int c = 0; c < md->n_ctrl; ++c) {
     if (md->ctrl_node[c] < 0 || md->ctrl_node[c] >= N) return fail(KT_ERR_ARG, "ctrl_node[%d] out of range", c);
@@ -967,6 +1121,8 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
   gf.ctrl.assign((size_t)nc * nl * nl, 0.0);
   for (size_t e = 0; e < gf.ctrl.size(); ++e) gf.ctrl[e] = cd(md->hc_local[2 * e], md->hc_local[2 * e + 1]);
   gf.ctrl_node.assign(md->ctrl_node, md->ctrl_node + nc);
+  gf.n_ctrl = nc;
+  for (int c = 0; c < nc; ++c) gf.term_ctrl.push_back(c);
   std::vector<cd> a(nl * nl, 0.0);
   if (md->a_local)
     for (int e = 0; e < nl * nl; ++e) a[e] = cd(md->a_local[2 * e], md->a_local[2 * e + 1]);
@@ -981,6 +1137,8 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
       amax = std::max(amax, std::abs(a[x * nl + y]));
     }
     if (nr > 1 || ncol > 1) return fail(KT_ERR_ARG, "a_local must have at most one nonzero per row and per column");
+    if (a[x * nl + x] != 0.0 && (md->n_pairs > 0 || md->n_lind > 0))
+      return fail(KT_ERR_ARG, "a_local must have no diagonal entry (a ladder factor moves the local state)");
   }
   std::vector<Pair> raw;
   for (int q = 0; q < md->n_pairs; ++q) {
@@ -1014,8 +1172,76 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
   gf.pairs.erase(std::remove_if(gf.pairs.begin(), gf.pairs.end(),
                                 [&](const Pair &q) { return std::abs(q.coef) <= 1e-13 * pmax; }),
                  gf.pairs.end());
+  std::vector<cd> psi_t(d), psi_0;                        // target (and density: initial) state vectors
+  for (int x = 0; x < d; ++x) psi_t[x] = cd(md->psi_tgt[2 * x], md->psi_tgt[2 * x + 1]);
+  int n_lind = md->n_lind;
+  if (density) {
+    // Liouville space (Sec. 2.2, Eq. lindblad): rho_{xy} -> vec(rho)[x d + y] evolves as
+    // d vec(rho)/dt = -i G vec(rho), G = H_eff (x) 1 - 1 (x) H_eff^* + i sum_l L_l (x) L_l^*, a network of
+    // 2N nodes (ket nodes 0..N-1, bra nodes N..2N-1, same local dimension): the ket nodes carry
+    // H_eff's factors and hops, the bra nodes minus their complex conjugates (the ladder factor is
+    // real, so conj(a) = a), and every pair (ket i, bra j) the hop i c_li conj(c_lj) a_i a_j (kind 1).
+    // A control eps_c acts through H_c (x) 1 - 1 (x) H_c^*: one term on its ket and one on its bra node.
+    for (int e = 0; e < nl * nl; ++e)
+      if (a[e].imag() != 0.0) return fail(KT_ERR_UNSUPPORTED, "density-matrix problems need a real ladder factor");
+    if (2 * N > KT_MAX_NODES) return fail(KT_ERR_UNSUPPORTED, "density-matrix problems need n_nodes <= %d", KT_MAX_NODES / 2);
+    Gen lg;
+    lg.N = 2 * N;
+    lg.nl = nl;
+    lg.n_ctrl = nc;
+    lg.loc.assign((size_t)2 * N * nl * nl, 0.0);
+    for (int i = 0; i < N; ++i)
+      for (int e = 0; e < nl * nl; ++e) {
+        lg.loc[(size_t)i * nl * nl + e] = gf.loc[(size_t)i * nl * nl + e];
+        lg.loc[(size_t)(N + i) * nl * nl + e] = -std::conj(gf.loc[(size_t)i * nl * nl + e]);
+      }
+    for (int c = 0; c < nc; ++c)
+      for (int side = 0; side < 2; ++side) {
+        for (int e = 0; e < nl * nl; ++e) {
+          const cd v = gf.ctrl[(size_t)c * nl * nl + e];
+          lg.ctrl.push_back(side == 0 ? v : -std::conj(v));
+        }
+        lg.ctrl_node.push_back(gf.ctrl_node[c] + side * N);
+        lg.term_ctrl.push_back(c);
+      }
+    for (const Pair &q : gf.pairs) {
+      lg.pairs.push_back(Pair{q.dst, q.src, q.coef, 0});
+      lg.pairs.push_back(Pair{N + q.dst, N + q.src, -std::conj(q.coef), 0});
+    }
+    for (int i = 0; i < N; ++i)
+      for (int jn = 0; jn < N; ++jn) {
+        cd w = 0.0;
+        for (int l = 0; l < md->n_lind; ++l) {
+          const cd ci = cd(md->lind_coef[2 * (l * N + i)], md->lind_coef[2 * (l * N + i) + 1]);
+          const cd cj = cd(md->lind_coef[2 * (l * N + jn)], md->lind_coef[2 * (l * N + jn) + 1]);
+          w += cd(0.0, 1.0) * ci * std::conj(cj);
+        }
+        if (w != 0.0) lg.pairs.push_back(Pair{i, N + jn, w, 1});
+      }
+    const long long dd = (long long)d * d;
+    if (dd > (1 << 24)) return fail(KT_ERR_UNSUPPORTED, "density-matrix problems need d^2 <= 2^24");
+    std::vector<cd> psi0v(d);
+    for (int x = 0; x < d; ++x) {
+      if (!md->psi0) return fail(KT_ERR_ARG, "density-matrix problems start from the pure state psi0");
+      psi0v[x] = cd(md->psi0[2 * x], md->psi0[2 * x + 1]);
+    }
+    psi_0.assign((size_t)dd, 0.0);
+    std::vector<cd> vt((size_t)dd);
+    for (int x = 0; x < d; ++x)
+      for (int y = 0; y < d; ++y) {
+        psi_0[(size_t)x * d + y] = psi0v[x] * std::conj(psi0v[y]);     // rho_0 = |psi0><psi0|
+        vt[(size_t)x * d + y] = psi_t[x] * std::conj(psi_t[y]);         // P(T) = |tgt><tgt|
+      }
+    psi_t.swap(vt);
+    gf = lg;
+    N = 2 * N;
+    d = (int)dd;
+    n_lind = 0;                            // no jumps: the density matrix evolves deterministically
+  }
   if ((int)gf.pairs.size() > KT_MAX_PAIRS) return fail(KT_ERR_UNSUPPORTED, "more than %d pair terms", KT_MAX_PAIRS);
+  if ((int)gf.ctrl_node.size() > KT_MAX_CTERMS) return fail(KT_ERR_UNSUPPORTED, "more than %d control terms", KT_MAX_CTERMS);
   const Gen gb = minus_adjoint(gf);
+  const int nterm = (int)gf.ctrl_node.size();
 
   // ---- a2
   double E = cfg->eps_bound;
@@ -1045,7 +1271,9 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
   const double dt = cfg->T / nt;
   const cd z(1.0, damp / r);
   const double rho = std::max(1.0, std::abs(z + std::sqrt(z - 1.0) * std::sqrt(z + 1.0)));
-  const double tol = cfg->cheb_tol > 0 ? cfg->cheb_tol : (cfg->prec == KT_FP64 ? 1e-15 : 1e-8);
+  // default truncation: 1e-16 in FP64 (the row bound is sharp, so the criterion's margin is the
+  // tolerance itself), 1e-8 in FP32 (below the recurrence's own rounding)
+  const double tol = cfg->cheb_tol > 0 ? cfg->cheb_tol : (cfg->prec == KT_FP64 ? 1e-16 : 1e-8);
   std::vector<double> J(256);
   kt_bessel_miller(r * dt, 256, J.data());
   int K = -1;
@@ -1072,7 +1300,12 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
   g.d = d;
   g.M = M;
   g.n_ctrl = nc;
-  g.n_lind = md->n_lind;
+  g.n_cterms = nterm;
+  for (int t = 0; t < nterm; ++t) {
+    g.cterm_ctrl[t] = gf.term_ctrl[t];
+    g.cterm_node[t] = gf.ctrl_node[t];
+  }
+  g.n_lind = n_lind;
   g.n_pairs = (int)gf.pairs.size();
   g.K = K;
   g.max_jumps = (cfg->draws_per_traj - 1) / 2;   // 0: any jump is reported as KT_ERR_RECORD_FULL
@@ -1098,9 +1331,9 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
       for (int y = 0; y < nl; ++y) {
         if (y == x) continue;
         bool nz = at(gf.loc, i * nl * nl, nl, x, y) != 0.0 || at(gb.loc, i * nl * nl, nl, x, y) != 0.0;
-        for (int c = 0; c < nc; ++c)
-          if (g.ctrl_node[c] == i)
-            nz = nz || at(gf.ctrl, c * nl * nl, nl, x, y) != 0.0 || at(gb.ctrl, c * nl * nl, nl, x, y) != 0.0;
+        for (int t = 0; t < nterm; ++t)
+          if (gf.ctrl_node[t] == i)
+            nz = nz || at(gf.ctrl, t * nl * nl, nl, x, y) != 0.0 || at(gb.ctrl, t * nl * nl, nl, x, y) != 0.0;
         if (nz) cl.push_back(y);
       }
       S = std::max(S, (int)cl.size());
@@ -1112,10 +1345,10 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
   if (ri) S = 2;
   g.S = std::max(S, 1);
   int SH = 1;
-  for (int c = 0; c < nc; ++c)
+  for (int t = 0; t < nterm; ++t)
     for (int x = 0; x < nl; ++x) {
       int n = 0;
-      for (int y = 0; y < nl; ++y) n += at(gf.ctrl, c * nl * nl, nl, x, y) != 0.0;
+      for (int y = 0; y < nl; ++y) n += at(gf.ctrl, t * nl * nl, nl, x, y) != 0.0;
       SH = std::max(SH, n);
     }
   if (SH > KT_MAX_SH) return fail(KT_ERR_UNSUPPORTED, "a control factor row has %d > %d entries", SH, KT_MAX_SH);
@@ -1146,18 +1379,40 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
     if (kt_smem_bytes(t, esz, false) > 227 * 1024) continue;
     Tsel = T;
     // prefer more tiles when the trajectories would not fill the GPU
-    if (cfg->tile_traj <= 0 && (M + T - 1) / T < 2 * 152 && T > 1 && (long long)d * (T / 2) >= 256) continue;
+    // (a shard plans with the whole problem's trajectory count: every shard needs the same tile width)
+    const int Mh = sharded ? cfg->M_total : M;
+    if (cfg->tile_traj <= 0 && (Mh + T - 1) / T < 2 * 152 && T > 1 && (long long)d * (T / 2) >= 256) continue;
     break;
   }
   if (Tsel == 0) return fail(KT_ERR_UNSUPPORTED, "dimension %d does not fit one trajectory tile in shared memory", d);
   g.T = Tsel;
   g.n_tiles = (M + Tsel - 1) / Tsel;
   g.M_pad = g.n_tiles * Tsel;
+  g.M_norm = (double)(sharded ? cfg->M_total : M);
+  g.inject_timeout = cfg->inject_copy_timeout != 0;
+  if (sharded) {
+    if (cfg->traj_offset % Tsel != 0 || (cfg->traj_offset + M != cfg->M_total && M % Tsel != 0))
+      return fail(KT_ERR_ARG, "shard boundaries must fall on tile boundaries (tile width %d)", Tsel);
+    P.sharded = 1;
+    P.M_total = cfg->M_total;
+    P.tile_off = cfg->traj_offset / Tsel;
+    P.n_tiles_total = (cfg->M_total + Tsel - 1) / Tsel;
+  }
   g.tile_elems = (d * Tsel + 3) / 4 * 4;
   {
     KtGeom t = g;
     t.nthreads = fiber ? std::max(32, ((d / nl) * Tsel + 31) / 32 * 32) : maxthr;
-    g.prefetch_chi = kt_smem_bytes(t, esz, true) <= 227 * 1024 ? 1 : 0;
+    const size_t smem3 = kt_smem_bytes(t, esz, true);
+    g.prefetch_chi = smem3 <= 227 * 1024 ? 1 : 0;
+    // backward kernel: when the tiles need several waves and a third buffer fits, CTAs loop over
+    // tiles (about one CTA per SM slot) and prefetch the next tile's input during the current series
+    int dev = 0, sms = 0;
+    g.bwd_grid = 0;
+    if (g.prefetch_chi && cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0) {
+      const int per_sm = std::max(1, std::min((int)((227 * 1024) / smem3), 2048 / std::max(32, t.nthreads)));
+      if (g.n_tiles > sms * per_sm) g.bwd_grid = sms * per_sm;
+    }
   }
   if (fiber) {
     // launcher codes -(100 v + nl): v = 0 fiber, 1 cavity structure, 2 the same with T = 1 compiled
@@ -1179,9 +1434,9 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
     const int nls = nl * g.S;
     im.dl.assign((size_t)N * nls, 0);
     im.base.assign((size_t)N * nls, KtCplx{0, 0});
-    im.cslot.assign((size_t)nc * nls, KtCplx{0, 0});
+    im.cslot.assign((size_t)nterm * nls, KtCplx{0, 0});
     im.dg.assign((size_t)N * nl, KtCplx{0, 0});
-    im.cdg.assign((size_t)nc * nl, KtCplx{0, 0});
+    im.cdg.assign((size_t)nterm * nl, KtCplx{0, 0});
     for (int i = 0; i < N; ++i)
       for (int x = 0; x < nl; ++x) {
         const std::vector<int> &cl = cols[(size_t)i * nl + x];
@@ -1196,17 +1451,17 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
         if (i == 0) dv -= cgen / r;
         im.dg[(size_t)i * nl + x] = KtCplx{dv.real(), dv.imag()};
       }
-    for (int c = 0; c < nc; ++c) {
-      const int i = g.ctrl_node[c];
+    for (int t = 0; t < nterm; ++t) {
+      const int i = gen.ctrl_node[t];
       for (int x = 0; x < nl; ++x) {
         const std::vector<int> &cl = cols[(size_t)i * nl + x];
         for (size_t q = 0; q < cl.size(); ++q) {
           if (cl[q] == x) continue;
-          const cd v = at(gen.ctrl, c * nl * nl, nl, x, cl[q]) / r;
-          im.cslot[(size_t)c * nls + x * g.S + q] = KtCplx{v.real(), v.imag()};
+          const cd v = at(gen.ctrl, t * nl * nl, nl, x, cl[q]) / r;
+          im.cslot[(size_t)t * nls + x * g.S + q] = KtCplx{v.real(), v.imag()};
         }
-        const cd dv = at(gen.ctrl, c * nl * nl, nl, x, x) / r;
-        im.cdg[(size_t)c * nl + x] = KtCplx{dv.real(), dv.imag()};
+        const cd dv = at(gen.ctrl, t * nl * nl, nl, x, x) / r;
+        im.cdg[(size_t)t * nl + x] = KtCplx{dv.real(), dv.imag()};
       }
     }
     const int nl2 = nl * nl;
@@ -1218,12 +1473,14 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
       im.pdst[q] = pr.dst;
       im.psrc[q] = pr.src;
       im.pc[q] = KtCplx{(pr.coef / r).real(), (pr.coef / r).imag()};
+      const bool rd = pr.kind != 1, rs = pr.kind == 2;     // raise the dst / src node?
       for (int xd = 0; xd < nl; ++xd)
         for (int xs = 0; xs < nl; ++xs) {
-          if (ra_val[xd] == 0.0 || lo_val[xs] == 0.0) continue;
+          const cd vd = rd ? ra_val[xd] : lo_val[xd], vs = rs ? ra_val[xs] : lo_val[xs];
+          if (vd == 0.0 || vs == 0.0) continue;
           const size_t e = (size_t)q * nl2 + xd * nl + xs;
-          im.poff[e] = ra_dl[xd] * g.stride[pr.dst] + lo_dl[xs] * g.stride[pr.src];
-          const cd v = pr.coef * ra_val[xd] * lo_val[xs] / r;
+          im.poff[e] = (rd ? ra_dl[xd] : lo_dl[xd]) * g.stride[pr.dst] + (rs ? ra_dl[xs] : lo_dl[xs]) * g.stride[pr.src];
+          const cd v = pr.coef * vd * vs / r;
           im.pval[e] = KtCplx{v.real(), v.imag()};
         }
     }
@@ -1246,19 +1503,19 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
     P.lo_val[x] = KtCplx{lo_val[x].real(), lo_val[x].imag()};
     P.ra_val[x] = KtCplx{ra_val[x].real(), ra_val[x].imag()};
   }
-  P.lind.assign((size_t)std::max(1, md->n_lind) * N, KtCplx{0, 0});
-  for (int e = 0; e < md->n_lind * N; ++e) P.lind[e] = KtCplx{md->lind_coef[2 * e], md->lind_coef[2 * e + 1]};
-  P.hc_dl.assign((size_t)nc * nl * SH, 0);
-  P.hc_val.assign((size_t)nc * nl * SH, KtCplx{0, 0});
-  for (int c = 0; c < nc; ++c)
+  P.lind.assign((size_t)std::max(1, n_lind) * N, KtCplx{0, 0});
+  for (int e = 0; e < n_lind * N; ++e) P.lind[e] = KtCplx{md->lind_coef[2 * e], md->lind_coef[2 * e + 1]};
+  // control factors of the update overlap, one table per control term (unscaled dG/deps_c part)
+  P.hc_dl.assign((size_t)nterm * nl * SH, 0);
+  P.hc_val.assign((size_t)nterm * nl * SH, KtCplx{0, 0});
+  for (int t = 0; t < nterm; ++t)
     for (int x = 0; x < nl; ++x) {
       int q = 0;
       for (int y = 0; y < nl; ++y) {
-        const size_t e = (size_t)c * nl * nl + x * nl + y;
-        const cd v = cd(md->hc_local[2 * e], md->hc_local[2 * e + 1]);
+        const cd v = gf.ctrl[(size_t)t * nl * nl + x * nl + y];
         if (v == 0.0) continue;
-        P.hc_dl[((size_t)c * nl + x) * SH + q] = y - x;
-        P.hc_val[((size_t)c * nl + x) * SH + q] = KtCplx{v.real(), v.imag()};
+        P.hc_dl[((size_t)t * nl + x) * SH + q] = y - x;
+        P.hc_val[((size_t)t * nl + x) * SH + q] = KtCplx{v.real(), v.imag()};
         ++q;
       }
     }
@@ -1269,7 +1526,16 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P) {
     P.digits[x] = w;
   }
   P.tgt.resize(d);
-  for (int x = 0; x < d; ++x) P.tgt[x] = KtCplx{md->psi_tgt[2 * x], md->psi_tgt[2 * x + 1]};
+  for (int x = 0; x < d; ++x) P.tgt[x] = KtCplx{psi_t[x].real(), psi_t[x].imag()};
+  P.density = density ? 1 : 0;
+  g.density = P.density;
+  if (density) {
+    P.psi0.resize((size_t)2 * d);
+    for (int x = 0; x < d; ++x) {
+      P.psi0[2 * x] = psi_0[x].real();
+      P.psi0[2 * x + 1] = psi_0[x].imag();
+    }
+  }
   return KT_OK;
 }
 
@@ -1348,6 +1614,11 @@ kt_status create_problem(const kt_model_desc *md, const kt_config *cfg, const Ho
   p->fp64 = P.fp64;
   p->ept = P.ept;
   p->cross = P.cross;
+  p->density = P.density;
+  p->sharded = P.sharded;
+  p->tile_off = P.tile_off;
+  p->n_tiles_total = P.n_tiles_total;
+  p->M_total = P.M_total;
   p->esz = P.fp64 ? 16 : 8;
   p->nt = nt;
   p->M = M;
@@ -1387,8 +1658,8 @@ kt_status create_problem(const kt_model_desc *md, const kt_config *cfg, const Ho
   {
     std::vector<double> buf64;
     std::vector<float> buf32;
-    const bool batch = md->psi0_batch != nullptr;
-    const double *src = batch ? md->psi0_batch : md->psi0;
+    const bool batch = !P.density && md->psi0_batch != nullptr;
+    const double *src = P.density ? P.psi0.data() : (batch ? md->psi0_batch : md->psi0);
     if (p->fp64) {
       to_tiles<double>(p, src, batch, buf64);
       TRY(upload(p, (double **)&p->psi_init, buf64.data(), buf64.size(), st));
@@ -1411,6 +1682,10 @@ kt_status create_problem(const kt_model_desc *md, const kt_config *cfg, const Ho
   }
   TRY(dev_alloc(p, (void **)&p->cursor, Mp * sizeof(int)));
   TRY(dev_alloc(p, (void **)&p->partials, (size_t)g.n_tiles * nc * sizeof(double)));
+  if (p->sharded) {
+    TRY(dev_alloc(p, (void **)&p->spart, (size_t)p->n_tiles_total * nc * sizeof(double)));
+    TRY(dev_alloc(p, (void **)&p->tau_all, (size_t)p->M_total * sizeof(KtCplx)));
+  }
   TRY(dev_alloc(p, (void **)&p->counter, sizeof(unsigned)));
   TRY(dev_alloc(p, (void **)&p->tau, Mp * sizeof(KtCplx)));
   TRY(dev_alloc(p, (void **)&p->norm2, Mp * sizeof(double)));
@@ -1517,7 +1792,33 @@ kt_status autotune(const kt_model_desc *md, const kt_config *cfg, cudaStream_t s
 
 }  // namespace
 
+// Configuration of a density-matrix problem: one Liouville-space "trajectory" whose threshold
+// r = -1 can never be reached (the density matrix has no jumps), the update of Eq. krotovupdate.
+static const double kNoJump = -1.0;
+static kt_config density_config(const kt_config *cfg) {
+  kt_config c = *cfg;
+  c.M = 1;
+  c.tile_traj = 1;                 // one state: one tile of width 1
+  c.uniforms = &kNoJump;
+  c.n_passes = 1;
+  c.draws_per_traj = 1;
+  c.update_rule = 0;
+  c.jump_scheme = 0;
+  return c;
+}
+
 extern "C" {
+
+KT_API kt_status krotov_init_density(const kt_model_desc *md, const kt_config *cfg, void *stream, kt_problem **out) {
+  if (!md || !cfg || !out) return fail(KT_ERR_ARG, "NULL descriptor or output pointer");
+  *out = nullptr;
+  if (cfg->tile_traj == -1) return fail(KT_ERR_ARG, "a density-matrix problem has one state: nothing to autotune");
+  const kt_config c = density_config(cfg);
+  HostPlan P;
+  kt_status s = plan(md, &c, P, true);
+  if (s != KT_OK) return s;
+  return create_problem(md, &c, P, (cudaStream_t)stream, false, out);
+}
 
 KT_API kt_status krotov_init(const kt_model_desc *md, const kt_config *cfg, void *stream, kt_problem **out) {
   if (!md || !cfg || !out) return fail(KT_ERR_ARG, "NULL descriptor or output pointer");
@@ -1535,12 +1836,19 @@ KT_API kt_status krotov_init(const kt_model_desc *md, const kt_config *cfg, void
 KT_API kt_status kt_generator_dense(const kt_model_desc *md, const kt_config *cfg, int direction, const double *eps,
                                     double *out) {
   if (!out || !eps) return fail(KT_ERR_ARG, "NULL argument");
+  if (direction < 0 || direction > 3) return fail(KT_ERR_ARG, "direction must be 0..3");
   HostPlan P;
-  kt_status s = plan(md, cfg, P);
+  kt_status s;
+  if (direction >= 2) {
+    kt_config c = density_config(cfg);
+    s = plan(md, &c, P, true);
+  } else {
+    s = plan(md, cfg, P);
+  }
   if (s != KT_OK) return s;
   const KtGeom &g = P.g;
-  const HostImage &im = direction ? P.bwd : P.fwd;
-  const double cgen = direction ? g.c_bwd : g.c_fwd;
+  const HostImage &im = (direction & 1) ? P.bwd : P.fwd;
+  const double cgen = (direction & 1) ? g.c_bwd : g.c_fwd;
   const int d = g.d, nl = g.n_loc, nls = nl * g.S, nl2 = nl * nl;
   std::fill(out, out + (size_t)d * d * 2, 0.0);
   auto add = [&](int x, int y, cd v) -> bool {
@@ -1555,14 +1863,16 @@ KT_API kt_status kt_generator_dense(const kt_model_desc *md, const kt_config *cf
     for (int i = 0; i < g.n_nodes; ++i) {
       const int xi = (dig >> (4 * i)) & 15;
       dv += cd(im.dg[(size_t)i * nl + xi].re, im.dg[(size_t)i * nl + xi].im);
-      for (int c = 0; c < g.n_ctrl; ++c)
-        if (g.ctrl_node[c] == i) dv += eps[c] * cd(im.cdg[(size_t)c * nl + xi].re, im.cdg[(size_t)c * nl + xi].im);
+      for (int t = 0; t < g.n_cterms; ++t)
+        if (g.cterm_node[t] == i)
+          dv += eps[g.cterm_ctrl[t]] * cd(im.cdg[(size_t)t * nl + xi].re, im.cdg[(size_t)t * nl + xi].im);
       for (int q = 0; q < g.S; ++q) {
         const size_t e = (size_t)i * nls + xi * g.S + q;
         if (!im.dl[e]) continue;
         cd v(im.base[e].re, im.base[e].im);
-        for (int c = 0; c < g.n_ctrl; ++c)
-          if (g.ctrl_node[c] == i) v += eps[c] * cd(im.cslot[(size_t)c * nls + xi * g.S + q].re, im.cslot[(size_t)c * nls + xi * g.S + q].im);
+        for (int t = 0; t < g.n_cterms; ++t)
+          if (g.cterm_node[t] == i)
+            v += eps[g.cterm_ctrl[t]] * cd(im.cslot[(size_t)t * nls + xi * g.S + q].re, im.cslot[(size_t)t * nls + xi * g.S + q].im);
         if (!add(x, x + im.dl[e] * g.stride[i], v * g.r)) return fail(KT_ERR_RANGE, "node entry leaves the space at row %d", x);
       }
     }
@@ -1718,7 +2028,7 @@ KT_API kt_status krotov_gradient(kt_problem *p, const double *eps_dev, double *d
 KT_API kt_status krotov_get_JT(kt_problem *p, double *JT_dev, void *stream) {
   if (!p || !JT_dev) return fail(KT_ERR_ARG, "NULL argument");
   if (!p->have_fwd) return fail(KT_ERR_STATE, "no forward sweep yet");
-  KT_CUDA(kt_launch_functional(p->tau, p->M, JT_dev, (cudaStream_t)stream));
+  KT_CUDA(kt_launch_functional(p->tau, p->M, p->density, JT_dev, (cudaStream_t)stream));
   return KT_OK;
 }
 
@@ -1976,6 +2286,166 @@ KT_API void krotov_batch_free(kt_batch *b) {
   for (kt_batch::Entry &e : b->cache) drop_entry(e);
   for (kt_problem *p : b->probs) krotov_free(p);
   delete b;
+}
+
+}  // extern "C"
+
+// ============================================================================ trajectory sharding
+// A problem's trajectories split into shards (kt_config.traj_offset / M_total): every shard
+// propagates its own trajectories, and the only exchange is, once per interval, the per-tile partial
+// sums of the update overlap (Sec. 2.3: the trajectories are independent, only scalars are
+// communicated), after which every shard forms the same Delta eps in the single-GPU order.
+struct kt_group {
+  std::vector<kt_problem *> shards;   // borrowed, ordered by trajectory offset
+};
+
+namespace {
+
+// Forward sweep of every shard of a group, interval by interval on one stream: the shards' overlaps at
+// t_j, the partial slices copied into every shard's copy of the global array, then Delta eps.
+kt_status group_forward(kt_group *gr, int update, cudaStream_t st) {
+  const size_t n = gr->shards.size();
+  std::vector<FwdArgs> a(n);
+  kt_status s;
+  for (size_t i = 0; i < n; ++i)
+    if ((s = fwd_begin(gr->shards[i], update, st, a[i])) != KT_OK) return s;
+  const int nt = gr->shards[0]->nt;
+  auto exchange = [&](int j) -> kt_status {
+    for (kt_problem *src : gr->shards) {
+      const size_t off = (size_t)src->tile_off * src->g.n_ctrl, len = (size_t)src->g.n_tiles * src->g.n_ctrl;
+      for (kt_problem *dst : gr->shards)
+        if (dst != src)
+          KT_CUDA(cudaMemcpyAsync(dst->spart + off, src->spart + off, len * sizeof(double), cudaMemcpyDefault, st));
+    }
+    for (kt_problem *p : gr->shards)
+      if ((s = shard_finish(p, j, st)) != KT_OK) return s;
+    return KT_OK;
+  };
+  if (update && (s = exchange(0)) != KT_OK) return s;
+  for (int j = 1; j <= nt; ++j) {
+    for (size_t i = 0; i < n; ++i)
+      if ((s = fwd_step(gr->shards[i], update, st, false, a[i], j)) != KT_OK) return s;
+    if (update && j < nt && (s = exchange(j)) != KT_OK) return s;
+  }
+  kt_status first = KT_OK;
+  for (kt_problem *p : gr->shards) {
+    s = read_status(p, st);
+    if (s != KT_OK && first == KT_OK) first = s;
+  }
+  if (first != KT_OK) {
+    for (kt_problem *p : gr->shards) p->have_fwd = p->have_bwd = false;
+    return first;
+  }
+  for (kt_problem *p : gr->shards) commit_forward(p, update, false);
+  return KT_OK;
+}
+
+// F over all shards' trajectories, summed in global trajectory order (as the unsharded problem does).
+kt_status group_fidelity(kt_group *gr, double *F, cudaStream_t st) {
+  double s = 0.0;
+  int M = 0;
+  for (kt_problem *p : gr->shards) {
+    std::vector<KtCplx> tau(p->M);
+    KT_CUDA(cudaMemcpyAsync(tau.data(), p->tau, sizeof(KtCplx) * p->M, cudaMemcpyDeviceToHost, st));
+    KT_CUDA(cudaStreamSynchronize(st));
+    for (int k = 0; k < p->M; ++k) s += tau[k].re * tau[k].re + tau[k].im * tau[k].im;
+    M += p->M;
+  }
+  *F = s / M;
+  return KT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+KT_API kt_status kt_nccl_unique_id(const char *nccl_library, void *id_out) {
+  if (!id_out) return fail(KT_ERR_ARG, "NULL output");
+  kt_status s = nccl_load(nccl_library);
+  if (s != KT_OK) return s;
+  const int r = g_nccl.get_unique_id(id_out);
+  if (r != 0) return fail(KT_ERR_CUDA, "ncclGetUniqueId failed: %s", g_nccl.error_string(r));
+  return KT_OK;
+}
+
+KT_API kt_status krotov_shard_nccl(kt_problem *p, const void *unique_id, int rank, int world, const char *nccl_library) {
+  if (!p || !unique_id) return fail(KT_ERR_ARG, "NULL argument");
+  if (!p->sharded) return fail(KT_ERR_ARG, "not a shard: create the problem with kt_config.M_total > 0");
+  if (p->in_group) return fail(KT_ERR_STATE, "the shard belongs to a group");
+  if (p->nccl_comm) return fail(KT_ERR_STATE, "the shard already has a communicator");
+  if (world < 1 || rank < 0 || rank >= world || (long long)world * p->M != p->M_total ||
+      p->tile_off * p->g.T != rank * p->M)
+    return fail(KT_ERR_ARG, "NCCL shards hold equal slices in rank order: M_total = world * M, traj_offset = rank * M");
+  kt_status s = nccl_load(nccl_library);
+  if (s != KT_OK) return s;
+  std::array<char, 128> id;
+  std::memcpy(id.data(), unique_id, 128);
+  void *comm = nullptr;
+  const int r = g_nccl.comm_init_rank(&comm, world, id, rank);
+  if (r != 0) return fail(KT_ERR_CUDA, "ncclCommInitRank failed: %s", g_nccl.error_string(r));
+  p->nccl_comm = comm;
+  p->nccl_rank = rank;
+  p->nccl_world = world;
+  return KT_OK;
+}
+
+KT_API kt_status krotov_group_init(kt_problem *const *shards, int n, kt_group **out) {
+  if (!shards || !out || n < 1) return fail(KT_ERR_ARG, "NULL argument or n < 1");
+  *out = nullptr;
+  std::vector<kt_problem *> v(shards, shards + n);
+  for (kt_problem *p : v)
+    if (!p || !p->sharded || p->in_group || p->nccl_comm)
+      return fail(KT_ERR_ARG, "every member must be a shard (M_total > 0) of no other group and without NCCL");
+  std::sort(v.begin(), v.end(), [](const kt_problem *a, const kt_problem *b) { return a->tile_off < b->tile_off; });
+  int next = 0;
+  for (kt_problem *p : v) {
+    const kt_problem *q = v[0];
+    if (p->tile_off != next || p->M_total != q->M_total || p->n_tiles_total != q->n_tiles_total ||
+        p->g.T != q->g.T || p->g.nthreads != q->g.nthreads || p->nt != q->nt || p->g.n_ctrl != q->g.n_ctrl)
+      return fail(KT_ERR_ARG, "the shards must tile one problem: same M_total, tile width, nt and controls, "
+                              "consecutive trajectory ranges");
+    next += p->g.n_tiles;
+  }
+  if (next != v[0]->n_tiles_total) return fail(KT_ERR_ARG, "the shards do not cover all %d tiles", v[0]->n_tiles_total);
+  kt_group *g = new kt_group();
+  g->shards = v;
+  for (kt_problem *p : v) p->in_group = true;
+  *out = g;
+  return KT_OK;
+}
+
+KT_API kt_status krotov_group_update(kt_group *gr, int n_iter, double *JT_out, void *stream) {
+  if (!gr) return fail(KT_ERR_ARG, "NULL group");
+  if (n_iter < 0) return fail(KT_ERR_ARG, "n_iter < 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  kt_status s;
+  bool fresh = false;
+  for (kt_problem *p : gr->shards) fresh = fresh || !p->have_fwd;
+  if (fresh && (s = group_forward(gr, 0, st)) != KT_OK) return s;
+  for (int it = 0; it < n_iter; ++it) {
+    for (kt_problem *p : gr->shards)
+      if ((s = backward_sweep(p, st)) != KT_OK) return s;
+    if ((s = group_forward(gr, 1, st)) != KT_OK) return s;
+    if (JT_out) {
+      double F = 0.0;
+      if ((s = group_fidelity(gr, &F, st)) != KT_OK) return s;
+      JT_out[it] = 1.0 - F;
+    }
+  }
+  return KT_OK;
+}
+
+KT_API kt_status krotov_group_fidelity(kt_group *gr, double *F_out, void *stream) {
+  if (!gr || !F_out) return fail(KT_ERR_ARG, "NULL argument");
+  for (kt_problem *p : gr->shards)
+    if (!p->have_fwd) return fail(KT_ERR_STATE, "no forward sweep yet");
+  return group_fidelity(gr, F_out, (cudaStream_t)stream);
+}
+
+KT_API void krotov_group_free(kt_group *gr) {
+  if (!gr) return;
+  for (kt_problem *p : gr->shards) p->in_group = false;
+  delete gr;
 }
 
 }  // extern "C"

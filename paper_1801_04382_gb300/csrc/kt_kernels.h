@@ -45,8 +45,9 @@ struct FwdArgs {
   int *rec_ch;
   double *rec_s;
   double *rec_c;
-  double *partials;      // [n_tiles][n_ctrl]
+  double *partials;      // [n_tiles][n_ctrl] (sharded: this shard's slice of the global array)
   unsigned *counter;     // last-CTA ticket, 0 between launches
+  int finish;            // 1: the last CTA forms Delta eps from the partials; 0 (sharded): partials only
   KtCplx *tau;           // [M_pad] (j == nt)
   double *norm2;         // [M_pad] (j == nt)
   int *status;
@@ -149,10 +150,17 @@ cudaError_t kt_launch_grad(int fp64, int ept, const KtGeom &g1, int T_layout, in
                            const KtGenImage &im_fwd, const KtGenImage &im_bwd, const KtOps &ops, const GradArgs &a,
                            cudaStream_t st);
 
+// Delta eps and the new pulse of interval j+1 (0-based index j) from the tile partials of all shards
+// [n_tiles][n_ctrl]: one block of g.nthreads threads summing in the order of the forward kernel's
+// last-CTA finisher (thread chunks of tiles, shuffle tree, warps in order), so a sharded problem
+// gives the single-GPU result bit for bit.
+cudaError_t kt_launch_finish_update(const KtGeom &g, int n_tiles, const double *partials, int j, int nt,
+                                    const double *shape, const double *eps_old, double *deps, double *eps_new,
+                                    int *status, cudaStream_t st);
 // status <- KT_DEV_NONFINITE / KT_DEV_RANGE if a value of eps [n] is not finite or |eps| > bound
 cudaError_t kt_launch_pulse_check(const double *eps, long long n, double bound, int *status, cudaStream_t st);
-// JT[0] = 1 - (1/M) sum_k |tau_k|^2
-cudaError_t kt_launch_functional(const KtCplx *tau, int M, double *JT, cudaStream_t st);
+// JT[0] = 1 - (1/M) sum_k |tau_k|^2, or 1 - Re tau_0 for a density matrix
+cudaError_t kt_launch_functional(const KtCplx *tau, int M, int density, double *JT, cudaStream_t st);
 
 cudaError_t kt_launch_chi_boundary(int fp64, const KtGeom &g, const KtOps &ops, const KtCplx *tau, void *chi,
                                    cudaStream_t st);

@@ -122,7 +122,7 @@ cudaError_t kt_launch_fwd(int fp64, int ept, const KtGeom &g, const KtGenImage &
 
 cudaError_t kt_launch_bwd(int fp64, int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops,
                           const BwdArgs &a, cudaStream_t st) {
-  const size_t smem = kt_smem_bytes(g, fp64 ? 16 : 8, false);
+  const size_t smem = kt_smem_bytes(g, fp64 ? 16 : 8, g.bwd_grid > 0);
   return fp64 ? kt_launch_bwd_f64(ept, g, im, ops, a, smem, st) : kt_launch_bwd_f32(ept, g, im, ops, a, smem, st);
 }
 
@@ -202,11 +202,13 @@ __global__ void pulse_check_kernel(const double *eps, long long n, double bound,
 }
 
 // J_T = 1 - (1/M) sum_k |tau_k|^2 (Eq. functional_traj) into one device double: one block, each
-// thread a fixed strided share of the trajectories, then a fixed shuffle and warp order.
-__global__ void functional_kernel(const KtCplx *tau, int M, double *JT) {
+// thread a fixed strided share of the trajectories, then a fixed shuffle and warp order.  A density
+// matrix (one Liouville-space state, tau = <<P_tgt|rho(T)>>): J_T = 1 - Re tau (Eq. functional).
+__global__ void functional_kernel(const KtCplx *tau, int M, int density, double *JT) {
   __shared__ double red[32];
   double s = 0.0;
-  for (int k = threadIdx.x; k < M; k += blockDim.x) s += tau[k].re * tau[k].re + tau[k].im * tau[k].im;
+  for (int k = threadIdx.x; k < M; k += blockDim.x)
+    s += density ? tau[k].re : tau[k].re * tau[k].re + tau[k].im * tau[k].im;
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
@@ -218,12 +220,49 @@ __global__ void functional_kernel(const KtCplx *tau, int M, double *JT) {
 }
 }  // namespace kt
 
+namespace kt {
+__global__ void finish_update_kernel(KtGeom g, int n_tiles, const double *partials, int j, int nt,
+                                     const double *shape, const double *eps_old, double *deps, double *eps_new,
+                                     int *status) {
+  __shared__ double red[32 * 8];
+  const int chunk = (n_tiles + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int t0 = threadIdx.x * chunk, t1 = min(n_tiles, t0 + chunk);
+  for (int c = 0; c < g.n_ctrl; ++c) {
+    double v = 0.0;
+    for (int t = t0; t < t1; ++t) v += __ldcg(partials + (size_t)t * g.n_ctrl + c);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[(threadIdx.x >> 5) * 8 + c] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < g.n_ctrl) {
+    const int c = threadIdx.x;
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w * 8 + c];
+    const size_t idx = (size_t)c * nt + j;
+    const double de = shape[idx] / (g.lam[c] * g.M_norm) * s;
+    const double en = eps_old[idx] + de;
+    deps[idx] = de;
+    eps_new[idx] = en;
+    if (!isfinite(de)) set_status(status, KT_DEV_NONFINITE);
+    if (fabs(en) > g.eps_bound) set_status(status, KT_DEV_RANGE);
+  }
+}
+}  // namespace kt
+
+cudaError_t kt_launch_finish_update(const KtGeom &g, int n_tiles, const double *partials, int j, int nt,
+                                    const double *shape, const double *eps_old, double *deps, double *eps_new,
+                                    int *status, cudaStream_t st) {
+  kt::finish_update_kernel<<<1, g.nthreads, 0, st>>>(g, n_tiles, partials, j, nt, shape, eps_old, deps, eps_new,
+                                                     status);
+  return cudaGetLastError();
+}
+
 cudaError_t kt_launch_pulse_check(const double *eps, long long n, double bound, int *status, cudaStream_t st) {
   kt::pulse_check_kernel<<<(int)std::min<long long>((n + 255) / 256, 1024), 256, 0, st>>>(eps, n, bound, status);
   return cudaGetLastError();
 }
 
-cudaError_t kt_launch_functional(const KtCplx *tau, int M, double *JT, cudaStream_t st) {
-  kt::functional_kernel<<<1, 256, 0, st>>>(tau, M, JT);
+cudaError_t kt_launch_functional(const KtCplx *tau, int M, int density, double *JT, cudaStream_t st) {
+  kt::functional_kernel<<<1, 256, 0, st>>>(tau, M, density, JT);
   return cudaGetLastError();
 }

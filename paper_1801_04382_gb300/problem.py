@@ -56,7 +56,8 @@ class Problem:
     def __init__(self, net: NetworkFactors, T: float, nt: int, M: int, eps_guess, shape, lam, uniforms,
                  precision: str = "fp64", ckpt_interval: int = 0, eps_bound: float = 0.0,
                  cheb_tol: float = 0.0, tile_traj: int = 0, psi0_batch=None, stream=None,
-                 update_rule: str = "independent", jump_scheme: str = "bisection", ckpt_prefix: int = 0):
+                 update_rule: str = "independent", jump_scheme: str = "bisection", ckpt_prefix: int = 0,
+                 traj_offset: int = 0, M_total: int = 0, inject_copy_timeout: bool = False):
         self._lib = _capi.load()
         self.net = net
         self.T, self.nt, self.M = float(T), int(nt), int(M)
@@ -66,7 +67,7 @@ class Problem:
             raise ValueError("uniforms must have shape [n_passes, M, draws_per_traj]")
         keep, md, cfg = _descriptors(net, self.T, self.nt, self.M, eps_guess, shape, lam, uniforms, precision,
                                      ckpt_interval, eps_bound, cheb_tol, tile_traj, psi0_batch, update_rule,
-                                     jump_scheme, ckpt_prefix)
+                                     jump_scheme, ckpt_prefix, traj_offset, M_total, inject_copy_timeout)
         handle = ct.c_void_p()
         self._h = None
         _capi.check(self._lib.krotov_init(ct.byref(md), ct.byref(cfg), _stream_handle(stream), ct.byref(handle)),
@@ -220,14 +221,22 @@ class Problem:
         _capi.check(self._lib.krotov_set_profiling(self._h, int(bool(on))), "krotov_set_profiling")
 
     def profile(self):
-        """{family: (total_ms, launches)} for the 'fwd' and 'bwd' interval kernels, the 'grad' kernel and
-        the 'cross' update kernels since profiling was enabled."""
-        ms = np.zeros(4)
-        n = np.zeros(4, dtype=np.int64)
+        """{family: (total_ms, launches)} for the 'fwd' and 'bwd' interval kernels, the 'grad' kernel, the
+        'cross' update kernels and the one-block update sums ('finish') since profiling was enabled."""
+        ms = np.zeros(5)
+        n = np.zeros(5, dtype=np.int64)
         _capi.check(self._lib.krotov_get_profile(self._h, _ptr(ms), n.ctypes.data_as(ct.POINTER(ct.c_longlong))),
                     "krotov_get_profile")
         return {"fwd": (float(ms[0]), int(n[0])), "bwd": (float(ms[1]), int(n[1])), "grad": (float(ms[2]), int(n[2])),
-                "cross": (float(ms[3]), int(n[3]))}
+                "cross": (float(ms[3]), int(n[3])), "finish": (float(ms[4]), int(n[4]))}
+
+    def shard_nccl(self, unique_id: bytes, rank: int, world: int, nccl_library: str = None) -> None:
+        """Join the NCCL communicator of the problem's shards (this shard = ``rank`` of ``world``; the
+        device must be current).  ``unique_id``: the 128 bytes of ``nccl_unique_id()`` from one rank."""
+        uid = ct.create_string_buffer(bytes(unique_id), 128)
+        _capi.check(self._lib.krotov_shard_nccl(self._h, uid, int(rank), int(world),
+                                                nccl_library.encode() if nccl_library else None),
+                    "krotov_shard_nccl")
 
     def checkpoint(self) -> dict:
         """What resumes this optimisation bit-identically: the current pulse, the pulse bound of the
@@ -336,6 +345,135 @@ class Batch:
         self.close()
 
 
+class DensityProblem(Problem):
+    """Density-matrix Krotov optimisation of one network (Sec. 2.2, Eqs. krotovupdate,
+    krotov_boundary; C ABI ``krotov_init_density``): rho runs forward under the master equation,
+    P backward from |tgt><tgt| under its adjoint, and the pulse is updated sequentially by
+    S/lambda Im <<P|[H_c, rho]>>.  The library propagates vec(rho) as one state of the 2N-node
+    Liouville-space network, so the sweep calls are those of ``Problem``; ``rho()`` and ``P(j)``
+    return d x d matrices.  The model's ``psi0`` is the (pure) initial state."""
+
+    def __init__(self, net: NetworkFactors, T: float, nt: int, eps_guess, shape, lam, precision: str = "fp64",
+                 ckpt_interval: int = 0, eps_bound: float = 0.0, cheb_tol: float = 0.0, stream=None,
+                 ckpt_prefix: int = 0):
+        self._lib = _capi.load()
+        self.net = net
+        self.T, self.nt, self.M = float(T), int(nt), 1
+        self.n_ctrl = net.n_ctrl
+        dummy = np.full((1, 1, 1), -1.0)
+        keep, md, cfg = _descriptors(net, self.T, self.nt, 1, eps_guess, shape, lam, dummy, precision,
+                                     ckpt_interval, eps_bound, cheb_tol, 0, None, "independent", "bisection",
+                                     ckpt_prefix)
+        handle = ct.c_void_p()
+        self._h = None
+        _capi.check(self._lib.krotov_init_density(ct.byref(md), ct.byref(cfg), _stream_handle(stream),
+                                                  ct.byref(handle)), "krotov_init_density")
+        self._h = handle
+        self._owned = True
+        self.precision = precision
+        self.info = self.get_info()
+
+    def rho(self) -> np.ndarray:
+        """rho(T) of the last forward sweep, d x d."""
+        d = self.net.d
+        out = np.zeros((1, d * d, 2))
+        _capi.check(self._lib.krotov_get_states(self._h, _ptr(out)), "krotov_get_states")
+        return (out[0, :, 0] + 1j * out[0, :, 1]).reshape(d, d)
+
+    def P(self, j: int) -> np.ndarray:
+        """Co-state P(t_j) of the last backward sweep, d x d (stored slots only)."""
+        d = self.net.d
+        out = np.zeros((1, d * d, 2))
+        _capi.check(self._lib.krotov_get_costate(self._h, int(j), _ptr(out)), "krotov_get_costate")
+        return (out[0, :, 0] + 1j * out[0, :, 1]).reshape(d, d)
+
+    def records(self):
+        return [[]]
+
+    def states(self):
+        raise AttributeError("a density-matrix problem has no trajectory states: use rho()")
+
+    def costate(self, j):
+        raise AttributeError("a density-matrix problem has no trajectory co-states: use P(j)")
+
+
+def shard_ranges(M_total: int, world: int, tile: int = 1):
+    """(traj_offset, M) of each of ``world`` shards of an M_total-trajectory problem: equal slices in
+    rank order (what krotov_shard_nccl requires), each a whole number of tiles."""
+    if world < 1 or M_total % world != 0 or (M_total // world) % tile != 0:
+        raise ValueError(f"M_total = {M_total} does not split into {world} equal slices of whole {tile}-trajectory tiles")
+    m = M_total // world
+    return [(r * m, m) for r in range(world)]
+
+
+def nccl_library_path():
+    """The NCCL shared library that torch's CUDA build ships (NVIDIA's nccl wheel), or None to let the
+    dynamic loader find libnccl.so.2."""
+    import os
+    try:
+        import nvidia.nccl
+        for d in list(getattr(nvidia.nccl, "__path__", [])):
+            cand = os.path.join(d, "lib", "libnccl.so.2")
+            if os.path.exists(cand):
+                return cand
+    except ImportError:
+        pass
+    return None
+
+
+def nccl_unique_id(nccl_library: str = None) -> bytes:
+    """A fresh NCCL unique id (128 bytes), created on one rank and sent to the others by the caller."""
+    buf = ct.create_string_buffer(128)
+    _capi.check(_capi.load().kt_nccl_unique_id(nccl_library.encode() if nccl_library else None, buf),
+                "kt_nccl_unique_id")
+    return buf.raw
+
+
+class ShardGroup:
+    """Shards of one problem (``Problem`` objects created with ``traj_offset``/``M_total``) driven
+    together in this process on one stream (C ABI ``kt_group``): per interval the tile partials of the
+    update overlap are copied between the shards before each forms Delta eps -- the exchange of a
+    trajectory-sharded run, here without a network.  The shards stay owned by the caller."""
+
+    def __init__(self, shards):
+        self._lib = _capi.load()
+        self.shards = list(shards)
+        arr = (ct.c_void_p * len(self.shards))(*[p._h.value for p in self.shards])
+        h = ct.c_void_p()
+        self._h = None
+        _capi.check(self._lib.krotov_group_init(arr, len(self.shards), ct.byref(h)), "krotov_group_init")
+        self._h = h
+
+    def update(self, n_iter: int = 1, stream=None) -> np.ndarray:
+        JT = np.zeros(int(n_iter))
+        _capi.check(self._lib.krotov_group_update(self._h, int(n_iter), _ptr(JT), _stream_handle(stream)),
+                    "krotov_group_update")
+        return JT
+
+    def fidelity(self, stream=None) -> float:
+        F = ct.c_double()
+        _capi.check(self._lib.krotov_group_fidelity(self._h, ct.byref(F), _stream_handle(stream)),
+                    "krotov_group_fidelity")
+        return F.value
+
+    def close(self) -> None:
+        if self._h is not None:
+            self._lib.krotov_group_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 def bessel_j(alpha: float, n: int) -> np.ndarray:
     """J_0..J_{n-1}(alpha) from the library's Miller recurrence (host-side helper)."""
     out = np.zeros(n)
@@ -349,7 +487,7 @@ _JUMP_SCHEMES = {"bisection": 0, "first_order": 1}
 
 def _descriptors(net, T, nt, M, eps_guess, shape, lam, uniforms, precision="fp64", ckpt_interval=0,
                  eps_bound=0.0, cheb_tol=0.0, tile_traj=0, psi0_batch=None, update_rule="independent",
-                 jump_scheme="bisection", ckpt_prefix=0):
+                 jump_scheme="bisection", ckpt_prefix=0, traj_offset=0, M_total=0, inject_copy_timeout=False):
     """kt_model_desc / kt_config for ``net`` (the returned ``keep`` dict owns the host arrays)."""
     uniforms = _c(uniforms)
     keep = {
@@ -374,15 +512,17 @@ def _descriptors(net, T, nt, M, eps_guess, shape, lam, uniforms, precision="fp64
         lambda_a=_ptr(keep["lam"]), uniforms=_ptr(keep["U"]), n_passes=uniforms.shape[0],
         draws_per_traj=uniforms.shape[2], eps_bound=float(eps_bound), cheb_tol=float(cheb_tol),
         tile_traj=int(tile_traj), update_rule=_UPDATE_RULES[update_rule], jump_scheme=_JUMP_SCHEMES[jump_scheme],
-        ckpt_prefix=int(ckpt_prefix))
+        ckpt_prefix=int(ckpt_prefix), traj_offset=int(traj_offset), M_total=int(M_total),
+        inject_copy_timeout=int(bool(inject_copy_timeout)))
     return keep, md, cfg
 
 
 def generator_dense(net, T, nt, M, eps_guess, shape, lam, uniforms, eps, direction=0, precision="fp64"):
-    """Dense d x d generator expanded from the library's structured tables (host only):
-    direction 0 gives H_eff(eps), direction 1 gives -H_eff(eps)^dag."""
+    """Dense generator expanded from the library's structured tables (host only): direction 0 gives
+    H_eff(eps), direction 1 gives -H_eff(eps)^dag (d x d); directions 2 and 3 the same for the
+    Liouville-space generator of a density-matrix problem (d^2 x d^2)."""
     keep, md, cfg = _descriptors(net, T, nt, M, eps_guess, shape, lam, uniforms, precision)
-    d = net.d
+    d = net.d if direction < 2 else net.d ** 2
     out = np.zeros((d, d, 2))
     e = _c(eps)
     _capi.check(_capi.load().kt_generator_dense(ct.byref(md), ct.byref(cfg), int(direction), _ptr(e), _ptr(out)),

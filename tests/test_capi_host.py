@@ -155,3 +155,29 @@ def test_structured_generator_tables_match_dense_heff(lib, N, nc, kappa, g, lind
         G1 = generator_dense(*args, eps=eps, direction=1)
         assert np.abs(G0 - Heff).max() <= 1e-12 * scale
         assert np.abs(G1 + Heff.conj().T).max() <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("N,nc,lind", [(1, 1, "collective"), (1, 2, "collective"), (2, 1, "collective"),
+                                       (2, 1, "local")])
+def test_liouville_generator_tables_match_oracle_liouvillian(lib, N, nc, lind):
+    """Density-matrix problems: the library's Liouville-space generator G (2N nodes, lower-lower pair
+    hops for L rho L^dag, a ket and a bra term per control), expanded with the kernels' indexing, equals
+    i times the oracle's Liouvillian of Eq. lindblad (d vec(rho)/dt = L vec(rho) = -i G vec(rho)), and
+    the adjoint direction equals -G^dag (the co-state P runs under the adjoint dynamics)."""
+    from oracle import lindblad as ol
+    from oracle import model as om
+    from paper_1801_04382_gb300.problem import generator_dense
+    net = pm.cascaded_chain(N, nc, lindblad=lind)
+    m = om.build_model(N, nc, lindblad=lind)
+    nt, T = 8, 1.0
+    args = (net, T, nt, 1, si.guess_pulses(N, nt, T, 2.0), si.shape_functions(N, nt, T), np.full(N, 10.0),
+            si.uniforms(0, 1, 1, 5))
+    rng = np.random.default_rng(7 + N + nc)
+    for _ in range(2):
+        eps = rng.uniform(-2.0, 2.0, size=N)
+        G = 1j * ol.liouvillian(m.Heff(eps), m.L).toarray()
+        scale = np.abs(G).max()
+        G2 = generator_dense(*args, eps=eps, direction=2)
+        G3 = generator_dense(*args, eps=eps, direction=3)
+        assert np.abs(G2 - G).max() <= 1e-12 * scale
+        assert np.abs(G3 + G.conj().T).max() <= 1e-12 * scale
