@@ -54,7 +54,10 @@ class ForwardResult:
     margin: np.ndarray                # [M] min over interval ends of | ||psi||^2 - r | (incl. those that jump)
     psi_t: np.ndarray = None          # [nt+1, M, d] if requested
     error: str = ""
-    deps_scale: np.ndarray = None     # [n_ctrl, nt] S/(lambda M) sum_k |Im<chi_k|H_i|psi_k>| (update only)
+    deps_scale: np.ndarray = None     # [n_ctrl, nt] magnitude of the summed terms (update only): the
+                                      # sum is over trajectories and elements x of Im(conj(chi_kx) (H_i psi_k)_x),
+                                      # S/(lambda M) sum_{k,x} |conj(chi_kx) (H_i psi_k)_x|; cross rule:
+                                      # S/(lambda M^2) sum_{k,k'} (sum_x |xi_kx||(H_i psi_k')_x|)(sum_x |xi_kx||psi_k'x|)
 
 
 def _norm2(v: np.ndarray) -> float:
@@ -115,12 +118,15 @@ def _step_with_jumps(prop: StepPropagator, Ls: list, psi: np.ndarray, dt: float,
 
 def cross_overlap(xi: np.ndarray, psi: np.ndarray, Hc: np.ndarray, scale: bool = False):
     """sum_{k,k'} Im[<xi_k|Hc|psi_k'> <psi_k'|xi_k>] for xi, psi [M, d] (Eq. cross_traj_update);
-    with scale, also the sum of the magnitudes of the terms."""
-    A = np.conj(xi) @ (psi @ Hc.T).T          # A[k, k'] = <xi_k|Hc|psi_k'>
+    with scale, also the magnitude of what is summed: sum_{k,k'} of the product of the two inner
+    products' element-magnitude sums (the size of the terms before any cancellation)."""
+    hpsi = psi @ Hc.T
+    A = np.conj(xi) @ hpsi.T                  # A[k, k'] = <xi_k|Hc|psi_k'>
     G = np.conj(xi) @ psi.T                   # G[k, k'] = <xi_k|psi_k'>, so <psi_k'|xi_k> = conj(G)
     terms = np.imag(A * np.conj(G))
     if scale:
-        return float(np.sum(terms)), float(np.sum(np.abs(terms)))
+        mag = (np.abs(xi) @ np.abs(hpsi).T) * (np.abs(xi) @ np.abs(psi).T)
+        return float(np.sum(terms)), float(np.sum(mag))
     return float(np.sum(terms))
 
 
@@ -159,10 +165,11 @@ def forward_pass(model, eps: np.ndarray, T: float, U_pass: np.ndarray, psi0: np.
                     deps_scale[i, j - 1] = shape[i, j - 1] / (lam[i] * M * M) * ga
                     continue
                 hpsi = psi @ model.Hc[i].T          # rows: Hc_i psi_k
-                gk = np.imag(np.sum(np.conj(chi[j - 1]) * hpsi, axis=1))
+                prod = np.conj(chi[j - 1]) * hpsi
+                gk = np.imag(np.sum(prod, axis=1))
                 g = np.sum(gk)
                 deps[i, j - 1] = shape[i, j - 1] / (lam[i] * M) * g
-                deps_scale[i, j - 1] = shape[i, j - 1] / (lam[i] * M) * np.sum(np.abs(gk))
+                deps_scale[i, j - 1] = shape[i, j - 1] / (lam[i] * M) * np.sum(np.abs(prod))
             eps_used[:, j - 1] = eps[:, j - 1] + deps[:, j - 1]
         prop = StepPropagator(model.Heff(eps_used[:, j - 1]))
         # every trajectory first takes the full interval; those whose norm fell to the
