@@ -152,6 +152,14 @@ typedef struct {
                                lets the copy land, the block leaves) and the sweep returns
                                KT_ERR_TIMEOUT; the device stays usable.  Each wait is bounded
                                (about 2 s) whatever this flag. */
+  int items_per_thread;     /* thread mapping of the interval kernels.  0 = automatic: for the node
+                               dimensions 6 and 9 one thread per last-node fiber (the cavity-structure
+                               kernels when the generator has that structure), else the strided mapping
+                               with the fewest items per thread that fit; with tile_traj = -1 the
+                               autotuner also times the strided mapping at 1, 2 and 4 items per thread.
+                               1, 2, 4, 8 or 16: the strided mapping (item q of thread t is element
+                               t + q * threads of the tile) with that many items per thread -- more
+                               threads per trajectory for problems too small to fill the GPU otherwise */
 } kt_config;
 
 /* Create a problem: validate, assemble H_eff in structured form (a1), choose the Chebyshev
@@ -311,6 +319,8 @@ typedef struct {
                                co-states of t_0 .. t_{ckpt_kept_prefix} kept, then every K-th */
   int ckpt_kept_prefix;
   int costate_slots;        /* co-state slots held in device memory */
+  int items_per_thread;     /* thread mapping of the interval kernels: 0 = one thread per last-node
+                               fiber, else the strided mapping with this many items per thread */
 } kt_info;
 KT_API kt_status krotov_get_info(kt_problem *p, kt_info *info);
 

@@ -16,6 +16,8 @@ static cudaError_t launch_bwd_t(const KtGeom &g, const KtGenImage &im, const KtO
 cudaError_t kt_launch_bwd_f64(int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops, const BwdArgs &a,
                              size_t smem, cudaStream_t st) {
   switch (ept) {
+    case 1: return kt::launch_bwd_t<double, 1, 0, 0>(g, im, ops, a, smem, st);   // strided, small problems
+    case 2: return kt::launch_bwd_t<double, 2, 0, 0>(g, im, ops, a, smem, st);
     case 4: return kt::launch_bwd_t<double, 4, 0, 0>(g, im, ops, a, smem, st);
     case 8: return kt::launch_bwd_t<double, 8, 0, 0>(g, im, ops, a, smem, st);
     case 16: return kt::launch_bwd_t<double, 16, 0, 0>(g, im, ops, a, smem, st);

@@ -88,6 +88,7 @@ struct KtGeom {
   int max_jumps, draws;              // jump cap and uniforms per trajectory and pass
   int prefetch_chi;                  // forward kernel keeps a third tile buffer for chi(t_j)
   int bwd_grid;                      // > 0: backward kernel CTAs looping over tiles, next input prefetched
+  int fwd_grid;                      // > 0: the same for the forward kernel (psi and chi of the next tile prefetched)
   int first_order;                   // jump scheme: 0 jump times by bisection, 1 at most one jump per interval, at its end
   int stride[KT_MAX_NODES];          // element stride of node i (n_loc^(N-1-i))
   int ctrl_node[KT_MAX_CTRL];        // node of control c (its ket node for a density matrix)

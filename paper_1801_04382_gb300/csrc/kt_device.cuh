@@ -132,7 +132,8 @@ __device__ __forceinline__ bool tile_wait(unsigned long long *bar, uint32_t phas
 struct Smem {
   void *bufA, *bufB;          // [tile_elems] complex each
   void *bufC;                 // [tile_elems] prefetched chi(t_j) (forward kernel, when it fits)
-  unsigned long long *mbar;   // [3] transaction barriers of the bulk copies; [2] never receives an arrival
+  void *bufD;                 // [tile_elems] the next tile's prefetched psi (forward kernel looping over tiles)
+  unsigned long long *mbar;   // [4] transaction barriers of the bulk copies ([0], [3] psi, [1] chi); [2] never receives an arrival
   int *loc_off;               // [N*n_loc*S]  element offset * T (0 = no entry)
   void *loc_val;              // [N*n_loc*S]
   void *diag;                 // [N*n_loc]
@@ -153,7 +154,8 @@ struct Smem {
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline size_t carve(const KtGeom &g, int esz, char *base, Smem *s, bool with_c) {
+__host__ __device__ inline size_t carve(const KtGeom &g, int esz, char *base, Smem *s, bool with_c,
+                                        bool with_d = false) {
   const int nl2 = g.n_loc * g.n_loc;
   const int nwarps = g.nthreads / 32;
   size_t off = 0;
@@ -166,7 +168,8 @@ __host__ __device__ inline size_t carve(const KtGeom &g, int esz, char *base, Sm
   const size_t tile = (size_t)g.tile_elems * esz;
   char *a = take(tile), *b = take(tile);
   char *cbuf = with_c ? take(tile) : nullptr;
-  char *mb = take(3 * sizeof(unsigned long long));
+  char *dbuf = with_d ? take(tile) : nullptr;
+  char *mb = take(4 * sizeof(unsigned long long));
   char *lo = take(sizeof(int) * g.n_nodes * g.n_loc * g.S);
   char *lv = take((size_t)esz * g.n_nodes * g.n_loc * g.S);
   char *dg = take((size_t)esz * g.n_nodes * g.n_loc);
@@ -184,7 +187,7 @@ __host__ __device__ inline size_t carve(const KtGeom &g, int esz, char *base, Sm
   char *lr = take((size_t)esz * 2 * g.n_loc);
   char *pc = take((size_t)esz * (g.n_pairs > 0 ? g.n_pairs : 1));
   if (s) {
-    s->bufA = a; s->bufB = b; s->bufC = cbuf; s->mbar = (unsigned long long *)mb; s->loc_off = (int *)lo; s->loc_val = lv; s->diag = dg;
+    s->bufA = a; s->bufB = b; s->bufC = cbuf; s->bufD = dbuf; s->mbar = (unsigned long long *)mb; s->loc_off = (int *)lo; s->loc_val = lv; s->diag = dg;
     s->pair_off = (int *)po; s->pair_val = pv; s->hc_off = (int *)ho; s->hc_val = hv;
     s->coef = cf; s->red = (double *)rd; s->tsc = (double *)ts; s->tin = (int *)ti;
     s->eps = (double *)ep; s->flag = (int *)fl;
@@ -904,6 +907,19 @@ __device__ __forceinline__ void cheb_dispatch(const KtGeom &g, const KtGenImage 
   else cheb_run<R, EPT>(g, im, sm, it, K, acc);
 }
 
+// End of a tile in the forward kernel looping over tiles: the generic-proxy writes of the tile are
+// ordered before the bulk copies that will overwrite its buffers, then the prefetched psi (fourth
+// buffer) becomes the next tile's input and the old input buffer (maybe still being stored) the next
+// prefetch target.
+__device__ __forceinline__ void end_fwd_tile(Smem &sm, bool persist) {
+  if (!persist) return;
+  fence_proxy_async_smem();
+  __syncthreads();
+  void *t = sm.bufA;
+  sm.bufA = sm.bufD;
+  sm.bufD = t;
+}
+
 // --------------------------------------------------------------------------------------
 // Forward interval kernel.  One Chebyshev call site serves every phase:
 //   MAIN    full interval from psi(t_{j-1}) (uniform coefficients),
@@ -917,11 +933,12 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
   typedef typename C2<R>::T C;
   extern __shared__ __align__(16) char smem_raw[];
   Smem sm;
-  carve(g, sizeof(C), smem_raw, &sm, g.prefetch_chi != 0);
-  const int tile = blockIdx.x;
+  // with g.fwd_grid > 0 the CTAs loop over tiles blockIdx.x, blockIdx.x + gridDim.x, ...: the tables and
+  // the item mapping are built once, and the next tile's psi (fourth buffer, barriers [0] / [3] in turn)
+  // and chi (third buffer) arrive by bulk copy while the current tile is propagated
+  const bool persist = g.fwd_grid > 0;
+  carve(g, sizeof(C), smem_raw, &sm, g.prefetch_chi != 0, persist);
   const int tau = threadIdx.x % g.T;
-  const C *psi_in = (const C *)a.psi_in + (size_t)tile * g.tile_elems;
-  C *psi_out = (C *)a.psi_out + (size_t)tile * g.tile_elems;
   const int j = a.j;
   // bisection stop: 2^-48 dt in FP64 (near the rounding of the FP64 norm it compares), 2^-40 dt in
   // FP32-mixed (far below the FP32 norm's own error)
@@ -937,32 +954,59 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
     sm.eps[c] = e;
   }
   if (threadIdx.x < 8) sm.flag[threadIdx.x] = 0;
-  // the trajectory's current threshold, read now so that its latency is off the path after the series
-  const double r_start = (threadIdx.x < g.T) ? a.rstate[(size_t)tile * g.T + threadIdx.x] : 0.0;
   if (threadIdx.x == 0) {
     mbar_init(&sm.mbar[0], 1);
     mbar_init(&sm.mbar[1], 1);
     mbar_init(&sm.mbar[2], 1);
+    mbar_init(&sm.mbar[3], 1);
     fence_mbar_init();
   }
   __syncthreads();
-  C *A = (C *)sm.bufA;
-  C *B = (C *)sm.bufB;
   const uint32_t tile_bytes = (uint32_t)(g.tile_elems * sizeof(C));
   const bool need_chi = a.overlap && j < a.nt;
-  const C *chi_g = need_chi ? (const C *)a.chi_t + (size_t)tile * g.tile_elems : nullptr;
+  int tile = blockIdx.x;
   // the bulk engine brings psi(t_{j-1}) (and chi(t_j) when there is room) while the tables are built
   if (threadIdx.x == 0) {
-    bulk_load(A, psi_in, tile_bytes, &sm.mbar[0]);
-    if (need_chi && g.prefetch_chi) bulk_load(sm.bufC, chi_g, tile_bytes, &sm.mbar[1]);
+    bulk_load(sm.bufA, (const C *)a.psi_in + (size_t)tile * g.tile_elems, tile_bytes, &sm.mbar[0]);
+    if (need_chi && g.prefetch_chi)
+      bulk_load(sm.bufC, (const C *)a.chi_t + (size_t)tile * g.tile_elems, tile_bytes, &sm.mbar[1]);
   }
   build_tables<R>(g, im, ops, sm, sm.eps, a.overlap != 0);
   Items<EPT, NL> it;
   load_items<EPT, NL>(g, ops, it);
+  bool store_pending = false;
+  for (int use = 0; tile < g.n_tiles; tile += gridDim.x, ++use) {
+  const int next = tile + (int)gridDim.x;
+  const C *psi_in = (const C *)a.psi_in + (size_t)tile * g.tile_elems;
+  C *psi_out = (C *)a.psi_out + (size_t)tile * g.tile_elems;
+  const C *chi_g = need_chi ? (const C *)a.chi_t + (size_t)tile * g.tile_elems : nullptr;
+  // the trajectory's current threshold, read now so that its latency is off the path after the series
+  const double r_start = (threadIdx.x < g.T) ? a.rstate[(size_t)tile * g.T + threadIdx.x] : 0.0;
+  if (threadIdx.x == 0) {
+    sm.flag[0] = 0;
+    sm.flag[1] = 0;
+    sm.flag[2] = 0;
+  }
+  C *A = (C *)sm.bufA;
+  C *B = (C *)sm.bufB;
   C acc[EPT];
-  if (!tile_wait(&sm.mbar[0], 0, &sm.flag[4], a.status, g.inject_timeout ? &sm.mbar[2] : nullptr)) {
-    if (threadIdx.x == 0 && need_chi && g.prefetch_chi) mbar_wait_bounded(&sm.mbar[1], 0);
+  // psi of this tile: load number `use`, barrier [0] / [3] in turn, phase parity (use >> 1) & 1
+  if (!tile_wait((use & 1) ? &sm.mbar[3] : &sm.mbar[0], (use >> 1) & 1, &sm.flag[4], a.status,
+                 g.inject_timeout ? &sm.mbar[2] : nullptr)) {
+    if (threadIdx.x == 0) {
+      if (need_chi && g.prefetch_chi) mbar_wait_bounded(&sm.mbar[1], use & 1);
+      if (store_pending) bulk_store_wait();
+    }
     return;
+  }
+  if (persist && next < g.n_tiles) {
+    // the fourth buffer fed the previous tile's bulk store: let that finish, then prefetch into it
+    if (threadIdx.x == 0) {
+      if (store_pending) bulk_store_wait();
+      bulk_load(sm.bufD, (const C *)a.psi_in + (size_t)next * g.tile_elems, tile_bytes,
+                (use & 1) ? &sm.mbar[0] : &sm.mbar[3]);
+    }
+    store_pending = false;
   }
   bool jumped = false, stored = false;
 
@@ -1197,14 +1241,16 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
       a.norm2[k] = nrm;
       if (!isfinite(nrm) || !isfinite(o[0]) || !isfinite(o[1])) set_status(a.status, KT_DEV_NONFINITE);
     }
-    if (threadIdx.x == 0 && stored) bulk_store_wait();
-    return;
+    store_pending = store_pending || stored;
+    end_fwd_tile(sm, persist);
+    continue;
   }
 
   // ---------------- update overlap at t_j: g_c = sum_k Im <chi_k|hc_c|psi_k> ----------------
   if (!a.overlap) {
-    if (threadIdx.x == 0 && stored) bulk_store_wait();
-    return;
+    store_pending = store_pending || stored;
+    end_fwd_tile(sm, persist);
+    continue;
   }
   if (jumped) {
     // final states came back through psi_out: put them into A for the neighbour reads
@@ -1222,8 +1268,12 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
     if (threadIdx.x == 0) bulk_load(B, chi_g, tile_bytes, &sm.mbar[1]);
     chi = B;
   }
-  if (!tile_wait(&sm.mbar[1], 0, &sm.flag[5], a.status, g.inject_timeout ? &sm.mbar[2] : nullptr)) {
-    if (threadIdx.x == 0 && stored) bulk_store_wait();
+  if (!tile_wait(&sm.mbar[1], use & 1, &sm.flag[5], a.status, g.inject_timeout ? &sm.mbar[2] : nullptr)) {
+    if (threadIdx.x == 0) {
+      if (store_pending || stored) bulk_store_wait();
+      // the next tile's psi is on its way into the fourth buffer: let it land before leaving
+      if (persist && next < g.n_tiles) mbar_wait_bounded((use & 1) ? &sm.mbar[0] : &sm.mbar[3], ((use + 1) >> 1) & 1);
+    }
     return;
   }
   const C *hv = (const C *)sm.hc_val;
@@ -1285,8 +1335,14 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
     for (int t = 0; t < g.T; ++t) s += sm.tsc[TS_V0 * g.T + t * KT_MAX_CTRL + threadIdx.x];
     a.partials[(size_t)tile * g.n_ctrl + threadIdx.x] = s;
   }
-  if (!a.finish) {   // sharded problem: the partials of all shards are summed after the exchange
-    if (threadIdx.x == 0 && stored) bulk_store_wait();
+  store_pending = store_pending || stored;
+  end_fwd_tile(sm, persist);
+  // every thread is done with this tile's chi (the barrier above): the third buffer takes the next tile's
+  if (persist && need_chi && g.prefetch_chi && next < g.n_tiles && threadIdx.x == 0)
+    bulk_load(sm.bufC, (const C *)a.chi_t + (size_t)next * g.tile_elems, tile_bytes, &sm.mbar[1]);
+  }   // tiles of this CTA
+  if (!a.overlap || j == a.nt || !a.finish) {   // no update sum here (a shard sums after its exchange)
+    if (threadIdx.x == 0 && store_pending) bulk_store_wait();
     return;
   }
   // ---------------- last CTA: Delta eps of interval j+1, summed in tile order ----------------
@@ -1297,13 +1353,13 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
     sm.flag[3] = (ticket == (unsigned)(gridDim.x - 1));
   }
   __syncthreads();
-  if (threadIdx.x == 0 && stored) bulk_store_wait();
+  if (threadIdx.x == 0 && store_pending) bulk_store_wait();
   if (!sm.flag[3]) return;
   __threadfence();
   // every thread adds a fixed, contiguous chunk of the tiles; a fixed shuffle/warp tree adds the
-  // chunks -- the same order on every run for a given grid
-  const int chunk = ((int)gridDim.x + blockDim.x - 1) / blockDim.x;
-  const int t0 = threadIdx.x * chunk, t1 = min((int)gridDim.x, t0 + chunk);
+  // chunks -- the same order on every run for a given tile count and block size
+  const int chunk = (g.n_tiles + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int t0 = threadIdx.x * chunk, t1 = min(g.n_tiles, t0 + chunk);
   for (int c = 0; c < g.n_ctrl; ++c) {
     double v = 0.0;
     for (int t = t0; t < t1; ++t) v += __ldcg(a.partials + (size_t)t * g.n_ctrl + c);

@@ -8,7 +8,7 @@ static cudaError_t launch_fwd_t(const KtGeom &g, const KtGenImage &im, const KtO
                                 cudaStream_t st) {
   const cudaError_t attr = kt_allow_large_smem((const void *)fwd_kernel<R, EPT, NL, ACS>);
   if (attr != cudaSuccess) return attr;
-  fwd_kernel<R, EPT, NL, ACS><<<g.n_tiles, g.nthreads, smem, st>>>(g, im, ops, a);
+  fwd_kernel<R, EPT, NL, ACS><<<g.fwd_grid > 0 ? g.fwd_grid : g.n_tiles, g.nthreads, smem, st>>>(g, im, ops, a);
   return cudaGetLastError();
 }
 }  // namespace kt
@@ -16,6 +16,8 @@ static cudaError_t launch_fwd_t(const KtGeom &g, const KtGenImage &im, const KtO
 cudaError_t kt_launch_fwd_f32(int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops, const FwdArgs &a,
                              size_t smem, cudaStream_t st) {
   switch (ept) {
+    case 1: return kt::launch_fwd_t<float, 1, 0, 0>(g, im, ops, a, smem, st);   // strided, small problems
+    case 2: return kt::launch_fwd_t<float, 2, 0, 0>(g, im, ops, a, smem, st);
     case 4: return kt::launch_fwd_t<float, 4, 0, 0>(g, im, ops, a, smem, st);
     case 8: return kt::launch_fwd_t<float, 8, 0, 0>(g, im, ops, a, smem, st);
     case 16: return kt::launch_fwd_t<float, 16, 0, 0>(g, im, ops, a, smem, st);

@@ -1339,7 +1339,10 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P, bool 
       S = std::max(S, (int)cl.size());
     }
   if (S > KT_MAX_S) return fail(KT_ERR_UNSUPPORTED, "a node row has %d > %d off-diagonal entries", S, KT_MAX_S);
-  const bool fiber = (nl == 6 || nl == 9);
+  const int ipt = cfg->items_per_thread;
+  if (ipt != 0 && ipt != 1 && ipt != 2 && ipt != 4 && ipt != 8 && ipt != 16)
+    return fail(KT_ERR_ARG, "items_per_thread must be 0 (automatic), 1, 2, 4, 8 or 16");
+  const bool fiber = (nl == 6 || nl == 9) && ipt == 0;
   const bool acs = fiber && cavity_structure(gf, gb, lo_dl, lo_val, ra_dl, ra_val);
   const bool ri = acs && S <= 2 && ri_classes(gf, gb, lo_val, ra_val, cols);
   if (ri) S = 2;
@@ -1372,6 +1375,9 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P, bool 
     if (fiber) {
       if ((long long)(d / nl) * T > fiber_max_threads) continue;
       t.nthreads = ((d / nl) * T + 31) / 32 * 32;
+    } else if (ipt > 0) {
+      if (((long long)d * T + ipt - 1) / ipt > maxthr) continue;
+      t.nthreads = maxthr;
     } else {
       if ((long long)d * T > (cfg->tile_traj > 0 ? 16LL * maxthr : max_items)) continue;
       t.nthreads = maxthr;
@@ -1408,10 +1414,17 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P, bool 
     // tiles (about one CTA per SM slot) and prefetch the next tile's input during the current series
     int dev = 0, sms = 0;
     g.bwd_grid = 0;
+    g.fwd_grid = 0;
     if (g.prefetch_chi && cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0) {
       const int per_sm = std::max(1, std::min((int)((227 * 1024) / smem3), 2048 / std::max(32, t.nthreads)));
       if (g.n_tiles > sms * per_sm) g.bwd_grid = sms * per_sm;
+      // forward kernel: the same tile loop when a fourth buffer (the next tile's psi) fits as well
+      const size_t smem4 = kt_smem_bytes(t, esz, true, true);
+      if (smem4 <= 227 * 1024) {
+        const int per_sm4 = std::max(1, std::min((int)((227 * 1024) / smem4), 2048 / std::max(32, t.nthreads)));
+        if (g.n_tiles > sms * per_sm4) g.fwd_grid = sms * per_sm4;
+      }
     }
   }
   if (fiber) {
@@ -1423,7 +1436,7 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P, bool 
     g.nthreads = std::max(32, ((d / nl) * Tsel + 31) / 32 * 32);
   } else {
     const int items = d * Tsel;
-    int ept = 4;
+    int ept = ipt > 0 ? ipt : 4;
     while ((items + ept - 1) / ept > maxthr) ept *= 2;
     P.ept = ept;
     g.nthreads = std::max(32, ((items + ept - 1) / ept + 31) / 32 * 32);
@@ -1758,15 +1771,20 @@ kt_status probe_forward_ms(kt_problem *q, cudaStream_t st, double *ms_out) {
   return KT_OK;
 }
 
-// Tile-width autotuner: plan every power-of-two tile width that fits, time the forward interval
-// kernel of each (thread count and items per thread follow from the width), keep the fastest.
+// Autotuner: plan every power-of-two tile width that fits, with the automatic thread mapping and
+// (unless the caller fixed items_per_thread) the strided mapping at 1, 2 and 4 items per thread,
+// time the forward interval kernel of each distinct plan, keep the fastest.
 kt_status autotune(const kt_model_desc *md, const kt_config *cfg, cudaStream_t st, HostPlan &best) {
   double best_ms = 0.0;
   int best_T = 0;
   kt_status last = KT_ERR_UNSUPPORTED;
-  for (int T = 1; T <= 32; T <<= 1) {
+  std::vector<std::pair<int, int>> seen;   // (tile width, launcher code) already timed
+  const int ipts[4] = {0, 1, 2, 4};
+  for (int T = 1; T <= 32; T <<= 1)
+  for (int m = 0; m < (cfg->items_per_thread > 0 ? 1 : 4); ++m) {
     kt_config c = *cfg;
     c.tile_traj = T;
+    if (cfg->items_per_thread == 0) c.items_per_thread = ipts[m];
     HostPlan P;
     kt_status s = plan(md, &c, P);
     if (s != KT_OK) {
@@ -1774,6 +1792,8 @@ kt_status autotune(const kt_model_desc *md, const kt_config *cfg, cudaStream_t s
       last = s;
       continue;
     }
+    if (std::find(seen.begin(), seen.end(), std::make_pair(P.g.T, P.ept)) != seen.end()) continue;
+    seen.emplace_back(P.g.T, P.ept);
     kt_problem *q = nullptr;
     if ((s = create_problem(md, &c, P, st, true, &q)) != KT_OK) return s;
     double ms = 0.0;
@@ -2101,6 +2121,7 @@ KT_API kt_status krotov_get_info(kt_problem *p, kt_info *info) {
   info->ckpt_interval = p->ckpt;
   info->ckpt_kept_prefix = p->ckpt == 0 ? p->nt : p->ckpt_dense;
   info->costate_slots = p->n_chi_slots;
+  info->items_per_thread = p->ept > 0 ? p->ept : 0;
   return KT_OK;
 }
 

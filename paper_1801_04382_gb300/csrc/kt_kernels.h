@@ -75,7 +75,7 @@ struct BwdArgs {
 // Record msg as the calling thread's last error (krotov_last_error) and return s.
 kt_status kt_fail(kt_status s, const char *msg);
 
-size_t kt_smem_bytes(const KtGeom &g, int elem_bytes, bool with_chi_buffer);
+size_t kt_smem_bytes(const KtGeom &g, int elem_bytes, bool with_chi_buffer, bool with_next_buffer = false);
 cudaError_t kt_launch_fwd(int fp64, int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops,
                           const FwdArgs &a, cudaStream_t st);
 cudaError_t kt_launch_bwd(int fp64, int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops,

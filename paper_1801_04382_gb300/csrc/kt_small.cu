@@ -110,13 +110,13 @@ cudaError_t kt_launch_pulse_noise(const double *eps, const double *ref, int n_ct
   return cudaGetLastError();
 }
 
-size_t kt_smem_bytes(const KtGeom &g, int elem_bytes, bool with_chi_buffer) {
-  return carve(g, elem_bytes, nullptr, nullptr, with_chi_buffer);
+size_t kt_smem_bytes(const KtGeom &g, int elem_bytes, bool with_chi_buffer, bool with_next_buffer) {
+  return carve(g, elem_bytes, nullptr, nullptr, with_chi_buffer, with_next_buffer);
 }
 
 cudaError_t kt_launch_fwd(int fp64, int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops,
                           const FwdArgs &a, cudaStream_t st) {
-  const size_t smem = kt_smem_bytes(g, fp64 ? 16 : 8, g.prefetch_chi != 0);
+  const size_t smem = kt_smem_bytes(g, fp64 ? 16 : 8, g.prefetch_chi != 0, g.fwd_grid > 0);
   return fp64 ? kt_launch_fwd_f64(ept, g, im, ops, a, smem, st) : kt_launch_fwd_f32(ept, g, im, ops, a, smem, st);
 }
 
