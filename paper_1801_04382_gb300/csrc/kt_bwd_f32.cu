@@ -8,7 +8,8 @@ static cudaError_t launch_bwd_t(const KtGeom &g, const KtGenImage &im, const KtO
                                 cudaStream_t st) {
   const cudaError_t attr = kt_allow_large_smem((const void *)bwd_kernel<R, EPT, NL, ACS>);
   if (attr != cudaSuccess) return attr;
-  bwd_kernel<R, EPT, NL, ACS><<<g.bwd_grid > 0 ? g.bwd_grid : g.n_tiles, g.nthreads, smem, st>>>(g, im, ops, a);
+  // a whole sweep runs one tile per CTA
+  bwd_kernel<R, EPT, NL, ACS><<<(g.bwd_grid > 0 && !a.sweep) ? g.bwd_grid : g.n_tiles, g.nthreads, smem, st>>>(g, im, ops, a);
   return cudaGetLastError();
 }
 }  // namespace kt

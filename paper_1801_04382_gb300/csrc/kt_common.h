@@ -14,6 +14,7 @@
 #define KT_MAX_CTERMS 16  // control terms (a control acting on one node; two per control in Liouville space)
 #define KT_MAX_LIND 4
 #define KT_MAX_PAIRS 28
+#define KT_MAX_NL 9       // local dimension of the cavity-structure kernels (atom x cavity, cutoff <= 2)
 #define KT_MAX_S 4        // off-diagonal entries per row of a node-local generator factor
 #define KT_MAX_SH 6       // entries per row of a control factor (update overlap)
 #define KT_MAX_K 96       // Chebyshev terms
@@ -116,6 +117,15 @@ struct KtGenImage {
   const KtCplx *pair_coef;    // [P] scaled coefficient of pair term p (value = coef * a^dag a entries)
   int pair_dst[KT_MAX_PAIRS]; // node raised by pair term p of this direction
   int pair_src[KT_MAX_PAIRS]; // node lowered by pair term p of this direction
+  // Cavity-structure kernels with real / imaginary coupling classes: the pulse-independent
+  // coefficients that every Chebyshev term reads, as kernel-parameter constants in both precisions
+  // (the kernels then take them as constant-bank operands instead of shared-memory loads).
+  float kd32[2 * KT_MAX_NL];  // last node's diagonal, (re, im) per local index
+  double kd64[2 * KT_MAX_NL];
+  float kc32[2 * 2];          // last node's cavity couplings: [n-1] row (r, n-1) <- (g, n), [NC + n-1] the reverse
+  double kc64[2 * 2];
+  float kp32[KT_MAX_PAIRS];   // imaginary part of pair coefficient p
+  double kp64[KT_MAX_PAIRS];
 };
 
 // Pulse-independent operators shared by both directions.

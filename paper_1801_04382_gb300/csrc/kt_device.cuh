@@ -108,6 +108,44 @@ __device__ __forceinline__ void bulk_store(void *dst_gmem, const void *src_smem,
 }
 __device__ __forceinline__ void bulk_store_wait() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Barrier of all CTAs of a cooperative launch (every CTA resident by the launch's guarantee):
+// sync[0] counts arrivals, the last arrival resets it and moves the generation sync[1] on to `gen`
+// + 1 (both words zero at the launch, gen counting the barriers passed).  Every write a CTA made
+// before the barrier is visible to every CTA after it.  Bounded: a CTA that waits longer than
+// KT_WAIT_CYCLES records KT_DEV_TIMEOUT and sees false (the launch's results are then void).
+__device__ __forceinline__ bool grid_barrier(unsigned *sync, unsigned gen, int *flag_slot, int *status) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bool ok = true;
+    __threadfence();
+    if (atomicAdd(&sync[0], 1u) == gridDim.x - 1) {
+      atomicExch(&sync[0], 0u);
+      __threadfence();
+      atomicExch(&sync[1], gen + 1);
+    } else {
+      const long long t0 = clock64();
+      while (ld_acquire_gpu(&sync[1]) != gen + 1) {
+        if (clock64() - t0 > KT_WAIT_CYCLES) {
+          ok = false;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    if (!ok) set_status(status, KT_DEV_TIMEOUT);
+    *flag_slot = ok ? 1 : 0;
+  }
+  __syncthreads();
+  return *flag_slot != 0;
+}
+
 // Whole-tile load by the bulk engine: thread 0 waits (bounded, ~2 s) and the block learns the
 // outcome.  On a timeout the status word gets KT_DEV_TIMEOUT, thread 0 waits once more (~2 s) so
 // that the copy in flight lands before the block leaves, and false is returned to every thread.
@@ -681,10 +719,30 @@ __device__ __forceinline__ void load_rows(const KtGeom &g, const Smem &sm, uint3
   }
 }
 
+// Constants of the real / imaginary kernels (kernel parameters of the image, see KtGenImage).
+template <typename R> __device__ __forceinline__ const R *acs_kd(const KtGenImage &im);
+template <> __device__ __forceinline__ const float *acs_kd<float>(const KtGenImage &im) { return im.kd32; }
+template <> __device__ __forceinline__ const double *acs_kd<double>(const KtGenImage &im) { return im.kd64; }
+template <typename R> __device__ __forceinline__ const R *acs_kc(const KtGenImage &im);
+template <> __device__ __forceinline__ const float *acs_kc<float>(const KtGenImage &im) { return im.kc32; }
+template <> __device__ __forceinline__ const double *acs_kc<double>(const KtGenImage &im) { return im.kc64; }
+template <typename R> __device__ __forceinline__ const R *acs_kp(const KtGenImage &im);
+template <> __device__ __forceinline__ const float *acs_kp<float>(const KtGenImage &im) { return im.kp32; }
+template <> __device__ __forceinline__ const double *acs_kp<double>(const KtGenImage &im) { return im.kp64; }
+// sqrt(n) for the photon numbers n <= 2 of the cavity-structure node (<n-1|a|n>; the host has
+// checked that the ladder factor holds exactly these values)
+template <typename R>
+__device__ __forceinline__ R sqrt_n(int n) {
+  return n >= 2 ? (R)1.4142135623730951 : (n == 1 ? (R)1 : (R)0);
+}
+
 // RI: the couplings are purely real or imaginary by class (host check: node rows hold
 // [real, imaginary] slots, last-node cavity real and drive imaginary, pair coefficients imaginary,
-// ladder values real), applied with two FMAs each.  CACHE: the other nodes' rows come from rc
-// (registers) instead of the shared tables.
+// ladder values sqrt(n), no control on the last node's diagonal or cavity couplings), applied with
+// two FMAs each; the pulse-independent coefficients (last node's diagonal and cavity couplings,
+// pair coefficients, ladder values) are kernel-parameter or compile-time constants, so only the
+// drive couplings, the other nodes' pair tables and the states are read from shared memory.
+// CACHE: the other nodes' rows come from rc (registers) instead of the shared tables.
 template <typename R, int NC, int TT, bool RI, bool CACHE>
 __device__ __forceinline__ void apply_acs(const KtGeom &g, const KtGenImage &im, const Smem &sm,
                                           const typename C2<R>::T *__restrict__ v, int base, uint32_t fdig,
@@ -703,7 +761,9 @@ __device__ __forceinline__ void apply_acs(const KtGeom &g, const KtGenImage &im,
   const int T = TT > 0 ? TT : g.T;   // TT > 0: tile width fixed at compile time
 #pragma unroll
   for (int q = 0; q < NL; ++q) {
-    const C dq = dg[last * NL + q];
+    C dq;
+    if constexpr (RI) dq = mkc(acs_kd<R>(im)[2 * q], acs_kd<R>(im)[2 * q + 1]);
+    else dq = dg[last * NL + q];
     out[q] = cmul(mkc(Df.x + dq.x, Df.y + dq.y), vk[q]);
   }
   // last node: cavity (r, n-1) <-> (g, n) and drive (r, n) <-> (e, n)
@@ -711,8 +771,8 @@ __device__ __forceinline__ void apply_acs(const KtGeom &g, const KtGenImage &im,
   for (int n = 1; n <= NC; ++n) {
     const int qr = 2 * NP + n - 1, qg = n;
     if constexpr (RI) {
-      out[qr] = rfma(ld[qr * NL + qg].x, vk[qg], out[qr]);
-      out[qg] = rfma(ld[qg * NL + qr].x, vk[qr], out[qg]);
+      out[qr] = rfma(acs_kc<R>(im)[n - 1], vk[qg], out[qr]);
+      out[qg] = rfma(acs_kc<R>(im)[NC + n - 1], vk[qr], out[qg]);
     } else {
       out[qr] = cfma(ld[qr * NL + qg], vk[qg], out[qr]);
       out[qg] = cfma(ld[qg * NL + qr], vk[qr], out[qg]);
@@ -793,11 +853,11 @@ __device__ __forceinline__ void apply_acs(const KtGeom &g, const KtGenImage &im,
       if (xs % NP < NC) {
         const int off = g.stride[ps] * T;
         if constexpr (RI) {
-          const R cb = pc[p].y * lo[xs].x;
+          const R cb = acs_kp<R>(im)[p] * sqrt_n<R>(xs % NP + 1);
 #pragma unroll
           for (int q = 0; q < NL; ++q) {
             if (q % NP == 0) continue;
-            out[q] = ifma(cb * ra[q].x, v[base + off + (q - 1) * T], out[q]);
+            out[q] = ifma(cb * sqrt_n<R>(q % NP), v[base + off + (q - 1) * T], out[q]);
           }
         } else {
           const C cf = cmul(pc[p], lo[xs]);
@@ -814,11 +874,11 @@ __device__ __forceinline__ void apply_acs(const KtGeom &g, const KtGenImage &im,
       if (xd % NP >= 1) {
         const int off = -g.stride[pd] * T;
         if constexpr (RI) {
-          const R cb = pc[p].y * ra[xd].x;
+          const R cb = acs_kp<R>(im)[p] * sqrt_n<R>(xd % NP);
 #pragma unroll
           for (int q = 0; q < NL; ++q) {
             if (q % NP == NC) continue;
-            out[q] = ifma(cb * lo[q].x, v[base + off + (q + 1) * T], out[q]);
+            out[q] = ifma(cb * sqrt_n<R>(q % NP + 1), v[base + off + (q + 1) * T], out[q]);
           }
         } else {
           const C cf = cmul(pc[p], ra[xd]);
@@ -935,14 +995,16 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
   Smem sm;
   // with g.fwd_grid > 0 the CTAs loop over tiles blockIdx.x, blockIdx.x + gridDim.x, ...: the tables and
   // the item mapping are built once, and the next tile's psi (fourth buffer, barriers [0] / [3] in turn)
-  // and chi (third buffer) arrive by bulk copy while the current tile is propagated
-  const bool persist = g.fwd_grid > 0;
+  // and chi (third buffer) arrive by bulk copy while the current tile is propagated.
+  // With a.sweep one cooperative launch runs intervals a.j .. nt of one tile per CTA (see FwdArgs).
+  const bool sweep = a.sweep != 0;
+  const bool persist = !sweep && g.fwd_grid > 0;
   carve(g, sizeof(C), smem_raw, &sm, g.prefetch_chi != 0, persist);
   const int tau = threadIdx.x % g.T;
-  const int j = a.j;
   // bisection stop: 2^-48 dt in FP64 (near the rounding of the FP64 norm it compares), 2^-40 dt in
   // FP32-mixed (far below the FP32 norm's own error)
   const double tol = (sizeof(R) == 8 ? 0x1p-48 : 0x1p-40) * g.dt;
+  int j = a.j;
 
   if (threadIdx.x < g.n_ctrl) {
     const int c = threadIdx.x;
@@ -963,23 +1025,42 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
   }
   __syncthreads();
   const uint32_t tile_bytes = (uint32_t)(g.tile_elems * sizeof(C));
-  const bool need_chi = a.overlap && j < a.nt;
-  int tile = blockIdx.x;
+  // co-states chi(t_i) of interval i's update overlap
+  auto chi_of = [&](int i, int t) -> const C * {
+    const C *base = sweep ? (const C *)((const char *)a.chi_slots + (size_t)i * a.slot_bytes) : (const C *)a.chi_t;
+    return base + (size_t)t * g.tile_elems;
+  };
   // the bulk engine brings psi(t_{j-1}) (and chi(t_j) when there is room) while the tables are built
   if (threadIdx.x == 0) {
-    bulk_load(sm.bufA, (const C *)a.psi_in + (size_t)tile * g.tile_elems, tile_bytes, &sm.mbar[0]);
-    if (need_chi && g.prefetch_chi)
-      bulk_load(sm.bufC, (const C *)a.chi_t + (size_t)tile * g.tile_elems, tile_bytes, &sm.mbar[1]);
+    bulk_load(sm.bufA, (const C *)a.psi_in + (size_t)blockIdx.x * g.tile_elems, tile_bytes, &sm.mbar[0]);
+    if (a.overlap && j < a.nt && g.prefetch_chi) bulk_load(sm.bufC, chi_of(j, blockIdx.x), tile_bytes, &sm.mbar[1]);
   }
   build_tables<R>(g, im, ops, sm, sm.eps, a.overlap != 0);
   Items<EPT, NL> it;
   load_items<EPT, NL>(g, ops, it);
   bool store_pending = false;
+  unsigned nchi = 0;        // chi loads waited for on barrier [1] (the n-th completes phase n & 1)
+  unsigned sync_gen = 0;    // grid barriers passed (sweep)
+  C acc[EPT];
+  for (;; ++j) {            // intervals: one unless sweep
+  const bool need_chi = a.overlap && j < a.nt;
+  if (j != a.j) {
+    // sweep: the next interval.  Its pulse is in sm.eps (guess sweep: eps_old; updating: the value
+    // the barrier's finisher formed), its chi goes to the third buffer once every thread is done
+    // with the previous one, and the tables are rebuilt for the new pulse.
+    if (!a.update && threadIdx.x < g.n_ctrl) sm.eps[threadIdx.x] = a.eps_old[threadIdx.x * a.nt + (j - 1)];
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0 && need_chi && g.prefetch_chi)
+      bulk_load(sm.bufC, chi_of(j, blockIdx.x), tile_bytes, &sm.mbar[1]);
+    build_tables<R>(g, im, ops, sm, sm.eps, a.overlap != 0);
+  }
+  int tile = blockIdx.x;
   for (int use = 0; tile < g.n_tiles; tile += gridDim.x, ++use) {
   const int next = tile + (int)gridDim.x;
-  const C *psi_in = (const C *)a.psi_in + (size_t)tile * g.tile_elems;
-  C *psi_out = (C *)a.psi_out + (size_t)tile * g.tile_elems;
-  const C *chi_g = need_chi ? (const C *)a.chi_t + (size_t)tile * g.tile_elems : nullptr;
+  const C *psi_in = (const C *)((!sweep || j <= 1) ? a.psi_in : a.psi_ring[(j - 1) & 1]) + (size_t)tile * g.tile_elems;
+  C *psi_out = (C *)(sweep ? a.psi_ring[j & 1] : a.psi_out) + (size_t)tile * g.tile_elems;
+  const C *chi_g = need_chi ? chi_of(j, tile) : nullptr;
   // the trajectory's current threshold, read now so that its latency is off the path after the series
   const double r_start = (threadIdx.x < g.T) ? a.rstate[(size_t)tile * g.T + threadIdx.x] : 0.0;
   if (threadIdx.x == 0) {
@@ -989,12 +1070,17 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
   }
   C *A = (C *)sm.bufA;
   C *B = (C *)sm.bufB;
-  C acc[EPT];
-  // psi of this tile: load number `use`, barrier [0] / [3] in turn, phase parity (use >> 1) & 1
-  if (!tile_wait((use & 1) ? &sm.mbar[3] : &sm.mbar[0], (use >> 1) & 1, &sm.flag[4], a.status,
-                 g.inject_timeout ? &sm.mbar[2] : nullptr)) {
+  if (sweep && j != a.j) {
+    // sweep: psi(t_{j-1}) is the previous interval's result, still in registers
+#pragma unroll
+    for (int q = 0; q < EPT; ++q)
+      if (it.ok(q)) A[it.item(q)] = acc[q];
+    __syncthreads();
+  } else if (!tile_wait((use & 1) ? &sm.mbar[3] : &sm.mbar[0], (use >> 1) & 1, &sm.flag[4], a.status,
+                        g.inject_timeout ? &sm.mbar[2] : nullptr)) {
+    // psi of this tile: load number `use`, barrier [0] / [3] in turn, phase parity (use >> 1) & 1
     if (threadIdx.x == 0) {
-      if (need_chi && g.prefetch_chi) mbar_wait_bounded(&sm.mbar[1], use & 1);
+      if (need_chi && g.prefetch_chi) mbar_wait_bounded(&sm.mbar[1], nchi & 1);
       if (store_pending) bulk_store_wait();
     }
     return;
@@ -1209,11 +1295,18 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
   }
 
   if (j >= 1 && !jumped) {
-    // psi(t_j) of the whole tile is in A: one bulk store to psi_out
-    fence_proxy_async_smem();
-    __syncthreads();
-    if (threadIdx.x == 0) bulk_store(psi_out, A, tile_bytes);
-    stored = true;
+    if (sweep) {
+      // sweep: plain stores, read back by the next interval's jump restarts after a CTA barrier
+#pragma unroll
+      for (int q = 0; q < EPT; ++q)
+        if (it.ok(q)) psi_out[it.item(q)] = acc[q];
+    } else {
+      // psi(t_j) of the whole tile is in A: one bulk store to psi_out
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (threadIdx.x == 0) bulk_store(psi_out, A, tile_bytes);
+      stored = true;
+    }
   }
 
   // ---------------- end of the sweep: tau_k = <tgt|psi_k>/||psi_k|| ----------------
@@ -1268,7 +1361,7 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
     if (threadIdx.x == 0) bulk_load(B, chi_g, tile_bytes, &sm.mbar[1]);
     chi = B;
   }
-  if (!tile_wait(&sm.mbar[1], use & 1, &sm.flag[5], a.status, g.inject_timeout ? &sm.mbar[2] : nullptr)) {
+  if (!tile_wait(&sm.mbar[1], nchi & 1, &sm.flag[5], a.status, g.inject_timeout ? &sm.mbar[2] : nullptr)) {
     if (threadIdx.x == 0) {
       if (store_pending || stored) bulk_store_wait();
       // the next tile's psi is on its way into the fourth buffer: let it land before leaving
@@ -1276,6 +1369,7 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
     }
     return;
   }
+  ++nchi;
   const C *hv = (const C *)sm.hc_val;
   // per-thread sums per control in the state precision (a trajectory problem has one term per
   // control; a density matrix a ket and a bra term), converted to FP64 once for the reduction
@@ -1333,7 +1427,9 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
   if (threadIdx.x < g.n_ctrl) {
     double s = 0.0;
     for (int t = 0; t < g.T; ++t) s += sm.tsc[TS_V0 * g.T + t * KT_MAX_CTRL + threadIdx.x];
-    a.partials[(size_t)tile * g.n_ctrl + threadIdx.x] = s;
+    // a sweep keeps two sets of partials (interval parity): a CTA may write the next interval's
+    // while a slower one still reads this interval's
+    a.partials[(sweep ? (size_t)(j & 1) * g.n_tiles * g.n_ctrl : 0) + (size_t)tile * g.n_ctrl + threadIdx.x] = s;
   }
   store_pending = store_pending || stored;
   end_fwd_tile(sm, persist);
@@ -1341,6 +1437,44 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
   if (persist && need_chi && g.prefetch_chi && next < g.n_tiles && threadIdx.x == 0)
     bulk_load(sm.bufC, (const C *)a.chi_t + (size_t)next * g.tile_elems, tile_bytes, &sm.mbar[1]);
   }   // tiles of this CTA
+  // Delta eps of interval j+1 from the partials of all tiles: every thread adds a fixed, contiguous
+  // chunk of the tiles and a fixed shuffle/warp tree adds the chunks -- the same order on every run
+  // for a given tile count and block size.  The new pulse value goes to sm.eps (the next interval of
+  // a sweep) and, with write_out, to deps / eps_new.
+  auto finish_update = [&](const double *part, bool write_out) {
+    const int chunk = (g.n_tiles + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int t0 = threadIdx.x * chunk, t1 = min(g.n_tiles, t0 + chunk);
+    for (int c = 0; c < g.n_ctrl; ++c) {
+      double v = 0.0;
+      for (int t = t0; t < t1; ++t) v += __ldcg(part + (size_t)t * g.n_ctrl + c);
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if ((threadIdx.x & 31) == 0) sm.red[(threadIdx.x >> 5) * 8 + c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < g.n_ctrl) {
+      const int c = threadIdx.x;
+      double s = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sm.red[w * 8 + c];
+      const size_t idx = (size_t)c * a.nt + j;   // interval j+1 (0-based index j)
+      const double de = a.shape[idx] / (g.lam[c] * g.M_norm) * s;
+      const double en = a.eps_old[idx] + de;
+      if (write_out) {
+        a.deps[idx] = de;
+        a.eps_new[idx] = en;
+        if (!isfinite(de)) set_status(a.status, KT_DEV_NONFINITE);
+        if (fabs(en) > g.eps_bound) set_status(a.status, KT_DEV_RANGE);
+      }
+      sm.eps[c] = en;
+    }
+  };
+  if (sweep) {
+    if (j == a.nt) break;
+    if (!need_chi) continue;                 // guess sweep: nothing to exchange between intervals
+    if (!grid_barrier(a.sync, sync_gen, &sm.flag[6], a.status)) break;   // timed out: results void
+    ++sync_gen;
+    finish_update(a.partials + (size_t)(j & 1) * g.n_tiles * g.n_ctrl, blockIdx.x == 0);
+    continue;
+  }
   if (!a.overlap || j == a.nt || !a.finish) {   // no update sum here (a shard sums after its exchange)
     if (threadIdx.x == 0 && store_pending) bulk_store_wait();
     return;
@@ -1356,30 +1490,11 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
   if (threadIdx.x == 0 && store_pending) bulk_store_wait();
   if (!sm.flag[3]) return;
   __threadfence();
-  // every thread adds a fixed, contiguous chunk of the tiles; a fixed shuffle/warp tree adds the
-  // chunks -- the same order on every run for a given tile count and block size
-  const int chunk = (g.n_tiles + (int)blockDim.x - 1) / (int)blockDim.x;
-  const int t0 = threadIdx.x * chunk, t1 = min(g.n_tiles, t0 + chunk);
-  for (int c = 0; c < g.n_ctrl; ++c) {
-    double v = 0.0;
-    for (int t = t0; t < t1; ++t) v += __ldcg(a.partials + (size_t)t * g.n_ctrl + c);
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) sm.red[(threadIdx.x >> 5) * 8 + c] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < g.n_ctrl) {
-    const int c = threadIdx.x;
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sm.red[w * 8 + c];
-    const size_t idx = (size_t)c * a.nt + j;   // interval j+1 (0-based index j)
-    const double de = a.shape[idx] / (g.lam[c] * g.M_norm) * s;
-    const double en = a.eps_old[idx] + de;
-    a.deps[idx] = de;
-    a.eps_new[idx] = en;
-    if (!isfinite(de)) set_status(a.status, KT_DEV_NONFINITE);
-    if (fabs(en) > g.eps_bound) set_status(a.status, KT_DEV_RANGE);
-  }
+  finish_update(a.partials, true);
   if (threadIdx.x == 0) *a.counter = 0u;
+  return;
+  }   // intervals
+  if (threadIdx.x == 0 && store_pending) bulk_store_wait();
 }
 
 // --------------------------------------------------------------------------------------
@@ -1393,16 +1508,21 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
 // blockIdx.x + gridDim.x, ...: the tables and the item mapping (which depend on the interval only)
 // are built once, and the next tile's input arrives by bulk copy in a third buffer while the current
 // tile's series runs (loads alternate between two transaction barriers).  Otherwise one tile per CTA.
+// With a.sweep one launch runs the whole backward sweep of its tile, intervals a.j down to 1 (the
+// co-states of different trajectories never meet, so the CTAs need no synchronisation): the state
+// stays in shared memory from one interval to the next, and each interval's result is stored to its
+// co-state slot.
 template <typename R, int EPT, int NL, int ACS>
 __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) bwd_kernel(KtGeom g, KtGenImage im, KtOps ops, BwdArgs a) {
   typedef typename C2<R>::T C;
   extern __shared__ __align__(16) char smem_raw[];
   Smem sm;
-  const bool persist = g.bwd_grid > 0;
+  const bool sweep = a.sweep != 0;
+  const bool persist = !sweep && g.bwd_grid > 0;
   carve(g, sizeof(C), smem_raw, &sm, persist);
   const int tau = threadIdx.x % g.T;
-  const int j = a.j;
-  if (threadIdx.x < g.n_ctrl) sm.eps[threadIdx.x] = a.eps[threadIdx.x * a.nt + (j - 1)];
+  const int j_first = a.j, j_last = sweep ? 1 : a.j;
+  if (threadIdx.x < g.n_ctrl) sm.eps[threadIdx.x] = a.eps[threadIdx.x * a.nt + (j_first - 1)];
   if (threadIdx.x < 8) sm.flag[threadIdx.x] = 0;
   if (threadIdx.x == 0) {
     mbar_init(&sm.mbar[0], 1);
@@ -1421,7 +1541,6 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
   load_items<EPT, NL>(g, ops, it);
   bool store_pending = false;
   for (int use = 0; tile < g.n_tiles; tile += gridDim.x, ++use) {
-    C *chi_out = (C *)a.chi_out + (size_t)tile * g.tile_elems;
     // this tile's input: load number `use`, on barrier use & 1 with phase parity (use >> 1) & 1
     if (!tile_wait(&sm.mbar[use & 1], (use >> 1) & 1, &sm.flag[4], a.status,
                    g.inject_timeout ? &sm.mbar[2] : nullptr)) {
@@ -1431,6 +1550,16 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
     const int next = tile + (int)gridDim.x;
     if (persist && next < g.n_tiles && threadIdx.x == 0)   // the third buffer is free: prefetch the next input
       bulk_load(sm.bufC, (const C *)a.chi_in + (size_t)next * g.tile_elems, tile_bytes, &sm.mbar[(use + 1) & 1]);
+  for (int j = j_first; j >= j_last; --j) {
+    if (j != j_first) {
+      // whole sweep: the pulse and the tables of the next interval (every read of the previous
+      // interval's tables ended at the barrier after its store)
+      if (threadIdx.x < g.n_ctrl) sm.eps[threadIdx.x] = a.eps[threadIdx.x * a.nt + (j - 1)];
+      __syncthreads();
+      build_tables<R>(g, im, ops, sm, sm.eps, false);
+    }
+    C *chi_out = sweep ? (C *)((char *)a.chi_slots + (size_t)(j - 1) * a.slot_bytes) + (size_t)tile * g.tile_elems
+                       : (C *)a.chi_out + (size_t)tile * g.tile_elems;
     if (threadIdx.x == 0) sm.flag[0] = 0;
     if (threadIdx.x == 0 && store_pending) bulk_store_wait();   // A still feeds the previous tile's store
     store_pending = false;
@@ -1517,10 +1646,17 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
 #pragma unroll
     for (int q = 0; q < EPT; ++q)
       if (it.ok(q)) A[it.item(q)] = acc[q];
+    if (sweep && j > j_last) {
+      // the next interval starts from this result (B's last reads ended at the rounds' barrier)
+#pragma unroll
+      for (int q = 0; q < EPT; ++q)
+        if (it.ok(q)) B[it.item(q)] = acc[q];
+    }
     fence_proxy_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) bulk_store(chi_out, A, tile_bytes);
     store_pending = true;
+  }   // intervals
     // the prefetched input becomes this CTA's input buffer; the old one (free) the next prefetch target
     void *tmp = sm.bufB;
     sm.bufB = sm.bufC;

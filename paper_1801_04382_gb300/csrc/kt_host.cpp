@@ -957,6 +957,7 @@ struct HostImage {
   std::vector<int> dl, poff;
   std::vector<KtCplx> base, cslot, dg, cdg, pval, cf, pc;
   int pdst[KT_MAX_PAIRS], psrc[KT_MAX_PAIRS];
+  double kd[2 * KT_MAX_NL] = {}, kc[4] = {}, kp[KT_MAX_PAIRS] = {};   // constants of the real / imaginary kernels
 };
 
 struct HostPlan {
@@ -1005,6 +1006,31 @@ bool cavity_structure(const Gen &gf, const Gen &gb, const std::vector<int> &lo_d
   if (!check(gf.loc, (size_t)last * nl * nl) || !check(gb.loc, (size_t)last * nl * nl)) return false;
   for (size_t c = 0; c < gf.ctrl_node.size(); ++c)
     if (gf.ctrl_node[c] == last && (!check(gf.ctrl, c * nl * nl) || !check(gb.ctrl, c * nl * nl))) return false;
+  return true;
+}
+
+// The real / imaginary cavity-structure kernels take as constants the last node's diagonal and
+// cavity couplings, the pair coefficients and the ladder values sqrt(n): true when no control term
+// on the last node touches its diagonal or cavity couplings (those entries are then the same in every
+// interval) and the ladder factor is the cavity annihilation operator, <n-1|a|n> = sqrt(n) exactly.
+bool acs_constants_ok(const Gen &gf, const Gen &gb, const std::vector<cd> &lo_val, const std::vector<cd> &ra_val) {
+  const int nl = gf.nl, NP = nl / 3, NC = NP - 1, last = gf.N - 1;
+  for (int x = 0; x < nl; ++x) {
+    const int n = x % NP;
+    if (n < NC && lo_val[x] != cd(std::sqrt((double)(n + 1)), 0.0)) return false;
+    if (n >= 1 && ra_val[x] != cd(std::sqrt((double)n), 0.0)) return false;
+  }
+  for (const Gen *gen : {&gf, &gb})
+    for (size_t t = 0; t < gen->ctrl_node.size(); ++t) {
+      if (gen->ctrl_node[t] != last) continue;
+      for (int x = 0; x < nl; ++x)
+        if (at(gen->ctrl, (int)t * nl * nl, nl, x, x) != 0.0) return false;
+      for (int n = 1; n <= NC; ++n) {
+        const int qr = 2 * NP + n - 1, qg = n;
+        if (at(gen->ctrl, (int)t * nl * nl, nl, qr, qg) != 0.0 || at(gen->ctrl, (int)t * nl * nl, nl, qg, qr) != 0.0)
+          return false;
+      }
+    }
   return true;
 }
 
@@ -1339,12 +1365,18 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P, bool 
       S = std::max(S, (int)cl.size());
     }
   if (S > KT_MAX_S) return fail(KT_ERR_UNSUPPORTED, "a node row has %d > %d off-diagonal entries", S, KT_MAX_S);
-  const int ipt = cfg->items_per_thread;
-  if (ipt != 0 && ipt != 1 && ipt != 2 && ipt != 4 && ipt != 8 && ipt != 16)
+  if (cfg->items_per_thread != 0 && cfg->items_per_thread != 1 && cfg->items_per_thread != 2 &&
+      cfg->items_per_thread != 4 && cfg->items_per_thread != 8 && cfg->items_per_thread != 16)
     return fail(KT_ERR_ARG, "items_per_thread must be 0 (automatic), 1, 2, 4, 8 or 16");
+  // automatic mapping: one thread per last-node fiber, unless a trajectory has fewer than 16 fibers
+  // (d <= 81) and the tile width is automatic too: then a CTA would hold a few warps at most, and the
+  // strided mapping with one item per thread runs n_loc times as many threads per trajectory
+  // (measured faster at d = 36 and 81, about 5x in FP64, where the fiber kernels' register arrays spill)
+  const bool small = (nl == 6 || nl == 9) && d / nl < 16 && cfg->tile_traj <= 0;
+  const int ipt = cfg->items_per_thread > 0 ? cfg->items_per_thread : (small ? 1 : 0);
   const bool fiber = (nl == 6 || nl == 9) && ipt == 0;
   const bool acs = fiber && cavity_structure(gf, gb, lo_dl, lo_val, ra_dl, ra_val);
-  const bool ri = acs && S <= 2 && ri_classes(gf, gb, lo_val, ra_val, cols);
+  const bool ri = acs && S <= 2 && ri_classes(gf, gb, lo_val, ra_val, cols) && acs_constants_ok(gf, gb, lo_val, ra_val);
   if (ri) S = 2;
   g.S = std::max(S, 1);
   int SH = 1;
@@ -1383,6 +1415,9 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P, bool 
       t.nthreads = maxthr;
     }
     if (kt_smem_bytes(t, esz, false) > 227 * 1024) continue;
+    // small problems on the automatic strided mapping: tiles of at most 128 items (a few warps),
+    // latency rather than throughput decides there
+    if (small && cfg->items_per_thread == 0 && cfg->tile_traj <= 0 && T > 1 && (long long)d * T > 128) continue;
     Tsel = T;
     // prefer more tiles when the trajectories would not fill the GPU
     // (a shard plans with the whole problem's trajectory count: every shard needs the same tile width)
@@ -1497,6 +1532,27 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P, bool 
           im.pval[e] = KtCplx{v.real(), v.imag()};
         }
     }
+    if (ri) {
+      // constants of the real / imaginary kernels: the values the shared tables would hold
+      const int last = N - 1, NP = nl / 3, NC = NP - 1;
+      for (int x = 0; x < nl; ++x) {
+        im.kd[2 * x] = im.dg[(size_t)last * nl + x].re;
+        im.kd[2 * x + 1] = im.dg[(size_t)last * nl + x].im;
+      }
+      auto slot_re = [&](int x, int y) {
+        for (int q = 0; q < g.S; ++q) {
+          const size_t e = (size_t)last * nls + x * g.S + q;
+          if (im.dl[e] == y - x) return im.base[e].re;
+        }
+        return 0.0;
+      };
+      for (int n = 1; n <= NC; ++n) {
+        const int qr = 2 * NP + n - 1, qg = n;
+        im.kc[n - 1] = slot_re(qr, qg);
+        im.kc[NC + n - 1] = slot_re(qg, qr);
+      }
+      for (int q = 0; q < g.n_pairs; ++q) im.kp[q] = im.pc[q].im;
+    }
     im.cf.resize(K);
     const cd ph = std::exp(cd(0.0, -cgen * dt));
     for (int k = 0; k < K; ++k) {
@@ -1566,6 +1622,16 @@ kt_status upload_image(kt_problem *p, const HostImage &h, KtGenImage &im, cudaSt
   for (int q = 0; q < KT_MAX_PAIRS; ++q) {
     im.pair_dst[q] = h.pdst[q];
     im.pair_src[q] = h.psrc[q];
+    im.kp32[q] = (float)h.kp[q];
+    im.kp64[q] = h.kp[q];
+  }
+  for (int q = 0; q < 2 * KT_MAX_NL; ++q) {
+    im.kd32[q] = (float)h.kd[q];
+    im.kd64[q] = h.kd[q];
+  }
+  for (int q = 0; q < 4; ++q) {
+    im.kc32[q] = (float)h.kc[q];
+    im.kc64[q] = h.kc[q];
   }
   return KT_OK;
 }
@@ -1739,13 +1805,16 @@ kt_status create_problem(const kt_model_desc *md, const kt_config *cfg, const Ho
   return KT_OK;
 }
 
-// Average duration of the forward interval kernel of probe q (no update, guess pulse), timed with
-// events on st over a few intervals after two warm-up launches.
+// Average duration of a forward plus a backward interval kernel of probe q (no update, guess pulse,
+// no jump records), timed with events on st over a few intervals after two warm-up intervals.
 kt_status probe_forward_ms(kt_problem *q, cudaStream_t st, double *ms_out) {
   const int warm = 2, timed = 12;
   KT_CUDA(kt_launch_init_pass(q->g, q->U, q->pass, q->rstate, q->jcount[0], st));
+  // the backward kernel follows the (empty) records of the other buffer: seek its cursor first
+  KT_CUDA(kt_launch_cursor_seek(q->g, q->rec_step[1 - q->cur], q->jcount[1 - q->cur], q->nt, q->cursor, st));
   FwdArgs a = fwd_args(q, 0);
   a.chi_t = nullptr;
+  BwdArgs b = bwd_args(q);
   cudaEvent_t e[2];
   KT_CUDA(cudaEventCreate(&e[0]));
   if (cudaEventCreate(&e[1]) != cudaSuccess) {
@@ -1759,6 +1828,11 @@ kt_status probe_forward_ms(kt_problem *q, cudaStream_t st, double *ms_out) {
     a.psi_in = i == 0 ? q->psi_init : q->psi[(i - 1) & 1];
     a.psi_out = q->psi[i & 1];
     if (err == cudaSuccess) err = kt_launch_fwd(q->fp64, q->ept, q->g, q->im_fwd, q->ops, a, st);
+    // one backward interval on the state just written (free propagation: no records)
+    b.j = q->nt - i % q->nt;
+    b.chi_in = q->psi[i & 1];
+    b.chi_out = q->psi[(i - 1) & 1];
+    if (err == cudaSuccess && i > 0) err = kt_launch_bwd(q->fp64, q->ept, q->g, q->im_bwd, q->ops, b, st);
   }
   if (err == cudaSuccess) err = cudaEventRecord(e[1], st);
   if (err == cudaSuccess) err = cudaEventSynchronize(e[1]);
@@ -1773,7 +1847,7 @@ kt_status probe_forward_ms(kt_problem *q, cudaStream_t st, double *ms_out) {
 
 // Autotuner: plan every power-of-two tile width that fits, with the automatic thread mapping and
 // (unless the caller fixed items_per_thread) the strided mapping at 1, 2 and 4 items per thread,
-// time the forward interval kernel of each distinct plan, keep the fastest.
+// time a forward and a backward interval kernel of each distinct plan, keep the fastest.
 kt_status autotune(const kt_model_desc *md, const kt_config *cfg, cudaStream_t st, HostPlan &best) {
   double best_ms = 0.0;
   int best_T = 0;

@@ -51,6 +51,17 @@ struct FwdArgs {
   KtCplx *tau;           // [M_pad] (j == nt)
   double *norm2;         // [M_pad] (j == nt)
   int *status;
+  // whole forward sweep in one cooperative launch (one tile per CTA, every CTA resident): intervals
+  // j .. nt, the state kept in shared memory between them; psi(t_i) goes to psi_ring[i & 1] (the
+  // input of interval 1 is psi_in), chi(t_i) is read from chi_slots + i * slot_bytes.  With the
+  // update the CTAs meet at a grid barrier (sync: two words, zero at the launch) after each
+  // interval's overlap, and every CTA forms Delta eps from all tiles' partials in the finisher's
+  // order (partials double-buffered by interval parity: [2][n_tiles][n_ctrl]).
+  int sweep;
+  void *psi_ring[2];
+  const void *chi_slots;
+  size_t slot_bytes;
+  unsigned *sync;
 };
 
 struct BwdArgs {
@@ -68,6 +79,11 @@ struct BwdArgs {
   const double *rec_s;
   const double *rec_c;
   int *status;
+  // whole backward sweep in one launch (one tile per CTA): intervals j, j-1, ..., 1, the state kept
+  // in shared memory between them; chi(t_{i-1}) of interval i goes to chi_slots + (i-1) * slot_bytes
+  int sweep;
+  void *chi_slots;
+  size_t slot_bytes;
 };
 
 #include "../../include/krotov_traj.h"

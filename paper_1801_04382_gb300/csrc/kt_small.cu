@@ -122,7 +122,7 @@ cudaError_t kt_launch_fwd(int fp64, int ept, const KtGeom &g, const KtGenImage &
 
 cudaError_t kt_launch_bwd(int fp64, int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops,
                           const BwdArgs &a, cudaStream_t st) {
-  const size_t smem = kt_smem_bytes(g, fp64 ? 16 : 8, g.bwd_grid > 0);
+  const size_t smem = kt_smem_bytes(g, fp64 ? 16 : 8, g.bwd_grid > 0 && !a.sweep);
   return fp64 ? kt_launch_bwd_f64(ept, g, im, ops, a, smem, st) : kt_launch_bwd_f32(ept, g, im, ops, a, smem, st);
 }
 
