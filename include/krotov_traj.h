@@ -154,12 +154,23 @@ typedef struct {
                                (about 2 s) whatever this flag. */
   int items_per_thread;     /* thread mapping of the interval kernels.  0 = automatic: for the node
                                dimensions 6 and 9 one thread per last-node fiber (the cavity-structure
-                               kernels when the generator has that structure), else the strided mapping
-                               with the fewest items per thread that fit; with tile_traj = -1 the
-                               autotuner also times the strided mapping at 1, 2 and 4 items per thread.
+                               kernels when the generator has that structure) -- unless a trajectory has
+                               fewer than 16 fibers and the tile width is automatic too, then the strided
+                               mapping with one item per thread -- else the strided mapping with the
+                               fewest items per thread that fit; with tile_traj = -1 the autotuner also
+                               times the strided mapping at 1, 2 and 4 items per thread.
                                1, 2, 4, 8 or 16: the strided mapping (item q of thread t is element
                                t + q * threads of the tile) with that many items per thread -- more
                                threads per trajectory for problems too small to fill the GPU otherwise */
+  int per_interval_launches; /* 0 = automatic: when the problem runs on the strided mapping, every tile
+                               is resident on the GPU at once and every co-state is kept (small
+                               problems), each sweep is one
+                               launch -- the backward sweep a plain one, the forward sweep a cooperative
+                               one whose CTAs meet at a grid barrier after each interval to form the
+                               update (Sec. 2.2: the update of interval j+1 needs every trajectory's
+                               state at t_j); bit-identical to the per-interval launches.  Not used for
+                               shards, the cross-trajectory rule, the sweeps that keep states for the
+                               gradient, or the problems of a batch.  1 = one launch per interval. */
 } kt_config;
 
 /* Create a problem: validate, assemble H_eff in structured form (a1), choose the Chebyshev
@@ -321,6 +332,7 @@ typedef struct {
   int costate_slots;        /* co-state slots held in device memory */
   int items_per_thread;     /* thread mapping of the interval kernels: 0 = one thread per last-node
                                fiber, else the strided mapping with this many items per thread */
+  int whole_sweep;          /* 1: sweeps run as one launch each (see kt_config.per_interval_launches) */
 } kt_info;
 KT_API kt_status krotov_get_info(kt_problem *p, kt_info *info);
 

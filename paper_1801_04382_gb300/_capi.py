@@ -40,7 +40,7 @@ class Config(ct.Structure):
         ("eps_bound", ct.c_double), ("cheb_tol", ct.c_double), ("tile_traj", ct.c_int),
         ("update_rule", ct.c_int), ("jump_scheme", ct.c_int), ("ckpt_prefix", ct.c_int),
         ("traj_offset", ct.c_int), ("M_total", ct.c_int), ("inject_copy_timeout", ct.c_int),
-        ("items_per_thread", ct.c_int),
+        ("items_per_thread", ct.c_int), ("per_interval_launches", ct.c_int),
     ]
 
 
@@ -51,6 +51,7 @@ class Info(ct.Structure):
         ("damping", ct.c_double), ("device_bytes", ct.c_longlong), ("passes", ct.c_longlong),
         ("eps_bound", ct.c_double), ("sweeps", ct.c_longlong), ("ckpt_interval", ct.c_int),
         ("ckpt_kept_prefix", ct.c_int), ("costate_slots", ct.c_int), ("items_per_thread", ct.c_int),
+        ("whole_sweep", ct.c_int),
     ]
 
 

@@ -3,13 +3,23 @@
 #include "kt_device.cuh"
 
 namespace kt {
+// a whole sweep (strided mapping only, the mapping of the small problems) runs one tile per CTA
 template <typename R, int EPT, int NL, int ACS>
 static cudaError_t launch_bwd_t(const KtGeom &g, const KtGenImage &im, const KtOps &ops, const BwdArgs &a, size_t smem,
                                 cudaStream_t st) {
-  const cudaError_t attr = kt_allow_large_smem((const void *)bwd_kernel<R, EPT, NL, ACS>);
+  if (a.sweep) {
+    if constexpr (NL == 0 && ACS == 0) {
+      const cudaError_t attr = kt_allow_large_smem((const void *)bwd_kernel<R, EPT, 0, 0, true>);
+      if (attr != cudaSuccess) return attr;
+      bwd_kernel<R, EPT, 0, 0, true><<<g.n_tiles, g.nthreads, smem, st>>>(g, im, ops, a);
+      return cudaGetLastError();
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  }
+  const cudaError_t attr = kt_allow_large_smem((const void *)bwd_kernel<R, EPT, NL, ACS, false>);
   if (attr != cudaSuccess) return attr;
-  // a whole sweep runs one tile per CTA
-  bwd_kernel<R, EPT, NL, ACS><<<(g.bwd_grid > 0 && !a.sweep) ? g.bwd_grid : g.n_tiles, g.nthreads, smem, st>>>(g, im, ops, a);
+  bwd_kernel<R, EPT, NL, ACS, false><<<g.bwd_grid > 0 ? g.bwd_grid : g.n_tiles, g.nthreads, smem, st>>>(g, im, ops, a);
   return cudaGetLastError();
 }
 }  // namespace kt

@@ -988,7 +988,7 @@ __device__ __forceinline__ void end_fwd_tile(Smem &sm, bool persist) {
 //   REST    the remainder of the interval from the collapsed state, tested again.
 enum { PH_MAIN = 0, PH_BISECT, PH_SSTAR, PH_REST, PH_DONE };
 
-template <typename R, int EPT, int NL, int ACS>
+template <typename R, int EPT, int NL, int ACS, bool SWEEP>
 __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) fwd_kernel(KtGeom g, KtGenImage im, KtOps ops, FwdArgs a) {
   typedef typename C2<R>::T C;
   extern __shared__ __align__(16) char smem_raw[];
@@ -996,8 +996,9 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
   // with g.fwd_grid > 0 the CTAs loop over tiles blockIdx.x, blockIdx.x + gridDim.x, ...: the tables and
   // the item mapping are built once, and the next tile's psi (fourth buffer, barriers [0] / [3] in turn)
   // and chi (third buffer) arrive by bulk copy while the current tile is propagated.
-  // With a.sweep one cooperative launch runs intervals a.j .. nt of one tile per CTA (see FwdArgs).
-  const bool sweep = a.sweep != 0;
+  // SWEEP (a.sweep): one cooperative launch runs intervals a.j .. nt of one tile per CTA (see FwdArgs);
+  // a compile-time switch, so that the per-interval kernels carry none of the sweep's state.
+  constexpr bool sweep = SWEEP;
   const bool persist = !sweep && g.fwd_grid > 0;
   carve(g, sizeof(C), smem_raw, &sm, g.prefetch_chi != 0, persist);
   const int tau = threadIdx.x % g.T;
@@ -1420,13 +1421,24 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
     for (int c = 0; c < KT_MAX_CTRL; ++c)
       if (c == ct) sc[c] += s;
   }
-  double v[KT_MAX_CTRL];
+  // FP64 block reduction of the per-control sums: four slots when there are at most four controls
+  // (FP64 runs at 1/64 of the FP32 rate here, and every slot costs additions in each lane)
+  int vstride = KT_MAX_CTRL;
+  if (g.n_ctrl <= 4) {
+    double v[4];
 #pragma unroll
-  for (int c = 0; c < KT_MAX_CTRL; ++c) v[c] = c < g.n_ctrl ? (double)sc[c] : 0.0;
-  reduce_tau<KT_MAX_CTRL>(v, g, sm.red, sm.tsc + TS_V0 * g.T);
+    for (int c = 0; c < 4; ++c) v[c] = c < g.n_ctrl ? (double)sc[c] : 0.0;
+    reduce_tau<4>(v, g, sm.red, sm.tsc + TS_V0 * g.T);
+    vstride = 4;
+  } else {
+    double v[KT_MAX_CTRL];
+#pragma unroll
+    for (int c = 0; c < KT_MAX_CTRL; ++c) v[c] = c < g.n_ctrl ? (double)sc[c] : 0.0;
+    reduce_tau<KT_MAX_CTRL>(v, g, sm.red, sm.tsc + TS_V0 * g.T);
+  }
   if (threadIdx.x < g.n_ctrl) {
     double s = 0.0;
-    for (int t = 0; t < g.T; ++t) s += sm.tsc[TS_V0 * g.T + t * KT_MAX_CTRL + threadIdx.x];
+    for (int t = 0; t < g.T; ++t) s += sm.tsc[TS_V0 * g.T + t * vstride + threadIdx.x];
     // a sweep keeps two sets of partials (interval parity): a CTA may write the next interval's
     // while a slower one still reads this interval's
     a.partials[(sweep ? (size_t)(j & 1) * g.n_tiles * g.n_ctrl : 0) + (size_t)tile * g.n_ctrl + threadIdx.x] = s;
@@ -1512,12 +1524,12 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
 // co-states of different trajectories never meet, so the CTAs need no synchronisation): the state
 // stays in shared memory from one interval to the next, and each interval's result is stored to its
 // co-state slot.
-template <typename R, int EPT, int NL, int ACS>
+template <typename R, int EPT, int NL, int ACS, bool SWEEP>
 __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) bwd_kernel(KtGeom g, KtGenImage im, KtOps ops, BwdArgs a) {
   typedef typename C2<R>::T C;
   extern __shared__ __align__(16) char smem_raw[];
   Smem sm;
-  const bool sweep = a.sweep != 0;
+  constexpr bool sweep = SWEEP;   // a.sweep, compiled in
   const bool persist = !sweep && g.bwd_grid > 0;
   carve(g, sizeof(C), smem_raw, &sm, persist);
   const int tau = threadIdx.x % g.T;

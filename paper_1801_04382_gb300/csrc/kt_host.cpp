@@ -305,6 +305,9 @@ struct kt_problem {
   int *cursor = nullptr;
   double *partials = nullptr;
   unsigned *counter = nullptr;
+  // whole-sweep launches (kt_config.per_interval_launches): sync = the grid barrier's two words
+  int whole_sweep = 0;
+  unsigned *sync = nullptr;
   KtCplx *tau = nullptr;
   double *norm2 = nullptr;
   int *status = nullptr;
@@ -448,6 +451,7 @@ kt_status read_status(kt_problem *p, cudaStream_t st) {
   KT_CUDA(cudaMemsetAsync(p->status, 0, sizeof(int), st));
   // a CTA that left early (a wait that ran out) took no last-CTA ticket: start the next sweep at zero
   KT_CUDA(cudaMemsetAsync(p->counter, 0, sizeof(unsigned), st));
+  if (p->sync) KT_CUDA(cudaMemsetAsync(p->sync, 0, 2 * sizeof(unsigned), st));
   KT_CUDA(cudaStreamSynchronize(st));
   switch (s) {
     case KT_DEV_NONFINITE: return fail(KT_ERR_NONFINITE, "non-finite norm, overlap or pulse value on the device");
@@ -625,6 +629,26 @@ kt_status enqueue_forward(kt_problem *p, int update, cudaStream_t st, bool save_
   if (p->sharded && !p->nccl_comm)
     return fail(KT_ERR_STATE, "a trajectory shard runs through its group (krotov_group_update) or over NCCL "
                               "(krotov_shard_nccl)");
+  if (p->whole_sweep && !save_psi) {
+    // the whole sweep as one cooperative launch: interval 0 (the update overlap at t_0) when
+    // updating, then 1 .. nt, psi(t_j) in psi[j & 1] as on the per-interval path
+    KT_CUDA(kt_launch_init_pass(p->g, p->U, p->pass, p->rstate, p->jcount[p->cur], st));
+    FwdArgs a = fwd_args(p, update);
+    a.sweep = 1;
+    a.j = (update && !p->cross) ? 0 : 1;
+    a.psi_in = p->psi_init;
+    a.psi_out = nullptr;
+    a.psi_ring[0] = p->psi[0];
+    a.psi_ring[1] = p->psi[1];
+    a.chi_slots = p->chi;
+    a.slot_bytes = p->state_bytes;
+    a.sync = p->sync;
+    KT_CUDA(cudaMemsetAsync(p->sync, 0, 2 * sizeof(unsigned), st));
+    kt_status s = prof_begin(p, KT_PROF_FWD, st);
+    if (s != KT_OK) return s;
+    KT_CUDA(kt_launch_fwd(p->fp64, p->ept, p->g, p->im_fwd, p->ops, a, st));
+    return prof_end(p, st);
+  }
   FwdArgs a;
   kt_status s = fwd_begin(p, update, st, a);
   if (s != KT_OK) return s;
@@ -773,6 +797,20 @@ kt_status enqueue_backward(kt_problem *p, cudaStream_t st) {
   // chi_k(T) = tau_k |tgt>; the cross-trajectory xi_k(T) = |tgt>; a density matrix's P(T) = P_tgt
   KT_CUDA(kt_launch_chi_boundary(p->fp64, p->g, p->ops, (p->cross || p->density) ? nullptr : p->tau, chiT, st));
   KT_CUDA(kt_launch_cursor_seek(p->g, p->rec_step[prev], p->jcount[prev], p->nt, p->cursor, st));
+  if (p->whole_sweep) {
+    // the whole sweep as one launch: chi(t_{j-1}) of interval j into co-state slot j-1
+    BwdArgs b = bwd_args(p);
+    b.j = p->nt;
+    b.sweep = 1;
+    b.chi_in = chiT;
+    b.chi_out = nullptr;
+    b.chi_slots = p->chi;
+    b.slot_bytes = p->state_bytes;
+    kt_status s = prof_begin(p, KT_PROF_BWD, st);
+    if (s != KT_OK) return s;
+    KT_CUDA(kt_launch_bwd(p->fp64, p->ept, p->g, p->im_bwd, p->ops, b, st));
+    return prof_end(p, st);
+  }
   const void *in = chiT;
   for (int j = p->nt; j >= 1; --j) {
     void *out;
@@ -1760,7 +1798,8 @@ kt_status create_problem(const kt_model_desc *md, const kt_config *cfg, const Ho
     if (cudaMemsetAsync(p->jcount[b], 0, Mp * sizeof(int), st) != cudaSuccess) { krotov_free(p); return fail(KT_ERR_CUDA, "memset"); }
   }
   TRY(dev_alloc(p, (void **)&p->cursor, Mp * sizeof(int)));
-  TRY(dev_alloc(p, (void **)&p->partials, (size_t)g.n_tiles * nc * sizeof(double)));
+  // two sets: a whole-sweep launch alternates them by interval parity
+  TRY(dev_alloc(p, (void **)&p->partials, (size_t)2 * g.n_tiles * nc * sizeof(double)));
   if (p->sharded) {
     TRY(dev_alloc(p, (void **)&p->spart, (size_t)p->n_tiles_total * nc * sizeof(double)));
     TRY(dev_alloc(p, (void **)&p->tau_all, (size_t)p->M_total * sizeof(KtCplx)));
@@ -1786,6 +1825,19 @@ kt_status create_problem(const kt_model_desc *md, const kt_config *cfg, const Ho
     p->n_chi_slots = n_ckpt_slots(nt, p->ckpt_dense, p->ckpt);
     TRY(dev_alloc(p, &p->chi, p->state_bytes * p->n_chi_slots));
     if (p->ckpt > 0) TRY(dev_alloc(p, &p->seg, p->state_bytes * (p->ckpt + 1)));
+    // whole-sweep launches: the strided mapping (the small problems' mapping; the sweep kernels are
+    // compiled for it only), every tile resident at once (the forward sweep's grid barrier), every
+    // co-state kept (each interval's co-state has its slot), no exchange with other shards and no
+    // pair sums between intervals
+    int dev = 0, sms = 0, per = 0;
+    if (!cfg->per_interval_launches && p->ept > 0 && p->ckpt == 0 && !p->sharded && !p->cross &&
+        cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        kt_fwd_blocks_per_sm(p->fp64, p->ept, g, &per) == cudaSuccess && (long long)per * sms >= g.n_tiles) {
+      TRY(dev_alloc(p, (void **)&p->sync, 2 * sizeof(unsigned)));
+      p->whole_sweep = 1;
+    }
+    cudaGetLastError();   // an occupancy query that failed leaves per-interval launches
   }
   p->eps_base = p->eps_old;
   if (kt_launch_pass_reset(p->pass, p->n_passes, st) != cudaSuccess ||
@@ -2196,6 +2248,7 @@ KT_API kt_status krotov_get_info(kt_problem *p, kt_info *info) {
   info->ckpt_kept_prefix = p->ckpt == 0 ? p->nt : p->ckpt_dense;
   info->costate_slots = p->n_chi_slots;
   info->items_per_thread = p->ept > 0 ? p->ept : 0;
+  info->whole_sweep = p->whole_sweep;
   return KT_OK;
 }
 
@@ -2287,6 +2340,9 @@ KT_API kt_status krotov_init_batch(const kt_model_desc *const *models, const kt_
       krotov_batch_free(b);
       return batch_fail(s, (size_t)i);
     }
+    // the problems of a batch run side by side in one graph: per-interval launches, so that no
+    // cooperative launch has to wait for the SMs the other problems hold
+    p->whole_sweep = 0;
     b->probs.push_back(p);
   }
   *out = b;

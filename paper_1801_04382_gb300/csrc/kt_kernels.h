@@ -94,12 +94,15 @@ kt_status kt_fail(kt_status s, const char *msg);
 size_t kt_smem_bytes(const KtGeom &g, int elem_bytes, bool with_chi_buffer, bool with_next_buffer = false);
 cudaError_t kt_launch_fwd(int fp64, int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops,
                           const FwdArgs &a, cudaStream_t st);
+// Resident forward-kernel CTAs per SM for the launch shape of g (a whole-sweep launch needs every tile
+// resident at once).
+cudaError_t kt_fwd_blocks_per_sm(int fp64, int ept, const KtGeom &g, int *blocks);
 cudaError_t kt_launch_bwd(int fp64, int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops,
                           const BwdArgs &a, cudaStream_t st);
 cudaError_t kt_launch_fwd_f32(int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops, const FwdArgs &a,
-                              size_t smem, cudaStream_t st);
+                              size_t smem, cudaStream_t st, int *occ = nullptr);
 cudaError_t kt_launch_fwd_f64(int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops, const FwdArgs &a,
-                              size_t smem, cudaStream_t st);
+                              size_t smem, cudaStream_t st, int *occ = nullptr);
 cudaError_t kt_launch_bwd_f32(int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops, const BwdArgs &a,
                               size_t smem, cudaStream_t st);
 cudaError_t kt_launch_bwd_f64(int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops, const BwdArgs &a,

@@ -116,8 +116,17 @@ size_t kt_smem_bytes(const KtGeom &g, int elem_bytes, bool with_chi_buffer, bool
 
 cudaError_t kt_launch_fwd(int fp64, int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops,
                           const FwdArgs &a, cudaStream_t st) {
-  const size_t smem = kt_smem_bytes(g, fp64 ? 16 : 8, g.prefetch_chi != 0, g.fwd_grid > 0);
+  const size_t smem = kt_smem_bytes(g, fp64 ? 16 : 8, g.prefetch_chi != 0, g.fwd_grid > 0 && !a.sweep);
   return fp64 ? kt_launch_fwd_f64(ept, g, im, ops, a, smem, st) : kt_launch_fwd_f32(ept, g, im, ops, a, smem, st);
+}
+
+cudaError_t kt_fwd_blocks_per_sm(int fp64, int ept, const KtGeom &g, int *blocks) {
+  const size_t smem = kt_smem_bytes(g, fp64 ? 16 : 8, g.prefetch_chi != 0, false);
+  KtGenImage im{};
+  KtOps ops{};
+  FwdArgs a{};
+  return fp64 ? kt_launch_fwd_f64(ept, g, im, ops, a, smem, nullptr, blocks)
+              : kt_launch_fwd_f32(ept, g, im, ops, a, smem, nullptr, blocks);
 }
 
 cudaError_t kt_launch_bwd(int fp64, int ept, const KtGeom &g, const KtGenImage &im, const KtOps &ops,

@@ -51,6 +51,8 @@ class Problem:
     ``tile_traj``: 0 automatic, -1 autotuned at init, else trajectories per CTA tile.
     ``items_per_thread``: 0 automatic thread mapping, else the strided mapping with 1, 2, 4, 8 or 16
     items per thread.
+    ``per_interval_launches``: False lets small problems run each sweep as one launch (info.whole_sweep);
+    True keeps one launch per interval.
     ``update_rule``: "independent" (Eq. independent_traj_update) or "cross" (Eq. cross_traj_update).
     ``jump_scheme``: "bisection" (exact jump times) or "first_order" (at most one jump per interval).
     """
@@ -60,7 +62,7 @@ class Problem:
                  cheb_tol: float = 0.0, tile_traj: int = 0, psi0_batch=None, stream=None,
                  update_rule: str = "independent", jump_scheme: str = "bisection", ckpt_prefix: int = 0,
                  traj_offset: int = 0, M_total: int = 0, inject_copy_timeout: bool = False,
-                 items_per_thread: int = 0):
+                 items_per_thread: int = 0, per_interval_launches: bool = False):
         self._lib = _capi.load()
         self.net = net
         self.T, self.nt, self.M = float(T), int(nt), int(M)
@@ -71,7 +73,7 @@ class Problem:
         keep, md, cfg = _descriptors(net, self.T, self.nt, self.M, eps_guess, shape, lam, uniforms, precision,
                                      ckpt_interval, eps_bound, cheb_tol, tile_traj, psi0_batch, update_rule,
                                      jump_scheme, ckpt_prefix, traj_offset, M_total, inject_copy_timeout,
-                                     items_per_thread)
+                                     items_per_thread, per_interval_launches)
         handle = ct.c_void_p()
         self._h = None
         _capi.check(self._lib.krotov_init(ct.byref(md), ct.byref(cfg), _stream_handle(stream), ct.byref(handle)),
@@ -281,7 +283,7 @@ class Batch:
     (net, T, nt, M, eps_guess, shape, lam, uniforms and the optional keywords)."""
 
     _KEYS = ("precision", "ckpt_interval", "eps_bound", "cheb_tol", "tile_traj", "psi0_batch", "update_rule",
-             "jump_scheme", "ckpt_prefix", "items_per_thread")
+             "jump_scheme", "ckpt_prefix", "items_per_thread", "per_interval_launches")
 
     def __init__(self, specs, stream=None):
         self._lib = _capi.load()
@@ -359,7 +361,7 @@ class DensityProblem(Problem):
 
     def __init__(self, net: NetworkFactors, T: float, nt: int, eps_guess, shape, lam, precision: str = "fp64",
                  ckpt_interval: int = 0, eps_bound: float = 0.0, cheb_tol: float = 0.0, stream=None,
-                 ckpt_prefix: int = 0):
+                 ckpt_prefix: int = 0, per_interval_launches: bool = False):
         self._lib = _capi.load()
         self.net = net
         self.T, self.nt, self.M = float(T), int(nt), 1
@@ -367,7 +369,7 @@ class DensityProblem(Problem):
         dummy = np.full((1, 1, 1), -1.0)
         keep, md, cfg = _descriptors(net, self.T, self.nt, 1, eps_guess, shape, lam, dummy, precision,
                                      ckpt_interval, eps_bound, cheb_tol, 0, None, "independent", "bisection",
-                                     ckpt_prefix)
+                                     ckpt_prefix, per_interval_launches=per_interval_launches)
         handle = ct.c_void_p()
         self._h = None
         _capi.check(self._lib.krotov_init_density(ct.byref(md), ct.byref(cfg), _stream_handle(stream),
@@ -492,7 +494,7 @@ _JUMP_SCHEMES = {"bisection": 0, "first_order": 1}
 def _descriptors(net, T, nt, M, eps_guess, shape, lam, uniforms, precision="fp64", ckpt_interval=0,
                  eps_bound=0.0, cheb_tol=0.0, tile_traj=0, psi0_batch=None, update_rule="independent",
                  jump_scheme="bisection", ckpt_prefix=0, traj_offset=0, M_total=0, inject_copy_timeout=False,
-                 items_per_thread=0):
+                 items_per_thread=0, per_interval_launches=False):
     """kt_model_desc / kt_config for ``net`` (the returned ``keep`` dict owns the host arrays)."""
     uniforms = _c(uniforms)
     keep = {
@@ -518,7 +520,8 @@ def _descriptors(net, T, nt, M, eps_guess, shape, lam, uniforms, precision="fp64
         draws_per_traj=uniforms.shape[2], eps_bound=float(eps_bound), cheb_tol=float(cheb_tol),
         tile_traj=int(tile_traj), update_rule=_UPDATE_RULES[update_rule], jump_scheme=_JUMP_SCHEMES[jump_scheme],
         ckpt_prefix=int(ckpt_prefix), traj_offset=int(traj_offset), M_total=int(M_total),
-        inject_copy_timeout=int(bool(inject_copy_timeout)), items_per_thread=int(items_per_thread))
+        inject_copy_timeout=int(bool(inject_copy_timeout)), items_per_thread=int(items_per_thread),
+        per_interval_launches=int(bool(per_interval_launches)))
     return keep, md, cfg
 
 
