@@ -63,8 +63,9 @@ METRIC = "Krotov iters/s and traj·steps/s, FP32-mixed vs FP64 path, % of HBM ro
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of each interval kernel at
 # this workload's launch size (1024 trajectories, d = 6561, FP32-mixed), from one ncu capture of the
-# current kernels; None where no capture of the current kernel exists.
-NCU_TRAFFIC_PER_LAUNCH = {"bwd": None, "fwd": None}
+# current kernels (`bench.py --workload profile`, full section set: an updating forward launch and a
+# backward launch); None where no capture of the current kernel exists.
+NCU_TRAFFIC_PER_LAUNCH = {"bwd": 53887232 + 6750720, "fwd": 108225280 + 23902976}
 FP32_LANES = 128              # FP32 FMA lanes per SM (Blackwell)
 
 

@@ -1407,10 +1407,11 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P, bool 
       cfg->items_per_thread != 4 && cfg->items_per_thread != 8 && cfg->items_per_thread != 16)
     return fail(KT_ERR_ARG, "items_per_thread must be 0 (automatic), 1, 2, 4, 8 or 16");
   // automatic mapping: one thread per last-node fiber, unless a trajectory has fewer than 16 fibers
-  // (d <= 81) and the tile width is automatic too: then a CTA would hold a few warps at most, and the
-  // strided mapping with one item per thread runs n_loc times as many threads per trajectory
-  // (measured faster at d = 36 and 81, about 5x in FP64, where the fiber kernels' register arrays spill)
-  const bool small = (nl == 6 || nl == 9) && d / nl < 16 && cfg->tile_traj <= 0;
+  // (d <= 81) and the tile width is automatic too (or fixed at 1 by a density matrix's single state):
+  // then a CTA would hold a few warps at most, and the strided mapping with one item per thread runs
+  // n_loc times as many threads per trajectory (measured faster at d = 36 and 81, about 5x in FP64,
+  // where the fiber kernels' register arrays spill)
+  const bool small = (nl == 6 || nl == 9) && d / nl < 16 && (cfg->tile_traj <= 0 || density);
   const int ipt = cfg->items_per_thread > 0 ? cfg->items_per_thread : (small ? 1 : 0);
   const bool fiber = (nl == 6 || nl == 9) && ipt == 0;
   const bool acs = fiber && cavity_structure(gf, gb, lo_dl, lo_val, ra_dl, ra_val);
