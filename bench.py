@@ -760,24 +760,35 @@ def run_ours(args, rank, world):
 
 
 def run_profile(args):
-    """Small case of the four-node interval kernels for ncu captures that must stay small: d = 6561,
-    dt = 0.01, M trajectories (--profile-M, default 1024 = the benchmark's launch size), 12 intervals:
-    guess sweep, backward sweep, updating forward sweep, with the library's per-launch event timing
-    printed at the end.  A few GB on the device."""
+    """Small case of the interval kernels for ncu captures that must stay small.  --profile-d 6561
+    (default): the four-node chain, dt = 0.01, M trajectories (--profile-M, default 1024 = the
+    benchmark's launch size), 12 intervals.  --profile-d 81: the two-node d = 81 workload (128
+    trajectories, nt = 1000, dt = 0.05, FP32-mixed), whose sweeps run as one launch each.  Guess
+    sweep, backward sweep, updating forward sweep, with the library's per-launch event timing printed
+    at the end.  A few GB on the device at most."""
     import torch
     if not torch.cuda.is_available():
         raise RuntimeError("bench.py needs a CUDA GPU (GB300); the CUDA path has no CPU fallback")
     from paper_1801_04382_gb300 import Problem, cascaded_chain
-    nt, T, M = 12, 0.12, args.profile_M
-    net = cascaded_chain(4, 2)
-    eps0 = si.guess_pulses(4, nt, T, 1.0)
-    S = si.shape_functions(4, nt, T)
-    lam = np.full(4, 10.0)
-    U = si.uniforms(4, 4, M, 25)
+    if args.profile_d == 81:
+        wl = si.CONFIGS["cfg2_d81"]
+        nt, T, M = wl.nt, wl.T, wl.M
+        net = cascaded_chain(wl.n_nodes, wl.n_cav, wl.delta, wl.g, wl.kappa)
+        eps0 = si.guess_pulses(net.n_ctrl, nt, T, wl.guess_amp)
+        S = si.shape_functions(net.n_ctrl, nt, T)
+        lam = np.full(net.n_ctrl, wl.lam)
+        U = si.uniforms(wl.seed, 4, M, wl.draws_per_traj)
+    else:
+        nt, T, M = 12, 0.12, args.profile_M
+        net = cascaded_chain(4, 2)
+        eps0 = si.guess_pulses(4, nt, T, 1.0)
+        S = si.shape_functions(4, nt, T)
+        lam = np.full(4, 10.0)
+        U = si.uniforms(4, 4, M, 25)
     with Problem(net, T, nt, M, eps0, S, lam, U, precision=args.precision) as p:
         info = p.info
         print(f"d={info.d} tile_traj={info.tile_traj} threads={info.threads} cheb_terms={info.cheb_terms} "
-              f"tiles={info.n_tiles}")
+              f"tiles={info.n_tiles} whole_sweep={info.whole_sweep}")
         p.forward(False)
         p.set_profiling(True)
         p.backward()
@@ -803,6 +814,7 @@ def main():
                     help="co-state storage of the cfg5 problem: -1 automatic from free memory (default), "
                          "0 all, K > 0 every K-th")
     ap.add_argument("--profile-M", type=int, default=1024)
+    ap.add_argument("--profile-d", type=int, choices=[6561, 81], default=6561)
     ap.add_argument("--shard", action="store_true",
                     help="split one problem's trajectories over the ranks (NCCL exchange of the update's "
                          "partials every interval; strong scaling) instead of one problem per rank")

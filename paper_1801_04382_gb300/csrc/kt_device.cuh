@@ -295,8 +295,10 @@ __device__ __forceinline__ void reduce_tau(double (&v)[NV], const KtGeom &g, dou
 // Per-interval tables: generator factors for pulse eps (scaled by 1/r, diagonal shifted),
 // plus control factors for the update overlap.
 template <typename R>
+// pulse_only: the tables of a later interval of a whole sweep -- only the entries that depend on the
+// pulse (node factors, diagonal, the last node's dense factor) are rebuilt, the rest is unchanged.
 __device__ void build_tables(const KtGeom &g, const KtGenImage &im, const KtOps &ops, const Smem &sm,
-                             const double *eps, bool with_hc) {
+                             const double *eps, bool with_hc, bool pulse_only = false) {
   typedef typename C2<R>::T C;
   C *lv = (C *)sm.loc_val;
   C *dg = (C *)sm.diag;
@@ -311,7 +313,7 @@ __device__ void build_tables(const KtGeom &g, const KtGenImage &im, const KtOps 
         imv += eps[g.cterm_ctrl[t]] * im.ctrl_slot[t * nls + rem].im;
       }
     lv[e] = mkc((R)re, (R)imv);
-    sm.loc_off[e] = im.loc_dl[e] * g.stride[i] * g.T;
+    if (!pulse_only) sm.loc_off[e] = im.loc_dl[e] * g.stride[i] * g.T;
   }
   for (int e = threadIdx.x; e < g.n_nodes * g.n_loc; e += blockDim.x) {
     const int i = e / g.n_loc, x = e % g.n_loc;
@@ -324,10 +326,11 @@ __device__ void build_tables(const KtGeom &g, const KtGenImage &im, const KtOps 
     dg[e] = mkc((R)re, (R)imv);
   }
   const int nl2 = g.n_loc * g.n_loc;
-  for (int e = threadIdx.x; e < g.n_pairs * nl2; e += blockDim.x) {
-    sm.pair_off[e] = im.pair_off[e] * g.T;
-    pv[e] = from_kc<C>(im.pair_val[e]);
-  }
+  if (!pulse_only)
+    for (int e = threadIdx.x; e < g.n_pairs * nl2; e += blockDim.x) {
+      sm.pair_off[e] = im.pair_off[e] * g.T;
+      pv[e] = from_kc<C>(im.pair_val[e]);
+    }
   {
     // last node's factor as a dense n_loc x n_loc table, ladder values, pair coefficients
     C *ld = (C *)sm.ldense;
@@ -335,18 +338,20 @@ __device__ void build_tables(const KtGeom &g, const KtGenImage &im, const KtOps 
     C *pc = (C *)sm.pcoef;
     const int last = g.n_nodes - 1;
     for (int e = threadIdx.x; e < g.n_loc * g.n_loc; e += blockDim.x) ld[e] = mkc((R)0, (R)0);
-    for (int e = threadIdx.x; e < g.n_loc; e += blockDim.x) {
-      lr[e] = from_kc<C>(ops.lo_val[e]);
-      lr[g.n_loc + e] = from_kc<C>(ops.ra_val[e]);
+    if (!pulse_only) {
+      for (int e = threadIdx.x; e < g.n_loc; e += blockDim.x) {
+        lr[e] = from_kc<C>(ops.lo_val[e]);
+        lr[g.n_loc + e] = from_kc<C>(ops.ra_val[e]);
+      }
+      for (int e = threadIdx.x; e < g.n_pairs; e += blockDim.x) pc[e] = from_kc<C>(im.pair_coef[e]);
     }
-    for (int e = threadIdx.x; e < g.n_pairs; e += blockDim.x) pc[e] = from_kc<C>(im.pair_coef[e]);
     __syncthreads();
     for (int e = threadIdx.x; e < g.n_loc * g.S; e += blockDim.x) {
       const int idx = last * nls + e, x = e / g.S, dl = im.loc_dl[idx];
       if (dl) ld[x * g.n_loc + x + dl] = lv[idx];
     }
   }
-  if (with_hc) {
+  if (with_hc && !pulse_only) {
     C *hv = (C *)sm.hc_val;
     const int nh = g.n_loc * g.SH;
     for (int e = threadIdx.x; e < g.n_cterms * nh; e += blockDim.x) {
@@ -1054,7 +1059,7 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
     __syncthreads();
     if (threadIdx.x == 0 && need_chi && g.prefetch_chi)
       bulk_load(sm.bufC, chi_of(j, blockIdx.x), tile_bytes, &sm.mbar[1]);
-    build_tables<R>(g, im, ops, sm, sm.eps, a.overlap != 0);
+    build_tables<R>(g, im, ops, sm, sm.eps, a.overlap != 0, true);
   }
   int tile = blockIdx.x;
   for (int use = 0; tile < g.n_tiles; tile += gridDim.x, ++use) {
@@ -1568,7 +1573,7 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
       // interval's tables ended at the barrier after its store)
       if (threadIdx.x < g.n_ctrl) sm.eps[threadIdx.x] = a.eps[threadIdx.x * a.nt + (j - 1)];
       __syncthreads();
-      build_tables<R>(g, im, ops, sm, sm.eps, false);
+      build_tables<R>(g, im, ops, sm, sm.eps, false, true);
     }
     C *chi_out = sweep ? (C *)((char *)a.chi_slots + (size_t)(j - 1) * a.slot_bytes) + (size_t)tile * g.tile_elems
                        : (C *)a.chi_out + (size_t)tile * g.tile_elems;
@@ -1632,7 +1637,8 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
       for (int q = 0; q < EPT; ++q)
         if (it.ok(q)) A[it.item(q)] = B[it.item(q)];
       __syncthreads();
-      cheb_dispatch<R, EPT, NL, ACS, false>(g, im, sm, it, g.K, acc);   // rows from the tables: measured faster here
+      // FP32: the other nodes' rows in registers (measured 2 % faster); FP64 has no registers to spare
+      cheb_dispatch<R, EPT, NL, ACS, sizeof(R) == 4>(g, im, sm, it, g.K, acc);
       if (rnd == rounds) break;
 #pragma unroll
       for (int q = 0; q < EPT; ++q)
