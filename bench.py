@@ -189,6 +189,15 @@ def cpu_baseline(wl, budget_s: float = 20.0):
     eps = si.guess_pulses(wl.n_nodes, nt_s, T_s, wl.guess_amp)
     S = si.shape_functions(wl.n_nodes, nt_s, T_s)
     lam = np.full(wl.n_nodes, wl.lam)
+    # one thread: the oracle's sparse products run on one core anyway, and a BLAS pool would only
+    # blur what "cores" means (threadpoolctl is absent on some hosts: then the pool is left as is)
+    try:
+        from threadpoolctl import threadpool_limits
+        limiter = threadpool_limits(limits=1)
+        cores = 1
+    except Exception:
+        limiter = None
+        cores = os.cpu_count() or 1
     t0 = time.perf_counter()
     reps = 0
     while True:
@@ -197,16 +206,13 @@ def cpu_baseline(wl, budget_s: float = 20.0):
         if time.perf_counter() - t0 > budget_s / 2 or reps >= 50:
             break
     el = time.perf_counter() - t0
+    if limiter is not None:
+        limiter.unregister()
     # per rep: guess forward + backward + updating forward = 3 sweeps of M_s * nt_s traj.steps;
     # the iteration itself is 2 of them
     traj_steps = reps * 3 * M_s * nt_s
     tsps = traj_steps / el
     iters = tsps / (2.0 * wl.M * wl.nt)
-    try:
-        from threadpoolctl import threadpool_info
-        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
-    except Exception:
-        cores = os.cpu_count() or 1
     return {"value": iters, "unit": "Krotov iters/s", "cores": cores, "kind": "oracle",
             "traj_steps_per_s": tsps,
             "sample": f"{reps} x (guess+backward+updating sweep) of {M_s} trajectory x {nt_s} intervals "
