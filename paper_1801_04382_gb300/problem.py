@@ -525,11 +525,14 @@ def _descriptors(net, T, nt, M, eps_guess, shape, lam, uniforms, precision="fp64
     return keep, md, cfg
 
 
-def generator_dense(net, T, nt, M, eps_guess, shape, lam, uniforms, eps, direction=0, precision="fp64"):
+def generator_dense(net, T, nt, M, eps_guess, shape, lam, uniforms, eps, direction=0, precision="fp64",
+                    items_per_thread=0):
     """Dense generator expanded from the library's structured tables (host only): direction 0 gives
     H_eff(eps), direction 1 gives -H_eff(eps)^dag (d x d); directions 2 and 3 the same for the
-    Liouville-space generator of a density-matrix problem (d^2 x d^2)."""
-    keep, md, cfg = _descriptors(net, T, nt, M, eps_guess, shape, lam, uniforms, precision)
+    Liouville-space generator of a density-matrix problem (d^2 x d^2).  ``items_per_thread`` selects
+    the thread mapping whose tables are expanded (the cavity-structure mapping re-slots its rows)."""
+    keep, md, cfg = _descriptors(net, T, nt, M, eps_guess, shape, lam, uniforms, precision,
+                                 items_per_thread=items_per_thread)
     d = net.d if direction < 2 else net.d ** 2
     out = np.zeros((d, d, 2))
     e = _c(eps)

@@ -181,3 +181,38 @@ def test_liouville_generator_tables_match_oracle_liouvillian(lib, N, nc, lind):
         G3 = generator_dense(*args, eps=eps, direction=3)
         assert np.abs(G2 - G).max() <= 1e-12 * scale
         assert np.abs(G3 + G.conj().T).max() <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("N,nc,ipts", [(2, 2, (0, 1, 4)), (3, 2, (0, 2, 4))])
+def test_generator_tables_of_every_thread_mapping_match_dense_heff(lib, N, nc, ipts):
+    """The tables of the automatic mapping (d = 81: the strided one-item mapping; d = 729: the
+    cavity-structure fiber mapping with its real / imaginary slot order and kernel-parameter
+    constants) and of the strided mapping at 1, 2 or 4 items per thread (an FP64 tile holds at most
+    512 threads) all expand to the oracle's H_eff and -H_eff^dag."""
+    from oracle import model as om
+    from paper_1801_04382_gb300.problem import generator_dense
+    net = pm.cascaded_chain(N, nc)
+    m = om.build_model(N, nc)
+    nt, T, M = 8, 1.0, 3
+    args = (net, T, nt, M, si.guess_pulses(N, nt, T, 2.0), si.shape_functions(N, nt, T), np.full(N, 10.0),
+            si.uniforms(0, 1, M, 5))
+    eps = np.random.default_rng(N).uniform(-2.0, 2.0, size=N)
+    Heff = m.Heff(eps)
+    Heff = Heff.toarray() if hasattr(Heff, "toarray") else Heff
+    scale = np.abs(Heff).max()
+    for ipt in ipts:
+        G0 = generator_dense(*args, eps=eps, direction=0, items_per_thread=ipt)
+        G1 = generator_dense(*args, eps=eps, direction=1, items_per_thread=ipt)
+        assert np.abs(G0 - Heff).max() <= 1e-12 * scale, ipt
+        assert np.abs(G1 + Heff.conj().T).max() <= 1e-12 * scale, ipt
+
+
+def test_items_per_thread_must_be_a_power_of_two_up_to_16(lib):
+    from paper_1801_04382_gb300.problem import generator_dense
+    net = pm.cascaded_chain(2, 1)
+    nt, T, M = 8, 1.0, 3
+    args = (net, T, nt, M, si.guess_pulses(2, nt, T, 2.0), si.shape_functions(2, nt, T), np.full(2, 10.0),
+            si.uniforms(0, 1, M, 5))
+    for bad in (3, 32, -2):
+        with pytest.raises(Exception, match="items_per_thread"):
+            generator_dense(*args, eps=np.zeros(2), direction=0, items_per_thread=bad)
