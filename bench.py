@@ -65,7 +65,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # this workload's launch size (1024 trajectories, d = 6561, FP32-mixed), from one ncu capture of the
 # current kernels (`bench.py --workload profile`, full section set: an updating forward launch and a
 # backward launch); None where no capture of the current kernel exists.
-NCU_TRAFFIC_PER_LAUNCH = {"bwd": 53887232 + 6750720, "fwd": 108225280 + 23902976}
+NCU_TRAFFIC_PER_LAUNCH = {"bwd": None, "fwd": 108225280 + 23902976}
 FP32_LANES = 128              # FP32 FMA lanes per SM (Blackwell)
 
 
