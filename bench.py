@@ -579,6 +579,37 @@ def run_density(args, rank, world):
     return 0
 
 
+def oracle_small_configs():
+    """The FP64 oracle, as it stands, on the two smallest workloads at full size (one thread: with a
+    BLAS pool on every core the oracle's small dense products run ~30x slower): one Krotov iteration
+    (guess sweep, backward sweep, updating sweep) each, as iterations/s and traj.steps/s."""
+    from oracle import mcwf
+    from oracle import model as om
+    out = {}
+    try:
+        from threadpoolctl import threadpool_limits
+        limiter = threadpool_limits(limits=1)
+    except Exception:
+        limiter = None
+    for name in ("cfg1_d36", "cfg2_d81"):
+        wl = si.CONFIGS[name]
+        m = om.build_model(wl.n_nodes, wl.n_cav, wl.delta, wl.g, wl.kappa)
+        eps = si.guess_pulses(wl.n_nodes, wl.nt, wl.T, wl.guess_amp)
+        S = si.shape_functions(wl.n_nodes, wl.nt, wl.T)
+        lam = np.full(wl.n_nodes, wl.lam)
+        U = si.uniforms(wl.seed, 2, wl.M, wl.draws_per_traj)
+        t0 = time.perf_counter()
+        mcwf.optimize(m, eps, wl.T, U, S, lam, 1, psi0=m.psi0)
+        el = time.perf_counter() - t0
+        # the iteration proper is two of the three sweeps timed
+        out[name] = {"krotov_iters_per_s": 1.0 / (el * 2.0 / 3.0), "traj_steps_per_s": 3 * wl.M * wl.nt / el,
+                     "seconds": el, "cores": 1 if limiter is not None else (os.cpu_count() or 1),
+                     "sample": f"full size: d={wl.d}, M={wl.M}, nt={wl.nt}, guess + backward + updating sweep"}
+    if limiter is not None:
+        limiter.unregister()
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -756,6 +787,7 @@ def run_ours(args, rank, world):
         line["fp32_vs_fp64"] = precision_comparison(stream)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
+        line["oracle_full_small_configs"] = oracle_small_configs()
     prob.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
