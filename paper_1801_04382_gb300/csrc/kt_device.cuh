@@ -1046,10 +1046,19 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
   load_items<EPT, NL>(g, ops, it);
   bool store_pending = false;
   unsigned nchi = 0;        // chi loads waited for on barrier [1] (the n-th completes phase n & 1)
+  bool coef_full = false;   // the full-step coefficients are in place (no jump phase overwrote them)
   unsigned sync_gen = 0;    // grid barriers passed (sweep)
   C acc[EPT];
   for (;; ++j) {            // intervals: one unless sweep
   const bool need_chi = a.overlap && j < a.nt;
+  // sweep: the update's pulse-independent factors for the finisher, read now, off its critical path
+  // (the per-interval kernels read them in the finisher: registers held across the tiles spill there)
+  double fin_scale = 0.0, fin_eold = 0.0;
+  if (sweep && need_chi && threadIdx.x < g.n_ctrl) {
+    const size_t idx = (size_t)threadIdx.x * a.nt + j;   // interval j+1 (0-based index j)
+    fin_scale = a.shape[idx] / (g.lam[threadIdx.x] * g.M_norm);
+    fin_eold = a.eps_old[idx];
+  }
   if (j != a.j) {
     // sweep: the next interval.  Its pulse is in sm.eps (guess sweep: eps_old; updating: the value
     // the barrier's finisher formed), its chi goes to the third buffer once every thread is done
@@ -1124,15 +1133,22 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
       if (sm.flag[1] == 0) phase = PH_SSTAR;
     }
     if (phase == PH_MAIN) {
-      uniform_coefs<R>(g, sm, im.cheb_full);
-    } else if (threadIdx.x < g.T) {
-      const int t = threadIdx.x;
-      const bool act = sm.tin[TI_ACT * g.T + t] != 0;
-      double len = 0.0;
-      if (phase == PH_BISECT) len = sm.tin[TI_BUSY * g.T + t] ? 0.5 * (sm.tsc[TS_LO * g.T + t] + sm.tsc[TS_HI * g.T + t]) : 0.0;
-      else if (phase == PH_SSTAR) len = act ? sm.tsc[TS_HI * g.T + t] : 0.0;
-      else len = act ? g.dt - sm.tsc[TS_S0 * g.T + t] : 0.0;
-      tau_coefs<R>(g, sm, t, g.c_fwd, len);
+      // the full-step coefficients are the same for every interval: a sweep loads them once, again
+      // only after a jump phase has overwritten them (the per-interval kernels reload them per tile:
+      // skipping there costs them registers)
+      if (!(sweep && coef_full)) uniform_coefs<R>(g, sm, im.cheb_full);
+      coef_full = true;
+    } else {
+      coef_full = false;
+      if (threadIdx.x < g.T) {
+        const int t = threadIdx.x;
+        const bool act = sm.tin[TI_ACT * g.T + t] != 0;
+        double len = 0.0;
+        if (phase == PH_BISECT) len = sm.tin[TI_BUSY * g.T + t] ? 0.5 * (sm.tsc[TS_LO * g.T + t] + sm.tsc[TS_HI * g.T + t]) : 0.0;
+        else if (phase == PH_SSTAR) len = act ? sm.tsc[TS_HI * g.T + t] : 0.0;
+        else len = act ? g.dt - sm.tsc[TS_S0 * g.T + t] : 0.0;
+        tau_coefs<R>(g, sm, t, g.c_fwd, len);
+      }
     }
     if (phase != PH_MAIN) load_tile<R, EPT>(g, it, psi_out, A);   // the main round's tile came by bulk copy
     __syncthreads();
@@ -1473,8 +1489,8 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
       double s = 0.0;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sm.red[w * 8 + c];
       const size_t idx = (size_t)c * a.nt + j;   // interval j+1 (0-based index j)
-      const double de = a.shape[idx] / (g.lam[c] * g.M_norm) * s;
-      const double en = a.eps_old[idx] + de;
+      const double de = (sweep ? fin_scale : a.shape[idx] / (g.lam[c] * g.M_norm)) * s;
+      const double en = (sweep ? fin_eold : a.eps_old[idx]) + de;
       if (write_out) {
         a.deps[idx] = de;
         a.eps_new[idx] = en;
