@@ -52,6 +52,12 @@ import sys
 import tempfile
 import time
 
+# The oracle timings run on one host thread: its sparse products use one core anyway, and a BLAS
+# pool on every core makes its small dense products ~30x slower.  Set before numpy loads (the GPU
+# path does no host linear algebra); a caller's own setting is kept.
+for _var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+    os.environ.setdefault(_var, "1")
+
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -189,15 +195,7 @@ def cpu_baseline(wl, budget_s: float = 20.0):
     eps = si.guess_pulses(wl.n_nodes, nt_s, T_s, wl.guess_amp)
     S = si.shape_functions(wl.n_nodes, nt_s, T_s)
     lam = np.full(wl.n_nodes, wl.lam)
-    # one thread: the oracle's sparse products run on one core anyway, and a BLAS pool would only
-    # blur what "cores" means (threadpoolctl is absent on some hosts: then the pool is left as is)
-    try:
-        from threadpoolctl import threadpool_limits
-        limiter = threadpool_limits(limits=1)
-        cores = 1
-    except Exception:
-        limiter = None
-        cores = os.cpu_count() or 1
+    cores = oracle_threads()
     t0 = time.perf_counter()
     reps = 0
     while True:
@@ -206,8 +204,6 @@ def cpu_baseline(wl, budget_s: float = 20.0):
         if time.perf_counter() - t0 > budget_s / 2 or reps >= 50:
             break
     el = time.perf_counter() - t0
-    if limiter is not None:
-        limiter.unregister()
     # per rep: guess forward + backward + updating forward = 3 sweeps of M_s * nt_s traj.steps;
     # the iteration itself is 2 of them
     traj_steps = reps * 3 * M_s * nt_s
@@ -579,18 +575,24 @@ def run_density(args, rank, world):
     return 0
 
 
+def oracle_threads() -> int:
+    """Threads the oracle's linear algebra runs on: the BLAS pools' sizes where threadpoolctl can
+    read them, else the thread-count setting made before numpy loaded."""
+    try:
+        from threadpoolctl import threadpool_info
+        return max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        return int(os.environ.get("OPENBLAS_NUM_THREADS") or os.environ.get("OMP_NUM_THREADS") or os.cpu_count() or 1)
+
+
 def oracle_small_configs():
-    """The FP64 oracle, as it stands, on the two smallest workloads at full size (one thread: with a
-    BLAS pool on every core the oracle's small dense products run ~30x slower): one Krotov iteration
-    (guess sweep, backward sweep, updating sweep) each, as iterations/s and traj.steps/s."""
+    """The FP64 oracle, as it stands, on the two smallest workloads at full size (one thread, see
+    the top of this file): one Krotov iteration (guess sweep, backward sweep, updating sweep) each,
+    as iterations/s and traj.steps/s."""
     from oracle import mcwf
     from oracle import model as om
     out = {}
-    try:
-        from threadpoolctl import threadpool_limits
-        limiter = threadpool_limits(limits=1)
-    except Exception:
-        limiter = None
+    cores = oracle_threads()
     for name in ("cfg1_d36", "cfg2_d81"):
         wl = si.CONFIGS[name]
         m = om.build_model(wl.n_nodes, wl.n_cav, wl.delta, wl.g, wl.kappa)
@@ -603,10 +605,8 @@ def oracle_small_configs():
         el = time.perf_counter() - t0
         # the iteration proper is two of the three sweeps timed
         out[name] = {"krotov_iters_per_s": 1.0 / (el * 2.0 / 3.0), "traj_steps_per_s": 3 * wl.M * wl.nt / el,
-                     "seconds": el, "cores": 1 if limiter is not None else (os.cpu_count() or 1),
+                     "seconds": el, "cores": cores,
                      "sample": f"full size: d={wl.d}, M={wl.M}, nt={wl.nt}, guess + backward + updating sweep"}
-    if limiter is not None:
-        limiter.unregister()
     return out
 
 
