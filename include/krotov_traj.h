@@ -120,7 +120,7 @@ typedef struct {
   int draws_per_traj;       /* odd, >= 1 */
   double eps_bound;         /* bound on |eps| used for the spectral estimate; 0 = automatic
                                (2 max|eps_guess| + 1) */
-  double cheb_tol;          /* Chebyshev truncation; 0 = 1e-16 (FP64) / 1e-8 (FP32-mixed) */
+  double cheb_tol;          /* Chebyshev truncation; 0 = 1e-16 (FP64) / 2^-24 (FP32-mixed) */
   int tile_traj;            /* trajectories per CTA tile (power of two <= 32); 0 = automatic
                                (heuristic); -1 = autotuned: krotov_init times the forward
                                interval kernel for every width that fits (12 launches each on

@@ -1336,8 +1336,9 @@ kt_status plan(const kt_model_desc *md, const kt_config *cfg, HostPlan &P, bool 
   const cd z(1.0, damp / r);
   const double rho = std::max(1.0, std::abs(z + std::sqrt(z - 1.0) * std::sqrt(z + 1.0)));
   // default truncation: 1e-16 in FP64 (the row bound is sharp, so the criterion's margin is the
-  // tolerance itself), 1e-8 in FP32 (below the recurrence's own rounding)
-  const double tol = cfg->cheb_tol > 0 ? cfg->cheb_tol : (cfg->prec == KT_FP64 ? 1e-16 : 1e-8);
+  // tolerance itself), the FP32 unit roundoff 2^-24 in FP32-mixed (the truncation error then stays
+  // an order of magnitude below the rounding the FP32 recurrence accumulates anyway)
+  const double tol = cfg->cheb_tol > 0 ? cfg->cheb_tol : (cfg->prec == KT_FP64 ? 1e-16 : 0x1p-24);
   std::vector<double> J(256);
   kt_bessel_miller(r * dt, 256, J.data());
   int K = -1;
