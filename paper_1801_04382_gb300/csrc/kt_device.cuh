@@ -1050,482 +1050,482 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
   unsigned sync_gen = 0;    // grid barriers passed (sweep)
   C acc[EPT];
   for (;; ++j) {            // intervals: one unless sweep
-  const bool need_chi = a.overlap && j < a.nt;
-  // sweep: the update's pulse-independent factors for the finisher, read now, off its critical path
-  // (the per-interval kernels read them in the finisher: registers held across the tiles spill there)
-  double fin_scale = 0.0, fin_eold = 0.0;
-  if (sweep && need_chi && threadIdx.x < g.n_ctrl) {
-    const size_t idx = (size_t)threadIdx.x * a.nt + j;   // interval j+1 (0-based index j)
-    fin_scale = a.shape[idx] / (g.lam[threadIdx.x] * g.M_norm);
-    fin_eold = a.eps_old[idx];
-  }
-  if (j != a.j) {
-    // sweep: the next interval.  Its pulse is in sm.eps (guess sweep: eps_old; updating: the value
-    // the barrier's finisher formed), its chi goes to the third buffer once every thread is done
-    // with the previous one, and the tables are rebuilt for the new pulse.
-    if (!a.update && threadIdx.x < g.n_ctrl) sm.eps[threadIdx.x] = a.eps_old[threadIdx.x * a.nt + (j - 1)];
-    fence_proxy_async_smem();
-    __syncthreads();
-    if (threadIdx.x == 0 && need_chi && g.prefetch_chi)
-      bulk_load(sm.bufC, chi_of(j, blockIdx.x), tile_bytes, &sm.mbar[1]);
-    build_tables<R>(g, im, ops, sm, sm.eps, a.overlap != 0, true);
-  }
-  int tile = blockIdx.x;
-  for (int use = 0; tile < g.n_tiles; tile += gridDim.x, ++use) {
-  const int next = tile + (int)gridDim.x;
-  const C *psi_in = (const C *)((!sweep || j <= 1) ? a.psi_in : a.psi_ring[(j - 1) & 1]) + (size_t)tile * g.tile_elems;
-  C *psi_out = (C *)(sweep ? a.psi_ring[j & 1] : a.psi_out) + (size_t)tile * g.tile_elems;
-  const C *chi_g = need_chi ? chi_of(j, tile) : nullptr;
-  // the trajectory's current threshold, read now so that its latency is off the path after the series
-  const double r_start = (threadIdx.x < g.T) ? a.rstate[(size_t)tile * g.T + threadIdx.x] : 0.0;
-  if (threadIdx.x == 0) {
-    sm.flag[0] = 0;
-    sm.flag[1] = 0;
-    sm.flag[2] = 0;
-  }
-  C *A = (C *)sm.bufA;
-  C *B = (C *)sm.bufB;
-  if (sweep && j != a.j) {
-    // sweep: psi(t_{j-1}) is the previous interval's result, still in registers
-#pragma unroll
-    for (int q = 0; q < EPT; ++q)
-      if (it.ok(q)) A[it.item(q)] = acc[q];
-    __syncthreads();
-  } else if (!tile_wait((use & 1) ? &sm.mbar[3] : &sm.mbar[0], (use >> 1) & 1, &sm.flag[4], a.status,
-                        g.inject_timeout ? &sm.mbar[2] : nullptr)) {
-    // psi of this tile: load number `use`, barrier [0] / [3] in turn, phase parity (use >> 1) & 1
-    if (threadIdx.x == 0) {
-      if (need_chi && g.prefetch_chi) mbar_wait_bounded(&sm.mbar[1], nchi & 1);
-      if (store_pending) bulk_store_wait();
+    const bool need_chi = a.overlap && j < a.nt;
+    // sweep: the update's pulse-independent factors for the finisher, read now, off its critical path
+    // (the per-interval kernels read them in the finisher: registers held across the tiles spill there)
+    double fin_scale = 0.0, fin_eold = 0.0;
+    if (sweep && need_chi && threadIdx.x < g.n_ctrl) {
+      const size_t idx = (size_t)threadIdx.x * a.nt + j;   // interval j+1 (0-based index j)
+      fin_scale = a.shape[idx] / (g.lam[threadIdx.x] * g.M_norm);
+      fin_eold = a.eps_old[idx];
     }
-    return;
-  }
-  if (persist && next < g.n_tiles) {
-    // the fourth buffer fed the previous tile's bulk store: let that finish, then prefetch into it
-    if (threadIdx.x == 0) {
-      if (store_pending) bulk_store_wait();
-      bulk_load(sm.bufD, (const C *)a.psi_in + (size_t)next * g.tile_elems, tile_bytes,
-                (use & 1) ? &sm.mbar[0] : &sm.mbar[3]);
-    }
-    store_pending = false;
-  }
-  bool jumped = false, stored = false;
-
-  int phase = (j >= 1) ? PH_MAIN : PH_DONE;
-  if (phase == PH_DONE) {
-#pragma unroll
-    for (int q = 0; q < EPT; ++q) acc[q] = it.ok(q) ? A[it.item(q)] : mkc((R)0, (R)0);
-  }
-  int guard = 0;
-  while (phase != PH_DONE) {
-    // ---- choose the propagation of this round
-    if (phase == PH_BISECT) {
-      if (threadIdx.x == 0) sm.flag[1] = 0;
-      __syncthreads();
-      if (threadIdx.x < g.T) {
-        const int t = threadIdx.x;
-        const double lo = sm.tsc[TS_LO * g.T + t], hi = sm.tsc[TS_HI * g.T + t];
-        const int busy = sm.tin[TI_ACT * g.T + t] && (hi - lo > tol) && sm.tin[TI_CH * g.T + t] < 60;
-        sm.tin[TI_BUSY * g.T + t] = busy;
-        if (busy) atomicAdd(&sm.flag[1], 1);
-      }
-      __syncthreads();
-      if (sm.flag[1] == 0) phase = PH_SSTAR;
-    }
-    if (phase == PH_MAIN) {
-      // the full-step coefficients are the same for every interval: a sweep loads them once, again
-      // only after a jump phase has overwritten them (the per-interval kernels reload them per tile:
-      // skipping there costs them registers)
-      if (!(sweep && coef_full)) uniform_coefs<R>(g, sm, im.cheb_full);
-      coef_full = true;
-    } else {
-      coef_full = false;
-      if (threadIdx.x < g.T) {
-        const int t = threadIdx.x;
-        const bool act = sm.tin[TI_ACT * g.T + t] != 0;
-        double len = 0.0;
-        if (phase == PH_BISECT) len = sm.tin[TI_BUSY * g.T + t] ? 0.5 * (sm.tsc[TS_LO * g.T + t] + sm.tsc[TS_HI * g.T + t]) : 0.0;
-        else if (phase == PH_SSTAR) len = act ? sm.tsc[TS_HI * g.T + t] : 0.0;
-        else len = act ? g.dt - sm.tsc[TS_S0 * g.T + t] : 0.0;
-        tau_coefs<R>(g, sm, t, g.c_fwd, len);
-      }
-    }
-    if (phase != PH_MAIN) load_tile<R, EPT>(g, it, psi_out, A);   // the main round's tile came by bulk copy
-    __syncthreads();
-    cheb_dispatch<R, EPT, NL, ACS, true>(g, im, sm, it, g.K, acc);   // rows cached: measured faster here
-    norms<R, EPT>(g, sm, it, acc);
-
-    // ---- consume the result
-    if (phase == PH_MAIN) {
-#pragma unroll
-      for (int q = 0; q < EPT; ++q)
-        if (it.ok(q)) A[it.item(q)] = acc[q];
-      if (threadIdx.x < g.T) {
-        const int t = threadIdx.x, k = tile * g.T + t;
-        const double nrm = sm.tsc[TS_NRM * g.T + t];
-        const double r = r_start;                        // padding trajectories carry r = -1
-        if (!isfinite(nrm)) set_status(a.status, KT_DEV_NONFINITE);
-        const int act = (k < g.M) && (nrm <= r);         // jump iff ||psi||^2 <= r
-        sm.tin[TI_ACT * g.T + t] = act;
-        sm.tsc[TS_R * g.T + t] = r;
-        sm.tsc[TS_S0 * g.T + t] = 0.0;
-        // first-order scheme: the bracket starts closed at dt, the jump is applied at the end
-        sm.tsc[TS_LO * g.T + t] = g.first_order ? g.dt : 0.0;
-        sm.tsc[TS_HI * g.T + t] = g.dt;
-        sm.tin[TI_CH * g.T + t] = 0;                     // bisection iteration counter
-        if (act) atomicAdd(&sm.flag[0], 1);
-      }
-      __syncthreads();
-      if (sm.flag[0] == 0) break;
-      // a jump: the tile's results go to psi_out now (coalesced), and flagged trajectories
-      // restart from psi(t_{j-1}), kept in psi_out
-      jumped = true;
-      for (int e = threadIdx.x; e < g.d * g.T; e += blockDim.x) psi_out[e] = A[e];
-      __syncthreads();
-#pragma unroll
-      for (int q = 0; q < EPT; ++q)
-        if (it.ok(q) && sm.tin[TI_ACT * g.T + tau]) psi_out[it.item(q)] = psi_in[it.item(q)];
-      __syncthreads();
-      phase = PH_BISECT;
-    } else if (phase == PH_BISECT) {
-      if (threadIdx.x < g.T) {
-        const int t = threadIdx.x;
-        if (sm.tin[TI_BUSY * g.T + t]) {
-          const double mid = 0.5 * (sm.tsc[TS_LO * g.T + t] + sm.tsc[TS_HI * g.T + t]);
-          if (sm.tsc[TS_NRM * g.T + t] <= sm.tsc[TS_R * g.T + t]) sm.tsc[TS_HI * g.T + t] = mid;
-          else sm.tsc[TS_LO * g.T + t] = mid;
-          sm.tin[TI_CH * g.T + t] += 1;
-        }
-      }
-      __syncthreads();
-    } else if (phase == PH_SSTAR) {
-#pragma unroll
-      for (int q = 0; q < EPT; ++q)
-        if (it.ok(q)) A[it.item(q)] = acc[q];
-      __syncthreads();
-      // channel probabilities p_l = ||L_l phi||^2
-      double v[KT_MAX_LIND];
-      for (int l = 0; l < KT_MAX_LIND; ++l) {
-        R s = 0;
-        if (l < g.n_lind) {
-#pragma unroll
-          for (int q = 0; q < EPT; ++q)
-            if (it.ok(q)) {
-              const C y = lind_item<R>(g, ops, l, 0, A, it.item(q), it.dig(q));
-              s += y.x * y.x + y.y * y.y;
-            }
-        }
-        v[l] = (double)s;
-      }
-      reduce_tau<KT_MAX_LIND>(v, g, sm.red, sm.tsc + TS_V0 * g.T);
-      if (threadIdx.x < g.T) {
-        const int t = threadIdx.x, k = tile * g.T + t;
-        int ch = -1;
-        if (sm.tin[TI_ACT * g.T + t]) {
-          const double *p = sm.tsc + TS_V0 * g.T + t * KT_MAX_LIND;
-          const int m = a.jcount[k] + 1;
-          if (m > g.max_jumps) {
-            set_status(a.status, KT_DEV_RECORD_FULL);
-            sm.tin[TI_ACT * g.T + t] = 0;
-          } else if (g.n_lind == 0) {
-            set_status(a.status, KT_DEV_ZERO_JUMP);      // norm loss without any jump operator
-            sm.tin[TI_ACT * g.T + t] = 0;
-          } else {
-            const double *U = a.U + ((size_t)*a.pass_row * g.M + k) * g.draws;
-            double tot = 0.0;
-            for (int l = 0; l < g.n_lind; ++l) tot += p[l];
-            const double target = U[2 * m - 1] * tot;   // first channel whose cumulative p reaches u * sum p
-            ch = g.n_lind - 1;
-            double cum = 0.0;
-            for (int l = 0; l < g.n_lind; ++l) {
-              cum += p[l];
-              if (cum >= target) { ch = l; break; }
-            }
-            if (!(p[ch] > 0.0)) {
-              set_status(a.status, KT_DEV_ZERO_JUMP);
-              sm.tin[TI_ACT * g.T + t] = 0;
-              ch = -1;
-            } else {
-              const double cnorm = 1.0 / sqrt(p[ch]);
-              const double sstar = sm.tsc[TS_S0 * g.T + t] + sm.tsc[TS_HI * g.T + t];
-              const size_t ri = (size_t)k * g.max_jumps + (m - 1);
-              a.rec_step[ri] = j;
-              a.rec_ch[ri] = ch;
-              a.rec_s[ri] = sstar;
-              a.rec_c[ri] = cnorm;
-              a.jcount[k] = m;
-              const double rn = U[2 * m];
-              a.rstate[k] = rn;
-              sm.tsc[TS_R * g.T + t] = rn;
-              sm.tsc[TS_S0 * g.T + t] = sstar;
-              sm.tsc[TS_C * g.T + t] = cnorm;
-            }
-          }
-        }
-        sm.tin[TI_NJ * g.T + t] = ch;
-      }
-      __syncthreads();
-      // collapse: start <- c L_ch phi
-      const int ch = sm.tin[TI_NJ * g.T + tau];
-      if (ch >= 0) {
-        const R cn = (R)sm.tsc[TS_C * g.T + tau];
-#pragma unroll
-        for (int q = 0; q < EPT; ++q) {
-          if (!it.ok(q)) continue;
-          const C y = lind_item<R>(g, ops, ch, 0, A, it.item(q), it.dig(q));
-          psi_out[it.item(q)] = mkc(cn * y.x, cn * y.y);
-        }
-      }
-      __syncthreads();
-      phase = PH_REST;
-    } else {  // PH_REST
-      if (threadIdx.x == 0) sm.flag[2] = 0;
-      __syncthreads();
-      if (threadIdx.x < g.T) {
-        const int t = threadIdx.x;
-        int done = 0;
-        if (sm.tin[TI_ACT * g.T + t]) {
-          if (sm.tsc[TS_NRM * g.T + t] > sm.tsc[TS_R * g.T + t]) done = 1;
-          else {
-            atomicAdd(&sm.flag[2], 1);      // another jump inside the remainder
-            sm.tsc[TS_HI * g.T + t] = g.dt - sm.tsc[TS_S0 * g.T + t];
-            sm.tsc[TS_LO * g.T + t] = g.first_order ? sm.tsc[TS_HI * g.T + t] : 0.0;
-            sm.tin[TI_CH * g.T + t] = 0;
-          }
-        }
-        sm.tin[TI_BUSY * g.T + t] = done;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int q = 0; q < EPT; ++q)
-        if (it.ok(q) && sm.tin[TI_BUSY * g.T + tau]) psi_out[it.item(q)] = acc[q];
-      __syncthreads();
-      if (threadIdx.x < g.T && sm.tin[TI_BUSY * g.T + threadIdx.x]) sm.tin[TI_ACT * g.T + threadIdx.x] = 0;
-      __syncthreads();
-      ++guard;
-      if (sm.flag[2] == 0 || guard > g.max_jumps + 1) {
-        // final states of the whole tile
-#pragma unroll
-        for (int q = 0; q < EPT; ++q)
-          if (it.ok(q)) acc[q] = psi_out[it.item(q)];
-        __syncthreads();
-        phase = PH_DONE;
-      } else {
-        phase = PH_BISECT;
-      }
-    }
-  }
-
-  if (j >= 1 && !jumped) {
-    if (sweep) {
-      // sweep: plain stores, read back by the next interval's jump restarts after a CTA barrier
-#pragma unroll
-      for (int q = 0; q < EPT; ++q)
-        if (it.ok(q)) psi_out[it.item(q)] = acc[q];
-    } else {
-      // psi(t_j) of the whole tile is in A: one bulk store to psi_out
+    if (j != a.j) {
+      // sweep: the next interval.  Its pulse is in sm.eps (guess sweep: eps_old; updating: the value
+      // the barrier's finisher formed), its chi goes to the third buffer once every thread is done
+      // with the previous one, and the tables are rebuilt for the new pulse.
+      if (!a.update && threadIdx.x < g.n_ctrl) sm.eps[threadIdx.x] = a.eps_old[threadIdx.x * a.nt + (j - 1)];
       fence_proxy_async_smem();
       __syncthreads();
-      if (threadIdx.x == 0) bulk_store(psi_out, A, tile_bytes);
-      stored = true;
+      if (threadIdx.x == 0 && need_chi && g.prefetch_chi)
+        bulk_load(sm.bufC, chi_of(j, blockIdx.x), tile_bytes, &sm.mbar[1]);
+      build_tables<R>(g, im, ops, sm, sm.eps, a.overlap != 0, true);
     }
-  }
+    int tile = blockIdx.x;
+    for (int use = 0; tile < g.n_tiles; tile += gridDim.x, ++use) {
+      const int next = tile + (int)gridDim.x;
+      const C *psi_in = (const C *)((!sweep || j <= 1) ? a.psi_in : a.psi_ring[(j - 1) & 1]) + (size_t)tile * g.tile_elems;
+      C *psi_out = (C *)(sweep ? a.psi_ring[j & 1] : a.psi_out) + (size_t)tile * g.tile_elems;
+      const C *chi_g = need_chi ? chi_of(j, tile) : nullptr;
+      // the trajectory's current threshold, read now so that its latency is off the path after the series
+      const double r_start = (threadIdx.x < g.T) ? a.rstate[(size_t)tile * g.T + threadIdx.x] : 0.0;
+      if (threadIdx.x == 0) {
+        sm.flag[0] = 0;
+        sm.flag[1] = 0;
+        sm.flag[2] = 0;
+      }
+      C *A = (C *)sm.bufA;
+      C *B = (C *)sm.bufB;
+      if (sweep && j != a.j) {
+        // sweep: psi(t_{j-1}) is the previous interval's result, still in registers
+    #pragma unroll
+        for (int q = 0; q < EPT; ++q)
+          if (it.ok(q)) A[it.item(q)] = acc[q];
+        __syncthreads();
+      } else if (!tile_wait((use & 1) ? &sm.mbar[3] : &sm.mbar[0], (use >> 1) & 1, &sm.flag[4], a.status,
+                            g.inject_timeout ? &sm.mbar[2] : nullptr)) {
+        // psi of this tile: load number `use`, barrier [0] / [3] in turn, phase parity (use >> 1) & 1
+        if (threadIdx.x == 0) {
+          if (need_chi && g.prefetch_chi) mbar_wait_bounded(&sm.mbar[1], nchi & 1);
+          if (store_pending) bulk_store_wait();
+        }
+        return;
+      }
+      if (persist && next < g.n_tiles) {
+        // the fourth buffer fed the previous tile's bulk store: let that finish, then prefetch into it
+        if (threadIdx.x == 0) {
+          if (store_pending) bulk_store_wait();
+          bulk_load(sm.bufD, (const C *)a.psi_in + (size_t)next * g.tile_elems, tile_bytes,
+                    (use & 1) ? &sm.mbar[0] : &sm.mbar[3]);
+        }
+        store_pending = false;
+      }
+      bool jumped = false, stored = false;
 
-  // ---------------- end of the sweep: tau_k = <tgt|psi_k>/||psi_k|| ----------------
-  if (j == a.nt) {
-    double v[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-      if (!it.ok(q)) continue;
-      const KtCplx t = ops.tgt[it.item(q) / g.T];
-      const double xr = (double)acc[q].x, xi = (double)acc[q].y;
-      v[0] += t.re * xr + t.im * xi;   // conj(tgt) * psi
-      v[1] += t.re * xi - t.im * xr;
-      v[2] += xr * xr + xi * xi;
-    }
-    reduce_tau<3>(v, g, sm.red, sm.tsc + TS_V0 * g.T);
-    if (threadIdx.x < g.T) {
-      const int k = tile * g.T + threadIdx.x;
-      const double *o = sm.tsc + TS_V0 * g.T + threadIdx.x * 3;
-      const double nrm = o[2];
-      // a trajectory's overlap is taken with the normalised state; a density matrix's
-      // <<P_tgt|rho(T)>> is linear in rho and is not normalised
-      const double inv = g.density ? 1.0 : (nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0);
-      a.tau[k].re = o[0] * inv;
-      a.tau[k].im = o[1] * inv;
-      a.norm2[k] = nrm;
-      if (!isfinite(nrm) || !isfinite(o[0]) || !isfinite(o[1])) set_status(a.status, KT_DEV_NONFINITE);
-    }
-    store_pending = store_pending || stored;
-    end_fwd_tile(sm, persist);
-    continue;
-  }
-
-  // ---------------- update overlap at t_j: g_c = sum_k Im <chi_k|hc_c|psi_k> ----------------
-  if (!a.overlap) {
-    store_pending = store_pending || stored;
-    end_fwd_tile(sm, persist);
-    continue;
-  }
-  if (jumped) {
-    // final states came back through psi_out: put them into A for the neighbour reads
-#pragma unroll
-    for (int q = 0; q < EPT; ++q)
-      if (it.ok(q)) A[it.item(q)] = acc[q];
-  }
-  const C *chi;
-  if (g.prefetch_chi) {
-    chi = (const C *)sm.bufC;
-  } else {
-    // B was written by ordinary stores during the Chebyshev rounds: order them before the copy
-    fence_proxy_async_smem();
-    __syncthreads();
-    if (threadIdx.x == 0) bulk_load(B, chi_g, tile_bytes, &sm.mbar[1]);
-    chi = B;
-  }
-  if (!tile_wait(&sm.mbar[1], nchi & 1, &sm.flag[5], a.status, g.inject_timeout ? &sm.mbar[2] : nullptr)) {
-    if (threadIdx.x == 0) {
-      if (store_pending || stored) bulk_store_wait();
-      // the next tile's psi is on its way into the fourth buffer: let it land before leaving
-      if (persist && next < g.n_tiles) mbar_wait_bounded((use & 1) ? &sm.mbar[0] : &sm.mbar[3], ((use + 1) >> 1) & 1);
-    }
-    return;
-  }
-  ++nchi;
-  const C *hv = (const C *)sm.hc_val;
-  // per-thread sums per control in the state precision (a trajectory problem has one term per
-  // control; a density matrix a ket and a bra term), converted to FP64 once for the reduction
-  R sc[KT_MAX_CTRL];
-#pragma unroll
-  for (int c = 0; c < KT_MAX_CTRL; ++c) sc[c] = (R)0;
-  for (int t = 0; t < g.n_cterms; ++t) {
-    const int node = g.cterm_node[t];
-    R s = 0;
-    if (NL > 0 && node != g.n_nodes - 1) {
-      // fiber mapping, control on another node: one factor row serves the whole fiber
-      if (it.ok(0)) {
-        const int base = (t * g.n_loc + ((it.dig(0) >> (4 * node)) & 15)) * g.SH;
-        C h[EPT];
-#pragma unroll
-        for (int q = 0; q < EPT; ++q) h[q] = mkc((R)0, (R)0);
-        for (int e = 0; e < g.SH; ++e) {
-          const C w = hv[base + e];
-          if (w.x != (R)0 || w.y != (R)0) {
-            const int off = sm.hc_off[base + e];
-#pragma unroll
-            for (int q = 0; q < EPT; ++q) h[q] = cfma(w, A[it.item(q) + off], h[q]);
+      int phase = (j >= 1) ? PH_MAIN : PH_DONE;
+      if (phase == PH_DONE) {
+    #pragma unroll
+        for (int q = 0; q < EPT; ++q) acc[q] = it.ok(q) ? A[it.item(q)] : mkc((R)0, (R)0);
+      }
+      int guard = 0;
+      while (phase != PH_DONE) {
+        // ---- choose the propagation of this round
+        if (phase == PH_BISECT) {
+          if (threadIdx.x == 0) sm.flag[1] = 0;
+          __syncthreads();
+          if (threadIdx.x < g.T) {
+            const int t = threadIdx.x;
+            const double lo = sm.tsc[TS_LO * g.T + t], hi = sm.tsc[TS_HI * g.T + t];
+            const int busy = sm.tin[TI_ACT * g.T + t] && (hi - lo > tol) && sm.tin[TI_CH * g.T + t] < 60;
+            sm.tin[TI_BUSY * g.T + t] = busy;
+            if (busy) atomicAdd(&sm.flag[1], 1);
+          }
+          __syncthreads();
+          if (sm.flag[1] == 0) phase = PH_SSTAR;
+        }
+        if (phase == PH_MAIN) {
+          // the full-step coefficients are the same for every interval: a sweep loads them once, again
+          // only after a jump phase has overwritten them (the per-interval kernels reload them per tile:
+          // skipping there costs them registers)
+          if (!(sweep && coef_full)) uniform_coefs<R>(g, sm, im.cheb_full);
+          coef_full = true;
+        } else {
+          coef_full = false;
+          if (threadIdx.x < g.T) {
+            const int t = threadIdx.x;
+            const bool act = sm.tin[TI_ACT * g.T + t] != 0;
+            double len = 0.0;
+            if (phase == PH_BISECT) len = sm.tin[TI_BUSY * g.T + t] ? 0.5 * (sm.tsc[TS_LO * g.T + t] + sm.tsc[TS_HI * g.T + t]) : 0.0;
+            else if (phase == PH_SSTAR) len = act ? sm.tsc[TS_HI * g.T + t] : 0.0;
+            else len = act ? g.dt - sm.tsc[TS_S0 * g.T + t] : 0.0;
+            tau_coefs<R>(g, sm, t, g.c_fwd, len);
           }
         }
-#pragma unroll
+        if (phase != PH_MAIN) load_tile<R, EPT>(g, it, psi_out, A);   // the main round's tile came by bulk copy
+        __syncthreads();
+        cheb_dispatch<R, EPT, NL, ACS, true>(g, im, sm, it, g.K, acc);   // rows cached: measured faster here
+        norms<R, EPT>(g, sm, it, acc);
+
+        // ---- consume the result
+        if (phase == PH_MAIN) {
+    #pragma unroll
+          for (int q = 0; q < EPT; ++q)
+            if (it.ok(q)) A[it.item(q)] = acc[q];
+          if (threadIdx.x < g.T) {
+            const int t = threadIdx.x, k = tile * g.T + t;
+            const double nrm = sm.tsc[TS_NRM * g.T + t];
+            const double r = r_start;                        // padding trajectories carry r = -1
+            if (!isfinite(nrm)) set_status(a.status, KT_DEV_NONFINITE);
+            const int act = (k < g.M) && (nrm <= r);         // jump iff ||psi||^2 <= r
+            sm.tin[TI_ACT * g.T + t] = act;
+            sm.tsc[TS_R * g.T + t] = r;
+            sm.tsc[TS_S0 * g.T + t] = 0.0;
+            // first-order scheme: the bracket starts closed at dt, the jump is applied at the end
+            sm.tsc[TS_LO * g.T + t] = g.first_order ? g.dt : 0.0;
+            sm.tsc[TS_HI * g.T + t] = g.dt;
+            sm.tin[TI_CH * g.T + t] = 0;                     // bisection iteration counter
+            if (act) atomicAdd(&sm.flag[0], 1);
+          }
+          __syncthreads();
+          if (sm.flag[0] == 0) break;
+          // a jump: the tile's results go to psi_out now (coalesced), and flagged trajectories
+          // restart from psi(t_{j-1}), kept in psi_out
+          jumped = true;
+          for (int e = threadIdx.x; e < g.d * g.T; e += blockDim.x) psi_out[e] = A[e];
+          __syncthreads();
+    #pragma unroll
+          for (int q = 0; q < EPT; ++q)
+            if (it.ok(q) && sm.tin[TI_ACT * g.T + tau]) psi_out[it.item(q)] = psi_in[it.item(q)];
+          __syncthreads();
+          phase = PH_BISECT;
+        } else if (phase == PH_BISECT) {
+          if (threadIdx.x < g.T) {
+            const int t = threadIdx.x;
+            if (sm.tin[TI_BUSY * g.T + t]) {
+              const double mid = 0.5 * (sm.tsc[TS_LO * g.T + t] + sm.tsc[TS_HI * g.T + t]);
+              if (sm.tsc[TS_NRM * g.T + t] <= sm.tsc[TS_R * g.T + t]) sm.tsc[TS_HI * g.T + t] = mid;
+              else sm.tsc[TS_LO * g.T + t] = mid;
+              sm.tin[TI_CH * g.T + t] += 1;
+            }
+          }
+          __syncthreads();
+        } else if (phase == PH_SSTAR) {
+    #pragma unroll
+          for (int q = 0; q < EPT; ++q)
+            if (it.ok(q)) A[it.item(q)] = acc[q];
+          __syncthreads();
+          // channel probabilities p_l = ||L_l phi||^2
+          double v[KT_MAX_LIND];
+          for (int l = 0; l < KT_MAX_LIND; ++l) {
+            R s = 0;
+            if (l < g.n_lind) {
+    #pragma unroll
+              for (int q = 0; q < EPT; ++q)
+                if (it.ok(q)) {
+                  const C y = lind_item<R>(g, ops, l, 0, A, it.item(q), it.dig(q));
+                  s += y.x * y.x + y.y * y.y;
+                }
+            }
+            v[l] = (double)s;
+          }
+          reduce_tau<KT_MAX_LIND>(v, g, sm.red, sm.tsc + TS_V0 * g.T);
+          if (threadIdx.x < g.T) {
+            const int t = threadIdx.x, k = tile * g.T + t;
+            int ch = -1;
+            if (sm.tin[TI_ACT * g.T + t]) {
+              const double *p = sm.tsc + TS_V0 * g.T + t * KT_MAX_LIND;
+              const int m = a.jcount[k] + 1;
+              if (m > g.max_jumps) {
+                set_status(a.status, KT_DEV_RECORD_FULL);
+                sm.tin[TI_ACT * g.T + t] = 0;
+              } else if (g.n_lind == 0) {
+                set_status(a.status, KT_DEV_ZERO_JUMP);      // norm loss without any jump operator
+                sm.tin[TI_ACT * g.T + t] = 0;
+              } else {
+                const double *U = a.U + ((size_t)*a.pass_row * g.M + k) * g.draws;
+                double tot = 0.0;
+                for (int l = 0; l < g.n_lind; ++l) tot += p[l];
+                const double target = U[2 * m - 1] * tot;   // first channel whose cumulative p reaches u * sum p
+                ch = g.n_lind - 1;
+                double cum = 0.0;
+                for (int l = 0; l < g.n_lind; ++l) {
+                  cum += p[l];
+                  if (cum >= target) { ch = l; break; }
+                }
+                if (!(p[ch] > 0.0)) {
+                  set_status(a.status, KT_DEV_ZERO_JUMP);
+                  sm.tin[TI_ACT * g.T + t] = 0;
+                  ch = -1;
+                } else {
+                  const double cnorm = 1.0 / sqrt(p[ch]);
+                  const double sstar = sm.tsc[TS_S0 * g.T + t] + sm.tsc[TS_HI * g.T + t];
+                  const size_t ri = (size_t)k * g.max_jumps + (m - 1);
+                  a.rec_step[ri] = j;
+                  a.rec_ch[ri] = ch;
+                  a.rec_s[ri] = sstar;
+                  a.rec_c[ri] = cnorm;
+                  a.jcount[k] = m;
+                  const double rn = U[2 * m];
+                  a.rstate[k] = rn;
+                  sm.tsc[TS_R * g.T + t] = rn;
+                  sm.tsc[TS_S0 * g.T + t] = sstar;
+                  sm.tsc[TS_C * g.T + t] = cnorm;
+                }
+              }
+            }
+            sm.tin[TI_NJ * g.T + t] = ch;
+          }
+          __syncthreads();
+          // collapse: start <- c L_ch phi
+          const int ch = sm.tin[TI_NJ * g.T + tau];
+          if (ch >= 0) {
+            const R cn = (R)sm.tsc[TS_C * g.T + tau];
+    #pragma unroll
+            for (int q = 0; q < EPT; ++q) {
+              if (!it.ok(q)) continue;
+              const C y = lind_item<R>(g, ops, ch, 0, A, it.item(q), it.dig(q));
+              psi_out[it.item(q)] = mkc(cn * y.x, cn * y.y);
+            }
+          }
+          __syncthreads();
+          phase = PH_REST;
+        } else {  // PH_REST
+          if (threadIdx.x == 0) sm.flag[2] = 0;
+          __syncthreads();
+          if (threadIdx.x < g.T) {
+            const int t = threadIdx.x;
+            int done = 0;
+            if (sm.tin[TI_ACT * g.T + t]) {
+              if (sm.tsc[TS_NRM * g.T + t] > sm.tsc[TS_R * g.T + t]) done = 1;
+              else {
+                atomicAdd(&sm.flag[2], 1);      // another jump inside the remainder
+                sm.tsc[TS_HI * g.T + t] = g.dt - sm.tsc[TS_S0 * g.T + t];
+                sm.tsc[TS_LO * g.T + t] = g.first_order ? sm.tsc[TS_HI * g.T + t] : 0.0;
+                sm.tin[TI_CH * g.T + t] = 0;
+              }
+            }
+            sm.tin[TI_BUSY * g.T + t] = done;
+          }
+          __syncthreads();
+    #pragma unroll
+          for (int q = 0; q < EPT; ++q)
+            if (it.ok(q) && sm.tin[TI_BUSY * g.T + tau]) psi_out[it.item(q)] = acc[q];
+          __syncthreads();
+          if (threadIdx.x < g.T && sm.tin[TI_BUSY * g.T + threadIdx.x]) sm.tin[TI_ACT * g.T + threadIdx.x] = 0;
+          __syncthreads();
+          ++guard;
+          if (sm.flag[2] == 0 || guard > g.max_jumps + 1) {
+            // final states of the whole tile
+    #pragma unroll
+            for (int q = 0; q < EPT; ++q)
+              if (it.ok(q)) acc[q] = psi_out[it.item(q)];
+            __syncthreads();
+            phase = PH_DONE;
+          } else {
+            phase = PH_BISECT;
+          }
+        }
+      }
+
+      if (j >= 1 && !jumped) {
+        if (sweep) {
+          // sweep: plain stores, read back by the next interval's jump restarts after a CTA barrier
+    #pragma unroll
+          for (int q = 0; q < EPT; ++q)
+            if (it.ok(q)) psi_out[it.item(q)] = acc[q];
+        } else {
+          // psi(t_j) of the whole tile is in A: one bulk store to psi_out
+          fence_proxy_async_smem();
+          __syncthreads();
+          if (threadIdx.x == 0) bulk_store(psi_out, A, tile_bytes);
+          stored = true;
+        }
+      }
+
+      // ---------------- end of the sweep: tau_k = <tgt|psi_k>/||psi_k|| ----------------
+      if (j == a.nt) {
+        double v[3] = {0.0, 0.0, 0.0};
+    #pragma unroll
         for (int q = 0; q < EPT; ++q) {
-          const C x = chi[it.item(q)];
-          s += x.x * h[q].y - x.y * h[q].x;       // Im(conj(chi) * h)
+          if (!it.ok(q)) continue;
+          const KtCplx t = ops.tgt[it.item(q) / g.T];
+          const double xr = (double)acc[q].x, xi = (double)acc[q].y;
+          v[0] += t.re * xr + t.im * xi;   // conj(tgt) * psi
+          v[1] += t.re * xi - t.im * xr;
+          v[2] += xr * xr + xi * xi;
         }
-      }
-    } else {
-#pragma unroll
-      for (int q = 0; q < EPT; ++q) {
-        if (!it.ok(q)) continue;
-        const int xi = (it.dig(q) >> (4 * node)) & 15;
-        const int base = (t * g.n_loc + xi) * g.SH;
-        C h = mkc((R)0, (R)0);
-        for (int e = 0; e < g.SH; ++e) {
-          const C w = hv[base + e];
-          if (w.x != (R)0 || w.y != (R)0) h = cfma(w, A[it.item(q) + sm.hc_off[base + e]], h);
+        reduce_tau<3>(v, g, sm.red, sm.tsc + TS_V0 * g.T);
+        if (threadIdx.x < g.T) {
+          const int k = tile * g.T + threadIdx.x;
+          const double *o = sm.tsc + TS_V0 * g.T + threadIdx.x * 3;
+          const double nrm = o[2];
+          // a trajectory's overlap is taken with the normalised state; a density matrix's
+          // <<P_tgt|rho(T)>> is linear in rho and is not normalised
+          const double inv = g.density ? 1.0 : (nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0);
+          a.tau[k].re = o[0] * inv;
+          a.tau[k].im = o[1] * inv;
+          a.norm2[k] = nrm;
+          if (!isfinite(nrm) || !isfinite(o[0]) || !isfinite(o[1])) set_status(a.status, KT_DEV_NONFINITE);
         }
-        const C x = chi[it.item(q)];
-        s += x.x * h.y - x.y * h.x;       // Im(conj(chi) * h)
+        store_pending = store_pending || stored;
+        end_fwd_tile(sm, persist);
+        continue;
       }
+
+      // ---------------- update overlap at t_j: g_c = sum_k Im <chi_k|hc_c|psi_k> ----------------
+      if (!a.overlap) {
+        store_pending = store_pending || stored;
+        end_fwd_tile(sm, persist);
+        continue;
+      }
+      if (jumped) {
+        // final states came back through psi_out: put them into A for the neighbour reads
+    #pragma unroll
+        for (int q = 0; q < EPT; ++q)
+          if (it.ok(q)) A[it.item(q)] = acc[q];
+      }
+      const C *chi;
+      if (g.prefetch_chi) {
+        chi = (const C *)sm.bufC;
+      } else {
+        // B was written by ordinary stores during the Chebyshev rounds: order them before the copy
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) bulk_load(B, chi_g, tile_bytes, &sm.mbar[1]);
+        chi = B;
+      }
+      if (!tile_wait(&sm.mbar[1], nchi & 1, &sm.flag[5], a.status, g.inject_timeout ? &sm.mbar[2] : nullptr)) {
+        if (threadIdx.x == 0) {
+          if (store_pending || stored) bulk_store_wait();
+          // the next tile's psi is on its way into the fourth buffer: let it land before leaving
+          if (persist && next < g.n_tiles) mbar_wait_bounded((use & 1) ? &sm.mbar[0] : &sm.mbar[3], ((use + 1) >> 1) & 1);
+        }
+        return;
+      }
+      ++nchi;
+      const C *hv = (const C *)sm.hc_val;
+      // per-thread sums per control in the state precision (a trajectory problem has one term per
+      // control; a density matrix a ket and a bra term), converted to FP64 once for the reduction
+      R sc[KT_MAX_CTRL];
+    #pragma unroll
+      for (int c = 0; c < KT_MAX_CTRL; ++c) sc[c] = (R)0;
+      for (int t = 0; t < g.n_cterms; ++t) {
+        const int node = g.cterm_node[t];
+        R s = 0;
+        if (NL > 0 && node != g.n_nodes - 1) {
+          // fiber mapping, control on another node: one factor row serves the whole fiber
+          if (it.ok(0)) {
+            const int base = (t * g.n_loc + ((it.dig(0) >> (4 * node)) & 15)) * g.SH;
+            C h[EPT];
+    #pragma unroll
+            for (int q = 0; q < EPT; ++q) h[q] = mkc((R)0, (R)0);
+            for (int e = 0; e < g.SH; ++e) {
+              const C w = hv[base + e];
+              if (w.x != (R)0 || w.y != (R)0) {
+                const int off = sm.hc_off[base + e];
+    #pragma unroll
+                for (int q = 0; q < EPT; ++q) h[q] = cfma(w, A[it.item(q) + off], h[q]);
+              }
+            }
+    #pragma unroll
+            for (int q = 0; q < EPT; ++q) {
+              const C x = chi[it.item(q)];
+              s += x.x * h[q].y - x.y * h[q].x;       // Im(conj(chi) * h)
+            }
+          }
+        } else {
+    #pragma unroll
+          for (int q = 0; q < EPT; ++q) {
+            if (!it.ok(q)) continue;
+            const int xi = (it.dig(q) >> (4 * node)) & 15;
+            const int base = (t * g.n_loc + xi) * g.SH;
+            C h = mkc((R)0, (R)0);
+            for (int e = 0; e < g.SH; ++e) {
+              const C w = hv[base + e];
+              if (w.x != (R)0 || w.y != (R)0) h = cfma(w, A[it.item(q) + sm.hc_off[base + e]], h);
+            }
+            const C x = chi[it.item(q)];
+            s += x.x * h.y - x.y * h.x;       // Im(conj(chi) * h)
+          }
+        }
+        const int ct = g.cterm_ctrl[t];
+    #pragma unroll
+        for (int c = 0; c < KT_MAX_CTRL; ++c)
+          if (c == ct) sc[c] += s;
+      }
+      // FP64 block reduction of the per-control sums: four slots when there are at most four controls
+      // (FP64 runs at 1/64 of the FP32 rate here, and every slot costs additions in each lane)
+      int vstride = KT_MAX_CTRL;
+      if (g.n_ctrl <= 4) {
+        double v[4];
+    #pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] = c < g.n_ctrl ? (double)sc[c] : 0.0;
+        reduce_tau<4>(v, g, sm.red, sm.tsc + TS_V0 * g.T);
+        vstride = 4;
+      } else {
+        double v[KT_MAX_CTRL];
+    #pragma unroll
+        for (int c = 0; c < KT_MAX_CTRL; ++c) v[c] = c < g.n_ctrl ? (double)sc[c] : 0.0;
+        reduce_tau<KT_MAX_CTRL>(v, g, sm.red, sm.tsc + TS_V0 * g.T);
+      }
+      if (threadIdx.x < g.n_ctrl) {
+        double s = 0.0;
+        for (int t = 0; t < g.T; ++t) s += sm.tsc[TS_V0 * g.T + t * vstride + threadIdx.x];
+        // a sweep keeps two sets of partials (interval parity): a CTA may write the next interval's
+        // while a slower one still reads this interval's
+        a.partials[(sweep ? (size_t)(j & 1) * g.n_tiles * g.n_ctrl : 0) + (size_t)tile * g.n_ctrl + threadIdx.x] = s;
+      }
+      store_pending = store_pending || stored;
+      end_fwd_tile(sm, persist);
+      // every thread is done with this tile's chi (the barrier above): the third buffer takes the next tile's
+      if (persist && need_chi && g.prefetch_chi && next < g.n_tiles && threadIdx.x == 0)
+        bulk_load(sm.bufC, (const C *)a.chi_t + (size_t)next * g.tile_elems, tile_bytes, &sm.mbar[1]);
+    }   // tiles of this CTA
+    // Delta eps of interval j+1 from the partials of all tiles: every thread adds a fixed, contiguous
+    // chunk of the tiles and a fixed shuffle/warp tree adds the chunks -- the same order on every run
+    // for a given tile count and block size.  The new pulse value goes to sm.eps (the next interval of
+    // a sweep) and, with write_out, to deps / eps_new.
+    auto finish_update = [&](const double *part, bool write_out) {
+      const int chunk = (g.n_tiles + (int)blockDim.x - 1) / (int)blockDim.x;
+      const int t0 = threadIdx.x * chunk, t1 = min(g.n_tiles, t0 + chunk);
+      for (int c = 0; c < g.n_ctrl; ++c) {
+        double v = 0.0;
+        for (int t = t0; t < t1; ++t) v += __ldcg(part + (size_t)t * g.n_ctrl + c);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) sm.red[(threadIdx.x >> 5) * 8 + c] = v;
+      }
+      __syncthreads();
+      if (threadIdx.x < g.n_ctrl) {
+        const int c = threadIdx.x;
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sm.red[w * 8 + c];
+        const size_t idx = (size_t)c * a.nt + j;   // interval j+1 (0-based index j)
+        const double de = (sweep ? fin_scale : a.shape[idx] / (g.lam[c] * g.M_norm)) * s;
+        const double en = (sweep ? fin_eold : a.eps_old[idx]) + de;
+        if (write_out) {
+          a.deps[idx] = de;
+          a.eps_new[idx] = en;
+          if (!isfinite(de)) set_status(a.status, KT_DEV_NONFINITE);
+          if (fabs(en) > g.eps_bound) set_status(a.status, KT_DEV_RANGE);
+        }
+        sm.eps[c] = en;
+      }
+    };
+    if (sweep) {
+      if (j == a.nt) break;
+      if (!need_chi) continue;                 // guess sweep: nothing to exchange between intervals
+      if (!grid_barrier(a.sync, sync_gen, &sm.flag[6], a.status)) break;   // timed out: results void
+      ++sync_gen;
+      finish_update(a.partials + (size_t)(j & 1) * g.n_tiles * g.n_ctrl, blockIdx.x == 0);
+      continue;
     }
-    const int ct = g.cterm_ctrl[t];
-#pragma unroll
-    for (int c = 0; c < KT_MAX_CTRL; ++c)
-      if (c == ct) sc[c] += s;
-  }
-  // FP64 block reduction of the per-control sums: four slots when there are at most four controls
-  // (FP64 runs at 1/64 of the FP32 rate here, and every slot costs additions in each lane)
-  int vstride = KT_MAX_CTRL;
-  if (g.n_ctrl <= 4) {
-    double v[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) v[c] = c < g.n_ctrl ? (double)sc[c] : 0.0;
-    reduce_tau<4>(v, g, sm.red, sm.tsc + TS_V0 * g.T);
-    vstride = 4;
-  } else {
-    double v[KT_MAX_CTRL];
-#pragma unroll
-    for (int c = 0; c < KT_MAX_CTRL; ++c) v[c] = c < g.n_ctrl ? (double)sc[c] : 0.0;
-    reduce_tau<KT_MAX_CTRL>(v, g, sm.red, sm.tsc + TS_V0 * g.T);
-  }
-  if (threadIdx.x < g.n_ctrl) {
-    double s = 0.0;
-    for (int t = 0; t < g.T; ++t) s += sm.tsc[TS_V0 * g.T + t * vstride + threadIdx.x];
-    // a sweep keeps two sets of partials (interval parity): a CTA may write the next interval's
-    // while a slower one still reads this interval's
-    a.partials[(sweep ? (size_t)(j & 1) * g.n_tiles * g.n_ctrl : 0) + (size_t)tile * g.n_ctrl + threadIdx.x] = s;
-  }
-  store_pending = store_pending || stored;
-  end_fwd_tile(sm, persist);
-  // every thread is done with this tile's chi (the barrier above): the third buffer takes the next tile's
-  if (persist && need_chi && g.prefetch_chi && next < g.n_tiles && threadIdx.x == 0)
-    bulk_load(sm.bufC, (const C *)a.chi_t + (size_t)next * g.tile_elems, tile_bytes, &sm.mbar[1]);
-  }   // tiles of this CTA
-  // Delta eps of interval j+1 from the partials of all tiles: every thread adds a fixed, contiguous
-  // chunk of the tiles and a fixed shuffle/warp tree adds the chunks -- the same order on every run
-  // for a given tile count and block size.  The new pulse value goes to sm.eps (the next interval of
-  // a sweep) and, with write_out, to deps / eps_new.
-  auto finish_update = [&](const double *part, bool write_out) {
-    const int chunk = (g.n_tiles + (int)blockDim.x - 1) / (int)blockDim.x;
-    const int t0 = threadIdx.x * chunk, t1 = min(g.n_tiles, t0 + chunk);
-    for (int c = 0; c < g.n_ctrl; ++c) {
-      double v = 0.0;
-      for (int t = t0; t < t1; ++t) v += __ldcg(part + (size_t)t * g.n_ctrl + c);
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if ((threadIdx.x & 31) == 0) sm.red[(threadIdx.x >> 5) * 8 + c] = v;
+    if (!a.overlap || j == a.nt || !a.finish) {   // no update sum here (a shard sums after its exchange)
+      if (threadIdx.x == 0 && store_pending) bulk_store_wait();
+      return;
+    }
+    // ---------------- last CTA: Delta eps of interval j+1, summed in tile order ----------------
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned ticket = atomicAdd(a.counter, 1u);
+      sm.flag[3] = (ticket == (unsigned)(gridDim.x - 1));
     }
     __syncthreads();
-    if (threadIdx.x < g.n_ctrl) {
-      const int c = threadIdx.x;
-      double s = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sm.red[w * 8 + c];
-      const size_t idx = (size_t)c * a.nt + j;   // interval j+1 (0-based index j)
-      const double de = (sweep ? fin_scale : a.shape[idx] / (g.lam[c] * g.M_norm)) * s;
-      const double en = (sweep ? fin_eold : a.eps_old[idx]) + de;
-      if (write_out) {
-        a.deps[idx] = de;
-        a.eps_new[idx] = en;
-        if (!isfinite(de)) set_status(a.status, KT_DEV_NONFINITE);
-        if (fabs(en) > g.eps_bound) set_status(a.status, KT_DEV_RANGE);
-      }
-      sm.eps[c] = en;
-    }
-  };
-  if (sweep) {
-    if (j == a.nt) break;
-    if (!need_chi) continue;                 // guess sweep: nothing to exchange between intervals
-    if (!grid_barrier(a.sync, sync_gen, &sm.flag[6], a.status)) break;   // timed out: results void
-    ++sync_gen;
-    finish_update(a.partials + (size_t)(j & 1) * g.n_tiles * g.n_ctrl, blockIdx.x == 0);
-    continue;
-  }
-  if (!a.overlap || j == a.nt || !a.finish) {   // no update sum here (a shard sums after its exchange)
     if (threadIdx.x == 0 && store_pending) bulk_store_wait();
+    if (!sm.flag[3]) return;
+    __threadfence();
+    finish_update(a.partials, true);
+    if (threadIdx.x == 0) *a.counter = 0u;
     return;
-  }
-  // ---------------- last CTA: Delta eps of interval j+1, summed in tile order ----------------
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned ticket = atomicAdd(a.counter, 1u);
-    sm.flag[3] = (ticket == (unsigned)(gridDim.x - 1));
-  }
-  __syncthreads();
-  if (threadIdx.x == 0 && store_pending) bulk_store_wait();
-  if (!sm.flag[3]) return;
-  __threadfence();
-  finish_update(a.partials, true);
-  if (threadIdx.x == 0) *a.counter = 0u;
-  return;
   }   // intervals
   if (threadIdx.x == 0 && store_pending) bulk_store_wait();
 }
@@ -1583,114 +1583,114 @@ __global__ void __launch_bounds__(NL > 0 ? 736 : (sizeof(R) == 8 ? 512 : 1024)) 
     const int next = tile + (int)gridDim.x;
     if (persist && next < g.n_tiles && threadIdx.x == 0)   // the third buffer is free: prefetch the next input
       bulk_load(sm.bufC, (const C *)a.chi_in + (size_t)next * g.tile_elems, tile_bytes, &sm.mbar[(use + 1) & 1]);
-  for (int j = j_first; j >= j_last; --j) {
-    if (j != j_first) {
-      // whole sweep: the pulse and the tables of the next interval (every read of the previous
-      // interval's tables ended at the barrier after its store)
-      if (threadIdx.x < g.n_ctrl) sm.eps[threadIdx.x] = a.eps[threadIdx.x * a.nt + (j - 1)];
-      __syncthreads();
-      build_tables<R>(g, im, ops, sm, sm.eps, false, true);
-    }
-    C *chi_out = sweep ? (C *)((char *)a.chi_slots + (size_t)(j - 1) * a.slot_bytes) + (size_t)tile * g.tile_elems
-                       : (C *)a.chi_out + (size_t)tile * g.tile_elems;
-    if (threadIdx.x == 0) sm.flag[0] = 0;
-    if (threadIdx.x == 0 && store_pending) bulk_store_wait();   // A still feeds the previous tile's store
-    store_pending = false;
-    __syncthreads();
-    if (threadIdx.x < g.T) {
-      const int t = threadIdx.x, k = tile * g.T + t;
-      int nj = 0;
-      if (k < g.M) {
-        int cur = a.cursor[k];
-        if (fw) {
-          const int cnt = a.jcount[k];
-          while (cur < cnt && a.rec_step[(size_t)k * g.max_jumps + cur] == j && nj < 12) {
-            sm.tin[(TI_J0 + nj) * g.T + t] = cur;  // ascending in time
-            ++nj;
-            ++cur;
-          }
-          if (cur < cnt && a.rec_step[(size_t)k * g.max_jumps + cur] == j) set_status(a.status, KT_DEV_RECORD_FULL);
-        } else {
-          while (cur >= 0 && a.rec_step[(size_t)k * g.max_jumps + cur] == j && nj < 12) {
-            sm.tin[(TI_J0 + nj) * g.T + t] = cur;  // descending in time
-            ++nj;
-            --cur;
-          }
-          if (cur >= 0 && a.rec_step[(size_t)k * g.max_jumps + cur] == j) set_status(a.status, KT_DEV_RECORD_FULL);
-        }
-        if (a.advance_cursor) a.cursor[k] = cur;
+    for (int j = j_first; j >= j_last; --j) {
+      if (j != j_first) {
+        // whole sweep: the pulse and the tables of the next interval (every read of the previous
+        // interval's tables ended at the barrier after its store)
+        if (threadIdx.x < g.n_ctrl) sm.eps[threadIdx.x] = a.eps[threadIdx.x * a.nt + (j - 1)];
+        __syncthreads();
+        build_tables<R>(g, im, ops, sm, sm.eps, false, true);
       }
-      sm.tin[TI_NJ * g.T + t] = nj;
-      atomicMax(&sm.flag[0], nj);
-    }
-    __syncthreads();
-    C *A = (C *)sm.bufA;
-    C *B = (C *)sm.bufB;
-    const int rounds = sm.flag[0];
-    C acc[EPT];
-    for (int rnd = 0; rnd <= rounds; ++rnd) {
-      if (rounds == 0) {
-        uniform_coefs<R>(g, sm, im.cheb_full);
-      } else if (threadIdx.x < g.T) {
-        const int t = threadIdx.x, k = tile * g.T + t, nj = sm.tin[TI_NJ * g.T + t];
-        double len = 0.0;
-        if (rnd <= nj) {
-          const double *rs = a.rec_s + (size_t)k * g.max_jumps;
-          if (fw) {   // pieces forwards: s_1 - 0, s_2 - s_1, ..., dt - s_m
-            const double lo = (rnd == 0) ? 0.0 : rs[sm.tin[(TI_J0 + rnd - 1) * g.T + t]];
-            const double hi = (rnd < nj) ? rs[sm.tin[(TI_J0 + rnd) * g.T + t]] : g.dt;
-            len = hi - lo;
-          } else {    // pieces backwards: dt - s_m, s_m - s_{m-1}, ..., s_1 - 0
-            const double hi = (rnd == 0) ? g.dt : rs[sm.tin[(TI_J0 + rnd - 1) * g.T + t]];
-            const double lo = (rnd < nj) ? rs[sm.tin[(TI_J0 + rnd) * g.T + t]] : 0.0;
-            len = hi - lo;
-          }
-        }
-        tau_coefs<R>(g, sm, t, fw ? g.c_fwd : g.c_bwd, len);
-      }
-      // B holds the vector to propagate
-#pragma unroll
-      for (int q = 0; q < EPT; ++q)
-        if (it.ok(q)) A[it.item(q)] = B[it.item(q)];
+      C *chi_out = sweep ? (C *)((char *)a.chi_slots + (size_t)(j - 1) * a.slot_bytes) + (size_t)tile * g.tile_elems
+                         : (C *)a.chi_out + (size_t)tile * g.tile_elems;
+      if (threadIdx.x == 0) sm.flag[0] = 0;
+      if (threadIdx.x == 0 && store_pending) bulk_store_wait();   // A still feeds the previous tile's store
+      store_pending = false;
       __syncthreads();
-      // FP32: the other nodes' rows in registers (measured 2 % faster); FP64 has no registers to spare
-      cheb_dispatch<R, EPT, NL, ACS, sizeof(R) == 4>(g, im, sm, it, g.K, acc);
-      if (rnd == rounds) break;
-#pragma unroll
+      if (threadIdx.x < g.T) {
+        const int t = threadIdx.x, k = tile * g.T + t;
+        int nj = 0;
+        if (k < g.M) {
+          int cur = a.cursor[k];
+          if (fw) {
+            const int cnt = a.jcount[k];
+            while (cur < cnt && a.rec_step[(size_t)k * g.max_jumps + cur] == j && nj < 12) {
+              sm.tin[(TI_J0 + nj) * g.T + t] = cur;  // ascending in time
+              ++nj;
+              ++cur;
+            }
+            if (cur < cnt && a.rec_step[(size_t)k * g.max_jumps + cur] == j) set_status(a.status, KT_DEV_RECORD_FULL);
+          } else {
+            while (cur >= 0 && a.rec_step[(size_t)k * g.max_jumps + cur] == j && nj < 12) {
+              sm.tin[(TI_J0 + nj) * g.T + t] = cur;  // descending in time
+              ++nj;
+              --cur;
+            }
+            if (cur >= 0 && a.rec_step[(size_t)k * g.max_jumps + cur] == j) set_status(a.status, KT_DEV_RECORD_FULL);
+          }
+          if (a.advance_cursor) a.cursor[k] = cur;
+        }
+        sm.tin[TI_NJ * g.T + t] = nj;
+        atomicMax(&sm.flag[0], nj);
+      }
+      __syncthreads();
+      C *A = (C *)sm.bufA;
+      C *B = (C *)sm.bufB;
+      const int rounds = sm.flag[0];
+      C acc[EPT];
+      for (int rnd = 0; rnd <= rounds; ++rnd) {
+        if (rounds == 0) {
+          uniform_coefs<R>(g, sm, im.cheb_full);
+        } else if (threadIdx.x < g.T) {
+          const int t = threadIdx.x, k = tile * g.T + t, nj = sm.tin[TI_NJ * g.T + t];
+          double len = 0.0;
+          if (rnd <= nj) {
+            const double *rs = a.rec_s + (size_t)k * g.max_jumps;
+            if (fw) {   // pieces forwards: s_1 - 0, s_2 - s_1, ..., dt - s_m
+              const double lo = (rnd == 0) ? 0.0 : rs[sm.tin[(TI_J0 + rnd - 1) * g.T + t]];
+              const double hi = (rnd < nj) ? rs[sm.tin[(TI_J0 + rnd) * g.T + t]] : g.dt;
+              len = hi - lo;
+            } else {    // pieces backwards: dt - s_m, s_m - s_{m-1}, ..., s_1 - 0
+              const double hi = (rnd == 0) ? g.dt : rs[sm.tin[(TI_J0 + rnd - 1) * g.T + t]];
+              const double lo = (rnd < nj) ? rs[sm.tin[(TI_J0 + rnd) * g.T + t]] : 0.0;
+              len = hi - lo;
+            }
+          }
+          tau_coefs<R>(g, sm, t, fw ? g.c_fwd : g.c_bwd, len);
+        }
+        // B holds the vector to propagate
+  #pragma unroll
+        for (int q = 0; q < EPT; ++q)
+          if (it.ok(q)) A[it.item(q)] = B[it.item(q)];
+        __syncthreads();
+        // FP32: the other nodes' rows in registers (measured 2 % faster); FP64 has no registers to spare
+        cheb_dispatch<R, EPT, NL, ACS, sizeof(R) == 4>(g, im, sm, it, g.K, acc);
+        if (rnd == rounds) break;
+  #pragma unroll
+        for (int q = 0; q < EPT; ++q)
+          if (it.ok(q)) A[it.item(q)] = acc[q];
+        __syncthreads();
+        const int nj = sm.tin[TI_NJ * g.T + tau];
+        const int k = tile * g.T + tau;
+  #pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+          if (!it.ok(q)) continue;
+          C y = A[it.item(q)];
+          if (rnd < nj) {
+            const size_t ri = (size_t)k * g.max_jumps + sm.tin[(TI_J0 + rnd) * g.T + tau];
+            const C z = lind_item<R>(g, ops, a.rec_ch[ri], fw ? 0 : 1, A, it.item(q), it.dig(q));
+            const R cn = (R)a.rec_c[ri];
+            y = mkc(cn * z.x, cn * z.y);
+          }
+          B[it.item(q)] = y;
+        }
+        __syncthreads();
+      }
+      // chi(t_{j-1}) of the whole tile: into A, then one bulk store (completed before A is reused)
+  #pragma unroll
       for (int q = 0; q < EPT; ++q)
         if (it.ok(q)) A[it.item(q)] = acc[q];
-      __syncthreads();
-      const int nj = sm.tin[TI_NJ * g.T + tau];
-      const int k = tile * g.T + tau;
-#pragma unroll
-      for (int q = 0; q < EPT; ++q) {
-        if (!it.ok(q)) continue;
-        C y = A[it.item(q)];
-        if (rnd < nj) {
-          const size_t ri = (size_t)k * g.max_jumps + sm.tin[(TI_J0 + rnd) * g.T + tau];
-          const C z = lind_item<R>(g, ops, a.rec_ch[ri], fw ? 0 : 1, A, it.item(q), it.dig(q));
-          const R cn = (R)a.rec_c[ri];
-          y = mkc(cn * z.x, cn * z.y);
-        }
-        B[it.item(q)] = y;
+      if (sweep && j > j_last) {
+        // the next interval starts from this result (B's last reads ended at the rounds' barrier)
+  #pragma unroll
+        for (int q = 0; q < EPT; ++q)
+          if (it.ok(q)) B[it.item(q)] = acc[q];
       }
+      fence_proxy_async_smem();
       __syncthreads();
-    }
-    // chi(t_{j-1}) of the whole tile: into A, then one bulk store (completed before A is reused)
-#pragma unroll
-    for (int q = 0; q < EPT; ++q)
-      if (it.ok(q)) A[it.item(q)] = acc[q];
-    if (sweep && j > j_last) {
-      // the next interval starts from this result (B's last reads ended at the rounds' barrier)
-#pragma unroll
-      for (int q = 0; q < EPT; ++q)
-        if (it.ok(q)) B[it.item(q)] = acc[q];
-    }
-    fence_proxy_async_smem();
-    __syncthreads();
-    if (threadIdx.x == 0) bulk_store(chi_out, A, tile_bytes);
-    store_pending = true;
-  }   // intervals
+      if (threadIdx.x == 0) bulk_store(chi_out, A, tile_bytes);
+      store_pending = true;
+    }   // intervals
     // the prefetched input becomes this CTA's input buffer; the old one (free) the next prefetch target
     void *tmp = sm.bufB;
     sm.bufB = sm.bufC;
